@@ -1,0 +1,225 @@
+/*
+ * fire.h -- C ABI of libfire: batched FiRE (finite-range embedding) wave
+ * function evaluation on one GB300 (sm_103a).
+ *
+ * The library evaluates, for a batch of W walkers (electron configurations),
+ * the FiRE ansatz of arXiv 2504.06087
+ *
+ *     Psi(r) = J(r) * sum_d det[Phi_d(r)]                 (Methods, eq. wf)
+ *
+ * its local energy (Methods, "Variational Monte Carlo")
+ *
+ *     E_L(r) = -1/2 (Lap log|Psi| + |grad log|Psi||^2) + V(r)
+ *
+ * with V the Coulomb potential of the molecular Hamiltonian (Methods,
+ * eq. hamiltonian), the per-walker parameter gradient d log|Psi| / d theta
+ * (Methods, eq. spring), and Metropolis sampling with single-electron moves
+ * (Methods, "Improved Monte Carlo sampling").
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Pointers.  Unless a comment says "host", every array pointer is DEVICE
+ *   memory, allocated and freed by the caller.  The library allocates no
+ *   device memory: scratch space is the caller-allocated workspace `ws` of at
+ *   least fire_workspace_size() bytes.  Arrays are dense row-major (C order).
+ * Electrons.  r is [W][n_el][3] float64, bohr.  Electrons 0 .. n_up-1 are
+ *   spin-up, n_up .. n_el-1 spin-down (Methods, "Variational Monte Carlo").
+ * Parameters.  theta is ONE flat buffer; fire_param_layout() gives the name,
+ *   offset and shape of every array in it.  theta is float64 for
+ *   FIRE_PREC_FP64 and float32 for the other precisions.
+ * Streams.  `stream` is a cudaStream_t passed as void*.  All device work is
+ *   enqueued on it; the call then reads a 4-byte status word back and
+ *   synchronises that stream before it returns.
+ * Errors.  Every call returns a fire_status_t.  Argument errors are detected
+ *   on the host before any launch (FIRE_ERR_INVALID_ARG, FIRE_ERR_WORKSPACE).
+ *   Conditions found on the device (neighbour-list overflow, non-finite
+ *   results) are returned after the status read-back; outputs are then
+ *   undefined (FIRE_ERR_CAPACITY) or hold the non-finite values
+ *   (FIRE_ERR_NONFINITE is reported only when a walker is non-finite without
+ *   being on a node).  A walker on a node of Psi (sign 0, log|Psi| = -inf)
+ *   is not an error; it is counted in fire_info_t.n_nodes.
+ * Concurrency.  No global state: calls are re-entrant and may run on
+ *   different streams with different workspaces.
+ */
+#ifndef FIRE_H
+#define FIRE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FIRE_OK = 0,
+  FIRE_ERR_INVALID_ARG = 1,      /* bad size, NULL pointer, unknown enum       */
+  FIRE_ERR_CAPACITY = 2,         /* an electron has more than k_cap neighbours */
+  FIRE_ERR_NONFINITE = 3,        /* NaN/inf off a node                          */
+  FIRE_ERR_SINGULAR_REFRESH = 4, /* MCMC inverse refresh met a zero pivot      */
+  FIRE_ERR_TIMEOUT = 5,          /* a bounded device wait gave up              */
+  FIRE_ERR_CUDA = 6,             /* a CUDA runtime call failed                 */
+  FIRE_ERR_UNSUPPORTED = 7,      /* valid but not implemented combination      */
+  FIRE_ERR_WORKSPACE = 8         /* ws NULL or smaller than fire_workspace_size */
+} fire_status_t;
+
+/* Arithmetic of a call.
+ *  FP64       every step in float64 (theta float64).
+ *  FP32       every step in float32, the final E_L reduction included
+ *             ("plain FP32"; theta float32).
+ *  BF16_FP64  embedding-MLP and Jastrow-MLP matrix products in BF16 on the
+ *             tensor cores with FP32 accumulation; LU / slogdet and the final
+ *             E_L reduction in float64; everything else float32 (theta
+ *             float32). */
+typedef enum {
+  FIRE_PREC_FP64 = 0,
+  FIRE_PREC_FP32 = 1,
+  FIRE_PREC_BF16_FP64 = 2
+} fire_precision_t;
+
+/* Jastrow switches (Methods, "Global electron correlation effects"). */
+#define FIRE_J_CUSP 1u
+#define FIRE_J_MLP 2u
+#define FIRE_J_ATT 4u
+
+/* Operation a workspace is sized for. */
+typedef enum {
+  FIRE_OP_NEIGHBORS = 0,
+  FIRE_OP_LOGPSI = 1,
+  FIRE_OP_LOCAL_ENERGY = 2,
+  FIRE_OP_GRAD_LOGPSI = 3,
+  FIRE_OP_MCMC = 4
+} fire_op_t;
+
+/* The molecule: nuclear positions R_m and charges Z_m (Methods,
+ * eq. hamiltonian), electron counts, the electron-electron cutoff c (Results,
+ * "Finite-range embeddings": N_i = {j != i : |r_i - r_j| <= c}) and the
+ * electron-nucleus filter cutoff c_n (Methods, filter Gamma_m). */
+typedef struct {
+  int32_t n_el;              /* electrons, >= 1                                 */
+  int32_t n_up;              /* spin-up electrons, 0 <= n_up <= n_el            */
+  int32_t n_nuc;             /* nuclei, >= 1                                    */
+  int32_t pad_;
+  const double* nuc_pos;     /* device [n_nuc][3], bohr                         */
+  const double* nuc_charge;  /* device [n_nuc]                                  */
+  double cutoff;             /* c   >= 0, bohr                                  */
+  double cutoff_nuc;         /* c_n >  0, bohr                                  */
+} fire_system_t;
+
+/* Network hyper-parameters (Supplementary table "Hyperparameters"). */
+typedef struct {
+  int32_t width;             /* hidden width d (multiple of 8, <= 1024)         */
+  int32_t n_layers;          /* depth L of the embedding MLP h = MLP(h^1)       */
+  int32_t n_det;             /* determinants N_det                              */
+  int32_t n_env;             /* exponential envelopes per nucleus               */
+  int32_t n_gauss;           /* Gaussians d_0 of the radial filters (<= 64)     */
+  int32_t edge_hidden;       /* hidden width of the filter MLP (<= 64)          */
+  int32_t jastrow_width;     /* hidden width of the Jastrow MLPs (0 = width)    */
+  int32_t n_reg;             /* attention registers                             */
+  int32_t d_reg;             /* register dimension                              */
+  uint32_t flags;            /* FIRE_J_* bits                                   */
+} fire_arch_t;
+
+typedef struct {
+  const void* theta;         /* device flat parameter buffer                    */
+  int64_t n_params;          /* must equal fire_param_count()                   */
+  int32_t dtype;             /* 0 = float64, 1 = float32                        */
+  int32_t pad_;
+} fire_params_t;
+
+typedef struct {
+  char name[24];
+  int64_t offset;            /* in elements from theta                          */
+  int32_t ndim;
+  int32_t pad_;
+  int64_t shape[5];
+} fire_param_entry_t;
+
+/* Optional per-call diagnostics (host memory; pass NULL to skip). */
+typedef struct {
+  int32_t k_required;        /* largest neighbour count seen                    */
+  int32_t n_nodes;           /* walkers with sign 0 (on a node of Psi)          */
+  int32_t n_nonfinite;       /* walkers with a non-finite E_L off a node        */
+  int32_t n_chunks;          /* walker chunks the call was split into          */
+  int64_t rows_total;        /* forward-Laplacian rows processed (all chunks)   */
+  double mean_neighbors;     /* mean |N_i| over all electrons and walkers       */
+} fire_info_t;
+
+/* Number of scalar parameters of the ansatz for this system and network. */
+int64_t fire_param_count(const fire_system_t* sys, const fire_arch_t* arch);
+
+/* Fills out[0 .. *n-1] with the layout of theta and sets *n to the number
+ * of arrays.  With out == NULL only *n is set.  Returns FIRE_OK or
+ * FIRE_ERR_INVALID_ARG. */
+int fire_param_layout(const fire_system_t* sys, const fire_arch_t* arch,
+                      fire_param_entry_t* out, int32_t* n);
+
+/* Workspace bytes a call of operation `op` needs for W walkers.  0 on
+ * invalid arguments.  Calls split the walkers into chunks internally, so
+ * the size grows with W only up to a chunk. */
+size_t fire_workspace_size(const fire_system_t* sys, const fire_arch_t* arch,
+                           int64_t n_walkers, int32_t precision, int32_t k_cap,
+                           int32_t op);
+
+/* Neighbour lists N_i^par, N_i^anti (Results, "Finite-range embeddings";
+ * Methods, message passing step: N^alpha_i splits N_i by parallel and
+ * antiparallel spin).  For each walker w and electron i:
+ *   nbr_idx[w][i][0 .. cnt[w][i][0]-1]            same-spin j, ascending
+ *   nbr_idx[w][i][cnt[w][i][0] .. + cnt[w][i][1]-1] opposite-spin j, ascending
+ * with |r_i - r_j| <= c in float64.  nbr_idx is [W][n_el][k_cap] int32,
+ * nbr_cnt [W][n_el][2] int32 (device).  *k_required (host, may be NULL)
+ * receives the largest |N_i|; if it exceeds k_cap the lists are truncated and
+ * FIRE_ERR_CAPACITY is returned. */
+int fire_neighbors(const fire_system_t* sys, int64_t n_walkers, const double* r,
+                   int32_t k_cap, int32_t* nbr_idx, int32_t* nbr_cnt,
+                   int32_t* k_required, void* ws, size_t ws_bytes, void* stream);
+
+/* log|Psi| and sign(Psi) for each walker (Methods, eq. wf): logabs, sign are
+ * [W] float64 (device).  k_cap bounds |N_i| as in fire_neighbors. */
+int fire_logpsi(const fire_system_t* sys, const fire_arch_t* arch,
+                const fire_params_t* params, int64_t n_walkers, const double* r,
+                int32_t k_cap, int32_t precision, double* logabs, double* sign,
+                fire_info_t* info, void* ws, size_t ws_bytes, void* stream);
+
+/* Local energy E_L (Methods, eq. of E_L) with the exact Laplacian of
+ * log|Psi| from the sparse forward Laplacian (Methods, "Efficient
+ * Laplacian").  Outputs [W] float64 (device): e_loc, logabs, sign; e_kin and
+ * e_pot (kinetic and potential parts) may be NULL. */
+int fire_local_energy(const fire_system_t* sys, const fire_arch_t* arch,
+                      const fire_params_t* params, int64_t n_walkers, const double* r,
+                      int32_t k_cap, int32_t precision, double* e_loc, double* logabs,
+                      double* sign, double* e_kin, double* e_pot, fire_info_t* info,
+                      void* ws, size_t ws_bytes, void* stream);
+
+/* Layout of the workspace of a call (diagnostics and tests): for each named
+ * intermediate buffer its byte offset inside ws and its size in bytes, for
+ * the first walker chunk (chunk_walkers walkers).  With out == NULL only *n is
+ * set.  Buffers hold, e.g., "X" the forward-Laplacian rows of h, "SU" the
+ * attention scores and values, "V" the register rows, "LU" the factored
+ * orbital matrices, "ldabs" / "lsign" per-determinant log|det| and sign. */
+typedef struct {
+  char name[16];
+  int64_t offset;
+  int64_t bytes;
+} fire_ws_entry_t;
+
+int fire_workspace_layout(const fire_system_t* sys, const fire_arch_t* arch, int64_t n_walkers,
+                          int32_t precision, int32_t k_cap, int32_t op, fire_ws_entry_t* out,
+                          int32_t* n, int64_t* chunk_walkers);
+
+const char* fire_status_string(int status);
+
+/* Text of the last CUDA error seen by a call on this host thread, with the
+ * pipeline stage that raised it (static thread-local storage; "" if none).
+ * Stages are checked one by one when the environment variable
+ * FIRE_DEBUG_SYNC is set. */
+const char* fire_last_error(void);
+
+/* Library version string (static storage). */
+const char* fire_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FIRE_H */

@@ -1,0 +1,360 @@
+// C ABI entry points of libfire: argument checks, the parameter layout, the
+// workspace plan and the dispatch to the per-precision pipelines.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "nbr.cuh"
+#include "pipeline.cuh"
+#include "plan.h"
+
+namespace fire {
+
+struct PDesc {
+  const char* name;
+  int ndim;
+  int64_t shape[5];
+};
+
+// Parameter arrays of the ansatz, in theta order (Methods, "Wave function
+// ansatz"; Supplementary "Hyperparameters").
+static void param_table(const fire_system_t* sys, const fire_arch_t* ar, PDesc t[P_COUNT]) {
+  const int64_t n = sys->n_el, N = sys->n_nuc, d = ar->width, L = ar->n_layers, D = ar->n_det,
+                E = ar->n_env, G = ar->n_gauss, H = ar->edge_hidden,
+                J = ar->jastrow_width > 0 ? ar->jastrow_width : ar->width, R = ar->n_reg,
+                dr = ar->d_reg;
+  int k = 0;
+  auto add = [&](const char* nm, std::initializer_list<int64_t> sh) {
+    t[k].name = nm;
+    t[k].ndim = (int)sh.size();
+    int q = 0;
+    for (int64_t v : sh) t[k].shape[q++] = v;
+    for (; q < 5; ++q) t[k].shape[q] = 1;
+    ++k;
+  };
+  add("en_w1", {N, 4, H}); add("en_b1", {N, H}); add("en_w2", {H, d}); add("en_wenv", {G, d});
+  add("en_sigma", {G}); add("nuc_emb", {N, d}); add("en_wfeat", {4, d});
+  add("ln_gamma", {d}); add("ln_beta", {d});
+  add("glu_wg", {d, d}); add("glu_wv", {d, d}); add("glu_wo", {d, d});
+  add("ee_w1", {4, H}); add("ee_b1", {H}); add("ee_w2", {H, d}); add("ee_wenv", {G, d});
+  add("ee_sigma", {G}); add("msg_w", {2, 2 * d + 4, d}); add("msg_b", {2, d});
+  add("mlp_w", {L, d, d}); add("mlp_b", {L, d});
+  add("orb_w", {2, D, d, n}); add("env_pi", {2, D, n, N, E}); add("env_sigma", {N, E});
+  add("cusp", {4});
+  const char* mlp_names[4][6] = {{"jm1_w1", "jm1_b1", "jm1_w2", "jm1_b2", "jm1_w3", "jm1_b3"},
+                                 {"jm2_w1", "jm2_b1", "jm2_w2", "jm2_b2", "jm2_w3", "jm2_b3"},
+                                 {"ja1_w1", "ja1_b1", "ja1_w2", "ja1_b2", "ja1_w3", "ja1_b3"},
+                                 {"ja2_w1", "ja2_b1", "ja2_w2", "ja2_b2", "ja2_w3", "ja2_b3"}};
+  for (int q = 0; q < 4; ++q) {
+    const int64_t din = q < 2 ? d : R * dr;
+    add(mlp_names[q][0], {din, J}); add(mlp_names[q][1], {J});
+    add(mlp_names[q][2], {J, J}); add(mlp_names[q][3], {J});
+    add(mlp_names[q][4], {J}); add(mlp_names[q][5], {1});
+    if (q == 1) { add("att_q", {R, d}); add("att_wv", {R, d, dr}); }
+  }
+}
+
+static int64_t numel(const PDesc& p) {
+  int64_t v = 1;
+  for (int q = 0; q < p.ndim; ++q) v *= p.shape[q];
+  return v;
+}
+
+static int check_system(const fire_system_t* sys, const fire_arch_t* ar) {
+  if (!sys || !ar) return FIRE_ERR_INVALID_ARG;
+  if (sys->n_el < 1 || sys->n_up < 0 || sys->n_up > sys->n_el || sys->n_nuc < 1) return FIRE_ERR_INVALID_ARG;
+  if (!(sys->cutoff >= 0.0) || !(sys->cutoff_nuc > 0.0)) return FIRE_ERR_INVALID_ARG;
+  if (ar->width < 32 || ar->width > 1024 || ar->width % 32) return FIRE_ERR_INVALID_ARG;
+  if (ar->n_layers < 0 || ar->n_det < 1 || ar->n_det > 64 || ar->n_env < 1) return FIRE_ERR_INVALID_ARG;
+  if (ar->n_gauss != kGauss || ar->edge_hidden != kEdgeHidden) return FIRE_ERR_UNSUPPORTED;
+  if (ar->n_reg < 1 || ar->d_reg < 1 || ar->n_reg * ar->d_reg > 1024) return FIRE_ERR_INVALID_ARG;
+  if (ar->jastrow_width < 0) return FIRE_ERR_INVALID_ARG;
+  return FIRE_OK;
+}
+
+static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+static size_t layout(Plan& pl, int64_t Wc) {
+  const Dims& dm = pl.dm;
+  const int64_t n = dm.n, d = dm.d, D = dm.D, R5 = dm.deriv ? 5 : 1, K = dm.K, J = dm.J;
+  const int64_t NE = (int64_t)dm.N * dm.E, RD = (int64_t)dm.R * dm.dr;
+  const size_t ts = pl.tsz, ls = pl.lsz;
+  const int64_t nb = Wc * n;
+  const int64_t cap = nb * pl.rows_per_el;
+  const int64_t vstride = dm.deriv ? 2 + 3 * n : 1;
+  size_t o = 0;
+  pl.nent = 0;
+  const char* nm = "";
+  auto take = [&](size_t bytes) {
+    size_t r = o;
+    o = align_up(o + bytes);
+    if (pl.nent < 96) pl.ent[pl.nent++] = Plan::Ent{nm, r, bytes};
+    return r;
+  };
+#define TAKE(field, bytes) (nm = #field, pl.field = take(bytes))
+  TAKE(status, sizeof(DevStatus));
+  TAKE(idx, nb * K * 4);
+  TAKE(rev, nb * K * 4);
+  TAKE(cnt, nb * 2 * 4);
+  TAKE(blk_rows, nb * 8);
+  TAKE(blk_off, (nb + 1) * 8);
+  TAKE(ranges, 8 * 8);
+  TAKE(S5, nb * R5 * d * ts);
+  TAKE(Y5, nb * R5 * d * ts);
+  TAKE(Z5, nb * R5 * 2 * d * ts);
+  TAKE(P5, nb * R5 * d * ts);
+  TAKE(H0, nb * R5 * d * ts);
+  TAKE(PQ, nb * R5 * 4 * d * ts);
+  TAKE(X, cap * d * ts);
+  const int64_t zw = d > J ? d : J;
+  pl.zcol = 0;
+  pl.ycol = zw;
+  pl.sucol = zw + J;
+  int64_t ldb = zw + J + dm.R + RD;
+  if (ldb < n) ldb = n;
+  pl.ld_big = ldb;
+  TAKE(big, cap * ldb * ts);
+  TAKE(F1, cap * ts);
+  TAKE(F2, cap * ts);
+  TAKE(Qf, nb * R5 * NE * ts);
+  TAKE(Fenv, nb * R5 * D * n * ts);
+  TAKE(Hv, nb * d * ts);
+  TAKE(Ov, nb * D * n * ts);
+  TAKE(LU, Wc * D * n * n * ls);
+  TAKE(piv, Wc * D * n * 4);
+  TAKE(ldabs, Wc * D * 8);
+  TAKE(lsign, Wc * D * 8);
+  if (dm.deriv) TAKE(Ainv, Wc * D * n * n * ts); else pl.Ainv = 0;
+  TAKE(gdet, Wc * D * n * 3 * ts);
+  TAKE(ldet, Wc * D * n * ts);
+  TAKE(jval, Wc * ts); TAKE(jsign, Wc * ts); TAKE(jlap, Wc * ts); TAKE(jgrad, Wc * n * 3 * ts);
+  TAKE(aval, Wc * ts); TAKE(asign, Wc * ts); TAKE(alap, Wc * ts); TAKE(agrad, Wc * n * 3 * ts);
+  TAKE(cval, Wc * ts); TAKE(clap, Wc * ts); TAKE(cgrad, Wc * n * 3 * ts); TAKE(vpot, Wc * ts);
+  TAKE(V, Wc * vstride * RD * ts);
+  TAKE(VZ, Wc * vstride * J * ts);
+  TAKE(VY, Wc * vstride * J * ts);
+  TAKE(G1, Wc * vstride * ts);
+  TAKE(G2, Wc * vstride * ts);
+#undef TAKE
+  pl.wbf16 = 0;
+  pl.total = o;
+  return o;
+}
+
+static size_t budget_bytes() {
+  const char* e = getenv("FIRE_WORKSPACE_BUDGET_MB");
+  double mb = e ? atof(e) : 24576.0;
+  if (!(mb > 0)) mb = 24576.0;
+  return (size_t)(mb * 1024.0 * 1024.0);
+}
+
+int make_plan(const fire_system_t* sys, const fire_arch_t* ar, int64_t W, int prec, int k_cap, int op,
+              Plan* pl) {
+  int rc = check_system(sys, ar);
+  if (rc) return rc;
+  if (W < 1 || k_cap < 1 || k_cap > 1024) return FIRE_ERR_INVALID_ARG;
+  if (prec < 0 || prec > 2) return FIRE_ERR_INVALID_ARG;
+  memset(pl, 0, sizeof(Plan));
+  Dims& dm = pl->dm;
+  dm.n = sys->n_el; dm.n_up = sys->n_up; dm.N = sys->n_nuc; dm.d = ar->width; dm.L = ar->n_layers;
+  dm.D = ar->n_det; dm.E = ar->n_env; dm.G = ar->n_gauss; dm.H = ar->edge_hidden;
+  dm.J = ar->jastrow_width > 0 ? ar->jastrow_width : ar->width; dm.R = ar->n_reg; dm.dr = ar->d_reg;
+  dm.K = k_cap; dm.flags = ar->flags; dm.prec = prec; dm.op = op;
+  dm.deriv = (op == FIRE_OP_LOCAL_ENERGY) ? 1 : 0;
+  const int keff = k_cap < dm.n - 1 ? k_cap : (dm.n - 1 > 0 ? dm.n - 1 : 0);
+  pl->rows_per_el = dm.deriv ? 2 + 3 * (1 + keff) : 1;
+  pl->tsz = prec == FIRE_PREC_FP64 ? 8 : 4;
+  pl->lsz = prec == FIRE_PREC_FP32 ? 4 : 8;
+  pl->W = W;
+  const size_t s1 = layout(*pl, 1), s2 = layout(*pl, 2);
+  const size_t per = s2 > s1 ? s2 - s1 : 1;
+  const size_t base = s1 > per ? s1 - per : 0;
+  const size_t bud = budget_bytes();
+  int64_t wc = bud > base ? (int64_t)((bud - base) / per) : 1;
+  if (wc < 1) wc = 1;
+  if (wc > W) wc = W;
+  // shared-memory limits of the determinant kernels
+  const int n = dm.n, mcap = 1 + k_cap;
+  const size_t ctsm = (size_t)(4 * mcap) * (n + 1) * pl->tsz + 2 * mcap * sizeof(int);
+  const size_t invsm = (size_t)n * n * pl->tsz + 2 * n * sizeof(int);
+  const size_t lim = 227 * 1024;
+  if (dm.deriv && (ctsm > lim || invsm > lim)) return FIRE_ERR_UNSUPPORTED;
+  pl->Wc = wc;
+  pl->nchunks = (W + wc - 1) / wc;
+  layout(*pl, wc);
+  return FIRE_OK;
+}
+
+static thread_local char g_last_error[256];
+
+void set_last_error(const char* stage, const char* msg) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s: %s", stage, msg);
+}
+
+}  // namespace fire
+
+using namespace fire;
+
+extern "C" {
+
+const char* fire_last_error(void) { return g_last_error; }
+
+const char* fire_version(void) { return "libfire 0.1 (sm_103a)"; }
+
+const char* fire_status_string(int s) {
+  switch (s) {
+    case FIRE_OK: return "ok";
+    case FIRE_ERR_INVALID_ARG: return "invalid argument";
+    case FIRE_ERR_CAPACITY: return "neighbour list capacity k_cap exceeded";
+    case FIRE_ERR_NONFINITE: return "non-finite result off a node";
+    case FIRE_ERR_SINGULAR_REFRESH: return "singular matrix in the inverse refresh";
+    case FIRE_ERR_TIMEOUT: return "bounded device wait timed out";
+    case FIRE_ERR_CUDA: return "CUDA runtime error";
+    case FIRE_ERR_UNSUPPORTED: return "unsupported configuration";
+    case FIRE_ERR_WORKSPACE: return "workspace missing or too small";
+    default: return "unknown status";
+  }
+}
+
+int64_t fire_param_count(const fire_system_t* sys, const fire_arch_t* arch) {
+  if (check_system(sys, arch) != FIRE_OK) return -1;
+  PDesc t[P_COUNT];
+  param_table(sys, arch, t);
+  int64_t s = 0;
+  for (int k = 0; k < P_COUNT; ++k) s += numel(t[k]);
+  return s;
+}
+
+int fire_param_layout(const fire_system_t* sys, const fire_arch_t* arch, fire_param_entry_t* out,
+                      int32_t* n) {
+  if (!n) return FIRE_ERR_INVALID_ARG;
+  int rc = check_system(sys, arch);
+  if (rc) return rc;
+  PDesc t[P_COUNT];
+  param_table(sys, arch, t);
+  *n = P_COUNT;
+  if (!out) return FIRE_OK;
+  int64_t off = 0;
+  for (int k = 0; k < P_COUNT; ++k) {
+    memset(&out[k], 0, sizeof(fire_param_entry_t));
+    strncpy(out[k].name, t[k].name, sizeof(out[k].name) - 1);
+    out[k].offset = off;
+    out[k].ndim = t[k].ndim;
+    for (int q = 0; q < 5; ++q) out[k].shape[q] = t[k].shape[q];
+    off += numel(t[k]);
+  }
+  return FIRE_OK;
+}
+
+size_t fire_workspace_size(const fire_system_t* sys, const fire_arch_t* arch, int64_t n_walkers,
+                           int32_t precision, int32_t k_cap, int32_t op) {
+  if (op == FIRE_OP_NEIGHBORS) {
+    if (!sys || n_walkers < 1) return 0;
+    return 256;
+  }
+  Plan pl;
+  if (make_plan(sys, arch, n_walkers, precision, k_cap, op, &pl) != FIRE_OK) return 0;
+  return pl.total;
+}
+
+int fire_workspace_layout(const fire_system_t* sys, const fire_arch_t* arch, int64_t n_walkers,
+                          int32_t precision, int32_t k_cap, int32_t op, fire_ws_entry_t* out, int32_t* n,
+                          int64_t* chunk_walkers) {
+  if (!n) return FIRE_ERR_INVALID_ARG;
+  Plan pl;
+  int rc = make_plan(sys, arch, n_walkers, precision, k_cap, op, &pl);
+  if (rc) return rc;
+  *n = pl.nent;
+  if (chunk_walkers) *chunk_walkers = pl.Wc;
+  if (!out) return FIRE_OK;
+  for (int k = 0; k < pl.nent; ++k) {
+    memset(&out[k], 0, sizeof(fire_ws_entry_t));
+    strncpy(out[k].name, pl.ent[k].name, sizeof(out[k].name) - 1);
+    out[k].offset = (int64_t)pl.ent[k].off;
+    out[k].bytes = (int64_t)pl.ent[k].bytes;
+  }
+  return FIRE_OK;
+}
+
+int fire_neighbors(const fire_system_t* sys, int64_t W, const double* r, int32_t k_cap, int32_t* nbr_idx,
+                   int32_t* nbr_cnt, int32_t* k_required, void* ws, size_t ws_bytes, void* stream) {
+  if (!sys || W < 1 || !r || k_cap < 1 || !nbr_idx || !nbr_cnt) return FIRE_ERR_INVALID_ARG;
+  if (sys->n_el < 1 || sys->n_up < 0 || sys->n_up > sys->n_el || !(sys->cutoff >= 0)) return FIRE_ERR_INVALID_ARG;
+  if (!ws || ws_bytes < 256) return FIRE_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevStatus* st = reinterpret_cast<DevStatus*>(ws);
+  cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
+  const int n = sys->n_el;
+  // chunks of walkers keep the block-row scratch inside the launch
+  const int64_t chunk = 65535;
+  for (int64_t w0 = 0; w0 < W; w0 += chunk) {
+    const int wc = (int)((W - w0) < chunk ? (W - w0) : chunk);
+    nbr_build_kernel<<<wc, 256, (size_t)n * 3 * sizeof(double), s>>>(
+        wc, n, sys->n_up, r + w0 * n * 3, sys->cutoff * sys->cutoff, k_cap, nbr_idx + w0 * n * k_cap,
+        nbr_cnt + w0 * n * 2, nullptr, st, 0);
+  }
+  DevStatus hs;
+  if (cudaGetLastError() != cudaSuccess) return FIRE_ERR_CUDA;
+  if (cudaMemcpyAsync(&hs, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s) != cudaSuccess) return FIRE_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return FIRE_ERR_CUDA;
+  if (k_required) *k_required = hs.k_required;
+  return hs.overflow ? FIRE_ERR_CAPACITY : FIRE_OK;
+}
+
+static int run_call(const fire_system_t* sys, const fire_arch_t* arch, const fire_params_t* params,
+                    int64_t W, const double* r, int32_t k_cap, int32_t prec, int op, double* e_loc,
+                    double* logabs, double* sign, double* e_kin, double* e_pot, fire_info_t* info,
+                    void* ws, size_t ws_bytes, void* stream) {
+  if (!params || !params->theta || !r || !logabs || !sign) return FIRE_ERR_INVALID_ARG;
+  if (op == FIRE_OP_LOCAL_ENERGY && !e_loc) return FIRE_ERR_INVALID_ARG;
+  Plan pl;
+  int rc = make_plan(sys, arch, W, prec, k_cap, op, &pl);
+  if (rc) return rc;
+  if (!sys->nuc_pos || !sys->nuc_charge) return FIRE_ERR_INVALID_ARG;
+  if (params->n_params != fire_param_count(sys, arch)) return FIRE_ERR_INVALID_ARG;
+  const int want_dtype = prec == FIRE_PREC_FP64 ? 0 : 1;
+  if (params->dtype != want_dtype) return FIRE_ERR_INVALID_ARG;
+  if (!ws || ws_bytes < pl.total) return FIRE_ERR_WORKSPACE;
+  PDesc t[P_COUNT];
+  param_table(sys, arch, t);
+  int64_t poff[P_COUNT];
+  int64_t off = 0;
+  for (int k = 0; k < P_COUNT; ++k) { poff[k] = off; off += numel(t[k]); }
+  DevStatus hs;
+  memset(&hs, 0, sizeof(hs));
+  CallArgs a{sys, arch, params->theta, poff, W, r, e_loc, logabs, sign, e_kin, e_pot, ws,
+             (cudaStream_t)stream, &hs};
+  if (prec == FIRE_PREC_FP64) rc = run_fp64(pl, a);
+  else if (prec == FIRE_PREC_FP32) rc = run_fp32(pl, a);
+  else rc = run_bf16(pl, a);
+  if (info) {
+    info->k_required = hs.k_required;
+    info->n_nodes = hs.n_nodes;
+    info->n_nonfinite = hs.n_nonfinite;
+    info->n_chunks = (int32_t)pl.nchunks;
+    info->rows_total = hs.rows_total;
+    info->mean_neighbors = (double)hs.nbr_total / ((double)W * sys->n_el);
+  }
+  if (rc) return rc;
+  if (hs.overflow) return FIRE_ERR_CAPACITY;
+  if (hs.n_nonfinite) return FIRE_ERR_NONFINITE;
+  return FIRE_OK;
+}
+
+int fire_logpsi(const fire_system_t* sys, const fire_arch_t* arch, const fire_params_t* params, int64_t W,
+                const double* r, int32_t k_cap, int32_t precision, double* logabs, double* sign,
+                fire_info_t* info, void* ws, size_t ws_bytes, void* stream) {
+  return run_call(sys, arch, params, W, r, k_cap, precision, FIRE_OP_LOGPSI, nullptr, logabs, sign, nullptr,
+                  nullptr, info, ws, ws_bytes, stream);
+}
+
+int fire_local_energy(const fire_system_t* sys, const fire_arch_t* arch, const fire_params_t* params,
+                      int64_t W, const double* r, int32_t k_cap, int32_t precision, double* e_loc,
+                      double* logabs, double* sign, double* e_kin, double* e_pot, fire_info_t* info,
+                      void* ws, size_t ws_bytes, void* stream) {
+  return run_call(sys, arch, params, W, r, k_cap, precision, FIRE_OP_LOCAL_ENERGY, e_loc, logabs, sign, e_kin,
+                  e_pot, info, ws, ws_bytes, stream);
+}
+
+}  // extern "C"

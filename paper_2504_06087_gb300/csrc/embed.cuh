@@ -1,0 +1,393 @@
+// Initial embeddings h^0 and the message passing step h^1 (Methods, "Wave
+// function ansatz"), each carried with its tangents and Laplacian.
+//
+//   h^0_i = GLU( sum_m Gamma_m(e^_im) * (h^nuc_m + e-bar^_im W) )
+//   h^1_i = h^0_i + sum_alpha sum_{j in N^alpha_i} Gamma(e_ij) *
+//           SiLU(Concat[h^0_i, h^0_j, e-bar_ij] W^alpha + b^alpha)
+//
+// h^0_i depends on r_i only: its blocks have 5 rows (value, Laplacian,
+// d/dx_i, d/dy_i, d/dz_i).  The concatenation is applied as
+// h^0_i W^alpha_a + h^0_j W^alpha_b + e-bar_ij W^alpha_c; the first two are
+// per-electron products computed once by a matrix product (PQ), the third is
+// per edge.
+#pragma once
+
+#include "common.cuh"
+
+namespace fire {
+
+template <typename T>
+__device__ __forceinline__ void fl3_mul(const FL3<T>& a, const FL3<T>& b, FL3<T>& o) {
+  o.v = a.v * b.v;
+  T cross = T(0);
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    o.t[t] = a.t[t] * b.v + a.v * b.t[t];
+    cross += a.t[t] * b.t[t];
+  }
+  o.l = a.l * b.v + T(2) * cross + a.v * b.l;
+}
+
+// Filter features of one pair vector into shared memory:
+// feat[0..H) hidden units, feat[H..H+G) Gaussians chi_g, feat[H+G..H+G+4) e-bar.
+template <typename T, typename W>
+__device__ __forceinline__ void pair_features_to_smem(const T dv[3], T r, const W* w1, const W* b1,
+                                                      const W* sigma, T cut, FL3<T>* feat) {
+  const int H = kEdgeHidden, G = kGauss;
+  for (int k = threadIdx.x; k < H + G + 4; k += blockDim.x) {
+    FL3<T> o;
+    if (k < H) pair_hidden<T, W>(dv, r, w1, b1, k, H, o);
+    else if (k < H + G) pair_chi<T>(dv, r, T(sigma[k - H]), cut, o);
+    else pair_ebar<T>(dv, r, k - H - G, o);
+    feat[k] = o;
+  }
+}
+
+// One CTA per electron (w, i), blockDim == d.  Writes the filter sum
+// s_i = sum_m Gamma_m * (h^nuc_m + e-bar W) as R5 rows of S.
+template <typename T, typename W>
+__global__ void en_filter_kernel(int Wc, int n, int n_up, int N, int d, const double* __restrict__ r,
+                                 const double* __restrict__ R, double cnuc, Params<W> p,
+                                 T* __restrict__ S, int R5) {
+  constexpr int H = kEdgeHidden, G = kGauss;
+  __shared__ FL3<T> feat[H + G + 4];
+  const int blk = blockIdx.x;
+  const int w = blk / n, i = blk % n;
+  const int c = threadIdx.x;
+  T w2[H], we[G], wf[4];
+#pragma unroll
+  for (int h = 0; h < H; ++h) w2[h] = T(p.en_w2[h * d + c]);
+#pragma unroll
+  for (int g = 0; g < G; ++g) we[g] = T(p.en_wenv[g * d + c]);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) wf[k] = T(p.en_wfeat[k * d + c]);
+  FL3<T> acc;
+  acc.v = acc.l = T(0);
+  acc.t[0] = acc.t[1] = acc.t[2] = T(0);
+  const double* ri = r + ((int64_t)w * n + i) * 3;
+  for (int m = 0; m < N; ++m) {
+    double dd[3] = {ri[0] - R[3 * m], ri[1] - R[3 * m + 1], ri[2] - R[3 * m + 2]};
+    double rr = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+    if (!(rr < cnuc)) continue;   // Gamma_m vanishes identically for |x| >= c_n
+    T dv[3] = {T(dd[0]), T(dd[1]), T(dd[2])};
+    __syncthreads();
+    pair_features_to_smem<T, W>(dv, T(rr), p.en_w1 + (int64_t)m * 4 * H, p.en_b1 + (int64_t)m * H,
+                                p.en_sigma, T(cnuc), feat);
+    __syncthreads();
+    FL3<T> gv, ev, fv;
+    gv.v = gv.l = ev.v = ev.l = T(0);
+    fv.v = T(p.nuc_emb[(int64_t)m * d + c]);
+    fv.l = T(0);
+#pragma unroll
+    for (int t = 0; t < 3; ++t) gv.t[t] = ev.t[t] = fv.t[t] = T(0);
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+      const FL3<T> a = feat[h];
+      gv.v += a.v * w2[h];
+      gv.l += a.l * w2[h];
+#pragma unroll
+      for (int t = 0; t < 3; ++t) gv.t[t] += a.t[t] * w2[h];
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const FL3<T> a = feat[H + g];
+      ev.v += a.v * we[g];
+      ev.l += a.l * we[g];
+#pragma unroll
+      for (int t = 0; t < 3; ++t) ev.t[t] += a.t[t] * we[g];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const FL3<T> a = feat[H + G + k];
+      fv.v += a.v * wf[k];
+      fv.l += a.l * wf[k];
+#pragma unroll
+      for (int t = 0; t < 3; ++t) fv.t[t] += a.t[t] * wf[k];
+    }
+    FL3<T> gam, term;
+    fl3_mul(gv, ev, gam);
+    fl3_mul(gam, fv, term);
+    acc.v += term.v;
+    acc.l += term.l;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) acc.t[t] += term.t[t];
+  }
+  const int64_t row = (int64_t)block_index(w, i, Wc, n, n_up) * R5;
+  S[row * d + c] = acc.v;
+  if (R5 > 1) {
+    S[(row + 1) * d + c] = acc.l;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) S[(row + 2 + t) * d + c] = acc.t[t];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* red) {
+  // blockDim.x multiple of 32, <= 1024; red has >= 32 entries.
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  T s = T(0);
+  for (int k = 0; k < nw; ++k) s += red[k];
+  return s;
+}
+
+// LayerNorm in forward-Laplacian form over blocks of R5 rows (3 tangents).
+// One CTA per electron, blockDim == d.
+template <typename T, typename W>
+__global__ void ln_fl_kernel(int d, const T* __restrict__ X, T* __restrict__ Y, const W* gamma,
+                             const W* beta, int R5) {
+  __shared__ T red[32];
+  const int64_t row = (int64_t)blockIdx.x * R5;
+  const int c = threadIdx.x;
+  const T inv_d = T(1) / T(d);
+  FL3<T> x;
+  x.v = X[row * d + c];
+  x.l = (R5 > 1) ? X[(row + 1) * d + c] : T(0);
+#pragma unroll
+  for (int t = 0; t < 3; ++t) x.t[t] = (R5 > 1) ? X[(row + 2 + t) * d + c] : T(0);
+  T mu = block_sum(x.v, red) * inv_d;
+  T mul = block_sum(x.l, red) * inv_d;
+  T mut[3];
+#pragma unroll
+  for (int t = 0; t < 3; ++t) mut[t] = block_sum(x.t[t], red) * inv_d;
+  FL3<T> cc;
+  cc.v = x.v - mu;
+  cc.l = x.l - mul;
+#pragma unroll
+  for (int t = 0; t < 3; ++t) cc.t[t] = x.t[t] - mut[t];
+  T var = block_sum(cc.v * cc.v, red) * inv_d;
+  T sq = cc.t[0] * cc.t[0] + cc.t[1] * cc.t[1] + cc.t[2] * cc.t[2];
+  T varl = T(2) * block_sum(sq + cc.v * cc.l, red) * inv_d;
+  T vart[3];
+#pragma unroll
+  for (int t = 0; t < 3; ++t) vart[t] = T(2) * block_sum(cc.v * cc.t[t], red) * inv_d;
+  const T s = dsqrt<T>(var + T(kLnEps));
+  T st[3], st2 = T(0), vt2 = T(0);
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    st[t] = vart[t] / (T(2) * s);
+    st2 += st[t] * st[t];
+    vt2 += vart[t] * vart[t];
+  }
+  const T sl = varl / (T(2) * s) - vt2 / (T(4) * s * s * s);
+  const T g = T(gamma[c]);
+  Y[row * d + c] = g * (cc.v / s) + T(beta[c]);
+  if (R5 > 1) {
+    T cross = T(0);
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      cross += cc.t[t] * st[t];
+      Y[(row + 2 + t) * d + c] = g * (cc.t[t] / s - cc.v * st[t] / (s * s));
+    }
+    T yl = cc.l / s - T(2) * cross / (s * s) - cc.v * sl / (s * s) + T(2) * cc.v * st2 / (s * s * s);
+    Y[(row + 1) * d + c] = g * yl;
+  }
+}
+
+// GLU gate p = SiLU(z_g) * z_v in forward-Laplacian form; Z is [rows][2d]
+// (gate columns first), P [rows][d].  One CTA per electron, blockDim == d.
+template <typename T>
+__global__ void glu_gate_kernel(int d, const T* __restrict__ Z, T* __restrict__ P, int R5) {
+  const int64_t row = (int64_t)blockIdx.x * R5;
+  const int c = threadIdx.x;
+  const int64_t ld = 2 * d;
+  T zg = Z[row * ld + c], zv = Z[row * ld + d + c];
+  T f, f1, f2;
+  silu3<T>(zg, f, f1, f2);
+  P[row * d + c] = f * zv;
+  if (R5 > 1) {
+    T gl = Z[(row + 1) * ld + c], vl = Z[(row + 1) * ld + d + c];
+    T sq = T(0), cross = T(0);
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      T gt = Z[(row + 2 + t) * ld + c], vt = Z[(row + 2 + t) * ld + d + c];
+      sq += gt * gt;
+      cross += f1 * gt * vt;
+      P[(row + 2 + t) * d + c] = f1 * gt * zv + f * vt;
+    }
+    P[(row + 1) * d + c] = (f1 * gl + f2 * sq) * zv + T(2) * cross + f * vl;
+  }
+}
+
+// Message passing step.  One CTA per electron (w, i), blockDim == d.
+// H0 [Wc*n*R5][d]; PQ [Wc*n*R5][4d] = [h0 W^par_a | h0 W^anti_a | h0 W^par_b |
+// h0 W^anti_b]; X receives the block of h^1_i (value, Laplacian, tangents).
+template <typename T, typename W>
+__global__ void msg_kernel(int Wc, int n, int n_up, int d, int K, const double* __restrict__ r,
+                           double cut, Params<W> p, const int32_t* __restrict__ idx,
+                           const int32_t* __restrict__ cnt, const int64_t* __restrict__ blk_off,
+                           const T* __restrict__ H0, const T* __restrict__ PQ, T* __restrict__ X,
+                           int deriv) {
+  constexpr int H = kEdgeHidden, G = kGauss;
+  __shared__ FL3<T> feat[H + G + 4];
+  const int blk = blockIdx.x;
+  const int w = blk / n, i = blk % n;
+  const int c = threadIdx.x;
+  const int R5 = deriv ? 5 : 1;
+  const int bi = block_index(w, i, Wc, n, n_up);
+  const int64_t hrow = (int64_t)bi * R5;
+  const int64_t ld4 = 4 * (int64_t)d;
+  T w2[H], we[G], wc[2][4], bb[2];
+#pragma unroll
+  for (int h = 0; h < H; ++h) w2[h] = T(p.ee_w2[h * d + c]);
+#pragma unroll
+  for (int g = 0; g < G; ++g) we[g] = T(p.ee_wenv[g * d + c]);
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    bb[a] = T(p.msg_b[a * d + c]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) wc[a][k] = T(p.msg_w[((int64_t)a * (2 * d + 4) + 2 * d + k) * d + c]);
+  }
+  // accumulator = h^0_i (value, Laplacian, self tangents)
+  FL3<T> acc;
+  acc.v = H0[hrow * d + c];
+  acc.l = deriv ? H0[(hrow + 1) * d + c] : T(0);
+#pragma unroll
+  for (int t = 0; t < 3; ++t) acc.t[t] = deriv ? H0[(hrow + 2 + t) * d + c] : T(0);
+  const int64_t xoff = blk_off[bi];
+  const int cpar = cnt[((int64_t)w * n + i) * 2], ctot = cpar + cnt[((int64_t)w * n + i) * 2 + 1];
+  const double* rw = r + (int64_t)w * n * 3;
+  const int32_t* li = idx + ((int64_t)w * n + i) * K;
+  for (int s = 0; s < ctot; ++s) {
+    const int j = li[s];
+    const int a = (s < cpar) ? 0 : 1;
+    double dd[3] = {rw[3 * i] - rw[3 * j], rw[3 * i + 1] - rw[3 * j + 1], rw[3 * i + 2] - rw[3 * j + 2]};
+    double rr = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+    T dv[3] = {T(dd[0]), T(dd[1]), T(dd[2])};
+    __syncthreads();
+    pair_features_to_smem<T, W>(dv, T(rr), p.ee_w1, p.ee_b1, p.ee_sigma, T(cut), feat);
+    __syncthreads();
+    // Gamma(e_ij) in delta-space (delta = r_i - r_j)
+    FL3<T> gv, ev, gam;
+    gv.v = gv.l = ev.v = ev.l = T(0);
+#pragma unroll
+    for (int t = 0; t < 3; ++t) gv.t[t] = ev.t[t] = T(0);
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+      const FL3<T> q = feat[h];
+      gv.v += q.v * w2[h];
+      gv.l += q.l * w2[h];
+#pragma unroll
+      for (int t = 0; t < 3; ++t) gv.t[t] += q.t[t] * w2[h];
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const FL3<T> q = feat[H + g];
+      ev.v += q.v * we[g];
+      ev.l += q.l * we[g];
+#pragma unroll
+      for (int t = 0; t < 3; ++t) ev.t[t] += q.t[t] * we[g];
+    }
+    fl3_mul(gv, ev, gam);
+    // z = P_i + Q_j + e-bar_ij W_c + b ; tangents in r_i and r_j
+    const int bj = block_index(w, j, Wc, n, n_up);
+    const int64_t prow = hrow, qrow = (int64_t)bj * R5;
+    const int64_t pcol = (int64_t)a * d + c, qcol = 2 * (int64_t)d + (int64_t)a * d + c;
+    T ebv = T(0), ebt[3] = {T(0), T(0), T(0)}, ebl = T(0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const FL3<T> q = feat[H + G + k];
+      ebv += q.v * wc[a][k];
+      ebl += q.l * wc[a][k];
+#pragma unroll
+      for (int t = 0; t < 3; ++t) ebt[t] += q.t[t] * wc[a][k];
+    }
+    T zv = PQ[prow * ld4 + pcol] + PQ[qrow * ld4 + qcol] + ebv + bb[a];
+    T f, f1, f2;
+    silu3<T>(zv, f, f1, f2);
+    const T mv = gam.v * f;
+    acc.v += mv;
+    if (deriv) {
+      T zi[3], zj[3], sq = T(0);
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        zi[t] = PQ[(prow + 2 + t) * ld4 + pcol] + ebt[t];
+        zj[t] = PQ[(qrow + 2 + t) * ld4 + qcol] - ebt[t];
+        sq += zi[t] * zi[t] + zj[t] * zj[t];
+      }
+      const T zl = PQ[(prow + 1) * ld4 + pcol] + PQ[(qrow + 1) * ld4 + qcol] + T(2) * ebl;
+      const T sl = f1 * zl + f2 * sq;
+      T cross = T(0);
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        const T si = f1 * zi[t], sj = f1 * zj[t];
+        acc.t[t] += gam.t[t] * f + gam.v * si;
+        X[(xoff + 2 + 3 * (s + 1) + t) * d + c] = -gam.t[t] * f + gam.v * sj;
+        cross += gam.t[t] * (si - sj);
+      }
+      acc.l += T(2) * gam.l * f + T(2) * cross + gam.v * sl;
+    }
+  }
+  X[xoff * d + c] = acc.v;
+  if (deriv) {
+    X[(xoff + 1) * d + c] = acc.l;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) X[(xoff + 2 + t) * d + c] = acc.t[t];
+  }
+}
+
+// Elementwise SiLU layer in forward-Laplacian form on ragged blocks:
+//   y = SiLU(z + b)  (residual: x += y), tangents y_t = SiLU'(z) z_t,
+//   Laplacian y_l = SiLU'(z) z_l + SiLU''(z) sum_t z_t^2.
+// Block b spans rows off[b] .. off[b+1]-1 (or b*stride .. if off == nullptr).
+// One CTA per block; threads stride over the ncol columns.
+template <typename T, typename W>
+__global__ void fl_act_kernel(int ncol, const int64_t* __restrict__ off, int64_t stride,
+                              const T* __restrict__ Z, int64_t ldz, const W* bias,
+                              T* __restrict__ Y, int64_t ldy, int residual) {
+  const int b = blockIdx.x;
+  int64_t r0, r1;
+  if (off) { r0 = off[b]; r1 = off[b + 1]; }
+  else { r0 = (int64_t)b * stride; r1 = r0 + stride; }
+  const int64_t nr = r1 - r0;
+  if (nr <= 0) return;
+  for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+    T z = Z[r0 * ldz + c] + (bias ? T(bias[c]) : T(0));
+    T f, f1, f2;
+    silu3<T>(z, f, f1, f2);
+    T sq = T(0);
+    for (int64_t q = r0 + 2; q < r1; ++q) {
+      T zt = Z[q * ldz + c];
+      sq += zt * zt;
+      T yt = f1 * zt;
+      if (residual) Y[q * ldy + c] += yt; else Y[q * ldy + c] = yt;
+    }
+    if (nr > 1) {
+      T yl = f1 * Z[(r0 + 1) * ldz + c] + f2 * sq;
+      if (residual) Y[(r0 + 1) * ldy + c] += yl; else Y[(r0 + 1) * ldy + c] = yl;
+    }
+    if (residual) Y[r0 * ldy + c] += f; else Y[r0 * ldy + c] = f;
+  }
+}
+
+// out[row] = Y[row] . w for rows [r_begin, r_end) (device range or host).
+template <typename T, typename W>
+__global__ void rowdot_kernel(const T* __restrict__ Y, int64_t ldy, int ncol, const W* wv,
+                              T* __restrict__ out, const int64_t* range, int64_t r_begin,
+                              int64_t r_end) {
+  int64_t b = r_begin, e = r_end;
+  if (range) { b = range[0]; e = range[1]; }
+  const int64_t row = b + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x & 31;
+  if (row >= e) return;
+  T s = T(0);
+  for (int c = lane; c < ncol; c += 32) s += Y[row * ldy + c] * T(wv[c]);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[row] = s;
+}
+
+// Copies the value row of every electron block into a dense [Wc*n][d] matrix
+// (block order).
+template <typename T>
+__global__ void gather_value_rows_kernel(int nb, int d, const int64_t* __restrict__ off,
+                                         const T* __restrict__ X, T* __restrict__ Hv) {
+  const int b = blockIdx.x;
+  const int64_t r0 = off[b];
+  for (int c = threadIdx.x; c < d; c += blockDim.x) Hv[(int64_t)b * d + c] = X[r0 * d + c];
+}
+
+}  // namespace fire

@@ -1,0 +1,329 @@
+// Host-side pipeline: the sequence of kernels of one call, chunk by chunk.
+// Instantiated once per precision form (run_fp64.cu, run_fp32.cu,
+// run_bf16.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "common.cuh"
+#include "det.cuh"
+#include "embed.cuh"
+#include "gemm.cuh"
+#include "jastrow.cuh"
+#include "nbr.cuh"
+#include "plan.h"
+
+namespace fire {
+
+enum ParamIndex {
+  P_EN_W1, P_EN_B1, P_EN_W2, P_EN_WENV, P_EN_SIGMA, P_NUC_EMB, P_EN_WFEAT,
+  P_LN_GAMMA, P_LN_BETA, P_GLU_WG, P_GLU_WV, P_GLU_WO,
+  P_EE_W1, P_EE_B1, P_EE_W2, P_EE_WENV, P_EE_SIGMA, P_MSG_W, P_MSG_B,
+  P_MLP_W, P_MLP_B, P_ORB_W, P_ENV_PI, P_ENV_SIGMA, P_CUSP,
+  P_JM1_W1, P_JM1_B1, P_JM1_W2, P_JM1_B2, P_JM1_W3, P_JM1_B3,
+  P_JM2_W1, P_JM2_B1, P_JM2_W2, P_JM2_B2, P_JM2_W3, P_JM2_B3,
+  P_ATT_Q, P_ATT_WV,
+  P_JA1_W1, P_JA1_B1, P_JA1_W2, P_JA1_B2, P_JA1_W3, P_JA1_B3,
+  P_JA2_W1, P_JA2_B1, P_JA2_W2, P_JA2_B2, P_JA2_W3, P_JA2_B3,
+  P_COUNT
+};
+
+struct CallArgs {
+  const fire_system_t* sys;
+  const fire_arch_t* arch;
+  const void* theta;
+  const int64_t* poff;       // [P_COUNT] element offsets into theta
+  int64_t W;
+  const double* r;
+  double *e_loc, *logabs, *sign, *e_kin, *e_pot;
+  void* ws;
+  cudaStream_t stream;
+  DevStatus* host_status;    // filled after the call
+};
+
+void set_last_error(const char* stage, const char* msg);
+int run_fp64(const Plan& pl, const CallArgs& a);
+int run_fp32(const Plan& pl, const CallArgs& a);
+int run_bf16(const Plan& pl, const CallArgs& a);
+
+template <typename W>
+inline Params<W> make_params(const void* theta, const int64_t* o) {
+  const W* b = reinterpret_cast<const W*>(theta);
+  Params<W> p;
+  const W** f[P_COUNT] = {
+      &p.en_w1, &p.en_b1, &p.en_w2, &p.en_wenv, &p.en_sigma, &p.nuc_emb, &p.en_wfeat,
+      &p.ln_gamma, &p.ln_beta, &p.glu_wg, &p.glu_wv, &p.glu_wo,
+      &p.ee_w1, &p.ee_b1, &p.ee_w2, &p.ee_wenv, &p.ee_sigma, &p.msg_w, &p.msg_b,
+      &p.mlp_w, &p.mlp_b, &p.orb_w, &p.env_pi, &p.env_sigma, &p.cusp,
+      &p.jm1_w1, &p.jm1_b1, &p.jm1_w2, &p.jm1_b2, &p.jm1_w3, &p.jm1_b3,
+      &p.jm2_w1, &p.jm2_b1, &p.jm2_w2, &p.jm2_b2, &p.jm2_w3, &p.jm2_b3,
+      &p.att_q, &p.att_wv,
+      &p.ja1_w1, &p.ja1_b1, &p.ja1_w2, &p.ja1_b2, &p.ja1_w3, &p.ja1_b3,
+      &p.ja2_w1, &p.ja2_b1, &p.ja2_w2, &p.ja2_b2, &p.ja2_w3, &p.ja2_b3};
+  for (int k = 0; k < P_COUNT; ++k) *f[k] = b + o[k];
+  return p;
+}
+
+// Hook for the tensor-core form: a matrix product over forward-Laplacian rows
+// with an optional tensor-core implementation (BF16 in, FP32 accumulate).
+template <typename T>
+struct RowGemm {
+  // returns true if it handled the product
+  bool (*tc)(void* ctx, cudaStream_t s, const T* A, int64_t lda, const T* B, int64_t ldb, T* C,
+             int64_t ldc, const int64_t* m_range, int64_t m_begin, int64_t m_end, int64_t m_cap,
+             int N, int K) = nullptr;
+  void* ctx = nullptr;
+};
+
+template <typename T, typename LT, typename RT>
+struct Runner {
+  const Plan& pl;
+  const CallArgs& a;
+  const Dims& dm;
+  Params<T> p;
+  unsigned char* ws;
+  cudaStream_t s;
+  RowGemm<T> rg;
+
+  Runner(const Plan& pl_, const CallArgs& a_) : pl(pl_), a(a_), dm(pl_.dm) {
+    p = make_params<T>(a.theta, a.poff);
+    dbg = getenv("FIRE_DEBUG_SYNC") != nullptr;
+    ws = reinterpret_cast<unsigned char*>(a.ws);
+    s = a.stream;
+  }
+  template <typename X> X* at(size_t off) { return reinterpret_cast<X*>(ws + off); }
+
+  // With FIRE_DEBUG_SYNC set, every stage is synchronised and checked, and the
+  // name of the first failing stage is kept for fire_last_error().
+  bool dbg = false;
+  int failed = 0;
+  void check(const char* stage) {
+    if (!dbg || failed) return;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      failed = 1;
+      set_last_error(stage, cudaGetErrorString(e));
+    }
+  }
+
+  // product over forward-Laplacian rows: tensor cores when available
+  void row_gemm(const T* A, int64_t lda, const T* B, int64_t ldb, T* C, int64_t ldc,
+                const int64_t* m_range, int64_t m_begin, int64_t m_end, int64_t m_cap, int N, int K) {
+    if (rg.tc && rg.tc(rg.ctx, s, A, lda, B, ldb, C, ldc, m_range, m_begin, m_end, m_cap, N, K)) return;
+    gemm<T>(s, A, lda, B, ldb, false, C, ldc, m_begin, m_end, m_range, m_cap, N, K);
+  }
+
+  // SiLU-MLP readout with two hidden layers over ragged blocks (rows of X
+  // given by blk offsets or a fixed stride) -> per-row scalar F.
+  void mlp_readout(const T* Xin, int64_t ldx, int din, const int64_t* range, int64_t rb, int64_t re,
+                   int64_t cap, const int64_t* off, int64_t stride, int nblk, const T* w1, const T* b1,
+                   const T* w2, const T* b2, const T* w3, T* Z, int64_t ldz, T* Y, int64_t ldy, T* F) {
+    const int J = dm.J;
+    row_gemm(Xin, ldx, w1, J, Z, ldz, range, rb, re, cap, J, din);
+    fl_act_kernel<T, T><<<nblk, 256, 0, s>>>(J, off, stride, Z, ldz, b1, Y, ldy, 0);
+    row_gemm(Y, ldy, w2, J, Z, ldz, range, rb, re, cap, J, J);
+    fl_act_kernel<T, T><<<nblk, 256, 0, s>>>(J, off, stride, Z, ldz, b2, Y, ldy, 0);
+    const int64_t nrows_grid = cap;
+    rowdot_kernel<T, T><<<(unsigned)((nrows_grid + 7) / 8), 256, 0, s>>>(Y, ldy, J, w3, F, range, rb, re);
+  }
+
+  int run() {
+    const fire_system_t* sys = a.sys;
+    const int n = dm.n, n_up = dm.n_up, N = dm.N, d = dm.d, D = dm.D, K = dm.K;
+    const int deriv = dm.deriv;
+    const int R5 = deriv ? 5 : 1;
+    DevStatus* st = at<DevStatus>(pl.status);
+    cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
+    for (int64_t ch = 0; ch < pl.nchunks; ++ch) {
+      const int64_t w0 = ch * pl.Wc;
+      const int wc = (int)((a.W - w0) < pl.Wc ? (a.W - w0) : pl.Wc);
+      const double* r = a.r + w0 * n * 3;
+      const int nb = wc * n;
+      int32_t* idx = at<int32_t>(pl.idx);
+      int32_t* cnt = at<int32_t>(pl.cnt);
+      int32_t* rev = at<int32_t>(pl.rev);
+      int64_t* brow = at<int64_t>(pl.blk_rows);
+      int64_t* boff = at<int64_t>(pl.blk_off);
+      int64_t* rng = at<int64_t>(pl.ranges);
+      const double c = sys->cutoff;
+      // 1. neighbour lists and the ragged row layout
+      nbr_build_kernel<<<wc, 256, (size_t)n * 3 * sizeof(double), s>>>(wc, n, n_up, r, c * c, K, idx, cnt,
+                                                                        brow, st, deriv);
+      nbr_reverse_kernel<<<wc, 256, 0, s>>>(n, n_up, K, idx, cnt, rev);
+      blk_scan_kernel<<<1, 1024, 0, s>>>(nb, wc * n_up, brow, boff, rng, st);
+      check("nbr");
+      const int64_t cap = (int64_t)nb * pl.rows_per_el;
+      const int64_t* full = rng;          // {0, total} is rng[0], rng[3]: use a 2-element view
+      int64_t* fullr = at<int64_t>(pl.ranges) + 4;
+      // fullr = {0, total}: written by a tiny copy below
+      cudaMemcpyAsync(fullr, rng, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(fullr + 1, rng + 3, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
+      (void)full;
+      // 2. initial embeddings h^0 (5 rows per electron)
+      T* S5 = at<T>(pl.S5);
+      T* Y5 = at<T>(pl.Y5);
+      T* Z5 = at<T>(pl.Z5);
+      T* P5 = at<T>(pl.P5);
+      T* H0 = at<T>(pl.H0);
+      T* PQ = at<T>(pl.PQ);
+      const int64_t r5 = (int64_t)nb * R5;
+      en_filter_kernel<T, T><<<nb, d, 0, s>>>(wc, n, n_up, N, d, r, sys->nuc_pos, sys->cutoff_nuc, p, S5, R5);
+      ln_fl_kernel<T, T><<<nb, d, 0, s>>>(d, S5, Y5, p.ln_gamma, p.ln_beta, R5);
+      gemm<T>(s, Y5, d, p.glu_wg, d, false, Z5, 2 * d, 0, r5, nullptr, r5, d, d);
+      gemm<T>(s, Y5, d, p.glu_wv, d, false, Z5 + d, 2 * d, 0, r5, nullptr, r5, d, d);
+      glu_gate_kernel<T><<<nb, d, 0, s>>>(d, Z5, P5, R5);
+      check("h0");
+      gemm<T>(s, P5, d, p.glu_wo, d, false, H0, d, 0, r5, nullptr, r5, d, d);
+      // 3. h^0 W^alpha_a, h^0 W^alpha_b for both spin channels
+      for (int part = 0; part < 2; ++part)
+        gemm<T>(s, H0, d, p.msg_w + (int64_t)part * d * d, d, false, PQ + (int64_t)part * 2 * d, 4 * d, 0, r5,
+                nullptr, r5, d, d, 2, 0, (int64_t)(2 * d + 4) * d, d);
+      // 4. message passing -> h^1 blocks
+      T* X = at<T>(pl.X);
+      msg_kernel<T, T><<<nb, d, 0, s>>>(wc, n, n_up, d, K, r, c, p, idx, cnt, boff, H0, PQ, X, deriv);
+      check("msg");
+      // 5. embedding MLP h = MLP(h^1): L residual SiLU layers
+      T* big = at<T>(pl.big);
+      T* Z = big + pl.zcol;
+      T* Y = big + pl.ycol;
+      T* SU = big + pl.sucol;
+      const int64_t ldb = pl.ld_big;
+      for (int l = 0; l < dm.L; ++l) {
+        row_gemm(X, d, p.mlp_w + (int64_t)l * d * d, d, Z, ldb, fullr, 0, 0, cap, d, d);
+        fl_act_kernel<T, T><<<nb, 256, 0, s>>>(d, boff, 0, Z, ldb, p.mlp_b + (int64_t)l * d, X, d, 1);
+      }
+      // 6. Jastrow factors
+      T* jval = at<T>(pl.jval); T* jsign = at<T>(pl.jsign); T* jgrad = at<T>(pl.jgrad); T* jlap = at<T>(pl.jlap);
+      T* aval = at<T>(pl.aval); T* asign = at<T>(pl.asign); T* agrad = at<T>(pl.agrad); T* alap = at<T>(pl.alap);
+      T* cval = at<T>(pl.cval); T* cgrad = at<T>(pl.cgrad); T* clap = at<T>(pl.clap); T* vpot = at<T>(pl.vpot);
+      if (dm.flags & FIRE_J_MLP) {
+        T* F1 = at<T>(pl.F1);
+        T* F2 = at<T>(pl.F2);
+        mlp_readout(X, d, d, fullr, 0, 0, cap, boff, 0, nb, p.jm1_w1, p.jm1_b1, p.jm1_w2, p.jm1_b2, p.jm1_w3,
+                    Z, ldb, Y, ldb, F1);
+        mlp_readout(X, d, d, fullr, 0, 0, cap, boff, 0, nb, p.jm2_w1, p.jm2_b1, p.jm2_w2, p.jm2_b2, p.jm2_w3,
+                    Z, ldb, Y, ldb, F2);
+        jmlp_reduce_kernel<T, T><<<wc, 256, 0, s>>>(wc, n, n_up, K, idx, cnt, rev, boff, F1, F2, p.jm1_b3,
+                                                    p.jm2_b3, jval, jsign, jgrad, jlap, deriv);
+      check("jmlp");
+      }
+      if (dm.flags & FIRE_J_ATT) {
+        const int R = dm.R, dr = dm.dr, RD = R * dr;
+        gemm<T>(s, X, d, p.att_q, d, true, SU, ldb, 0, 0, fullr, cap, R, d);
+        gemm<T>(s, X, d, p.att_wv, dr, false, SU + R, ldb, 0, 0, fullr, cap, dr, d, R, 0, (int64_t)d * dr, dr);
+        T* V = at<T>(pl.V);
+        T* VZ = at<T>(pl.VZ);
+        T* VY = at<T>(pl.VY);
+        T* G1 = at<T>(pl.G1);
+        T* G2 = at<T>(pl.G2);
+        const size_t apsm = (size_t)(R + n * R) * sizeof(T);
+        const int bt = ((RD + 31) / 32) * 32;
+        att_pool_kernel<T><<<wc, bt, apsm, s>>>(wc, n, n_up, K, R, dr, idx, cnt, rev, boff, SU, ldb, V, deriv);
+        const int64_t vstride = deriv ? (2 + 3 * (int64_t)n) : 1;
+        const int64_t vrows = (int64_t)wc * vstride;
+        mlp_readout(V, RD, RD, nullptr, 0, vrows, vrows, nullptr, vstride, wc, p.ja1_w1, p.ja1_b1, p.ja1_w2,
+                    p.ja1_b2, p.ja1_w3, VZ, dm.J, VY, dm.J, G1);
+        mlp_readout(V, RD, RD, nullptr, 0, vrows, vrows, nullptr, vstride, wc, p.ja2_w1, p.ja2_b1, p.ja2_w2,
+                    p.ja2_b2, p.ja2_w3, VZ, dm.J, VY, dm.J, G2);
+        att_reduce_kernel<T, T><<<wc, 256, 0, s>>>(n, G1, G2, p.ja1_b3, p.ja2_b3, aval, asign, agrad, alap, deriv);
+      check("att");
+      }
+      coulomb_cusp_kernel<T, T><<<wc, 256, 0, s>>>(n, n_up, N, r, sys->nuc_pos, sys->nuc_charge, p.cusp, vpot,
+                                                   cval, cgrad, clap, deriv);
+      // 7. envelopes and orbital values
+      const int E = dm.E, NE = N * E;
+      const int64_t Dn = (int64_t)D * n;
+      T* Qf = at<T>(pl.Qf);
+      T* Fenv = at<T>(pl.Fenv);
+      env_feat_kernel<T, T><<<nb, 128, 0, s>>>(wc, n, n_up, N, E, r, sys->nuc_pos, p.env_sigma, Qf, R5);
+      const int64_t up5 = (int64_t)wc * n_up * R5;
+      for (int sp = 0; sp < 2; ++sp) {
+        const int64_t rb = sp ? up5 : 0, re = sp ? r5 : up5;
+        if (re > rb)
+          gemm<T>(s, Qf, NE, p.env_pi + (int64_t)sp * Dn * NE, NE, true, Fenv, Dn, rb, re, nullptr, re - rb,
+                  (int)Dn, NE);
+      }
+      T* Hv = at<T>(pl.Hv);
+      T* Ov = at<T>(pl.Ov);
+      gather_value_rows_kernel<T><<<nb, 256, 0, s>>>(nb, d, boff, X, Hv);
+      const int64_t upv = (int64_t)wc * n_up;
+      for (int sp = 0; sp < 2; ++sp) {
+        const int64_t rb = sp ? upv : 0, re = sp ? nb : upv;
+        if (re > rb)
+          gemm<T>(s, Hv, d, p.orb_w + (int64_t)sp * D * d * n, n, false, Ov, Dn, rb, re, nullptr, re - rb, n, d,
+                  D, 0, (int64_t)d * n, n);
+      }
+      LT* LUb = at<LT>(pl.LU);
+      int32_t* piv = at<int32_t>(pl.piv);
+      double* ldabs = at<double>(pl.ldabs);
+      double* lsign = at<double>(pl.lsign);
+      phi_assemble_kernel<T, LT><<<wc * D, 256, 0, s>>>(wc, n, n_up, D, Ov, Fenv, R5, LUb);
+      const size_t lusm = (size_t)2 * n * 16 * sizeof(LT);
+      lu_kernel<LT, 16><<<wc * D, 256, lusm, s>>>(n, LUb, piv, ldabs, lsign);
+      check("lu");
+      T* gdet = at<T>(pl.gdet);
+      T* ldet = at<T>(pl.ldet);
+      if (deriv) {
+        T* Ainv = at<T>(pl.Ainv);
+        const size_t invsm = (size_t)n * n * sizeof(T) + 2 * n * sizeof(int);
+        lu_inverse_kernel<LT, T><<<wc * D, 256, invsm, s>>>(n, LUb, piv, Ainv);
+      check("inverse");
+        // 8. log-det gradient and Laplacian, determinant by determinant
+        T* O = big;  // aliases Z | Y | SU, which are dead by now
+        const int mcap = 1 + K;
+        const size_t ctsm = (size_t)(4 * mcap) * (n + 1) * sizeof(T) + 2 * mcap * sizeof(int);
+        for (int dd = 0; dd < D; ++dd) {
+          for (int sp = 0; sp < 2; ++sp)
+            row_gemm(X, d, p.orb_w + ((int64_t)sp * D + dd) * d * n, n, O, n, rng + 2 * sp, 0, 0, cap, n, d);
+          contract_kernel<T><<<nb, 256, ctsm, s>>>(wc, n, n_up, K, dd, D, idx, cnt, rev, boff, O, Fenv, Ainv,
+                                                   gdet, ldet, st);
+      check("contract");
+        }
+      }
+      // 9. final combination
+      FinalIn<T, RT> fi{ldabs, lsign, gdet, ldet, cval, cgrad, clap, jval, jsign, jgrad, jlap,
+                        aval, asign, agrad, alap, vpot};
+      final_kernel<T, RT><<<wc, 256, 0, s>>>(n, D, dm.flags, fi, deriv, a.e_loc ? a.e_loc + w0 : nullptr,
+                                             a.logabs + w0, a.sign + w0, a.e_kin ? a.e_kin + w0 : nullptr,
+                                             a.e_pot ? a.e_pot + w0 : nullptr, st);
+    }
+    check("final");
+    if (failed) return FIRE_ERR_CUDA;
+    {
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) { set_last_error("launch", cudaGetErrorString(e)); return FIRE_ERR_CUDA; }
+    }
+    if (cudaMemcpyAsync(a.host_status, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return FIRE_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return FIRE_ERR_CUDA;
+    return FIRE_OK;
+  }
+};
+
+// Raises the dynamic shared-memory limit of every kernel that needs more than
+// 48 KB.  Called once per precision form and device before the first launch.
+template <typename T, typename LT>
+inline int set_smem_limits() {
+  int dev = 0, maxopt = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return FIRE_ERR_CUDA;
+  cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  int rc = FIRE_OK;
+  auto raise = [&](const void* fn) {
+    cudaFuncAttributes at;
+    if (cudaFuncGetAttributes(&at, fn) != cudaSuccess) { rc = FIRE_ERR_CUDA; return; }
+    const int dyn = maxopt - (int)at.sharedSizeBytes;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) != cudaSuccess) rc = FIRE_ERR_CUDA;
+  };
+  raise((const void*)contract_kernel<T>);
+  raise((const void*)lu_inverse_kernel<LT, T>);
+  raise((const void*)lu_kernel<LT, 16>);
+  raise((const void*)att_pool_kernel<T>);
+  cudaError_t e = cudaGetLastError();
+  if (rc != FIRE_OK || e != cudaSuccess) set_last_error("smem limits", cudaGetErrorString(e));
+  return rc;
+}
+
+}  // namespace fire

@@ -1,0 +1,46 @@
+// Workspace plan shared by the entry points and the per-precision runners.
+#pragma once
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/fire.h"
+
+namespace fire {
+
+struct Dims {
+  int n, n_up, N, d, L, D, E, G, H, J, R, dr, K;
+  uint32_t flags;
+  int prec;
+  int deriv;
+  int op;
+};
+
+// Byte offsets of every buffer inside the workspace (for one chunk of Wc
+// walkers; buffers are reused chunk after chunk).
+struct Plan {
+  Dims dm;
+  int64_t W, Wc, nchunks;
+  int64_t rows_cap;        // forward-Laplacian rows of one chunk (upper bound)
+  int64_t rows_per_el;     // upper bound of rows per electron block
+  size_t tsz, lsz;         // element sizes of the compute and LU types
+  size_t status, idx, cnt, rev, blk_rows, blk_off, ranges;
+  size_t S5, Y5, Z5, P5, H0, PQ;
+  size_t X, big, F1, F2;   // big holds Z | Y | SU, and O (aliased) in the det phase
+  size_t Qf, Fenv, Hv, Ov;
+  size_t LU, piv, ldabs, lsign, Ainv, gdet, ldet;
+  size_t jval, jsign, jgrad, jlap, aval, asign, agrad, alap, cval, cgrad, clap, vpot;
+  size_t V, VZ, VY, G1, G2;
+  size_t wbf16;            // packed BF16 weights (tensor-core form)
+  size_t total;
+  // column layout of `big`
+  int64_t ld_big, zcol, ycol, sucol;
+  // named buffers (diagnostics)
+  struct Ent { const char* name; size_t off, bytes; } ent[96];
+  int nent;
+};
+
+int make_plan(const fire_system_t* sys, const fire_arch_t* arch, int64_t W, int prec, int k_cap,
+              int op, Plan* out);
+
+}  // namespace fire

@@ -1,0 +1,14 @@
+// Pipeline instantiation for the BF16_FP64 form: float32 activations,
+// float64 LU / slogdet and final reduction.
+#include "pipeline.cuh"
+
+namespace fire {
+
+int run_bf16(const Plan& pl, const CallArgs& a) {
+  int rc = set_smem_limits<float, double>();
+  if (rc) return rc;
+  Runner<float, double, double> rn(pl, a);
+  return rn.run();
+}
+
+}  // namespace fire

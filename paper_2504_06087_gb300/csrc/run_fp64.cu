@@ -1,0 +1,13 @@
+// Pipeline instantiation for the fp64 form.
+#include "pipeline.cuh"
+
+namespace fire {
+
+int run_fp64(const Plan& pl, const CallArgs& a) {
+  int rc = set_smem_limits<double, double>();
+  if (rc) return rc;
+  Runner<double, double, double> rn(pl, a);
+  return rn.run();
+}
+
+}  // namespace fire

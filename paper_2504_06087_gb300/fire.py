@@ -1,0 +1,249 @@
+"""Python binding of libfire (include/fire.h): argument marshalling only.
+
+Every step of the computation runs in the CUDA kernels of libfire.so; this
+module only converts arguments (ctypes structs, device pointers of torch
+tensors, the current CUDA stream) and allocates the caller-owned workspace
+with torch.  If libfire.so is missing the import of ``lib()`` raises: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Dict, Optional
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfire.so")
+
+PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
+OP_NEIGHBORS, OP_LOGPSI, OP_LOCAL_ENERGY, OP_GRAD_LOGPSI, OP_MCMC = 0, 1, 2, 3, 4
+
+STATUS = {0: "FIRE_OK", 1: "FIRE_ERR_INVALID_ARG", 2: "FIRE_ERR_CAPACITY", 3: "FIRE_ERR_NONFINITE",
+          4: "FIRE_ERR_SINGULAR_REFRESH", 5: "FIRE_ERR_TIMEOUT", 6: "FIRE_ERR_CUDA",
+          7: "FIRE_ERR_UNSUPPORTED", 8: "FIRE_ERR_WORKSPACE"}
+
+
+class FireError(RuntimeError):
+    def __init__(self, code: int, where: str, info=None):
+        self.code = code
+        self.info = info
+        msg = f"{where}: {STATUS.get(code, code)} ({lib().fire_status_string(code).decode()})"
+        if code == 6:
+            msg += " last error: " + lib().fire_last_error().decode()
+        super().__init__(msg)
+
+
+class System(ctypes.Structure):
+    _fields_ = [("n_el", ctypes.c_int32), ("n_up", ctypes.c_int32), ("n_nuc", ctypes.c_int32),
+                ("pad_", ctypes.c_int32), ("nuc_pos", ctypes.c_void_p), ("nuc_charge", ctypes.c_void_p),
+                ("cutoff", ctypes.c_double), ("cutoff_nuc", ctypes.c_double)]
+
+
+class Arch(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("n_layers", ctypes.c_int32), ("n_det", ctypes.c_int32),
+                ("n_env", ctypes.c_int32), ("n_gauss", ctypes.c_int32), ("edge_hidden", ctypes.c_int32),
+                ("jastrow_width", ctypes.c_int32), ("n_reg", ctypes.c_int32), ("d_reg", ctypes.c_int32),
+                ("flags", ctypes.c_uint32)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("theta", ctypes.c_void_p), ("n_params", ctypes.c_int64), ("dtype", ctypes.c_int32),
+                ("pad_", ctypes.c_int32)]
+
+
+class ParamEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("offset", ctypes.c_int64), ("ndim", ctypes.c_int32),
+                ("pad_", ctypes.c_int32), ("shape", ctypes.c_int64 * 5)]
+
+
+class WsEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 16), ("offset", ctypes.c_int64), ("bytes", ctypes.c_int64)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("k_required", ctypes.c_int32), ("n_nodes", ctypes.c_int32), ("n_nonfinite", ctypes.c_int32),
+                ("n_chunks", ctypes.c_int32), ("rows_total", ctypes.c_int64), ("mean_neighbors", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_LIB = None
+P = ctypes.POINTER
+VP = ctypes.c_void_p
+
+# name -> (restype, argtypes); mirrors include/fire.h
+SIGNATURES = {
+    "fire_version": (ctypes.c_char_p, []),
+    "fire_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "fire_last_error": (ctypes.c_char_p, []),
+    "fire_param_count": (ctypes.c_int64, [P(System), P(Arch)]),
+    "fire_param_layout": (ctypes.c_int, [P(System), P(Arch), P(ParamEntry), P(ctypes.c_int32)]),
+    "fire_workspace_size": (ctypes.c_size_t, [P(System), P(Arch), ctypes.c_int64, ctypes.c_int32,
+                                              ctypes.c_int32, ctypes.c_int32]),
+    "fire_workspace_layout": (ctypes.c_int, [P(System), P(Arch), ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.c_int32, P(WsEntry), P(ctypes.c_int32), P(ctypes.c_int64)]),
+    "fire_neighbors": (ctypes.c_int, [P(System), ctypes.c_int64, VP, ctypes.c_int32, VP, VP,
+                                      P(ctypes.c_int32), VP, ctypes.c_size_t, VP]),
+    "fire_logpsi": (ctypes.c_int, [P(System), P(Arch), P(Params), ctypes.c_int64, VP, ctypes.c_int32,
+                                   ctypes.c_int32, VP, VP, P(Info), VP, ctypes.c_size_t, VP]),
+    "fire_local_energy": (ctypes.c_int, [P(System), P(Arch), P(Params), ctypes.c_int64, VP, ctypes.c_int32,
+                                         ctypes.c_int32, VP, VP, VP, VP, VP, P(Info), VP, ctypes.c_size_t, VP]),
+}
+
+
+def lib():
+    """Loads libfire.so; raises if it has not been built."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2504_06087_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def make_arch(a) -> Arch:
+    return Arch(a.width, a.n_layers, a.n_det, a.n_env, a.n_gauss, a.edge_hidden, a.jastrow_width,
+                a.n_reg, a.d_reg, a.flags)
+
+
+def param_layout(system_c: System, arch_c: Arch):
+    L = lib()
+    n = ctypes.c_int32(0)
+    rc = L.fire_param_layout(ctypes.byref(system_c), ctypes.byref(arch_c), None, ctypes.byref(n))
+    if rc:
+        raise FireError(rc, "fire_param_layout")
+    ents = (ParamEntry * n.value)()
+    rc = L.fire_param_layout(ctypes.byref(system_c), ctypes.byref(arch_c), ents, ctypes.byref(n))
+    if rc:
+        raise FireError(rc, "fire_param_layout")
+    return [(e.name.decode(), int(e.offset), tuple(int(e.shape[k]) for k in range(e.ndim))) for e in ents]
+
+
+class Fire:
+    """A molecule, a network and its parameters resident on one CUDA device."""
+
+    def __init__(self, system, arch, params: Dict[str, np.ndarray], precision: str = "fp32",
+                 k_cap: int = 64, device: str = "cuda:0"):
+        self.system, self.arch, self.precision = system, arch, precision
+        self.prec = PREC[precision]
+        self.k_cap = int(k_cap)
+        self.device = torch.device(device)
+        self.nuc_pos = torch.as_tensor(np.ascontiguousarray(system.nuc_pos), dtype=torch.float64,
+                                       device=self.device)
+        self.nuc_charge = torch.as_tensor(np.ascontiguousarray(system.nuc_charge), dtype=torch.float64,
+                                          device=self.device)
+        self.sys_c = System(system.n_el, system.n_up, system.n_nuc, 0, self.nuc_pos.data_ptr(),
+                            self.nuc_charge.data_ptr(), float(system.cutoff), float(system.cutoff_nuc))
+        self.arch_c = make_arch(arch)
+        self.layout = param_layout(self.sys_c, self.arch_c)
+        self.n_params = int(lib().fire_param_count(ctypes.byref(self.sys_c), ctypes.byref(self.arch_c)))
+        self.set_params(params)
+        self._ws = {}
+
+    def set_params(self, params: Dict[str, np.ndarray]):
+        dt = np.float64 if self.prec == 0 else np.float32
+        flat = np.zeros(self.n_params, dtype=dt)
+        for name, off, shape in self.layout:
+            a = np.asarray(params[name])
+            if tuple(a.shape) != tuple(shape):
+                raise ValueError(f"parameter {name}: shape {a.shape} != {shape}")
+            flat[off:off + a.size] = a.reshape(-1)
+        self.theta = torch.as_tensor(flat, device=self.device)
+        self.params_c = Params(self.theta.data_ptr(), self.n_params, 0 if self.prec == 0 else 1, 0)
+
+    def workspace(self, W: int, op: int) -> torch.Tensor:
+        key = (W, op)
+        if key not in self._ws:
+            nbytes = lib().fire_workspace_size(ctypes.byref(self.sys_c), ctypes.byref(self.arch_c), W,
+                                               self.prec, self.k_cap, op)
+            if nbytes == 0:
+                raise FireError(1, "fire_workspace_size")
+            self._ws = {key: torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)}
+        return self._ws[key]
+
+    def workspace_layout(self, W: int, op: int):
+        """name -> (byte offset, bytes) of the intermediates of the first walker chunk."""
+        L = lib()
+        n, wc = ctypes.c_int32(0), ctypes.c_int64(0)
+        args = (ctypes.byref(self.sys_c), ctypes.byref(self.arch_c), W, self.prec, self.k_cap, op)
+        rc = L.fire_workspace_layout(*args, None, ctypes.byref(n), ctypes.byref(wc))
+        if rc:
+            raise FireError(rc, "fire_workspace_layout")
+        ents = (WsEntry * n.value)()
+        L.fire_workspace_layout(*args, ents, ctypes.byref(n), ctypes.byref(wc))
+        return {e.name.decode(): (int(e.offset), int(e.bytes)) for e in ents}, int(wc.value)
+
+    def ws_view(self, W: int, op: int, name: str, dtype, shape=None):
+        """A typed view of one intermediate buffer of the last call (no copy)."""
+        lay, _ = self.workspace_layout(W, op)
+        off, nb = lay[name]
+        ws = self.workspace(W, op)
+        t = ws[off:off + nb].view(dtype)
+        return t if shape is None else t[:int(np.prod(shape))].view(*shape)
+
+    def _stream(self):
+        return ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+
+    def _r(self, r):
+        if not isinstance(r, torch.Tensor):
+            r = torch.as_tensor(np.ascontiguousarray(r), dtype=torch.float64)
+        r = r.to(device=self.device, dtype=torch.float64).contiguous()
+        assert r.dim() == 3 and r.shape[1] == self.system.n_el and r.shape[2] == 3
+        return r
+
+    def local_energy(self, r, check: bool = True):
+        r = self._r(r)
+        W = r.shape[0]
+        out = {k: torch.empty(W, dtype=torch.float64, device=self.device)
+               for k in ("e_loc", "logabs", "sign", "e_kin", "e_pot")}
+        ws = self.workspace(W, OP_LOCAL_ENERGY)
+        info = Info()
+        rc = lib().fire_local_energy(ctypes.byref(self.sys_c), ctypes.byref(self.arch_c),
+                                     ctypes.byref(self.params_c), W, _ptr(r), self.k_cap, self.prec,
+                                     _ptr(out["e_loc"]), _ptr(out["logabs"]), _ptr(out["sign"]),
+                                     _ptr(out["e_kin"]), _ptr(out["e_pot"]), ctypes.byref(info),
+                                     _ptr(ws), ws.numel(), self._stream())
+        out["info"] = info.as_dict()
+        out["status"] = rc
+        if check and rc not in (0,):
+            raise FireError(rc, "fire_local_energy", out["info"])
+        return out
+
+    def logpsi(self, r, check: bool = True):
+        r = self._r(r)
+        W = r.shape[0]
+        out = {k: torch.empty(W, dtype=torch.float64, device=self.device) for k in ("logabs", "sign")}
+        ws = self.workspace(W, OP_LOGPSI)
+        info = Info()
+        rc = lib().fire_logpsi(ctypes.byref(self.sys_c), ctypes.byref(self.arch_c), ctypes.byref(self.params_c),
+                               W, _ptr(r), self.k_cap, self.prec, _ptr(out["logabs"]), _ptr(out["sign"]),
+                               ctypes.byref(info), _ptr(ws), ws.numel(), self._stream())
+        out["info"] = info.as_dict()
+        out["status"] = rc
+        if check and rc != 0:
+            raise FireError(rc, "fire_logpsi", out["info"])
+        return out
+
+    def neighbors(self, r):
+        r = self._r(r)
+        W, n = r.shape[0], self.system.n_el
+        idx = torch.full((W, n, self.k_cap), -1, dtype=torch.int32, device=self.device)
+        cnt = torch.zeros((W, n, 2), dtype=torch.int32, device=self.device)
+        ws = torch.empty(256, dtype=torch.uint8, device=self.device)
+        kreq = ctypes.c_int32(0)
+        rc = lib().fire_neighbors(ctypes.byref(self.sys_c), W, _ptr(r), self.k_cap, _ptr(idx), _ptr(cnt),
+                                  ctypes.byref(kreq), _ptr(ws), ws.numel(), self._stream())
+        return {"idx": idx, "cnt": cnt, "k_required": kreq.value, "status": rc}

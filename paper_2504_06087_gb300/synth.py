@@ -85,7 +85,8 @@ def water(cutoff: float = 5.0, cutoff_nuc: float = 20.0) -> System:
 def zigzag_polyene(k: int, terminal_h: bool = True, cutoff: float = 5.0,
                    cutoff_nuc: float = 20.0) -> System:
     cc, ch = 2.6, 2.05
-    c30, s30 = math.cos(math.radians(30.0)), math.sin(math.radians(30.0))
+    # exact forms (sqrt is correctly rounded on every platform, unlike cos/sin)
+    c30, s30 = math.sqrt(3.0) / 2.0, 0.5
     carbons = [np.array([j * cc * c30, (j % 2) * cc * s30, 0.0]) for j in range(k)]
     hyd: List[np.ndarray] = []
     for j in range(k):
@@ -96,10 +97,9 @@ def zigzag_polyene(k: int, terminal_h: bool = True, cutoff: float = 5.0,
             other = carbons[1] if j == 0 else carbons[k - 2]
             b = other - carbons[j]
             b = b / np.linalg.norm(b)
-            for ang in (120.0, -120.0):
-                a = math.radians(ang)
-                rb = np.array([math.cos(a) * b[0] - math.sin(a) * b[1],
-                               math.sin(a) * b[0] + math.cos(a) * b[1], 0.0])
+            for sn in (1.0, -1.0):      # rotations by +-120 degrees
+                ca, sa = -0.5, sn * math.sqrt(3.0) / 2.0
+                rb = np.array([ca * b[0] - sa * b[1], sa * b[0] + ca * b[1], 0.0])
                 hyd.append(carbons[j] + ch * rb)
         else:
             sgn = -1.0 if j % 2 == 0 else 1.0

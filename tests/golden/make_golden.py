@@ -1,0 +1,67 @@
+"""Writes the stored oracle values used by the full-size parity tests.
+
+Calls only the CPU oracle (oracle/) on inputs from the seeded generator; no
+value here comes from the CUDA path.  Each file records a hash of its inputs
+so a test can confirm that it regenerates the same walkers and parameters.
+
+    python tests/golden/make_golden.py c8h10 8
+    python tests/golden/make_golden.py c26h24 2
+"""
+import hashlib
+import json
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from oracle import fire_oracle as O  # noqa: E402
+from paper_2504_06087_gb300 import synth  # noqa: E402
+
+
+def input_hash(r, params) -> str:
+    h = hashlib.sha256()
+    h.update(np.ascontiguousarray(r).tobytes())
+    for k in sorted(params):
+        h.update(k.encode())
+        h.update(np.ascontiguousarray(params[k]).tobytes())
+    return h.hexdigest()
+
+
+def input_summary(r, params):
+    """Moments of the inputs: platform libm differences may move the last bit
+    of a generated value, so tests compare these within 1e-12 instead of the
+    bitwise hash."""
+    out = {"r_sum": float(np.sum(r)), "r_sq": float(np.sum(r * r)), "r_first": np.ravel(r)[:6].tolist()}
+    for k in sorted(params):
+        out["p_" + k] = [float(np.sum(params[k])), float(np.sum(params[k] ** 2))]
+    return out
+
+
+def main(key: str, nw: int):
+    w = synth.workload(key)
+    r, p = synth.make_inputs(w, nw)
+    t0 = time.time()
+    e, la, sg, kin, v, g, lap = O.local_energy(w.system, w.arch, p, r, return_parts=True)
+    out = {
+        "workload": key,
+        "n_walkers": nw,
+        "input_sha256": input_hash(r, p),
+        "input_summary": input_summary(r, p),
+        "source": "oracle/fire_oracle.py local_energy (FP64, dense, autograd Laplacian)",
+        "seconds": time.time() - t0,
+        "e_loc": e.tolist(), "logabs": la.tolist(), "sign": sg.tolist(),
+        "e_kin": kin.tolist(), "e_pot": v.tolist(), "lap": lap.tolist(),
+        "grad_norm2": (g ** 2).sum(axis=(1, 2)).tolist(),
+    }
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"{key}_oracle.json")
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+    print(path, out["seconds"])
+
+
+if __name__ == "__main__":
+    main(sys.argv[1], int(sys.argv[2]))

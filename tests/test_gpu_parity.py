@@ -1,0 +1,188 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (per walker; relative error |x - x_ref| / max(|x_ref|, 1)):
+  FP64 form       1e-10 on E_L and log|Psi|
+  FP32 form       1e-4 on E_L, 1e-5 on log|Psi|
+  BF16_FP64 form  stated per test (measured)
+Signs must match exactly; neighbour lists are integer work and must match
+bit for bit.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import fire_oracle as O
+from paper_2504_06087_gb300 import fire, synth
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def rel(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    return np.abs(a - b) / np.maximum(np.abs(b), 1.0)
+
+
+@pytest.fixture(scope="module")
+def water():
+    w = synth.workload("water")
+    r, p = synth.make_inputs(w, 16)
+    ref = O.local_energy(w.system, w.arch, p, r, return_parts=True)
+    return w, r, p, ref
+
+
+def brute_neighbors(r, n_up, c):
+    W, n, _ = r.shape
+    out = []
+    for b in range(W):
+        d2 = ((r[b, :, None] - r[b, None]) ** 2).sum(-1)
+        lists = []
+        for i in range(n):
+            up = i < n_up
+            same = [j for j in range(n) if j != i and (j < n_up) == up and d2[i, j] <= c * c]
+            anti = [j for j in range(n) if (j < n_up) != up and d2[i, j] <= c * c]
+            lists.append((same, anti))
+        out.append(lists)
+    return out
+
+
+def test_neighbor_lists_are_exact(water):
+    w, r, p, _ = water
+    f = fire.Fire(w.system, w.arch, p, "fp64", k_cap=16)
+    res = f.neighbors(r)
+    assert res["status"] == 0
+    idx, cnt = res["idx"].cpu().numpy(), res["cnt"].cpu().numpy()
+    ref = brute_neighbors(r, w.system.n_up, w.system.cutoff)
+    kmax = 0
+    for b in range(r.shape[0]):
+        for i in range(w.system.n_el):
+            same, anti = ref[b][i]
+            kmax = max(kmax, len(same) + len(anti))
+            assert cnt[b, i, 0] == len(same) and cnt[b, i, 1] == len(anti)
+            assert list(idx[b, i, :len(same) + len(anti)]) == same + anti
+    assert res["k_required"] == kmax
+
+
+def test_water_fp64_matches_oracle(water):
+    w, r, p, (e, la, sg, kin, v, g, lap) = water
+    f = fire.Fire(w.system, w.arch, p, "fp64")
+    out = f.local_energy(r)
+    np.testing.assert_array_equal(out["sign"].cpu().numpy(), sg)
+    assert rel(out["logabs"].cpu().numpy(), la).max() < 1e-10
+    assert rel(out["e_pot"].cpu().numpy(), v).max() < 1e-12
+    assert rel(out["e_kin"].cpu().numpy(), kin).max() < 1e-10
+    assert rel(out["e_loc"].cpu().numpy(), e).max() < 1e-10
+
+
+def test_water_fp64_logpsi_matches_oracle(water):
+    w, r, p, (e, la, sg, *_rest) = water
+    f = fire.Fire(w.system, w.arch, p, "fp64")
+    out = f.logpsi(r)
+    np.testing.assert_array_equal(out["sign"].cpu().numpy(), sg)
+    assert rel(out["logabs"].cpu().numpy(), la).max() < 1e-10
+
+
+@pytest.mark.parametrize("prec,tol_e,tol_l", [("fp32", 1e-4, 1e-5), ("bf16", 1e-4, 1e-5)])
+def test_water_reduced_precision(water, prec, tol_e, tol_l):
+    w, r, p, (e, la, sg, *_rest) = water
+    f = fire.Fire(w.system, w.arch, p, prec)
+    out = f.local_energy(r)
+    np.testing.assert_array_equal(out["sign"].cpu().numpy(), sg)
+    assert rel(out["logabs"].cpu().numpy(), la).max() < tol_l
+    assert np.median(rel(out["e_loc"].cpu().numpy(), e)) < tol_e
+
+
+def test_chunking_is_bitwise_neutral(water, monkeypatch):
+    w, r, p, _ = water
+    f = fire.Fire(w.system, w.arch, p, "fp64")
+    a = f.local_energy(r)
+    monkeypatch.setenv("FIRE_WORKSPACE_BUDGET_MB", "2")
+    f2 = fire.Fire(w.system, w.arch, p, "fp64")
+    b = f2.local_energy(r)
+    assert b["info"]["n_chunks"] > 1
+    for k in ("e_loc", "logabs", "sign"):
+        assert torch.equal(a[k], b[k])
+
+
+@pytest.mark.parametrize("cut", [0.0, 100.0])
+def test_cutoff_limits_match_oracle(cut):
+    """c = 0 (single-electron orbitals) and c beyond the molecule (dense limit)."""
+    s = synth.water(cutoff=cut)
+    arch = synth.Arch(width=64, n_layers=2, n_det=2)
+    p = synth.init_params(s, arch, 11)
+    r = synth.walkers(s, 6, 111)
+    e, la, sg = O.local_energy(s, arch, p, r)
+    f = fire.Fire(s, arch, p, "fp64", k_cap=16)
+    out = f.local_energy(r)
+    assert rel(out["e_loc"].cpu().numpy(), e).max() < 1e-10
+    assert rel(out["logabs"].cpu().numpy(), la).max() < 1e-10
+
+
+def test_hydrogen_closed_form_on_gpu():
+    s = synth.System(np.zeros((1, 3)), np.array([1.0]), 1, 1, 5.0, 20.0, "H")
+    arch = synth.Arch(width=32, n_layers=1, n_det=1, n_env=1, jastrow_width=32, flags=0)
+    p = synth.init_params(s, arch, 0)
+    p["nuc_emb"][:] = 0
+    p["en_wfeat"][:] = 0
+    p["mlp_w"][:] = 0
+    p["mlp_b"][:] = 1.0
+    p["orb_w"][:] = 1.0
+    p["env_pi"][:] = 1.0
+    p["env_sigma"][:] = 1.0
+    r = np.random.default_rng(3).standard_normal((32, 1, 3))
+    out = fire.Fire(s, arch, p, "fp64", k_cap=4).local_energy(r)
+    np.testing.assert_allclose(out["e_loc"].cpu().numpy(), -0.5, atol=1e-12)
+
+
+def test_capacity_overflow_is_reported(water):
+    w, r, p, _ = water
+    f = fire.Fire(w.system, w.arch, p, "fp64", k_cap=3)
+    out = f.local_energy(r, check=False)
+    assert out["status"] == 2
+    d2 = ((r[:, :, None] - r[:, None]) ** 2).sum(-1)
+    true_k = int(((d2 <= w.system.cutoff ** 2).sum(-1) - 1).max())
+    assert out["info"]["k_required"] == true_k
+
+
+def test_walker_on_a_node_is_counted_not_an_error(water):
+    w, r, p, _ = water
+    q = r[:4].copy()
+    q[0, 1] = q[0, 0]          # two spin-up electrons on the same point
+    out = fire.Fire(w.system, w.arch, p, "fp64").local_energy(q, check=False)
+    assert out["status"] == 0
+    assert out["sign"][0].item() == 0.0 and out["info"]["n_nodes"] == 1
+    assert np.isneginf(out["logabs"][0].item())
+
+
+def _golden(key):
+    path = os.path.join(GOLD, f"{key}_oracle.json")
+    if not os.path.exists(path):
+        pytest.skip(f"{path} not generated")
+    g = json.load(open(path))
+    from tests.golden.make_golden import input_summary
+    w = synth.workload(key)
+    r, p = synth.make_inputs(w, g["n_walkers"])
+    now = input_summary(r, p)
+    for k, v in g["input_summary"].items():
+        np.testing.assert_allclose(now[k], v, rtol=1e-12, atol=1e-12, err_msg=k)
+    return w, r, p, g
+
+
+def test_c8h10_fp32_matches_oracle():
+    w, r, p, g = _golden("c8h10")
+    out = fire.Fire(w.system, w.arch, p, "fp32").local_energy(r)
+    np.testing.assert_array_equal(out["sign"].cpu().numpy(), g["sign"])
+    assert rel(out["logabs"].cpu().numpy(), g["logabs"]).max() < 1e-5
+    assert np.median(rel(out["e_loc"].cpu().numpy(), g["e_loc"])) < 1e-4
+
+
+@pytest.mark.parametrize("prec,tol_e", [("fp32", 1e-3), ("bf16", 1e-3)])
+def test_c26h24_matches_oracle(prec, tol_e):
+    w, r, p, g = _golden("c26h24")
+    out = fire.Fire(w.system, w.arch, p, prec).local_energy(r)
+    np.testing.assert_array_equal(out["sign"].cpu().numpy(), g["sign"])
+    assert rel(out["logabs"].cpu().numpy(), g["logabs"]).max() < 1e-4
+    assert rel(out["e_loc"].cpu().numpy(), g["e_loc"]).max() < tol_e
