@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Throughput of batched FiRE local-energy evaluation on GB300.
+
+Metric: walker local-energy evaluations per second at n_el = 180 (zigzag
+C26H24, 90 up / 90 down, 4096 walkers per GPU, width 256, 4 MLP layers,
+16 determinants, c = 5 bohr), BF16+FP64 form, compared with the plain FP32
+form at the E_L errors each shows against the FP64 oracle.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+One step = one fire_local_energy call over all walkers of the GPU (neighbour
+lists included).  Inputs are resident in HBM for `value`; `e2e` adds the
+pinned host->device copy of the positions and the device->host copy of E_L.
+L2 is flushed (256 MB write) before every timed step.  With torchrun, every
+rank evaluates its own 4096 walkers (weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+METRIC = "walker local-energy evals/sec at n_el=180 (BF16+FP64 vs plain FP32, same E_L error)"
+UNIT = "walkers/s"
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return json.load(open(path)), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work per stage (for the roofline of the dominant kernel)
+# ---------------------------------------------------------------------------
+
+def stage_work(stage, w, info, n_walkers, nbr_sq_sum):
+    """(flops_total, bytes_total, bound) of one call's stage, from the shapes.
+
+    rows = forward-Laplacian rows of the call (value + Laplacian + 3 tangent
+    rows per slot of every electron block)."""
+    a, s = w.arch, w.system
+    d, J, n, D, L = a.width, a.jw, s.n_el, a.n_det, a.n_layers
+    rows = info["rows_total"]
+    if stage == "mlp_gemm":
+        return 2.0 * rows * d * d * L, None, "tensor"
+    if stage == "orb_gemm":
+        return 2.0 * rows * d * n * D, None, "tensor"
+    if stage == "jastrow_mlp":
+        return 2.0 * 2 * rows * (d * J + J * J + J), None, "tensor"
+    if stage == "att_gemm":
+        return 2.0 * rows * d * (a.n_reg + a.n_reg * a.d_reg), None, "tensor"
+    if stage == "contract":
+        # M_ik,nx for i, k in Nbar_n: 3 |Nbar_n|^2 n MACs per (walker, n, det)
+        return 2.0 * 3 * nbr_sq_sum * n * D, None, "alu"
+    if stage == "lu":
+        return (2.0 / 3.0) * n ** 3 * D * n_walkers, None, "fp64"
+    if stage == "inverse":
+        return 2.0 * n ** 3 * D * n_walkers, None, "alu"
+    return None, None, None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fire", choices=["fire", "reference"])
+    ap.add_argument("--walkers", type=int, default=4096)
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "fp64"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP32 comparison leg")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-coords", type=int, default=8,
+                    help="second-derivative passes in one oracle sample (of 3 n_el)")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = world > 1
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+
+    from paper_2504_06087_gb300 import fire, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if dist:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=dev)
+
+    w = synth.workload("c26h24", args.walkers)
+    r_np, p = synth.make_inputs(w, args.walkers)
+    k_cap = 64
+    f = fire.Fire(w.system, w.arch, p, args.precision, k_cap=k_cap, device=str(dev))
+    r = torch.as_tensor(r_np, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist:
+            tdist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # warm-up
+    for _ in range(max(args.warmup, 0)):
+        out = f.local_energy(r)
+    torch.cuda.synchronize(dev)
+
+    # timed region: device-resident inputs
+    sampler = ClockSampler(local)
+    sampler.start()
+    times = []
+    barrier()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = f.local_energy(r)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    barrier()
+    clocks = sampler.stop()
+    info = out["info"]
+    total_ms = float(sum(times))
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / max(args.steps, 1)
+    value = world * args.walkers * args.steps / (total_ms / 1e3)
+
+    # end to end through the public API: pinned host positions in, E_L out
+    r_host = torch.as_tensor(r_np).pin_memory()
+    e_host = torch.empty(args.walkers, dtype=torch.float64).pin_memory()
+    e2e_times = []
+    barrier()
+    for k in range(max(1, min(args.steps, 2))):
+        flush.fill_(float(k))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rd = r_host.to(dev, non_blocking=True)
+        o2 = f.local_energy(rd)
+        e_host.copy_(o2["e_loc"], non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_times.append(e0.elapsed_time(e1))
+    e2e_ms = float(np.mean(e2e_times))
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": world * args.walkers / (e2e_ms / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": int(r_host.numel() * 8), "d2h_bytes_per_step": int(e_host.numel() * 8)}
+
+    if rank != 0:
+        if dist:
+            tdist.barrier()
+            tdist.destroy_process_group()
+        return
+
+    # one profiled call: per-stage device time (CUDA events on the call's stream)
+    fire.profile(True)
+    outp = f.local_energy(r)
+    torch.cuda.synchronize(dev)
+    stages = fire.profile_report()
+    fire.profile(False)
+    nb = f.neighbors(r)
+    cnt = nb["cnt"].sum(-1).to(torch.float64)
+    nbr_sq_sum = float(((1.0 + cnt) ** 2).sum().item())
+    peaks, peak_src = load_peaks()
+    dom = max(stages.items(), key=lambda kv: kv[1][1])
+    dname, (dl, dms) = dom
+    flops, _, bound = stage_work(dname, w, info, args.walkers, nbr_sq_sum)
+    roof = {"kernel": dname, "share_of_step": dms / sum(v[1] for v in stages.values()), "launches": dl,
+            "traffic": None}
+    if flops is not None:
+        per_launch = flops / dl
+        achieved = per_launch / (dms / dl / 1e3) / 1e12
+        if bound == "tensor":
+            peak, pnote = peaks["bf16_tflops_sustained"], f"bf16 dense sustained, {peak_src}"
+            if args.precision != "bf16":
+                peak, pnote = 80.5, "FP32 SIMT, 152 SMs x 128 FMA/clk x 2070 MHz (derived)"
+        elif bound == "fp64":
+            peak, pnote = 1.25, "FP64 nominal 1.25 TFLOP/s (GB300 table)"
+        else:
+            peak, pnote = 80.5, "FP32 SIMT, 152 SMs x 128 FMA/clk x 2070 MHz (derived)"
+        roof.update({"bound": "tensor" if bound == "tensor" else "alu", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "peak_source": pnote,
+                     "flops_per_launch": per_launch, "ms_per_launch": dms / dl})
+    roof["stages_ms"] = {k: round(v[1], 3) for k, v in sorted(stages.items(), key=lambda kv: -kv[1][1])}
+
+    # accuracy of this form and of plain FP32 against the stored FP64 oracle values
+    comparison = {}
+    gpath = os.path.join(ROOT, "tests", "golden", "c26h24_oracle.json")
+    forms = [args.precision] + ([] if args.no_compare or args.precision == "fp32" else ["fp32"])
+    if os.path.exists(gpath):
+        g = json.load(open(gpath))
+        rg, pg = synth.make_inputs(w, g["n_walkers"])
+        for prec in forms:
+            fo = fire.Fire(w.system, w.arch, pg, prec, k_cap=k_cap, device=str(dev))
+            oo = fo.local_energy(rg)
+            e = oo["e_loc"].cpu().numpy()
+            la = oo["logabs"].cpu().numpy()
+            ref = np.asarray(g["e_loc"])
+            comparison[prec] = {"e_loc_rel_err_max": float(np.max(np.abs(e - ref) / np.maximum(np.abs(ref), 1))),
+                                "logabs_rel_err_max": float(np.max(np.abs(la - np.asarray(g["logabs"])) /
+                                                                   np.maximum(np.abs(np.asarray(g["logabs"])), 1))),
+                                "oracle_walkers": g["n_walkers"]}
+    if not args.no_compare and args.precision != "fp32":
+        f32 = fire.Fire(w.system, w.arch, p, "fp32", k_cap=k_cap, device=str(dev))
+        f32.local_energy(r)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        flush.fill_(1.0)
+        e0.record(stream)
+        f32.local_energy(r)
+        e1.record(stream)
+        e1.synchronize()
+        comparison.setdefault("fp32", {})["value"] = args.walkers / (e0.elapsed_time(e1) / 1e3)
+        del f32
+    comparison.setdefault(args.precision, {})["value"] = value / world
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = oracle_baseline(w, args.oracle_coords)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"bf16": "bf16+f32+f64", "fp32": "f32", "fp64": "f64"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": f"zigzag C26H24, n_el=180 (90 up/90 down), {args.walkers} walkers per GPU, "
+                               "width 256, 4 MLP layers, 16 determinants, c=5 bohr, c_n=20 bohr, k_cap=64",
+                   "precision": {"bf16": "bf16_fp64", "fp32": "fp32", "fp64": "fp64"}[args.precision],
+                   "walkers_per_gpu": args.walkers, "l2": "flushed before every step (256 MB write)",
+                   "parallelism": f"replicas x{world} (walkers sharded, no collective)"},
+        "e2e": e2e, "gpu_launches": int(info["n_launches"]) * args.steps,
+        "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "comparison": comparison,
+        "diag": {"rows_total": info["rows_total"], "mean_neighbors": info["mean_neighbors"],
+                 "k_required": info["k_required"], "n_chunks": info["n_chunks"], "n_nodes": info["n_nodes"],
+                 "launches_per_step": info["n_launches"], "step_ms": times},
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        tdist.barrier()
+        tdist.destroy_process_group()
+
+
+def oracle_sample(w, r1, p, coords):
+    """One bounded sample of the oracle local energy on one walker: forward,
+    gradient and `coords` of the 3 n_el second-derivative passes of its
+    Laplacian.  Returns (seconds, seconds scaled to the full walker)."""
+    from oracle import fire_oracle as O
+    n = w.system.n_el
+    pt = O.params_to_torch(p)
+    t0 = time.perf_counter()
+    r = torch.as_tensor(r1).clone().requires_grad_(True)
+    la, _ = O.logpsi(w.system, w.arch, pt, r)
+    (g,) = torch.autograd.grad(la.sum(), r, create_graph=True)
+    t1 = time.perf_counter()
+    lap = 0.0
+    for q in range(coords):
+        i, x = q // 3, q % 3
+        (gg,) = torch.autograd.grad(g[:, i, x].sum(), r, retain_graph=True)
+        lap += float(gg[0, i, x])
+    with torch.no_grad():
+        O.potential(w.system, r.detach())
+    t2 = time.perf_counter()
+    full = (t1 - t0) + (t2 - t1) * (3 * n) / coords
+    return t2 - t0, full
+
+
+def oracle_baseline(w, coords):
+    from paper_2504_06087_gb300 import synth
+    torch.set_num_threads(os.cpu_count() or 1)
+    r1, p = synth.make_inputs(w, 1)
+    spent, full = oracle_sample(w, r1, p, coords)
+    return {"value": 1.0 / full, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"1 walker of the same workload: forward, gradient and {coords} of the {3 * w.system.n_el} "
+                      f"second-derivative passes of the FP64 dense oracle ({spent:.1f} s measured), time scaled "
+                      f"to the full Laplacian"}
+
+
+def reference_arm(args, rank, world):
+    """The oracle, as it stands, timed on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    from paper_2504_06087_gb300 import synth
+    torch.set_num_threads(os.cpu_count() or 1)
+    w = synth.workload("c26h24", args.walkers)
+    r1, p = synth.make_inputs(w, 1)
+    for _ in range(args.warmup):
+        oracle_sample(w, r1, p, args.oracle_coords)
+    tot = 0.0
+    for _ in range(args.steps):
+        tot += oracle_sample(w, r1, p, args.oracle_coords)[1]
+    value = args.steps / tot
+    cpu = {"value": value, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+           "sample": f"per step 1 walker: forward, gradient and {args.oracle_coords} of {3 * w.system.n_el} "
+                     f"second-derivative passes, scaled to the full Laplacian"}
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "zigzag C26H24, n_el=180 (90 up/90 down), width 256, 4 MLP layers, "
+                                   "16 determinants, c=5 bohr (FP64 dense CPU oracle)",
+                       "precision": "fp64"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -143,7 +143,23 @@ typedef struct {
   int32_t n_chunks;          /* walker chunks the call was split into          */
   int64_t rows_total;        /* forward-Laplacian rows processed (all chunks)   */
   double mean_neighbors;     /* mean |N_i| over all electrons and walkers       */
+  int64_t n_launches;        /* kernels launched by the call                    */
 } fire_info_t;
+
+/* Opt-in stage profiler (diagnostics).  While enabled, calls on this host
+ * thread bracket every pipeline stage with CUDA events on their stream and
+ * add the measured device time to a thread-local table; the stages are then
+ * serialised by the event waits, so profiled calls are slower.  Stage names
+ * are stable ("row_gemm", "contract", "lu", ...). */
+typedef struct {
+  char name[24];
+  int64_t launches;
+  double ms_total;
+} fire_prof_entry_t;
+
+int fire_profile_enable(int on);
+int fire_profile_reset(void);
+int fire_profile_report(fire_prof_entry_t* out, int32_t* n);
 
 /* Number of scalar parameters of the ansatz for this system and network. */
 int64_t fire_param_count(const fire_system_t* sys, const fire_arch_t* arch);
@@ -206,6 +222,15 @@ typedef struct {
 int fire_workspace_layout(const fire_system_t* sys, const fire_arch_t* arch, int64_t n_walkers,
                           int32_t precision, int32_t k_cap, int32_t op, fire_ws_entry_t* out,
                           int32_t* n, int64_t* chunk_walkers);
+
+/* Diagnostic: the tensor-core matrix product used by the BF16_FP64 form on
+ * its own.  C[M][N] (fp32, row-major) = A[M][K] (bf16, row-major) times the
+ * transpose of Bt[N][K] (bf16, row-major, i.e. B given K-major), with
+ * tcgen05.mma and FP32 accumulation; K a multiple of 64.  *err (device int,
+ * caller-zeroed) becomes non-zero if a bounded wait gave up.  The paper has
+ * no counterpart: this exists to test the kernel in isolation. */
+int fire_selftest_tc_gemm(int64_t M, int32_t N, int32_t K, const void* A, const void* Bt, float* C,
+                          int32_t* err, void* stream);
 
 const char* fire_status_string(int status);
 

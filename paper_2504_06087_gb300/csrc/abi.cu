@@ -109,12 +109,15 @@ static size_t layout(Plan& pl, int64_t Wc) {
   TAKE(X, cap * d * ts);
   const int64_t zw = d > J ? d : J;
   pl.zcol = 0;
-  pl.ycol = zw;
-  pl.sucol = zw + J;
-  int64_t ldb = zw + J + dm.R + RD;
+  pl.ycol = 0;
+  pl.sucol = zw;
+  int64_t ldb = zw + dm.R + RD;
   if (ldb < n) ldb = n;
   pl.ld_big = ldb;
   TAKE(big, cap * ldb * ts);
+  TAKE(Y, cap * J * ts);
+  const bool bf = dm.prec == FIRE_PREC_BF16_FP64;
+  if (bf) { TAKE(Xb, cap * d * 2); TAKE(Yb, cap * J * 2); } else { pl.Xb = pl.Yb = 0; }
   TAKE(F1, cap * ts);
   TAKE(F2, cap * ts);
   TAKE(Qf, nb * R5 * NE * ts);
@@ -136,8 +139,18 @@ static size_t layout(Plan& pl, int64_t Wc) {
   TAKE(VY, Wc * vstride * J * ts);
   TAKE(G1, Wc * vstride * ts);
   TAKE(G2, Wc * vstride * ts);
+  if (bf) {
+    int64_t e = 0;
+    pl.wb_mlp = e; e += (int64_t)dm.L * d * d;
+    pl.wb_jm1 = e; e += d * J + J * J;
+    pl.wb_jm2 = e; e += d * J + J * J;
+    pl.wb_att = e; e += (dm.R + RD) * d;
+    pl.wb_orb = e; e += 2 * D * n * d;
+    TAKE(wbf16, e * 2);
+  } else {
+    pl.wbf16 = 0;
+  }
 #undef TAKE
-  pl.wbf16 = 0;
   pl.total = o;
   return o;
 }
@@ -188,6 +201,27 @@ int make_plan(const fire_system_t* sys, const fire_arch_t* ar, int64_t W, int pr
 
 static thread_local char g_last_error[256];
 
+struct ProfRow { char name[24]; int64_t launches; double ms; };
+static thread_local ProfRow g_prof[64];
+static thread_local int g_nprof = 0;
+static thread_local bool g_prof_on = false;
+
+bool prof_enabled() { return g_prof_on; }
+
+void prof_add(const char* name, int launches, float ms) {
+  int k = 0;
+  for (; k < g_nprof; ++k)
+    if (strncmp(g_prof[k].name, name, sizeof(g_prof[k].name)) == 0) break;
+  if (k == g_nprof) {
+    if (g_nprof >= 64) return;
+    memset(&g_prof[k], 0, sizeof(ProfRow));
+    strncpy(g_prof[k].name, name, sizeof(g_prof[k].name) - 1);
+    ++g_nprof;
+  }
+  g_prof[k].launches += launches;
+  g_prof[k].ms += ms;
+}
+
 void set_last_error(const char* stage, const char* msg) {
   snprintf(g_last_error, sizeof(g_last_error), "%s: %s", stage, msg);
 }
@@ -199,6 +233,29 @@ using namespace fire;
 extern "C" {
 
 const char* fire_last_error(void) { return g_last_error; }
+
+int fire_profile_enable(int on) {
+  g_prof_on = on != 0;
+  return FIRE_OK;
+}
+
+int fire_profile_reset(void) {
+  g_nprof = 0;
+  return FIRE_OK;
+}
+
+int fire_profile_report(fire_prof_entry_t* out, int32_t* n) {
+  if (!n) return FIRE_ERR_INVALID_ARG;
+  *n = g_nprof;
+  if (!out) return FIRE_OK;
+  for (int k = 0; k < g_nprof; ++k) {
+    memset(&out[k], 0, sizeof(fire_prof_entry_t));
+    strncpy(out[k].name, g_prof[k].name, sizeof(out[k].name) - 1);
+    out[k].launches = g_prof[k].launches;
+    out[k].ms_total = g_prof[k].ms;
+  }
+  return FIRE_OK;
+}
 
 const char* fire_version(void) { return "libfire 0.1 (sm_103a)"; }
 
@@ -323,8 +380,9 @@ static int run_call(const fire_system_t* sys, const fire_arch_t* arch, const fir
   for (int k = 0; k < P_COUNT; ++k) { poff[k] = off; off += numel(t[k]); }
   DevStatus hs;
   memset(&hs, 0, sizeof(hs));
+  int64_t nl = 0;
   CallArgs a{sys, arch, params->theta, poff, W, r, e_loc, logabs, sign, e_kin, e_pot, ws,
-             (cudaStream_t)stream, &hs};
+             (cudaStream_t)stream, &hs, &nl};
   if (prec == FIRE_PREC_FP64) rc = run_fp64(pl, a);
   else if (prec == FIRE_PREC_FP32) rc = run_fp32(pl, a);
   else rc = run_bf16(pl, a);
@@ -334,9 +392,11 @@ static int run_call(const fire_system_t* sys, const fire_arch_t* arch, const fir
     info->n_nonfinite = hs.n_nonfinite;
     info->n_chunks = (int32_t)pl.nchunks;
     info->rows_total = hs.rows_total;
+    info->n_launches = nl;
     info->mean_neighbors = (double)hs.nbr_total / ((double)W * sys->n_el);
   }
   if (rc) return rc;
+  if (hs.tc_err) return FIRE_ERR_TIMEOUT;
   if (hs.overflow) return FIRE_ERR_CAPACITY;
   if (hs.n_nonfinite) return FIRE_ERR_NONFINITE;
   return FIRE_OK;

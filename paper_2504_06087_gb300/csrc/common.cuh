@@ -10,6 +10,7 @@
 // elementwise function f adds f''(x) * sum_k (d x / d t_k)^2 to the Laplacian.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -198,6 +199,8 @@ struct DevStatus {
   int32_t n_nonfinite;
   int64_t rows_total;
   int64_t nbr_total;
+  int32_t tc_err;       // bounded wait of a tensor-core kernel gave up
+  int32_t pad_;
 };
 
 __device__ __forceinline__ int block_index(int w, int i, int Wc, int n, int n_up) {

@@ -221,7 +221,7 @@ __global__ void msg_kernel(int Wc, int n, int n_up, int d, int K, const double* 
                            double cut, Params<W> p, const int32_t* __restrict__ idx,
                            const int32_t* __restrict__ cnt, const int64_t* __restrict__ blk_off,
                            const T* __restrict__ H0, const T* __restrict__ PQ, T* __restrict__ X,
-                           int deriv) {
+                           __nv_bfloat16* __restrict__ Xb, int deriv) {
   constexpr int H = kEdgeHidden, G = kGauss;
   __shared__ FL3<T> feat[H + G + 4];
   const int blk = blockIdx.x;
@@ -316,17 +316,24 @@ __global__ void msg_kernel(int Wc, int n, int n_up, int d, int K, const double* 
       for (int t = 0; t < 3; ++t) {
         const T si = f1 * zi[t], sj = f1 * zj[t];
         acc.t[t] += gam.t[t] * f + gam.v * si;
-        X[(xoff + 2 + 3 * (s + 1) + t) * d + c] = -gam.t[t] * f + gam.v * sj;
+        const T xt = -gam.t[t] * f + gam.v * sj;
+        X[(xoff + 2 + 3 * (s + 1) + t) * d + c] = xt;
+        if (Xb) Xb[(xoff + 2 + 3 * (s + 1) + t) * d + c] = __float2bfloat16_rn((float)xt);
         cross += gam.t[t] * (si - sj);
       }
       acc.l += T(2) * gam.l * f + T(2) * cross + gam.v * sl;
     }
   }
   X[xoff * d + c] = acc.v;
+  if (Xb) Xb[xoff * d + c] = __float2bfloat16_rn((float)acc.v);
   if (deriv) {
     X[(xoff + 1) * d + c] = acc.l;
+    if (Xb) Xb[(xoff + 1) * d + c] = __float2bfloat16_rn((float)acc.l);
 #pragma unroll
-    for (int t = 0; t < 3; ++t) X[(xoff + 2 + t) * d + c] = acc.t[t];
+    for (int t = 0; t < 3; ++t) {
+      X[(xoff + 2 + t) * d + c] = acc.t[t];
+      if (Xb) Xb[(xoff + 2 + t) * d + c] = __float2bfloat16_rn((float)acc.t[t]);
+    }
   }
 }
 
@@ -338,7 +345,8 @@ __global__ void msg_kernel(int Wc, int n, int n_up, int d, int K, const double* 
 template <typename T, typename W>
 __global__ void fl_act_kernel(int ncol, const int64_t* __restrict__ off, int64_t stride,
                               const T* __restrict__ Z, int64_t ldz, const W* bias,
-                              T* __restrict__ Y, int64_t ldy, int residual) {
+                              T* __restrict__ Y, int64_t ldy, int residual,
+                              __nv_bfloat16* __restrict__ Yb = nullptr) {
   const int b = blockIdx.x;
   int64_t r0, r1;
   if (off) { r0 = off[b]; r1 = off[b + 1]; }
@@ -350,17 +358,18 @@ __global__ void fl_act_kernel(int ncol, const int64_t* __restrict__ off, int64_t
     T f, f1, f2;
     silu3<T>(z, f, f1, f2);
     T sq = T(0);
+    auto put = [&](int64_t q, T v) {
+      T o = residual ? Y[q * ldy + c] + v : v;
+      Y[q * ldy + c] = o;
+      if (Yb) Yb[q * ldy + c] = __float2bfloat16_rn((float)o);
+    };
     for (int64_t q = r0 + 2; q < r1; ++q) {
       T zt = Z[q * ldz + c];
       sq += zt * zt;
-      T yt = f1 * zt;
-      if (residual) Y[q * ldy + c] += yt; else Y[q * ldy + c] = yt;
+      put(q, f1 * zt);
     }
-    if (nr > 1) {
-      T yl = f1 * Z[(r0 + 1) * ldz + c] + f2 * sq;
-      if (residual) Y[(r0 + 1) * ldy + c] += yl; else Y[(r0 + 1) * ldy + c] = yl;
-    }
-    if (residual) Y[r0 * ldy + c] += f; else Y[r0 * ldy + c] = f;
+    if (nr > 1) put(r0 + 1, f1 * Z[(r0 + 1) * ldz + c] + f2 * sq);
+    put(r0, f);
   }
 }
 

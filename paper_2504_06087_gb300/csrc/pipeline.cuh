@@ -14,6 +14,7 @@
 #include "jastrow.cuh"
 #include "nbr.cuh"
 #include "plan.h"
+#include "tc_api.h"
 
 namespace fire {
 
@@ -41,9 +42,12 @@ struct CallArgs {
   void* ws;
   cudaStream_t stream;
   DevStatus* host_status;    // filled after the call
+  int64_t* n_launches;       // kernels launched (host out)
 };
 
 void set_last_error(const char* stage, const char* msg);
+bool prof_enabled();
+void prof_add(const char* name, int launches, float ms);
 int run_fp64(const Plan& pl, const CallArgs& a);
 int run_fp32(const Plan& pl, const CallArgs& a);
 int run_bf16(const Plan& pl, const CallArgs& a);
@@ -90,6 +94,10 @@ struct Runner {
   Runner(const Plan& pl_, const CallArgs& a_) : pl(pl_), a(a_), dm(pl_.dm) {
     p = make_params<T>(a.theta, a.poff);
     dbg = getenv("FIRE_DEBUG_SYNC") != nullptr;
+    // FIRE_TC_MASK (diagnostic): bit 0 embedding MLP, 1 Jastrow MLPs,
+    // 2 attention, 3 orbitals -- which products may use the tensor cores.
+    if (const char* m = getenv("FIRE_TC_MASK")) tc_mask = atoi(m);
+    prof = prof_enabled();
     ws = reinterpret_cast<unsigned char*>(a.ws);
     s = a.stream;
   }
@@ -109,22 +117,63 @@ struct Runner {
     }
   }
 
-  // product over forward-Laplacian rows: tensor cores when available
-  void row_gemm(const T* A, int64_t lda, const T* B, int64_t ldb, T* C, int64_t ldc,
-                const int64_t* m_range, int64_t m_begin, int64_t m_end, int64_t m_cap, int N, int K) {
-    if (rg.tc && rg.tc(rg.ctx, s, A, lda, B, ldb, C, ldc, m_range, m_begin, m_end, m_cap, N, K)) return;
+  // Stage marks: the device time between two marks is attributed to the
+  // first one's name (profiler enabled); every mark adds its launch count.
+  bool prof = false;
+  int64_t launches = 0;
+  struct Mark { const char* name; cudaEvent_t ev; int nl; };
+  Mark marks[1024];
+  int nmarks = 0;
+  void mark(const char* name, int nl) {
+    launches += nl;
+    if (!prof || nmarks >= 1024) return;
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, s);
+    marks[nmarks++] = Mark{name, e, nl};
+  }
+  void flush_marks() {
+    if (!prof) return;
+    cudaStreamSynchronize(s);
+    for (int k = 0; k + 1 < nmarks; ++k) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, marks[k].ev, marks[k + 1].ev);
+      prof_add(marks[k].name, marks[k].nl, ms);
+    }
+    for (int k = 0; k < nmarks; ++k) cudaEventDestroy(marks[k].ev);
+    nmarks = 0;
+  }
+
+  // Product over forward-Laplacian rows.  With a bf16 copy Ab of A (row
+  // stride lda, a_rows rows allocated) and packed bf16 weights Bt [N][K] it
+  // runs on the tensor cores (BF16_FP64 form); otherwise SIMT in T.
+  int tc_rc = FIRE_OK;
+  int tc_mask = 0xF;
+  void row_gemm(const T* A, const __nv_bfloat16* Ab, int64_t lda, int64_t a_rows, const T* B,
+                const __nv_bfloat16* Bt, int64_t ldb, T* C, int64_t ldc, const int64_t* m_range,
+                int64_t m_begin, int64_t m_end, int64_t m_cap, int N, int K) {
+    if constexpr (sizeof(T) == 4) {
+      if (Ab && Bt && K % 64 == 0) {
+        int rc = tc::gemm_bf16(s, Ab, lda, a_rows, Bt, N, K, reinterpret_cast<float*>(C), ldc, m_begin, m_end,
+                               m_range, m_cap, &at<DevStatus>(pl.status)->tc_err);
+        if (rc == FIRE_OK) return;
+        tc_rc = rc;
+      }
+    }
     gemm<T>(s, A, lda, B, ldb, false, C, ldc, m_begin, m_end, m_range, m_cap, N, K);
   }
 
   // SiLU-MLP readout with two hidden layers over ragged blocks (rows of X
   // given by blk offsets or a fixed stride) -> per-row scalar F.
-  void mlp_readout(const T* Xin, int64_t ldx, int din, const int64_t* range, int64_t rb, int64_t re,
-                   int64_t cap, const int64_t* off, int64_t stride, int nblk, const T* w1, const T* b1,
-                   const T* w2, const T* b2, const T* w3, T* Z, int64_t ldz, T* Y, int64_t ldy, T* F) {
+  void mlp_readout(const T* Xin, const __nv_bfloat16* Xinb, int64_t ldx, int din, const int64_t* range,
+                   int64_t rb, int64_t re, int64_t cap, const int64_t* off, int64_t stride, int nblk,
+                   const T* w1, const __nv_bfloat16* w1b, const T* b1, const T* w2,
+                   const __nv_bfloat16* w2b, const T* b2, const T* w3, T* Z, int64_t ldz, T* Y,
+                   __nv_bfloat16* Yb, int64_t ldy, T* F) {
     const int J = dm.J;
-    row_gemm(Xin, ldx, w1, J, Z, ldz, range, rb, re, cap, J, din);
-    fl_act_kernel<T, T><<<nblk, 256, 0, s>>>(J, off, stride, Z, ldz, b1, Y, ldy, 0);
-    row_gemm(Y, ldy, w2, J, Z, ldz, range, rb, re, cap, J, J);
+    row_gemm(Xin, Xinb, ldx, cap, w1, w1b, J, Z, ldz, range, rb, re, cap, J, din);
+    fl_act_kernel<T, T><<<nblk, 256, 0, s>>>(J, off, stride, Z, ldz, b1, Y, ldy, 0, Yb);
+    row_gemm(Y, Yb, ldy, cap, w2, w2b, J, Z, ldz, range, rb, re, cap, J, J);
     fl_act_kernel<T, T><<<nblk, 256, 0, s>>>(J, off, stride, Z, ldz, b2, Y, ldy, 0);
     const int64_t nrows_grid = cap;
     rowdot_kernel<T, T><<<(unsigned)((nrows_grid + 7) / 8), 256, 0, s>>>(Y, ldy, J, w3, F, range, rb, re);
@@ -137,6 +186,35 @@ struct Runner {
     const int R5 = deriv ? 5 : 1;
     DevStatus* st = at<DevStatus>(pl.status);
     cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
+    if constexpr (sizeof(T) == 4) {
+      if (pl.wbf16) {
+        // bf16 K-major copies of the weights of every tensor-core product
+        mark("pack_weights", 0);
+        void* WBm = at<unsigned char>(pl.wbf16);
+        auto dst = [&](int64_t off) { return reinterpret_cast<__nv_bfloat16*>(WBm) + off; };
+        const int64_t d = dm.d, J = dm.J, n = dm.n, D = dm.D, R = dm.R, dr = dm.dr;
+        int np = 0;
+        for (int l = 0; l < dm.L; ++l, ++np)
+          tc::pack_bf16(s, reinterpret_cast<const float*>(p.mlp_w) + l * d * d, d, (int)d, (int)d, 1,
+                        dst(pl.wb_mlp + l * d * d));
+        const T* jw[2][2] = {{p.jm1_w1, p.jm1_w2}, {p.jm2_w1, p.jm2_w2}};
+        const int64_t jo[2] = {pl.wb_jm1, pl.wb_jm2};
+        for (int q = 0; q < 2; ++q) {
+          tc::pack_bf16(s, reinterpret_cast<const float*>(jw[q][0]), J, (int)d, (int)J, 1, dst(jo[q]));
+          tc::pack_bf16(s, reinterpret_cast<const float*>(jw[q][1]), J, (int)J, (int)J, 1, dst(jo[q] + d * J));
+          np += 2;
+        }
+        tc::pack_bf16(s, reinterpret_cast<const float*>(p.att_q), d, (int)d, (int)R, 0, dst(pl.wb_att));
+        for (int rr = 0; rr < R; ++rr, ++np)
+          tc::pack_bf16(s, reinterpret_cast<const float*>(p.att_wv) + rr * d * dr, dr, (int)d, (int)dr, 1,
+                        dst(pl.wb_att + (R + rr * dr) * d));
+        for (int sp = 0; sp < 2; ++sp)
+          for (int dd = 0; dd < D; ++dd, ++np)
+            tc::pack_bf16(s, reinterpret_cast<const float*>(p.orb_w) + (sp * D + dd) * d * n, n, (int)d, (int)n, 1,
+                          dst(pl.wb_orb + (sp * D + dd) * n * d));
+        launches += np + 1;
+      }
+    }
     for (int64_t ch = 0; ch < pl.nchunks; ++ch) {
       const int64_t w0 = ch * pl.Wc;
       const int wc = (int)((a.W - w0) < pl.Wc ? (a.W - w0) : pl.Wc);
@@ -150,6 +228,7 @@ struct Runner {
       int64_t* rng = at<int64_t>(pl.ranges);
       const double c = sys->cutoff;
       // 1. neighbour lists and the ragged row layout
+      mark("neighbors", 3);
       nbr_build_kernel<<<wc, 256, (size_t)n * 3 * sizeof(double), s>>>(wc, n, n_up, r, c * c, K, idx, cnt,
                                                                         brow, st, deriv);
       nbr_reverse_kernel<<<wc, 256, 0, s>>>(n, n_up, K, idx, cnt, rev);
@@ -170,7 +249,9 @@ struct Runner {
       T* H0 = at<T>(pl.H0);
       T* PQ = at<T>(pl.PQ);
       const int64_t r5 = (int64_t)nb * R5;
+      mark("en_filter", 1);
       en_filter_kernel<T, T><<<nb, d, 0, s>>>(wc, n, n_up, N, d, r, sys->nuc_pos, sys->cutoff_nuc, p, S5, R5);
+      mark("glu", 5);
       ln_fl_kernel<T, T><<<nb, d, 0, s>>>(d, S5, Y5, p.ln_gamma, p.ln_beta, R5);
       gemm<T>(s, Y5, d, p.glu_wg, d, false, Z5, 2 * d, 0, r5, nullptr, r5, d, d);
       gemm<T>(s, Y5, d, p.glu_wv, d, false, Z5 + d, 2 * d, 0, r5, nullptr, r5, d, d);
@@ -178,42 +259,65 @@ struct Runner {
       check("h0");
       gemm<T>(s, P5, d, p.glu_wo, d, false, H0, d, 0, r5, nullptr, r5, d, d);
       // 3. h^0 W^alpha_a, h^0 W^alpha_b for both spin channels
+      mark("msg_proj_gemm", 2);
       for (int part = 0; part < 2; ++part)
         gemm<T>(s, H0, d, p.msg_w + (int64_t)part * d * d, d, false, PQ + (int64_t)part * 2 * d, 4 * d, 0, r5,
                 nullptr, r5, d, d, 2, 0, (int64_t)(2 * d + 4) * d, d);
       // 4. message passing -> h^1 blocks
       T* X = at<T>(pl.X);
-      msg_kernel<T, T><<<nb, d, 0, s>>>(wc, n, n_up, d, K, r, c, p, idx, cnt, boff, H0, PQ, X, deriv);
+      T* Y = at<T>(pl.Y);
+      __nv_bfloat16* Xb = pl.Xb ? at<__nv_bfloat16>(pl.Xb) : nullptr;
+      __nv_bfloat16* Yb = pl.Yb ? at<__nv_bfloat16>(pl.Yb) : nullptr;
+      const __nv_bfloat16* WB = pl.wbf16 ? at<__nv_bfloat16>(pl.wbf16) : nullptr;
+      auto wbm = [&](int bit, int64_t off) -> const __nv_bfloat16* {
+        return (WB && (tc_mask >> bit & 1)) ? WB + off : nullptr;
+      };
+      mark("msg", 1);
+      msg_kernel<T, T><<<nb, d, 0, s>>>(wc, n, n_up, d, K, r, c, p, idx, cnt, boff, H0, PQ, X, Xb, deriv);
       check("msg");
       // 5. embedding MLP h = MLP(h^1): L residual SiLU layers
       T* big = at<T>(pl.big);
       T* Z = big + pl.zcol;
-      T* Y = big + pl.ycol;
       T* SU = big + pl.sucol;
       const int64_t ldb = pl.ld_big;
       for (int l = 0; l < dm.L; ++l) {
-        row_gemm(X, d, p.mlp_w + (int64_t)l * d * d, d, Z, ldb, fullr, 0, 0, cap, d, d);
-        fl_act_kernel<T, T><<<nb, 256, 0, s>>>(d, boff, 0, Z, ldb, p.mlp_b + (int64_t)l * d, X, d, 1);
+        mark("mlp_gemm", 1);
+        row_gemm(X, Xb, d, cap, p.mlp_w + (int64_t)l * d * d, wbm(0, pl.wb_mlp + (int64_t)l * d * d), d, Z, ldb,
+                 fullr, 0, 0, cap, d, d);
+        mark("fl_act", 1);
+        fl_act_kernel<T, T><<<nb, 256, 0, s>>>(d, boff, 0, Z, ldb, p.mlp_b + (int64_t)l * d, X, d, 1, Xb);
       }
       // 6. Jastrow factors
       T* jval = at<T>(pl.jval); T* jsign = at<T>(pl.jsign); T* jgrad = at<T>(pl.jgrad); T* jlap = at<T>(pl.jlap);
       T* aval = at<T>(pl.aval); T* asign = at<T>(pl.asign); T* agrad = at<T>(pl.agrad); T* alap = at<T>(pl.alap);
       T* cval = at<T>(pl.cval); T* cgrad = at<T>(pl.cgrad); T* clap = at<T>(pl.clap); T* vpot = at<T>(pl.vpot);
       if (dm.flags & FIRE_J_MLP) {
+        mark("jastrow_mlp", 10);
         T* F1 = at<T>(pl.F1);
         T* F2 = at<T>(pl.F2);
-        mlp_readout(X, d, d, fullr, 0, 0, cap, boff, 0, nb, p.jm1_w1, p.jm1_b1, p.jm1_w2, p.jm1_b2, p.jm1_w3,
-                    Z, ldb, Y, ldb, F1);
-        mlp_readout(X, d, d, fullr, 0, 0, cap, boff, 0, nb, p.jm2_w1, p.jm2_b1, p.jm2_w2, p.jm2_b2, p.jm2_w3,
-                    Z, ldb, Y, ldb, F2);
+        const int64_t JJ = (int64_t)dm.J;
+        mlp_readout(X, Xb, d, d, fullr, 0, 0, cap, boff, 0, nb, p.jm1_w1, wbm(1, pl.wb_jm1), p.jm1_b1, p.jm1_w2,
+                    wbm(1, pl.wb_jm1 + d * JJ), p.jm1_b2, p.jm1_w3, Z, ldb, Y, Yb, JJ, F1);
+        mlp_readout(X, Xb, d, d, fullr, 0, 0, cap, boff, 0, nb, p.jm2_w1, wbm(1, pl.wb_jm2), p.jm2_b1, p.jm2_w2,
+                    wbm(1, pl.wb_jm2 + d * JJ), p.jm2_b2, p.jm2_w3, Z, ldb, Y, Yb, JJ, F2);
+        mark("jastrow_reduce", 1);
         jmlp_reduce_kernel<T, T><<<wc, 256, 0, s>>>(wc, n, n_up, K, idx, cnt, rev, boff, F1, F2, p.jm1_b3,
                                                     p.jm2_b3, jval, jsign, jgrad, jlap, deriv);
       check("jmlp");
       }
       if (dm.flags & FIRE_J_ATT) {
         const int R = dm.R, dr = dm.dr, RD = R * dr;
-        gemm<T>(s, X, d, p.att_q, d, true, SU, ldb, 0, 0, fullr, cap, R, d);
-        gemm<T>(s, X, d, p.att_wv, dr, false, SU + R, ldb, 0, 0, fullr, cap, dr, d, R, 0, (int64_t)d * dr, dr);
+        mark("att_gemm", 2);
+        bool att_tc = false;
+        if constexpr (sizeof(T) == 4) {
+          if (Xb && WB && d % 64 == 0 && (tc_mask & 4))
+            att_tc = tc::gemm_bf16(s, Xb, d, cap, WB + pl.wb_att, R + RD, d, reinterpret_cast<float*>(SU), ldb, 0, 0,
+                                   fullr, cap, &st->tc_err) == FIRE_OK;
+        }
+        if (!att_tc) {
+          gemm<T>(s, X, d, p.att_q, d, true, SU, ldb, 0, 0, fullr, cap, R, d);
+          gemm<T>(s, X, d, p.att_wv, dr, false, SU + R, ldb, 0, 0, fullr, cap, dr, d, R, 0, (int64_t)d * dr, dr);
+        }
         T* V = at<T>(pl.V);
         T* VZ = at<T>(pl.VZ);
         T* VY = at<T>(pl.VY);
@@ -221,16 +325,19 @@ struct Runner {
         T* G2 = at<T>(pl.G2);
         const size_t apsm = (size_t)(R + n * R) * sizeof(T);
         const int bt = ((RD + 31) / 32) * 32;
+        mark("att_pool", 1);
         att_pool_kernel<T><<<wc, bt, apsm, s>>>(wc, n, n_up, K, R, dr, idx, cnt, rev, boff, SU, ldb, V, deriv);
         const int64_t vstride = deriv ? (2 + 3 * (int64_t)n) : 1;
         const int64_t vrows = (int64_t)wc * vstride;
-        mlp_readout(V, RD, RD, nullptr, 0, vrows, vrows, nullptr, vstride, wc, p.ja1_w1, p.ja1_b1, p.ja1_w2,
-                    p.ja1_b2, p.ja1_w3, VZ, dm.J, VY, dm.J, G1);
-        mlp_readout(V, RD, RD, nullptr, 0, vrows, vrows, nullptr, vstride, wc, p.ja2_w1, p.ja2_b1, p.ja2_w2,
-                    p.ja2_b2, p.ja2_w3, VZ, dm.J, VY, dm.J, G2);
+        mark("att_mlp", 11);
+        mlp_readout(V, nullptr, RD, RD, nullptr, 0, vrows, vrows, nullptr, vstride, wc, p.ja1_w1, nullptr,
+                    p.ja1_b1, p.ja1_w2, nullptr, p.ja1_b2, p.ja1_w3, VZ, dm.J, VY, nullptr, dm.J, G1);
+        mlp_readout(V, nullptr, RD, RD, nullptr, 0, vrows, vrows, nullptr, vstride, wc, p.ja2_w1, nullptr,
+                    p.ja2_b1, p.ja2_w2, nullptr, p.ja2_b2, p.ja2_w3, VZ, dm.J, VY, nullptr, dm.J, G2);
         att_reduce_kernel<T, T><<<wc, 256, 0, s>>>(n, G1, G2, p.ja1_b3, p.ja2_b3, aval, asign, agrad, alap, deriv);
       check("att");
       }
+      mark("coulomb_cusp", 1);
       coulomb_cusp_kernel<T, T><<<wc, 256, 0, s>>>(n, n_up, N, r, sys->nuc_pos, sys->nuc_charge, p.cusp, vpot,
                                                    cval, cgrad, clap, deriv);
       // 7. envelopes and orbital values
@@ -238,6 +345,7 @@ struct Runner {
       const int64_t Dn = (int64_t)D * n;
       T* Qf = at<T>(pl.Qf);
       T* Fenv = at<T>(pl.Fenv);
+      mark("envelope", 3);
       env_feat_kernel<T, T><<<nb, 128, 0, s>>>(wc, n, n_up, N, E, r, sys->nuc_pos, p.env_sigma, Qf, R5);
       const int64_t up5 = (int64_t)wc * n_up * R5;
       for (int sp = 0; sp < 2; ++sp) {
@@ -248,6 +356,7 @@ struct Runner {
       }
       T* Hv = at<T>(pl.Hv);
       T* Ov = at<T>(pl.Ov);
+      mark("orb_values", 4);
       gather_value_rows_kernel<T><<<nb, 256, 0, s>>>(nb, d, boff, X, Hv);
       const int64_t upv = (int64_t)wc * n_up;
       for (int sp = 0; sp < 2; ++sp) {
@@ -262,6 +371,7 @@ struct Runner {
       double* lsign = at<double>(pl.lsign);
       phi_assemble_kernel<T, LT><<<wc * D, 256, 0, s>>>(wc, n, n_up, D, Ov, Fenv, R5, LUb);
       const size_t lusm = (size_t)2 * n * 16 * sizeof(LT);
+      mark("lu", 1);
       lu_kernel<LT, 16><<<wc * D, 256, lusm, s>>>(n, LUb, piv, ldabs, lsign);
       check("lu");
       T* gdet = at<T>(pl.gdet);
@@ -269,6 +379,7 @@ struct Runner {
       if (deriv) {
         T* Ainv = at<T>(pl.Ainv);
         const size_t invsm = (size_t)n * n * sizeof(T) + 2 * n * sizeof(int);
+        mark("inverse", 1);
         lu_inverse_kernel<LT, T><<<wc * D, 256, invsm, s>>>(n, LUb, piv, Ainv);
       check("inverse");
         // 8. log-det gradient and Laplacian, determinant by determinant
@@ -276,8 +387,11 @@ struct Runner {
         const int mcap = 1 + K;
         const size_t ctsm = (size_t)(4 * mcap) * (n + 1) * sizeof(T) + 2 * mcap * sizeof(int);
         for (int dd = 0; dd < D; ++dd) {
+          mark("orb_gemm", 2);
           for (int sp = 0; sp < 2; ++sp)
-            row_gemm(X, d, p.orb_w + ((int64_t)sp * D + dd) * d * n, n, O, n, rng + 2 * sp, 0, 0, cap, n, d);
+            row_gemm(X, Xb, d, cap, p.orb_w + ((int64_t)sp * D + dd) * d * n,
+                     wbm(3, pl.wb_orb + ((int64_t)sp * D + dd) * n * d), n, O, n, rng + 2 * sp, 0, 0, cap, n, d);
+          mark("contract", 1);
           contract_kernel<T><<<nb, 256, ctsm, s>>>(wc, n, n_up, K, dd, D, idx, cnt, rev, boff, O, Fenv, Ainv,
                                                    gdet, ldet, st);
       check("contract");
@@ -286,11 +400,16 @@ struct Runner {
       // 9. final combination
       FinalIn<T, RT> fi{ldabs, lsign, gdet, ldet, cval, cgrad, clap, jval, jsign, jgrad, jlap,
                         aval, asign, agrad, alap, vpot};
+      mark("final", 1);
       final_kernel<T, RT><<<wc, 256, 0, s>>>(n, D, dm.flags, fi, deriv, a.e_loc ? a.e_loc + w0 : nullptr,
                                              a.logabs + w0, a.sign + w0, a.e_kin ? a.e_kin + w0 : nullptr,
                                              a.e_pot ? a.e_pot + w0 : nullptr, st);
     }
+    mark("end", 0);
     check("final");
+    flush_marks();
+    if (a.n_launches) *a.n_launches = launches;
+    if (tc_rc != FIRE_OK) { set_last_error("tensor-core product", "setup failed; SIMT fallback used"); }
     if (failed) return FIRE_ERR_CUDA;
     {
       cudaError_t e = cudaGetLastError();

@@ -26,7 +26,9 @@ struct Plan {
   size_t tsz, lsz;         // element sizes of the compute and LU types
   size_t status, idx, cnt, rev, blk_rows, blk_off, ranges;
   size_t S5, Y5, Z5, P5, H0, PQ;
-  size_t X, big, F1, F2;   // big holds Z | Y | SU, and O (aliased) in the det phase
+  size_t X, big, F1, F2;   // big holds Z | SU, and O (aliased) in the det phase
+  size_t Y, Xb, Yb;        // Jastrow hidden rows; bf16 copies of X and Y (BF16 form)
+  int64_t wb_mlp, wb_jm1, wb_jm2, wb_att, wb_orb;   // element offsets inside wbf16
   size_t Qf, Fenv, Hv, Ov;
   size_t LU, piv, ldabs, lsign, Ainv, gdet, ldet;
   size_t jval, jsign, jgrad, jlap, aval, asign, agrad, alap, cval, cgrad, clap, vpot;

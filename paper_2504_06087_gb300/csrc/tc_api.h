@@ -1,0 +1,22 @@
+// Host API of the tensor-core matrix product (tc_gemm.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fire {
+namespace tc {
+
+// C[m][0..N) = A[m][0..K) * Bt[0..N)[0..K)^T for rows m in [begin, end)
+// (device range m_range or host m_begin/m_end); A bf16 with row stride lda
+// and a_rows rows allocated; Bt bf16 [N][K]; C fp32 with row stride ldc.
+// K must be a multiple of 64.  Timeouts of bounded waits set *err.
+int gemm_bf16(cudaStream_t s, const void* A, int64_t lda, int64_t a_rows, const void* Bt, int N, int K,
+              float* C, int64_t ldc, int64_t m_begin, int64_t m_end, const int64_t* m_range, int64_t m_cap,
+              int* err);
+
+// dst = bf16 K-major copy of a weight matrix (see pack_bf16_kernel).
+void pack_bf16(cudaStream_t s, const float* src, int64_t lds, int K, int N, int trans, void* dst);
+
+}  // namespace tc
+}  // namespace fire

@@ -1,0 +1,96 @@
+// Host side of the tensor-core matrix product: tensor maps, launch, weight
+// packing to bf16 K-major form, and a self-test entry point.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "../../include/fire.h"
+#include "tc_api.h"
+#include "tc_gemm.cuh"
+
+namespace fire {
+namespace tc {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// bf16 matrix [rows][cols] with row stride ld (elements), box box_rows x 64.
+static bool make_map(CUtensorMap* m, const void* base, uint64_t rows, uint64_t cols, uint64_t ld,
+                     uint32_t box_rows) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || ((ld * 2) & 15)) return false;
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, box_rows};
+  cuuint32_t es[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+constexpr int kStages = 4;
+
+static size_t smem_bytes(int BN) { return (size_t)kStages * (BM * BK * 2 + (size_t)BN * BK * 2) + 1024; }
+
+int gemm_bf16(cudaStream_t s, const void* A, int64_t lda, int64_t a_rows, const void* Bt, int N, int K,
+              float* C, int64_t ldc, int64_t m_begin, int64_t m_end, const int64_t* m_range, int64_t m_cap,
+              int* err) {
+  if (N < 1 || K < BK || K % BK || m_cap <= 0) return FIRE_ERR_UNSUPPORTED;
+  const int nt = (N + 255) / 256;
+  int BN = (N + nt - 1) / nt;
+  BN = (BN + 15) / 16 * 16;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, A, (uint64_t)a_rows, (uint64_t)K, (uint64_t)lda, BM)) return FIRE_ERR_CUDA;
+  if (!make_map(&mb, Bt, (uint64_t)N, (uint64_t)K, (uint64_t)K, (uint32_t)BN)) return FIRE_ERR_CUDA;
+  const size_t sm = smem_bytes(BN);
+  if (cudaFuncSetAttribute(tc_gemm_kernel<kStages>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+      cudaSuccess)
+    return FIRE_ERR_CUDA;
+  TcArgs g{C, ldc, m_begin, m_end, m_range, N, K, BN, err};
+  dim3 grid((unsigned)((m_cap + BM - 1) / BM), (unsigned)nt);
+  tc_gemm_kernel<kStages><<<grid, 128, sm, s>>>(ma, mb, g);
+  return cudaGetLastError() == cudaSuccess ? FIRE_OK : FIRE_ERR_CUDA;
+}
+
+// dst[n][k] = bf16(src[k * lds + n]) for a [K][N] source (trans = 1), or
+// dst[n][k] = bf16(src[n * lds + k]) for an [N][K] source (trans = 0).
+__global__ void pack_bf16_kernel(const float* __restrict__ src, int64_t lds, int K, int N, int trans,
+                                 __nv_bfloat16* __restrict__ dst) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)N * K) return;
+  const int nn = (int)(e / K), kk = (int)(e % K);
+  const float v = trans ? src[(int64_t)kk * lds + nn] : src[(int64_t)nn * lds + kk];
+  dst[e] = __float2bfloat16_rn(v);
+}
+
+void pack_bf16(cudaStream_t s, const float* src, int64_t lds, int K, int N, int trans, void* dst) {
+  const int64_t tot = (int64_t)N * K;
+  pack_bf16_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(src, lds, K, N, trans,
+                                                                 reinterpret_cast<__nv_bfloat16*>(dst));
+}
+
+}  // namespace tc
+}  // namespace fire
+
+extern "C" int fire_selftest_tc_gemm(int64_t M, int32_t N, int32_t K, const void* A, const void* Bt, float* C,
+                                     int32_t* err, void* stream) {
+  if (M < 1 || N < 1 || K < 64 || K % 64 || !A || !Bt || !C || !err) return FIRE_ERR_INVALID_ARG;
+  return fire::tc::gemm_bf16((cudaStream_t)stream, A, K, M, Bt, N, K, C, N, 0, M, nullptr, M, err);
+}

@@ -63,9 +63,14 @@ class WsEntry(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 16), ("offset", ctypes.c_int64), ("bytes", ctypes.c_int64)]
 
 
+class ProfEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int64), ("ms_total", ctypes.c_double)]
+
+
 class Info(ctypes.Structure):
     _fields_ = [("k_required", ctypes.c_int32), ("n_nodes", ctypes.c_int32), ("n_nonfinite", ctypes.c_int32),
-                ("n_chunks", ctypes.c_int32), ("rows_total", ctypes.c_int64), ("mean_neighbors", ctypes.c_double)]
+                ("n_chunks", ctypes.c_int32), ("rows_total", ctypes.c_int64), ("mean_neighbors", ctypes.c_double),
+                ("n_launches", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -81,11 +86,15 @@ SIGNATURES = {
     "fire_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "fire_last_error": (ctypes.c_char_p, []),
     "fire_param_count": (ctypes.c_int64, [P(System), P(Arch)]),
+    "fire_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+    "fire_profile_reset": (ctypes.c_int, []),
+    "fire_profile_report": (ctypes.c_int, [P(ProfEntry), P(ctypes.c_int32)]),
     "fire_param_layout": (ctypes.c_int, [P(System), P(Arch), P(ParamEntry), P(ctypes.c_int32)]),
     "fire_workspace_size": (ctypes.c_size_t, [P(System), P(Arch), ctypes.c_int64, ctypes.c_int32,
                                               ctypes.c_int32, ctypes.c_int32]),
     "fire_workspace_layout": (ctypes.c_int, [P(System), P(Arch), ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                              ctypes.c_int32, P(WsEntry), P(ctypes.c_int32), P(ctypes.c_int64)]),
+    "fire_selftest_tc_gemm": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, VP, VP, VP, VP, VP]),
     "fire_neighbors": (ctypes.c_int, [P(System), ctypes.c_int64, VP, ctypes.c_int32, VP, VP,
                                       P(ctypes.c_int32), VP, ctypes.c_size_t, VP]),
     "fire_logpsi": (ctypes.c_int, [P(System), P(Arch), P(Params), ctypes.c_int64, VP, ctypes.c_int32,
@@ -108,6 +117,38 @@ def lib():
             fn.argtypes = args
         _LIB = L
     return _LIB
+
+
+def profile(on: bool = True):
+    L = lib()
+    L.fire_profile_reset()
+    L.fire_profile_enable(1 if on else 0)
+
+
+def profile_report():
+    """{stage: (launches, total ms)} accumulated on this host thread."""
+    L = lib()
+    n = ctypes.c_int32(0)
+    L.fire_profile_report(None, ctypes.byref(n))
+    ents = (ProfEntry * max(n.value, 1))()
+    L.fire_profile_report(ents, ctypes.byref(n))
+    return {e.name.decode(): (int(e.launches), float(e.ms_total)) for e in ents[:n.value]}
+
+
+def tc_gemm_selftest(A: torch.Tensor, Bt: torch.Tensor) -> torch.Tensor:
+    """C = A @ Bt^T on the tensor cores (A [M,K], Bt [N,K] bf16 CUDA tensors)."""
+    M, K = A.shape
+    N = Bt.shape[0]
+    C = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    err = torch.zeros(1, dtype=torch.int32, device=A.device)
+    rc = lib().fire_selftest_tc_gemm(M, N, K, _ptr(A.contiguous()), _ptr(Bt.contiguous()), _ptr(C), _ptr(err),
+                                     ctypes.c_void_p(torch.cuda.current_stream(A.device).cuda_stream))
+    torch.cuda.synchronize(A.device)
+    if rc:
+        raise FireError(rc, "fire_selftest_tc_gemm")
+    if int(err.item()):
+        raise RuntimeError(f"tensor-core product: bounded wait gave up (code {int(err.item())})")
+    return C
 
 
 def _ptr(t: Optional[torch.Tensor]):
