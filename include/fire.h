@@ -232,6 +232,36 @@ int fire_workspace_layout(const fire_system_t* sys, const fire_arch_t* arch, int
 int fire_selftest_tc_gemm(int64_t M, int32_t N, int32_t K, const void* A, const void* Bt, float* C,
                           int32_t* err, void* stream);
 
+/* Size of the workspace that fire_local_energy_static() owns (32 MiB). */
+#define FIRE_STATIC_WORKSPACE_BYTES (32u * 1024u * 1024u)
+
+/* fire_local_energy() for callers that cannot allocate device memory (code
+ * that runs inside another runtime's memory pool or allocator hooks, plug-ins
+ * whose host application owns every device allocation, paths that must not
+ * allocate after set-up).  The paper has no counterpart: this is a deployment
+ * convenience.
+ *
+ * Arguments, outputs and errors are those of fire_local_energy() without the
+ * workspace: the call uses one static device array of
+ * FIRE_STATIC_WORKSPACE_BYTES, which every GPU that loads the library holds
+ * until the process exits.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *  - Problems whose workspace (fire_workspace_size() for
+ *    FIRE_OP_LOCAL_ENERGY) exceeds FIRE_STATIC_WORKSPACE_BYTES are rejected
+ *    with FIRE_ERR_WORKSPACE before any launch; fire_last_error() then
+ *    states the size needed.  (About 20 water-sized walkers in FP64.)
+ *  - The first call on a device looks up the array's device address on that
+ *    device (with it current); make that first call before any stream
+ *    capture.
+ *  - Every call on a device shares the one array, which keeps the previous
+ *    call's contents (the call clears what must start at zero): calls that
+ *    overlap on the GPU, on different streams or host threads, race. */
+int fire_local_energy_static(const fire_system_t* sys, const fire_arch_t* arch,
+                             const fire_params_t* params, int64_t n_walkers, const double* r,
+                             int32_t k_cap, int32_t precision, double* e_loc, double* logabs,
+                             double* sign, double* e_kin, double* e_pot, fire_info_t* info,
+                             void* stream);
+
 const char* fire_status_string(int status);
 
 /* Text of the last CUDA error seen by a call on this host thread, with the

@@ -101,7 +101,12 @@ SIGNATURES = {
                                    ctypes.c_int32, VP, VP, P(Info), VP, ctypes.c_size_t, VP]),
     "fire_local_energy": (ctypes.c_int, [P(System), P(Arch), P(Params), ctypes.c_int64, VP, ctypes.c_int32,
                                          ctypes.c_int32, VP, VP, VP, VP, VP, P(Info), VP, ctypes.c_size_t, VP]),
+    "fire_local_energy_static": (ctypes.c_int, [P(System), P(Arch), P(Params), ctypes.c_int64, VP,
+                                                ctypes.c_int32, ctypes.c_int32, VP, VP, VP, VP, VP, P(Info), VP]),
 }
+
+# Bytes of the library-owned workspace of fire_local_energy_static (include/fire.h).
+STATIC_WORKSPACE_BYTES = 32 * 1024 * 1024
 
 
 def lib():
@@ -261,6 +266,26 @@ class Fire:
         out["status"] = rc
         if check and rc not in (0,):
             raise FireError(rc, "fire_local_energy", out["info"])
+        return out
+
+    def local_energy_static(self, r, check: bool = True):
+        """fire_local_energy_static: the library's own static workspace, no
+        device allocation inside the call (the outputs here are torch tensors
+        allocated by this wrapper, as a caller would provide them)."""
+        r = self._r(r)
+        W = r.shape[0]
+        out = {k: torch.empty(W, dtype=torch.float64, device=self.device)
+               for k in ("e_loc", "logabs", "sign", "e_kin", "e_pot")}
+        info = Info()
+        rc = lib().fire_local_energy_static(ctypes.byref(self.sys_c), ctypes.byref(self.arch_c),
+                                            ctypes.byref(self.params_c), W, _ptr(r), self.k_cap, self.prec,
+                                            _ptr(out["e_loc"]), _ptr(out["logabs"]), _ptr(out["sign"]),
+                                            _ptr(out["e_kin"]), _ptr(out["e_pot"]), ctypes.byref(info),
+                                            self._stream())
+        out["info"] = info.as_dict()
+        out["status"] = rc
+        if check and rc != 0:
+            raise FireError(rc, "fire_local_energy_static", out["info"])
         return out
 
     def logpsi(self, r, check: bool = True):
