@@ -224,13 +224,16 @@ int fire_workspace_layout(const fire_system_t* sys, const fire_arch_t* arch, int
                           int32_t* n, int64_t* chunk_walkers);
 
 /* Diagnostic: the tensor-core matrix product used by the BF16_FP64 form on
- * its own.  C[M][N] (fp32, row-major) = A[M][K] (bf16, row-major) times the
- * transpose of Bt[N][K] (bf16, row-major, i.e. B given K-major), with
- * tcgen05.mma and FP32 accumulation; K a multiple of 64.  *err (device int,
- * caller-zeroed) becomes non-zero if a bounded wait gave up.  The paper has
- * no counterpart: this exists to test the kernel in isolation. */
-int fire_selftest_tc_gemm(int64_t M, int32_t N, int32_t K, const void* A, const void* Bt, float* C,
-                          int32_t* err, void* stream);
+ * its own.  C[M][N] (fp32, row-major) = A[M][K] times the transpose of
+ * Bt[N][K] (B given K-major), with tcgen05.mma and FP32 accumulation; K a
+ * multiple of 64.  A and Bt hold nc = 1, 2 or 3 bf16 components each
+ * ([nc][M][K] and [nc][N][K]; x = x0 + x1 + x2), multiplied as the
+ * split-bf16 product of Henry, Tang & Heinecke (2019): 1, 3 or 6 component
+ * products.  *err (device int, caller-zeroed) becomes non-zero if a bounded
+ * wait gave up.  The paper has no counterpart: this exists to test the kernel
+ * in isolation. */
+int fire_selftest_tc_gemm(int64_t M, int32_t N, int32_t K, int32_t nc, const void* A, const void* Bt,
+                          float* C, int32_t* err, void* stream);
 
 /* Size of the workspace that fire_local_energy_static() owns (32 MiB). */
 #define FIRE_STATIC_WORKSPACE_BYTES (32u * 1024u * 1024u)

@@ -117,18 +117,21 @@ static size_t layout(Plan& pl, int64_t Wc) {
   TAKE(big, cap * ldb * ts);
   TAKE(Y, cap * J * ts);
   const bool bf = dm.prec == FIRE_PREC_BF16_FP64;
-  if (bf) { TAKE(Xb, cap * d * 2); TAKE(Yb, cap * J * 2); } else { pl.Xb = pl.Yb = 0; }
+  if (bf) { TAKE(Xb, kMaxSplit * cap * d * 2); TAKE(Yb, kMaxSplit * cap * J * 2); } else { pl.Xb = pl.Yb = 0; }
   TAKE(F1, cap * ts);
   TAKE(F2, cap * ts);
   TAKE(Qf, nb * R5 * NE * ts);
   TAKE(Fenv, nb * R5 * D * n * ts);
-  TAKE(Hv, nb * d * ts);
-  TAKE(Ov, nb * D * n * ts);
+  // Hv / Ov also serve as value-row scratch of the tensor-core products
+  const int64_t wmax = (d > J ? d : J) > dm.R + RD ? (d > J ? d : J) : dm.R + RD;
+  TAKE(Hv, nb * (wmax > d ? wmax : d) * ts);
+  TAKE(Ov, nb * (D * n > wmax ? D * n : wmax) * ts);
   TAKE(LU, Wc * D * n * n * ls);
   TAKE(piv, Wc * D * n * 4);
   TAKE(ldabs, Wc * D * 8);
   TAKE(lsign, Wc * D * 8);
   if (dm.deriv) TAKE(Ainv, Wc * D * n * n * ts); else pl.Ainv = 0;
+  if (dm.deriv && ts == 4) TAKE(Phif, Wc * D * n * n * 4); else pl.Phif = 0;
   TAKE(gdet, Wc * D * n * 3 * ts);
   TAKE(ldet, Wc * D * n * ts);
   TAKE(jval, Wc * ts); TAKE(jsign, Wc * ts); TAKE(jlap, Wc * ts); TAKE(jgrad, Wc * n * 3 * ts);
@@ -140,12 +143,14 @@ static size_t layout(Plan& pl, int64_t Wc) {
   TAKE(G1, Wc * vstride * ts);
   TAKE(G2, Wc * vstride * ts);
   if (bf) {
+    // every weight block [N][K] is stored as kMaxSplit components [c][N][K]
+    const int64_t S = kMaxSplit;
     int64_t e = 0;
-    pl.wb_mlp = e; e += (int64_t)dm.L * d * d;
-    pl.wb_jm1 = e; e += d * J + J * J;
-    pl.wb_jm2 = e; e += d * J + J * J;
-    pl.wb_att = e; e += (dm.R + RD) * d;
-    pl.wb_orb = e; e += 2 * D * n * d;
+    pl.wb_mlp = e; e += S * (int64_t)dm.L * d * d;
+    pl.wb_jm1 = e; e += S * (d * J + J * J);
+    pl.wb_jm2 = e; e += S * (d * J + J * J);
+    pl.wb_att = e; e += S * (dm.R + RD) * d;
+    pl.wb_orb = e; e += S * 2 * D * n * d;
     TAKE(wbf16, e * 2);
   } else {
     pl.wbf16 = 0;
@@ -188,8 +193,8 @@ int make_plan(const fire_system_t* sys, const fire_arch_t* ar, int64_t W, int pr
   if (wc < 1) wc = 1;
   if (wc > W) wc = W;
   // shared-memory limits of the determinant kernels
-  const int n = dm.n, mcap = 1 + k_cap;
-  const size_t ctsm = (size_t)(4 * mcap) * (n + 1) * pl->tsz + 2 * mcap * sizeof(int);
+  const int n = dm.n, mcap = 1 + (k_cap < dm.n - 1 ? k_cap : dm.n - 1);
+  const size_t ctsm = (size_t)(4 * mcap) * 65 * pl->tsz + 2 * mcap * sizeof(int) + 2 * mcap * sizeof(int64_t) + 16;
   const size_t invsm = (size_t)n * n * pl->tsz + 2 * n * sizeof(int);
   const size_t lim = 227 * 1024;
   if (dm.deriv && (ctsm > lim || invsm > lim)) return FIRE_ERR_UNSUPPORTED;

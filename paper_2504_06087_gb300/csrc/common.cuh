@@ -203,6 +203,18 @@ struct DevStatus {
   int32_t pad_;
 };
 
+// Stores v as nc bf16 components (split-bf16: v ~ c0 + c1 + c2), cstride
+// elements apart.
+__device__ __forceinline__ void store_split_bf16(__nv_bfloat16* p, int64_t cstride, int nc, float v) {
+  for (int c = 0; c < nc; ++c) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    p[c * cstride] = h;
+    v -= __bfloat162float(h);
+  }
+}
+
+constexpr int kMaxSplit = 3;
+
 __device__ __forceinline__ int block_index(int w, int i, int Wc, int n, int n_up) {
   // spin-major block order: all spin-up electrons of the chunk first
   return (i < n_up) ? (w * n_up + i) : (Wc * n_up + w * (n - n_up) + (i - n_up));

@@ -44,14 +44,17 @@ __global__ void env_feat_kernel(int Wc, int n, int n_up, int N, int E, const dou
 // One CTA per (w, d).
 template <typename T, typename LT>
 __global__ void phi_assemble_kernel(int Wc, int n, int n_up, int D, const T* __restrict__ Ov,
-                                    const T* __restrict__ Fenv, int R5, LT* __restrict__ Phi) {
+                                    const T* __restrict__ Fenv, int R5, LT* __restrict__ Phi,
+                                    float* __restrict__ Phif) {
   const int w = blockIdx.x / D, dd = blockIdx.x % D;
   const int64_t Dn = (int64_t)D * n;
   LT* P = Phi + (int64_t)blockIdx.x * n * n;
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     const int i = e / n, l = e % n;
     const int64_t b = block_index(w, i, Wc, n, n_up);
-    P[e] = LT(Ov[b * Dn + dd * n + l]) * LT(Fenv[b * R5 * Dn + dd * n + l]);
+    const LT v = LT(Ov[b * Dn + dd * n + l]) * LT(Fenv[b * R5 * Dn + dd * n + l]);
+    P[e] = v;
+    if (Phif) Phif[(int64_t)blockIdx.x * n * n + e] = (float)v;
   }
 }
 
@@ -192,7 +195,8 @@ __global__ void lu_kernel(int n, LT* __restrict__ M, int32_t* __restrict__ piv,
 }
 
 // A = Phi^-1 from the LU factors: column j of A solves L U x = e_{pinv[j]}.
-// One CTA per matrix, one thread per column, x kept in shared memory.
+// One CTA per matrix, one thread per column, x kept in shared memory; the
+// result is written transposed (Ainv[k][l] = A[l][k]).
 template <typename LT, typename AT>
 __global__ void lu_inverse_kernel(int n, const LT* __restrict__ M, const int32_t* __restrict__ piv,
                                   AT* __restrict__ Ainv) {
@@ -226,113 +230,294 @@ __global__ void lu_inverse_kernel(int n, const LT* __restrict__ M, const int32_t
     }
   }
   __syncthreads();
+  // stored transposed: out[k][l] = A[l][k], so a column of A is one row
   AT* out = Ainv + (int64_t)blockIdx.x * n * n;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) out[e] = X[e];
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) out[e] = X[(int64_t)(e % n) * n + e / n];
 }
+
+// A = Phi^-1 by in-place Gauss-Jordan elimination with partial pivoting, in
+// float32, register-tiled: thread (tr, tc) of a G x G grid (G = ceil(n/8))
+// keeps the 8 x 8 block of rows 8tr.., columns 8tc.. in registers.  Step k
+// picks the unused row p with the largest |a_pk|, broadcasts row p and
+// column k through shared memory and updates every block:
+//   a_pj /= v (j != k), a_pk = 1/v;  a_ij -= a_ik a_pj / v, a_ik = -a_ik / v.
+// Rows are never moved: with piv[s] the row used at step s and step[r] its
+// inverse, the stored matrix S satisfies A^-1[r][piv[c]] = S[piv[r]][c].
+// The result is written transposed (AT[k][l] = A^-1[l][k]).  n <= 192.
+template <typename IT, typename OT>
+__global__ void __launch_bounds__(576, 1) gj_inverse_kernel(int n, const IT* __restrict__ Phi, OT* __restrict__ AT) {
+  extern __shared__ unsigned char gj_smem[];
+  float* S = reinterpret_cast<float*>(gj_smem);          // [n][n] final matrix
+  float* prow = S + (int64_t)n * n;                      // [Gp] pivot row
+  float* pcol = prow + 256;                              // [Gp] pivot column
+  int* piv = reinterpret_cast<int*>(pcol + 256);         // [n]
+  int* stp = piv + 256;                                  // [n]
+  int* used = stp + 256;                                 // [n]
+  float* cv = reinterpret_cast<float*>(used + 256);      // [32] candidate |a|
+  int* ci = reinterpret_cast<int*>(cv + 32);             // [32] candidate row
+  const int G = (n + 7) / 8;
+  const int tid = threadIdx.x;
+  const int tr = tid / G, tc = tid % G;
+  const bool live = tr < G;
+  const IT* P = Phi + (int64_t)blockIdx.x * n * n;
+  float a[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int r = 8 * tr + i, c = 8 * tc + j;
+      a[i][j] = (live && r < n && c < n) ? (float)P[(int64_t)r * n + c] : 0.f;
+    }
+  for (int r = tid; r < n; r += blockDim.x) used[r] = 0;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    const int kt = k / 8, kj = k % 8;
+    // candidates: the threads of column block kt, one per row block
+    if (live && tc == kt) {
+      float best = -1.f;
+      int bi = n;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int r = 8 * tr + i;
+        float v = -1.f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (j == kj) v = fabsf(a[i][j]);
+        if (r < n && !used[r] && v > best) { best = v; bi = r; }
+      }
+      cv[tr] = best;
+      ci[tr] = bi;
+    }
+    __syncthreads();
+    if (tid < 32) {
+      float best = -1.f;
+      int bi = n;
+      for (int q = tid; q < G; q += 32)
+        if (cv[q] > best || (cv[q] == best && ci[q] < bi)) { best = cv[q]; bi = ci[q]; }
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+      }
+      if (tid == 0) {
+        if (bi >= n) bi = 0;   // singular: any row, the result is not finite
+        piv[k] = bi;
+        stp[bi] = k;
+        used[bi] = 1;
+      }
+    }
+    __syncthreads();
+    const int p = piv[k];
+    const int pt = p / 8, pi = p % 8;
+    if (live && tr == pt)
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (i == pi)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) prow[8 * tc + j] = a[i][j];
+    if (live && tc == kt)
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (j == kj)
+#pragma unroll
+          for (int i = 0; i < 8; ++i) pcol[8 * tr + i] = a[i][j];
+    __syncthreads();
+    const float v = pcol[p];
+    const float iv = 1.f / v;
+    if (live) {
+      float sp[8], f[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) sp[j] = prow[8 * tc + j] * iv;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) f[i] = pcol[8 * tr + i];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const bool isp = (tr == pt) && (i == pi);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const bool isk = (tc == kt) && (j == kj);
+          float x;
+          if (isp) x = isk ? iv : sp[j];
+          else x = isk ? -f[i] * iv : fmaf(-f[i], sp[j], a[i][j]);
+          a[i][j] = x;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (live)
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int r = 8 * tr + i, c = 8 * tc + j;
+        if (r < n && c < n) S[r * n + c] = a[i][j];
+      }
+  __syncthreads();
+  // AT[k][l] = A^-1[l][k] = S[piv[l]][stp[k]]
+  OT* out = AT + (int64_t)blockIdx.x * n * n;
+  for (int e = tid; e < n * n; e += blockDim.x) {
+    const int kk = e / n, l = e % n;
+    out[e] = (OT)S[piv[l] * n + stp[kk]];
+  }
+}
+
+inline size_t gj_smem_bytes(int n) { return (size_t)n * n * 4 + 512 * 4 + 768 * 4 + 64 * 4; }
 
 // Gradient and Laplacian of log det Phi_d restricted to the neighbourhoods.
 // One CTA per (walker, tangent electron n').  O holds h W_d for every row of
 // the forward-Laplacian blocks ([rows][n]); Fenv the envelope rows
-// ([Wc*n*5][D*n]); Ainv the inverses ([Wc][D][n][n]).
+// ([Wc*n*5][D*n]); AT the transposed inverses (AT[k][l] = A[l][k],
+// [Wc][D][n][n]).
+//
+// With Nbar = {i_0 = n', i_1, ...} (m members) the CTA forms
+//   T[(k,x)][l] = d Phi_{i_k l} / d r_{n' x}      (3m rows)
+//   M[(k,x)][k'] = sum_l T[(k,x)][l] A[l][i_k']   (3m x m)
+// as a register-blocked product (3 x 4 outputs per thread) over chunks of
+// LC orbitals staged in shared memory, then
+//   d log det / d r_{n'x} = sum_k M[(k,x)][k]
+//   trace_{n'} = sum_x sum_{k,k'} M[(k,x)][k'] M[(k',x)][k].
 template <typename T>
-__global__ void contract_kernel(int Wc, int n, int n_up, int K, int dd, int D,
-                                const int32_t* __restrict__ idx, const int32_t* __restrict__ cnt,
-                                const int32_t* __restrict__ rev, const int64_t* __restrict__ blk_off,
-                                const T* __restrict__ O, const T* __restrict__ Fenv,
-                                const T* __restrict__ Ainv, T* __restrict__ gdet,
-                                T* __restrict__ ldet, DevStatus* st) {
+__global__ void __launch_bounds__(256)
+contract_kernel(int Wc, int n, int n_up, int K, int mcap, int dd, int D, const int32_t* __restrict__ idx,
+                const int32_t* __restrict__ cnt, const int32_t* __restrict__ rev,
+                const int64_t* __restrict__ blk_off, const T* __restrict__ O, const T* __restrict__ Fenv,
+                const T* __restrict__ AT, T* __restrict__ gdet, T* __restrict__ ldet, DevStatus* st) {
+  constexpr int LC = 64, LDC = LC + 1, MAXT = 5, NT = 256;
   extern __shared__ unsigned char ct_smem[];
-  const int ldn = n + 1;
-  const int mcap = 1 + K;
-  T* Tt = reinterpret_cast<T*>(ct_smem);            // [3*mcap][ldn]
-  T* As = Tt + (int64_t)3 * mcap * ldn;              // [mcap][ldn], As[k][l] = A[l][i_k]
-  int* mi = reinterpret_cast<int*>(As + (int64_t)mcap * ldn);
+  T* Tc = reinterpret_cast<T*>(ct_smem);              // [3*mcap][LDC]
+  T* Ac = Tc + (int64_t)3 * mcap * LDC;               // [mcap][LDC]
+  int64_t* ro = reinterpret_cast<int64_t*>(Ac + (int64_t)mcap * LDC);   // O row of (k, x = 0)
+  int64_t* fo = ro + mcap;                                              // Fenv value row of member k
+  int* mi = reinterpret_cast<int*>(fo + mcap);
   int* ms = mi + mcap;
   __shared__ T red[32];
+  const int tid = threadIdx.x;
   const int w = blockIdx.x / n, np = blockIdx.x % n;
   const int64_t Dn = (int64_t)D * n;
   const int64_t base = (int64_t)w * n + np;
-  const int m = 1 + cnt[base * 2] + cnt[base * 2 + 1];
-  for (int k = threadIdx.x; k < m; k += blockDim.x) {
+  int m = 1 + cnt[base * 2] + cnt[base * 2 + 1];
+  if (m > mcap) m = mcap;
+  for (int k = tid; k < m; k += NT) {
     if (k == 0) { mi[0] = np; ms[0] = 0; }
     else {
       mi[k] = idx[base * K + k - 1];
-      int rv = rev[base * K + k - 1];
-      ms[k] = rv + 1;
+      const int rv = rev[base * K + k - 1];
+      ms[k] = rv < 0 ? -1 : rv + 1;
       if (rv < 0) atomicExch(&st->overflow, 1);
     }
-  }
-  __syncthreads();
-  const T* Aw = Ainv + ((int64_t)w * D + dd) * n * n;
-  for (int e = threadIdx.x; e < m * n; e += blockDim.x) {
-    const int k = e / n, l = e % n;
-    As[(int64_t)k * ldn + l] = Aw[(int64_t)l * n + mi[k]];
-  }
-  for (int e = threadIdx.x; e < 3 * m * n; e += blockDim.x) {
-    const int row = e / n, l = e % n;
-    const int k = row / 3, x = row % 3;
-    const int i = mi[k];
+    const int i = k == 0 ? np : idx[base * K + k - 1];
     const int64_t b = block_index(w, i, Wc, n, n_up);
-    const int slot = ms[k] > 0 ? ms[k] : 0;
-    const int64_t orow = blk_off[b] + 2 + 3 * slot + x;
-    const T phi = Fenv[(b * 5) * Dn + dd * n + l];
-    T v = (ms[k] < 0 && k > 0) ? T(0) : O[orow * n + l] * phi;
-    if (k == 0) v += O[blk_off[b] * n + l] * Fenv[(b * 5 + 2 + x) * Dn + dd * n + l];
-    Tt[(int64_t)row * ldn + l] = v;
+    const int slot = k == 0 ? 0 : (ms[k] < 0 ? 0 : ms[k]);
+    ro[k] = (k > 0 && ms[k] < 0) ? -1 : (blk_off[b] + 2 + 3 * slot) * n;
+    fo[k] = b * 5 * Dn + (int64_t)dd * n;
   }
   __syncthreads();
-  T g0 = T(0), g1 = T(0), g2 = T(0), tr = T(0);
-  const int mm = m * m;
-  for (int e = threadIdx.x; e < 3 * mm; e += blockDim.x) {
-    const int x = e / mm, rem = e % mm;
+  const T* Aw = AT + ((int64_t)w * D + dd) * n * n;
+  const int bnp = block_index(w, np, Wc, n, n_up);
+  const int64_t onp = blk_off[bnp];
+  const int nq = (m + 3) / 4;
+  const int ntile = m * nq;
+  T g0 = T(0), g1 = T(0), g2 = T(0), tr = T(0), lt = T(0);
+  T* Ms = Tc;                                         // [3m][m], reuses the staging area
+  for (int tb = 0; tb < ntile; tb += NT * MAXT) {    // one pass for m <= 55
+    T acc[MAXT][12];
+#pragma unroll
+    for (int t = 0; t < MAXT; ++t)
+#pragma unroll
+      for (int q = 0; q < 12; ++q) acc[t][q] = T(0);
+    for (int l0 = 0; l0 < n; l0 += LC) {
+      const int lc = min(LC, n - l0);
+      __syncthreads();
+      for (int e = tid; e < m * lc; e += NT) {
+        const int k = e / lc, l = e % lc;
+        Ac[k * LDC + l] = Aw[(int64_t)mi[k] * n + l0 + l];
+      }
+      for (int e = tid; e < 3 * m * lc; e += NT) {
+        const int row = e / lc, l = e % lc;
+        const int k = row / 3, x = row - 3 * k;
+        const int64_t r0 = ro[k];
+        const T phi = Fenv[fo[k] + l0 + l];
+        T v = r0 >= 0 ? O[r0 + (int64_t)x * n + l0 + l] * phi : T(0);
+        if (k == 0) v += O[onp * n + l0 + l] * Fenv[fo[0] + (2 + x) * Dn + l0 + l];
+        Tc[row * LDC + l] = v;
+      }
+      // sum_l LapPhi_{n' l} A_{l n'} for this chunk (first pass only)
+      if (tb == 0)
+        for (int l = tid; l < lc; l += NT) {
+          const int64_t fc = dd * n + l0 + l;
+          const int64_t fb = (int64_t)bnp * 5 * Dn;
+          const T ov = O[onp * n + l0 + l], ol = O[(onp + 1) * n + l0 + l];
+          T cross = T(0);
+          for (int x = 0; x < 3; ++x) cross += O[(onp + 2 + x) * n + l0 + l] * Fenv[fb + (2 + x) * Dn + fc];
+          const T lap = ol * Fenv[fb + fc] + T(2) * cross + ov * Fenv[fb + Dn + fc];
+          lt += lap * Aw[(int64_t)np * n + l0 + l];
+        }
+      __syncthreads();
+#pragma unroll
+      for (int t = 0; t < MAXT; ++t) {
+        const int tile = tb + tid + t * NT;
+        if (tile < ntile) {
+          const int k = tile / nq, kq = tile % nq;
+          const T* t0 = Tc + (3 * k) * LDC;
+          const T* b0 = Ac + (4 * kq) * LDC;
+          const bool full = (4 * kq + 3) < m;
+          for (int l = 0; l < lc; ++l) {
+            const T a0 = t0[l], a1 = t0[LDC + l], a2 = t0[2 * LDC + l];
+            T bb[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bb[j] = (full || 4 * kq + j < m) ? b0[j * LDC + l] : T(0);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              acc[t][j] += a0 * bb[j];
+              acc[t][4 + j] += a1 * bb[j];
+              acc[t][8 + j] += a2 * bb[j];
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+    // M of this tile batch into shared memory
+#pragma unroll
+    for (int t = 0; t < MAXT; ++t) {
+      const int tile = tb + tid + t * NT;
+      if (tile < ntile) {
+        const int k = tile / nq, kq = tile % nq;
+#pragma unroll
+        for (int x = 0; x < 3; ++x)
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (4 * kq + j < m) Ms[(3 * k + x) * m + 4 * kq + j] = acc[t][4 * x + j];
+      }
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < 3 * m; e += NT) {
+    const int k = e / 3, x = e % 3;
+    const T v = Ms[(3 * k + x) * m + k];
+    if (x == 0) g0 += v; else if (x == 1) g1 += v; else g2 += v;
+  }
+  for (int e = tid; e < 3 * m * m; e += NT) {
+    const int x = e / (m * m), rem = e % (m * m);
     const int k = rem / m, kp = rem % m;
-    if (kp < k) continue;
-    const T* ta = Tt + (int64_t)(3 * k + x) * ldn;
-    const T* ab = As + (int64_t)kp * ldn;
-    T s1 = T(0);
-    for (int l = 0; l < n; ++l) s1 += ta[l] * ab[l];
-    if (k == kp) {
-      tr += s1 * s1;
-      if (x == 0) g0 += s1; else if (x == 1) g1 += s1; else g2 += s1;
-    } else {
-      const T* tb = Tt + (int64_t)(3 * kp + x) * ldn;
-      const T* aa = As + (int64_t)k * ldn;
-      T s2 = T(0);
-      for (int l = 0; l < n; ++l) s2 += tb[l] * aa[l];
-      tr += T(2) * s1 * s2;
-    }
+    tr += Ms[(3 * k + x) * m + kp] * Ms[(3 * kp + x) * m + k];
   }
-  // sum_l LapPhi_{n' l} A_{l n'}
-  T lt = T(0);
-  {
-    const int64_t b = block_index(w, np, Wc, n, n_up);
-    const int64_t o0 = blk_off[b];
-    for (int l = threadIdx.x; l < n; l += blockDim.x) {
-      const int64_t fc = dd * n + l;
-      const T ov = O[o0 * n + l], ol = O[(o0 + 1) * n + l];
-      const T fv = Fenv[(b * 5) * Dn + fc], fl = Fenv[(b * 5 + 1) * Dn + fc];
-      T cross = T(0);
-      for (int x = 0; x < 3; ++x) cross += O[(o0 + 2 + x) * n + l] * Fenv[(b * 5 + 2 + x) * Dn + fc];
-      const T lap = ol * fv + T(2) * cross + ov * fl;
-      lt += lap * As[l];
-    }
-  }
-  // block reductions
   auto bsum = [&](T v) -> T {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    if ((tid & 31) == 0) red[tid >> 5] = v;
     __syncthreads();
-    T s = T(0);
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[q];
-    return s;
+    T sm = T(0);
+    for (int q = 0; q < NT / 32; ++q) sm += red[q];
+    return sm;
   };
   g0 = bsum(g0);
   g1 = bsum(g1);
   g2 = bsum(g2);
   tr = bsum(tr);
   lt = bsum(lt);
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     T* gp = gdet + (((int64_t)w * D + dd) * n + np) * 3;
     gp[0] = g0;
     gp[1] = g1;

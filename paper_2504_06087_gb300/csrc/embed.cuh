@@ -221,7 +221,7 @@ __global__ void msg_kernel(int Wc, int n, int n_up, int d, int K, const double* 
                            double cut, Params<W> p, const int32_t* __restrict__ idx,
                            const int32_t* __restrict__ cnt, const int64_t* __restrict__ blk_off,
                            const T* __restrict__ H0, const T* __restrict__ PQ, T* __restrict__ X,
-                           __nv_bfloat16* __restrict__ Xb, int deriv) {
+                           __nv_bfloat16* __restrict__ Xb, int xnc, int64_t xcs, int deriv) {
   constexpr int H = kEdgeHidden, G = kGauss;
   __shared__ FL3<T> feat[H + G + 4];
   const int blk = blockIdx.x;
@@ -318,21 +318,21 @@ __global__ void msg_kernel(int Wc, int n, int n_up, int d, int K, const double* 
         acc.t[t] += gam.t[t] * f + gam.v * si;
         const T xt = -gam.t[t] * f + gam.v * sj;
         X[(xoff + 2 + 3 * (s + 1) + t) * d + c] = xt;
-        if (Xb) Xb[(xoff + 2 + 3 * (s + 1) + t) * d + c] = __float2bfloat16_rn((float)xt);
+        if (Xb) store_split_bf16(Xb + (xoff + 2 + 3 * (s + 1) + t) * d + c, xcs, xnc, (float)xt);
         cross += gam.t[t] * (si - sj);
       }
       acc.l += T(2) * gam.l * f + T(2) * cross + gam.v * sl;
     }
   }
   X[xoff * d + c] = acc.v;
-  if (Xb) Xb[xoff * d + c] = __float2bfloat16_rn((float)acc.v);
+  if (Xb) store_split_bf16(Xb + xoff * d + c, xcs, xnc, (float)acc.v);
   if (deriv) {
     X[(xoff + 1) * d + c] = acc.l;
-    if (Xb) Xb[(xoff + 1) * d + c] = __float2bfloat16_rn((float)acc.l);
+    if (Xb) store_split_bf16(Xb + (xoff + 1) * d + c, xcs, xnc, (float)acc.l);
 #pragma unroll
     for (int t = 0; t < 3; ++t) {
       X[(xoff + 2 + t) * d + c] = acc.t[t];
-      if (Xb) Xb[(xoff + 2 + t) * d + c] = __float2bfloat16_rn((float)acc.t[t]);
+      if (Xb) store_split_bf16(Xb + (xoff + 2 + t) * d + c, xcs, xnc, (float)acc.t[t]);
     }
   }
 }
@@ -346,7 +346,7 @@ template <typename T, typename W>
 __global__ void fl_act_kernel(int ncol, const int64_t* __restrict__ off, int64_t stride,
                               const T* __restrict__ Z, int64_t ldz, const W* bias,
                               T* __restrict__ Y, int64_t ldy, int residual,
-                              __nv_bfloat16* __restrict__ Yb = nullptr) {
+                              __nv_bfloat16* __restrict__ Yb = nullptr, int ync = 1, int64_t ycs = 0) {
   const int b = blockIdx.x;
   int64_t r0, r1;
   if (off) { r0 = off[b]; r1 = off[b + 1]; }
@@ -361,7 +361,7 @@ __global__ void fl_act_kernel(int ncol, const int64_t* __restrict__ off, int64_t
     auto put = [&](int64_t q, T v) {
       T o = residual ? Y[q * ldy + c] + v : v;
       Y[q * ldy + c] = o;
-      if (Yb) Yb[q * ldy + c] = __float2bfloat16_rn((float)o);
+      if (Yb) store_split_bf16(Yb + q * ldy + c, ycs, ync, (float)o);
     };
     for (int64_t q = r0 + 2; q < r1; ++q) {
       T zt = Z[q * ldz + c];
@@ -393,10 +393,20 @@ __global__ void rowdot_kernel(const T* __restrict__ Y, int64_t ldy, int ncol, co
 // (block order).
 template <typename T>
 __global__ void gather_value_rows_kernel(int nb, int d, const int64_t* __restrict__ off,
-                                         const T* __restrict__ X, T* __restrict__ Hv) {
+                                         const T* __restrict__ X, T* __restrict__ Hv, int64_t ldx = -1) {
   const int b = blockIdx.x;
   const int64_t r0 = off[b];
-  for (int c = threadIdx.x; c < d; c += blockDim.x) Hv[(int64_t)b * d + c] = X[r0 * d + c];
+  const int64_t ld = ldx < 0 ? d : ldx;
+  for (int c = threadIdx.x; c < d; c += blockDim.x) Hv[(int64_t)b * d + c] = X[r0 * ld + c];
+}
+
+// Writes dense rows back into the value row of every block: Z[off[b]] = Zv[b].
+template <typename T>
+__global__ void scatter_value_rows_kernel(int N, const int64_t* __restrict__ off, const T* __restrict__ Zv,
+                                          T* __restrict__ Z, int64_t ldz) {
+  const int b = blockIdx.x;
+  const int64_t r0 = off[b];
+  for (int c = threadIdx.x; c < N; c += blockDim.x) Z[r0 * ldz + c] = Zv[(int64_t)b * N + c];
 }
 
 }  // namespace fire

@@ -97,6 +97,17 @@ struct Runner {
     // FIRE_TC_MASK (diagnostic): bit 0 embedding MLP, 1 Jastrow MLPs,
     // 2 attention, 3 orbitals -- which products may use the tensor cores.
     if (const char* m = getenv("FIRE_TC_MASK")) tc_mask = atoi(m);
+    if (const char* m = getenv("FIRE_TC_FIX_VALUES")) fix_values = atoi(m);
+    auto nc_env = [](const char* k, int dflt) {
+      const char* v = getenv(k);
+      int x = v ? atoi(v) : dflt;
+      return x < 1 ? 1 : (x > kMaxSplit ? kMaxSplit : x);
+    };
+    nc_mlp = nc_env("FIRE_TC_SPLIT_MLP", nc_mlp);
+    nc_jas = nc_env("FIRE_TC_SPLIT_JASTROW", nc_jas);
+    nc_att = nc_env("FIRE_TC_SPLIT_ATT", nc_att);
+    nc_orb = nc_env("FIRE_TC_SPLIT_ORB", nc_orb);
+    capA = pl.Wc * dm.n * pl.rows_per_el;
     prof = prof_enabled();
     ws = reinterpret_cast<unsigned char*>(a.ws);
     s = a.stream;
@@ -149,14 +160,33 @@ struct Runner {
   // runs on the tensor cores (BF16_FP64 form); otherwise SIMT in T.
   int tc_rc = FIRE_OK;
   int tc_mask = 0xF;
+  int fix_values = 1;         // value rows recomputed in fp32 after a tensor-core product
+  // split-bf16 components of each tensor-core product (1: 1 product, 2: 3, 3: 6)
+  // (6 component products everywhere: the E_L error then matches plain fp32)
+  int nc_mlp = 3, nc_jas = 3, nc_att = 3, nc_orb = 3;
+  int64_t capA = 0;           // allocated rows of X / Y: the component stride of Xb / Yb
+  // value-row fix-up context of the current chunk
+  const int64_t* vr_off = nullptr;
+  int vr_nb = 0;
+  T* vr_A = nullptr;           // [nb][K] gathered value rows
+  T* vr_C = nullptr;           // [nb][N] their products
   void row_gemm(const T* A, const __nv_bfloat16* Ab, int64_t lda, int64_t a_rows, const T* B,
                 const __nv_bfloat16* Bt, int64_t ldb, T* C, int64_t ldc, const int64_t* m_range,
-                int64_t m_begin, int64_t m_end, int64_t m_cap, int N, int K) {
+                int64_t m_begin, int64_t m_end, int64_t m_cap, int N, int K, int nc = 1) {
     if constexpr (sizeof(T) == 4) {
       if (Ab && Bt && K % 64 == 0) {
         int rc = tc::gemm_bf16(s, Ab, lda, a_rows, Bt, N, K, reinterpret_cast<float*>(C), ldc, m_begin, m_end,
-                               m_range, m_cap, &at<DevStatus>(pl.status)->tc_err);
-        if (rc == FIRE_OK) return;
+                               m_range, m_cap, &at<DevStatus>(pl.status)->tc_err, nc);
+        if (rc == FIRE_OK) {
+          if (fix_values && vr_off && m_range) {
+            // value rows (one per block) again in fp32: they set Phi and log|Psi|
+            gather_value_rows_kernel<T><<<vr_nb, 256, 0, s>>>(vr_nb, K, vr_off, A, vr_A, lda);
+            gemm<T>(s, vr_A, K, B, ldb, false, vr_C, N, 0, vr_nb, nullptr, vr_nb, N, K);
+            scatter_value_rows_kernel<T><<<vr_nb, 256, 0, s>>>(N, vr_off, vr_C, C, ldc);
+            launches += 3;
+          }
+          return;
+        }
         tc_rc = rc;
       }
     }
@@ -171,9 +201,10 @@ struct Runner {
                    const __nv_bfloat16* w2b, const T* b2, const T* w3, T* Z, int64_t ldz, T* Y,
                    __nv_bfloat16* Yb, int64_t ldy, T* F) {
     const int J = dm.J;
-    row_gemm(Xin, Xinb, ldx, cap, w1, w1b, J, Z, ldz, range, rb, re, cap, J, din);
-    fl_act_kernel<T, T><<<nblk, 256, 0, s>>>(J, off, stride, Z, ldz, b1, Y, ldy, 0, Yb);
-    row_gemm(Y, Yb, ldy, cap, w2, w2b, J, Z, ldz, range, rb, re, cap, J, J);
+    row_gemm(Xin, Xinb, ldx, capA, w1, w1b, J, Z, ldz, range, rb, re, cap, J, din, nc_jas);
+    fl_act_kernel<T, T><<<nblk, 256, 0, s>>>(J, off, stride, Z, ldz, b1, Y, ldy, 0, Yb, kMaxSplit,
+                                             capA * ldy);
+    row_gemm(Y, Yb, ldy, capA, w2, w2b, J, Z, ldz, range, rb, re, cap, J, J, nc_jas);
     fl_act_kernel<T, T><<<nblk, 256, 0, s>>>(J, off, stride, Z, ldz, b2, Y, ldy, 0);
     const int64_t nrows_grid = cap;
     rowdot_kernel<T, T><<<(unsigned)((nrows_grid + 7) / 8), 256, 0, s>>>(Y, ldy, J, w3, F, range, rb, re);
@@ -194,24 +225,27 @@ struct Runner {
         auto dst = [&](int64_t off) { return reinterpret_cast<__nv_bfloat16*>(WBm) + off; };
         const int64_t d = dm.d, J = dm.J, n = dm.n, D = dm.D, R = dm.R, dr = dm.dr;
         int np = 0;
+        const int S = kMaxSplit;
         for (int l = 0; l < dm.L; ++l, ++np)
           tc::pack_bf16(s, reinterpret_cast<const float*>(p.mlp_w) + l * d * d, d, (int)d, (int)d, 1,
-                        dst(pl.wb_mlp + l * d * d));
+                        dst(pl.wb_mlp + S * l * d * d), S, d * d);
         const T* jw[2][2] = {{p.jm1_w1, p.jm1_w2}, {p.jm2_w1, p.jm2_w2}};
         const int64_t jo[2] = {pl.wb_jm1, pl.wb_jm2};
         for (int q = 0; q < 2; ++q) {
-          tc::pack_bf16(s, reinterpret_cast<const float*>(jw[q][0]), J, (int)d, (int)J, 1, dst(jo[q]));
-          tc::pack_bf16(s, reinterpret_cast<const float*>(jw[q][1]), J, (int)J, (int)J, 1, dst(jo[q] + d * J));
+          tc::pack_bf16(s, reinterpret_cast<const float*>(jw[q][0]), J, (int)d, (int)J, 1, dst(jo[q]), S, d * J);
+          tc::pack_bf16(s, reinterpret_cast<const float*>(jw[q][1]), J, (int)J, (int)J, 1, dst(jo[q] + S * d * J),
+                        S, J * J);
           np += 2;
         }
-        tc::pack_bf16(s, reinterpret_cast<const float*>(p.att_q), d, (int)d, (int)R, 0, dst(pl.wb_att));
+        const int64_t acs = (R + R * dr) * d;
+        tc::pack_bf16(s, reinterpret_cast<const float*>(p.att_q), d, (int)d, (int)R, 0, dst(pl.wb_att), S, acs);
         for (int rr = 0; rr < R; ++rr, ++np)
           tc::pack_bf16(s, reinterpret_cast<const float*>(p.att_wv) + rr * d * dr, dr, (int)d, (int)dr, 1,
-                        dst(pl.wb_att + (R + rr * dr) * d));
+                        dst(pl.wb_att + (R + rr * dr) * d), S, acs);
         for (int sp = 0; sp < 2; ++sp)
           for (int dd = 0; dd < D; ++dd, ++np)
             tc::pack_bf16(s, reinterpret_cast<const float*>(p.orb_w) + (sp * D + dd) * d * n, n, (int)d, (int)n, 1,
-                          dst(pl.wb_orb + (sp * D + dd) * n * d));
+                          dst(pl.wb_orb + S * (sp * D + dd) * n * d), S, n * d);
         launches += np + 1;
       }
     }
@@ -273,19 +307,25 @@ struct Runner {
         return (WB && (tc_mask >> bit & 1)) ? WB + off : nullptr;
       };
       mark("msg", 1);
-      msg_kernel<T, T><<<nb, d, 0, s>>>(wc, n, n_up, d, K, r, c, p, idx, cnt, boff, H0, PQ, X, Xb, deriv);
+      msg_kernel<T, T><<<nb, d, 0, s>>>(wc, n, n_up, d, K, r, c, p, idx, cnt, boff, H0, PQ, X, Xb, kMaxSplit,
+                                        capA * d, deriv);
       check("msg");
       // 5. embedding MLP h = MLP(h^1): L residual SiLU layers
       T* big = at<T>(pl.big);
       T* Z = big + pl.zcol;
       T* SU = big + pl.sucol;
+      vr_off = boff;
+      vr_nb = nb;
+      vr_A = at<T>(pl.Hv);
+      vr_C = at<T>(pl.Ov);
       const int64_t ldb = pl.ld_big;
       for (int l = 0; l < dm.L; ++l) {
         mark("mlp_gemm", 1);
-        row_gemm(X, Xb, d, cap, p.mlp_w + (int64_t)l * d * d, wbm(0, pl.wb_mlp + (int64_t)l * d * d), d, Z, ldb,
-                 fullr, 0, 0, cap, d, d);
+        row_gemm(X, Xb, d, capA, p.mlp_w + (int64_t)l * d * d, wbm(0, pl.wb_mlp + kMaxSplit * (int64_t)l * d * d),
+                 d, Z, ldb, fullr, 0, 0, cap, d, d, nc_mlp);
         mark("fl_act", 1);
-        fl_act_kernel<T, T><<<nb, 256, 0, s>>>(d, boff, 0, Z, ldb, p.mlp_b + (int64_t)l * d, X, d, 1, Xb);
+        fl_act_kernel<T, T><<<nb, 256, 0, s>>>(d, boff, 0, Z, ldb, p.mlp_b + (int64_t)l * d, X, d, 1, Xb,
+                                               kMaxSplit, capA * d);
       }
       // 6. Jastrow factors
       T* jval = at<T>(pl.jval); T* jsign = at<T>(pl.jsign); T* jgrad = at<T>(pl.jgrad); T* jlap = at<T>(pl.jlap);
@@ -297,9 +337,9 @@ struct Runner {
         T* F2 = at<T>(pl.F2);
         const int64_t JJ = (int64_t)dm.J;
         mlp_readout(X, Xb, d, d, fullr, 0, 0, cap, boff, 0, nb, p.jm1_w1, wbm(1, pl.wb_jm1), p.jm1_b1, p.jm1_w2,
-                    wbm(1, pl.wb_jm1 + d * JJ), p.jm1_b2, p.jm1_w3, Z, ldb, Y, Yb, JJ, F1);
+                    wbm(1, pl.wb_jm1 + kMaxSplit * d * JJ), p.jm1_b2, p.jm1_w3, Z, ldb, Y, Yb, JJ, F1);
         mlp_readout(X, Xb, d, d, fullr, 0, 0, cap, boff, 0, nb, p.jm2_w1, wbm(1, pl.wb_jm2), p.jm2_b1, p.jm2_w2,
-                    wbm(1, pl.wb_jm2 + d * JJ), p.jm2_b2, p.jm2_w3, Z, ldb, Y, Yb, JJ, F2);
+                    wbm(1, pl.wb_jm2 + kMaxSplit * d * JJ), p.jm2_b2, p.jm2_w3, Z, ldb, Y, Yb, JJ, F2);
         mark("jastrow_reduce", 1);
         jmlp_reduce_kernel<T, T><<<wc, 256, 0, s>>>(wc, n, n_up, K, idx, cnt, rev, boff, F1, F2, p.jm1_b3,
                                                     p.jm2_b3, jval, jsign, jgrad, jlap, deriv);
@@ -311,8 +351,8 @@ struct Runner {
         bool att_tc = false;
         if constexpr (sizeof(T) == 4) {
           if (Xb && WB && d % 64 == 0 && (tc_mask & 4))
-            att_tc = tc::gemm_bf16(s, Xb, d, cap, WB + pl.wb_att, R + RD, d, reinterpret_cast<float*>(SU), ldb, 0, 0,
-                                   fullr, cap, &st->tc_err) == FIRE_OK;
+            att_tc = tc::gemm_bf16(s, Xb, d, capA, WB + pl.wb_att, R + RD, d, reinterpret_cast<float*>(SU), ldb, 0,
+                                   0, fullr, cap, &st->tc_err, nc_att) == FIRE_OK;
         }
         if (!att_tc) {
           gemm<T>(s, X, d, p.att_q, d, true, SU, ldb, 0, 0, fullr, cap, R, d);
@@ -369,7 +409,10 @@ struct Runner {
       int32_t* piv = at<int32_t>(pl.piv);
       double* ldabs = at<double>(pl.ldabs);
       double* lsign = at<double>(pl.lsign);
-      phi_assemble_kernel<T, LT><<<wc * D, 256, 0, s>>>(wc, n, n_up, D, Ov, Fenv, R5, LUb);
+      // float32 inverse by Gauss-Jordan from a float copy of Phi (n <= 192)
+      const bool gj = deriv && sizeof(T) == 4 && n <= 192;
+      float* Phif = gj ? at<float>(pl.Phif) : nullptr;
+      phi_assemble_kernel<T, LT><<<wc * D, 256, 0, s>>>(wc, n, n_up, D, Ov, Fenv, R5, LUb, Phif);
       const size_t lusm = (size_t)2 * n * 16 * sizeof(LT);
       mark("lu", 1);
       lu_kernel<LT, 16><<<wc * D, 256, lusm, s>>>(n, LUb, piv, ldabs, lsign);
@@ -378,21 +421,29 @@ struct Runner {
       T* ldet = at<T>(pl.ldet);
       if (deriv) {
         T* Ainv = at<T>(pl.Ainv);
-        const size_t invsm = (size_t)n * n * sizeof(T) + 2 * n * sizeof(int);
         mark("inverse", 1);
-        lu_inverse_kernel<LT, T><<<wc * D, 256, invsm, s>>>(n, LUb, piv, Ainv);
+        if (gj) {
+          const int G = (n + 7) / 8;
+          const int thr = ((G * G + 31) / 32) * 32;
+          gj_inverse_kernel<float, T><<<wc * D, thr, gj_smem_bytes(n), s>>>(n, Phif, Ainv);
+        } else {
+          const size_t invsm = (size_t)n * n * sizeof(T) + 2 * n * sizeof(int);
+          lu_inverse_kernel<LT, T><<<wc * D, 256, invsm, s>>>(n, LUb, piv, Ainv);
+        }
       check("inverse");
         // 8. log-det gradient and Laplacian, determinant by determinant
         T* O = big;  // aliases Z | Y | SU, which are dead by now
-        const int mcap = 1 + K;
-        const size_t ctsm = (size_t)(4 * mcap) * (n + 1) * sizeof(T) + 2 * mcap * sizeof(int);
+        vr_off = nullptr;   // orbital values come from the Ov product
+        const int mcap = 1 + (K < n - 1 ? K : n - 1);
+        const size_t ctsm = (size_t)(4 * mcap) * 65 * sizeof(T) + 2 * mcap * sizeof(int) + 2 * mcap * sizeof(int64_t) + 16;
         for (int dd = 0; dd < D; ++dd) {
           mark("orb_gemm", 2);
           for (int sp = 0; sp < 2; ++sp)
-            row_gemm(X, Xb, d, cap, p.orb_w + ((int64_t)sp * D + dd) * d * n,
-                     wbm(3, pl.wb_orb + ((int64_t)sp * D + dd) * n * d), n, O, n, rng + 2 * sp, 0, 0, cap, n, d);
+            row_gemm(X, Xb, d, capA, p.orb_w + ((int64_t)sp * D + dd) * d * n,
+                     wbm(3, pl.wb_orb + kMaxSplit * ((int64_t)sp * D + dd) * n * d), n, O, n, rng + 2 * sp, 0, 0,
+                     cap, n, d, nc_orb);
           mark("contract", 1);
-          contract_kernel<T><<<nb, 256, ctsm, s>>>(wc, n, n_up, K, dd, D, idx, cnt, rev, boff, O, Fenv, Ainv,
+          contract_kernel<T><<<nb, 256, ctsm, s>>>(wc, n, n_up, K, mcap, dd, D, idx, cnt, rev, boff, O, Fenv, Ainv,
                                                    gdet, ldet, st);
       check("contract");
         }
@@ -440,6 +491,7 @@ inline int set_smem_limits() {
   raise((const void*)lu_inverse_kernel<LT, T>);
   raise((const void*)lu_kernel<LT, 16>);
   raise((const void*)att_pool_kernel<T>);
+  raise((const void*)gj_inverse_kernel<float, T>);
   cudaError_t e = cudaGetLastError();
   if (rc != FIRE_OK || e != cudaSuccess) set_last_error("smem limits", cudaGetErrorString(e));
   return rc;

@@ -30,7 +30,7 @@ struct Plan {
   size_t Y, Xb, Yb;        // Jastrow hidden rows; bf16 copies of X and Y (BF16 form)
   int64_t wb_mlp, wb_jm1, wb_jm2, wb_att, wb_orb;   // element offsets inside wbf16
   size_t Qf, Fenv, Hv, Ov;
-  size_t LU, piv, ldabs, lsign, Ainv, gdet, ldet;
+  size_t LU, piv, ldabs, lsign, Ainv, gdet, ldet, Phif;
   size_t jval, jsign, jgrad, jlap, aval, asign, agrad, alap, cval, cgrad, clap, vpot;
   size_t V, VZ, VY, G1, G2;
   size_t wbf16;            // packed BF16 weights (tensor-core form)

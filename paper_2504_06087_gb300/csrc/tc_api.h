@@ -11,12 +11,15 @@ namespace tc {
 // (device range m_range or host m_begin/m_end); A bf16 with row stride lda
 // and a_rows rows allocated; Bt bf16 [N][K]; C fp32 with row stride ldc.
 // K must be a multiple of 64.  Timeouts of bounded waits set *err.
+// nc = 1, 2, 3: A and Bt hold nc bf16 components each (split-bf16 product),
+// the components of A a_rows rows apart and those of Bt N rows apart.
 int gemm_bf16(cudaStream_t s, const void* A, int64_t lda, int64_t a_rows, const void* Bt, int N, int K,
               float* C, int64_t ldc, int64_t m_begin, int64_t m_end, const int64_t* m_range, int64_t m_cap,
-              int* err);
+              int* err, int nc);
 
-// dst = bf16 K-major copy of a weight matrix (see pack_bf16_kernel).
-void pack_bf16(cudaStream_t s, const float* src, int64_t lds, int K, int N, int trans, void* dst);
+// dst = nc-component bf16 K-major copy of a weight matrix (pack_bf16_kernel).
+void pack_bf16(cudaStream_t s, const float* src, int64_t lds, int K, int N, int trans, void* dst, int nc,
+               int64_t comp_stride);
 
 }  // namespace tc
 }  // namespace fire

@@ -45,52 +45,65 @@ static bool make_map(CUtensorMap* m, const void* base, uint64_t rows, uint64_t c
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-constexpr int kStages = 4;
-
-static size_t smem_bytes(int BN) { return (size_t)kStages * (BM * BK * 2 + (size_t)BN * BK * 2) + 1024; }
-
-int gemm_bf16(cudaStream_t s, const void* A, int64_t lda, int64_t a_rows, const void* Bt, int N, int K,
-              float* C, int64_t ldc, int64_t m_begin, int64_t m_end, const int64_t* m_range, int64_t m_cap,
-              int* err) {
-  if (N < 1 || K < BK || K % BK || m_cap <= 0) return FIRE_ERR_UNSUPPORTED;
-  const int nt = (N + 255) / 256;
-  int BN = (N + nt - 1) / nt;
-  BN = (BN + 15) / 16 * 16;
-  CUtensorMap ma, mb;
-  if (!make_map(&ma, A, (uint64_t)a_rows, (uint64_t)K, (uint64_t)lda, BM)) return FIRE_ERR_CUDA;
-  if (!make_map(&mb, Bt, (uint64_t)N, (uint64_t)K, (uint64_t)K, (uint32_t)BN)) return FIRE_ERR_CUDA;
-  const size_t sm = smem_bytes(BN);
-  if (cudaFuncSetAttribute(tc_gemm_kernel<kStages>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+template <int STAGES, int NC>
+static int launch(cudaStream_t s, const CUtensorMap& ma, const CUtensorMap& mb, const TcArgs& g, int64_t m_cap,
+                  int nt) {
+  const size_t sm = (size_t)STAGES * NC * (BM * BK * 2 + (size_t)g.BN * BK * 2) + 1024;
+  if (cudaFuncSetAttribute(tc_gemm_kernel<STAGES, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
       cudaSuccess)
     return FIRE_ERR_CUDA;
-  TcArgs g{C, ldc, m_begin, m_end, m_range, N, K, BN, err};
   dim3 grid((unsigned)((m_cap + BM - 1) / BM), (unsigned)nt);
-  tc_gemm_kernel<kStages><<<grid, 128, sm, s>>>(ma, mb, g);
+  tc_gemm_kernel<STAGES, NC><<<grid, 128, sm, s>>>(ma, mb, g);
   return cudaGetLastError() == cudaSuccess ? FIRE_OK : FIRE_ERR_CUDA;
 }
 
-// dst[n][k] = bf16(src[k * lds + n]) for a [K][N] source (trans = 1), or
-// dst[n][k] = bf16(src[n * lds + k]) for an [N][K] source (trans = 0).
+int gemm_bf16(cudaStream_t s, const void* A, int64_t lda, int64_t a_rows, const void* Bt, int N, int K,
+              float* C, int64_t ldc, int64_t m_begin, int64_t m_end, const int64_t* m_range, int64_t m_cap,
+              int* err, int nc) {
+  if (N < 1 || K < BK || K % BK || m_cap <= 0 || nc < 1 || nc > 3) return FIRE_ERR_UNSUPPORTED;
+  const int bn_max = nc == 3 ? 128 : 256;       // keeps two pipeline stages in shared memory
+  const int nt = (N + bn_max - 1) / bn_max;
+  int BN = (N + nt - 1) / nt;
+  BN = (BN + 15) / 16 * 16;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, A, (uint64_t)a_rows * nc, (uint64_t)K, (uint64_t)lda, BM)) return FIRE_ERR_CUDA;
+  if (!make_map(&mb, Bt, (uint64_t)N * nc, (uint64_t)K, (uint64_t)K, (uint32_t)BN)) return FIRE_ERR_CUDA;
+  TcArgs g{C, ldc, m_begin, m_end, m_range, N, K, BN, a_rows, N, err};
+  if (nc == 1) return launch<4, 1>(s, ma, mb, g, m_cap, nt);
+  if (nc == 2) return launch<2, 2>(s, ma, mb, g, m_cap, nt);
+  return launch<2, 3>(s, ma, mb, g, m_cap, nt);
+}
+
+// dst[c][n][k] = component c of src[k * lds + n] for a [K][N] source
+// (trans = 1), or of src[n * lds + k] for an [N][K] source (trans = 0);
+// components are comp_stride elements apart.
 __global__ void pack_bf16_kernel(const float* __restrict__ src, int64_t lds, int K, int N, int trans,
-                                 __nv_bfloat16* __restrict__ dst) {
+                                 __nv_bfloat16* __restrict__ dst, int nc, int64_t comp_stride) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)N * K) return;
   const int nn = (int)(e / K), kk = (int)(e % K);
-  const float v = trans ? src[(int64_t)kk * lds + nn] : src[(int64_t)nn * lds + kk];
-  dst[e] = __float2bfloat16_rn(v);
+  float v = trans ? src[(int64_t)kk * lds + nn] : src[(int64_t)nn * lds + kk];
+  for (int c = 0; c < nc; ++c) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    dst[c * comp_stride + e] = h;
+    v -= __bfloat162float(h);
+  }
 }
 
-void pack_bf16(cudaStream_t s, const float* src, int64_t lds, int K, int N, int trans, void* dst) {
+void pack_bf16(cudaStream_t s, const float* src, int64_t lds, int K, int N, int trans, void* dst, int nc,
+               int64_t comp_stride) {
   const int64_t tot = (int64_t)N * K;
   pack_bf16_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(src, lds, K, N, trans,
-                                                                 reinterpret_cast<__nv_bfloat16*>(dst));
+                                                                 reinterpret_cast<__nv_bfloat16*>(dst), nc,
+                                                                 comp_stride);
 }
 
 }  // namespace tc
 }  // namespace fire
 
-extern "C" int fire_selftest_tc_gemm(int64_t M, int32_t N, int32_t K, const void* A, const void* Bt, float* C,
-                                     int32_t* err, void* stream) {
-  if (M < 1 || N < 1 || K < 64 || K % 64 || !A || !Bt || !C || !err) return FIRE_ERR_INVALID_ARG;
-  return fire::tc::gemm_bf16((cudaStream_t)stream, A, K, M, Bt, N, K, C, N, 0, M, nullptr, M, err);
+extern "C" int fire_selftest_tc_gemm(int64_t M, int32_t N, int32_t K, int32_t nc, const void* A, const void* Bt,
+                                     float* C, int32_t* err, void* stream) {
+  if (M < 1 || N < 1 || K < 64 || K % 64 || nc < 1 || nc > 3 || !A || !Bt || !C || !err)
+    return FIRE_ERR_INVALID_ARG;
+  return fire::tc::gemm_bf16((cudaStream_t)stream, A, K, M, Bt, N, K, C, N, 0, M, nullptr, M, err, nc);
 }

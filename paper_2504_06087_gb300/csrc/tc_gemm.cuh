@@ -137,11 +137,26 @@ struct TcArgs {
   int64_t m_begin, m_end;        // used when m_range == nullptr
   const int64_t* m_range;
   int N, K, BN;                  // BN multiple of 16, <= 256
+  int64_t a_comp_rows;           // rows between the bf16 components of A
+  int64_t b_comp_rows;           // rows between the bf16 components of Bt
   int* err;                      // device error word (timeouts)
 };
 
-// Dynamic shared memory: STAGES x (A tile 16 KB + B tile BN*128 B), 1024-aligned.
-template <int STAGES>
+// Split-bf16 products (Henry, Tang & Heinecke 2019): a value x is stored as
+// NC bf16 components x0 + x1 + x2; the product sums the component pairs
+// (p, q) with p + q < NC, smallest terms first.  NC = 1 is plain bf16, NC = 2
+// takes 3 products, NC = 3 takes 6.
+__host__ __device__ constexpr int split_count(int nc) { return nc == 1 ? 1 : (nc == 2 ? 3 : 6); }
+__host__ __device__ constexpr int split_p(int nc, int k) {
+  return nc == 1 ? 0 : (nc == 2 ? (k == 0 ? 1 : 0) : (k == 0 ? 2 : (k == 1 ? 1 : (k == 2 ? 0 : (k == 3 ? 1 : 0)))));
+}
+__host__ __device__ constexpr int split_q(int nc, int k) {
+  return nc == 1 ? 0 : (nc == 2 ? (k == 1 ? 1 : 0) : (k == 0 ? 0 : (k == 1 ? 1 : (k == 2 ? 2 : (k == 4 ? 1 : 0)))));
+}
+
+// Dynamic shared memory: STAGES x NC x (A tile 16 KB + B tile BN*128 B),
+// 1024-aligned.
+template <int STAGES, int NC>
 __global__ void __launch_bounds__(128, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcArgs g) {
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
@@ -157,7 +172,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int BN = g.BN;
   const uint32_t a_bytes = BM * BK * 2, b_bytes = (uint32_t)BN * BK * 2;
-  const uint32_t stage_bytes = a_bytes + b_bytes;
+  const uint32_t stage_bytes = NC * (a_bytes + b_bytes);
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
   uint32_t ncols = 32;
@@ -186,8 +201,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       if (abort_flag) break;
       unsigned char* sa = base + (size_t)s * stage_bytes;
       mbar_expect_tx(&full_bar[s], stage_bytes);
-      tma_load_2d(sa, &mapA, &full_bar[s], kb * BK, (int)m0);
-      tma_load_2d(sa + a_bytes, &mapB, &full_bar[s], kb * BK, n0);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        tma_load_2d(sa + c * a_bytes, &mapA, &full_bar[s], kb * BK, (int)(c * g.a_comp_rows + m0));
+        tma_load_2d(sa + NC * a_bytes + c * b_bytes, &mapB, &full_bar[s], kb * BK, (int)(c * g.b_comp_rows + n0));
+      }
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
@@ -198,12 +216,17 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       if (!mbar_wait(&full_bar[s], (kb / STAGES) & 1)) { atomicExch(g.err, 2); abort_flag = 1; ok = false; break; }
       fence_after_sync();
       const uint32_t sa = smem_u32(base + (size_t)s * stage_bytes);
-      const uint32_t sb = sa + a_bytes;
+      const uint32_t sb = sa + NC * a_bytes;
 #pragma unroll
-      for (int k = 0; k < BK / UMMA_K; ++k) {
-        const uint64_t ad = smem_desc_sw128(sa + k * UMMA_K * 2);
-        const uint64_t bd = smem_desc_sw128(sb + k * UMMA_K * 2);
-        mma_bf16(tmem, ad, bd, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+      for (int pr = 0; pr < split_count(NC); ++pr) {
+        const uint32_t ap = sa + split_p(NC, pr) * a_bytes;
+        const uint32_t bq = sb + split_q(NC, pr) * b_bytes;
+#pragma unroll
+        for (int k = 0; k < BK / UMMA_K; ++k) {
+          const uint64_t ad = smem_desc_sw128(ap + k * UMMA_K * 2);
+          const uint64_t bd = smem_desc_sw128(bq + k * UMMA_K * 2);
+          mma_bf16(tmem, ad, bd, idesc, (kb > 0 || pr > 0 || k > 0) ? 1u : 0u);
+        }
       }
       mma_commit(&empty_bar[s]);
     }

@@ -94,7 +94,8 @@ SIGNATURES = {
                                               ctypes.c_int32, ctypes.c_int32]),
     "fire_workspace_layout": (ctypes.c_int, [P(System), P(Arch), ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                              ctypes.c_int32, P(WsEntry), P(ctypes.c_int32), P(ctypes.c_int64)]),
-    "fire_selftest_tc_gemm": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, VP, VP, VP, VP, VP]),
+    "fire_selftest_tc_gemm": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, VP, VP,
+                                             VP, VP, VP]),
     "fire_neighbors": (ctypes.c_int, [P(System), ctypes.c_int64, VP, ctypes.c_int32, VP, VP,
                                       P(ctypes.c_int32), VP, ctypes.c_size_t, VP]),
     "fire_logpsi": (ctypes.c_int, [P(System), P(Arch), P(Params), ctypes.c_int64, VP, ctypes.c_int32,
@@ -140,13 +141,26 @@ def profile_report():
     return {e.name.decode(): (int(e.launches), float(e.ms_total)) for e in ents[:n.value]}
 
 
-def tc_gemm_selftest(A: torch.Tensor, Bt: torch.Tensor) -> torch.Tensor:
-    """C = A @ Bt^T on the tensor cores (A [M,K], Bt [N,K] bf16 CUDA tensors)."""
-    M, K = A.shape
-    N = Bt.shape[0]
+def split_bf16(x: torch.Tensor, nc: int) -> torch.Tensor:
+    """[nc, *x.shape] bf16 components with x ~ sum of components."""
+    out, r = [], x.float()
+    for _ in range(nc):
+        h = r.to(torch.bfloat16)
+        out.append(h)
+        r = r - h.float()
+    return torch.stack(out)
+
+
+def tc_gemm_selftest(A: torch.Tensor, Bt: torch.Tensor, nc: int = 1) -> torch.Tensor:
+    """C = A @ Bt^T on the tensor cores.  A [nc, M, K] / Bt [nc, N, K] bf16
+    components (or [M, K] / [N, K] for nc = 1)."""
+    if A.dim() == 2:
+        A, Bt = A[None], Bt[None]
+    _, M, K = A.shape
+    N = Bt.shape[1]
     C = torch.empty((M, N), dtype=torch.float32, device=A.device)
     err = torch.zeros(1, dtype=torch.int32, device=A.device)
-    rc = lib().fire_selftest_tc_gemm(M, N, K, _ptr(A.contiguous()), _ptr(Bt.contiguous()), _ptr(C), _ptr(err),
+    rc = lib().fire_selftest_tc_gemm(M, N, K, nc, _ptr(A.contiguous()), _ptr(Bt.contiguous()), _ptr(C), _ptr(err),
                                      ctypes.c_void_p(torch.cuda.current_stream(A.device).cuda_stream))
     torch.cuda.synchronize(A.device)
     if rc:

@@ -19,3 +19,17 @@ def test_tc_gemm_matches_float32_product(M, N, K):
     err = (C - ref).abs().max().item()
     scale = ref.abs().max().item()
     assert err <= 1e-5 * scale * (K / 64) ** 0.5, (err, scale)
+
+
+@pytest.mark.parametrize("nc,tol", [(1, 1e-2), (2, 5e-5), (3, 5e-6)])
+def test_split_bf16_product_reaches_its_precision(nc, tol):
+    """x = x0 + x1 (+ x2) in bf16 components; the 1 / 3 / 6 component
+    products approach the float32 product of the unsplit values."""
+    g = torch.Generator(device="cpu").manual_seed(7 + nc)
+    M, N, K = 640, 200, 256
+    A = torch.randn(M, K, generator=g, dtype=torch.float32).cuda()
+    B = torch.randn(N, K, generator=g, dtype=torch.float32).cuda()
+    C = fire.tc_gemm_selftest(fire.split_bf16(A, nc), fire.split_bf16(B, nc), nc)
+    ref = (A.double() @ B.double().T)
+    err = ((C.double() - ref).abs().max() / ref.abs().max()).item()
+    assert err < tol, err
