@@ -194,7 +194,7 @@ int make_plan(const fire_system_t* sys, const fire_arch_t* ar, int64_t W, int pr
   if (wc > W) wc = W;
   // shared-memory limits of the determinant kernels
   const int n = dm.n, mcap = 1 + (k_cap < dm.n - 1 ? k_cap : dm.n - 1);
-  const size_t ctsm = (size_t)(4 * mcap) * 65 * pl->tsz + 2 * mcap * sizeof(int) + 2 * mcap * sizeof(int64_t) + 16;
+  const size_t ctsm = contract_smem_bytes(mcap, pl->tsz);
   const size_t invsm = (size_t)n * n * pl->tsz + 2 * n * sizeof(int);
   const size_t lim = 227 * 1024;
   if (dm.deriv && (ctsm > lim || invsm > lim)) return FIRE_ERR_UNSUPPORTED;

@@ -362,6 +362,19 @@ __global__ void __launch_bounds__(576, 1) gj_inverse_kernel(int n, const IT* __r
   }
 }
 
+// Tiles per thread of contract_kernel for neighbourhoods of up to mcap members.
+inline int contract_maxt(int mcap) {
+  const int tiles = mcap * ((mcap + 3) / 4);
+  for (int t : {1, 2, 3, 5, 9})
+    if (256 * t >= tiles) return t;
+  return 0;
+}
+
+inline size_t contract_smem_bytes(int mcap, size_t tsz) {
+  const size_t region = (size_t)(4 * mcap * 33 > 3 * mcap * mcap ? 4 * mcap * 33 : 3 * mcap * mcap) + 2;
+  return region * tsz + 2 * (size_t)mcap * sizeof(int) + 2 * (size_t)mcap * sizeof(int64_t) + 16;
+}
+
 inline size_t gj_smem_bytes(int n) { return (size_t)n * n * 4 + 512 * 4 + 768 * 4 + 64 * 4; }
 
 // Gradient and Laplacian of log det Phi_d restricted to the neighbourhoods.
@@ -373,21 +386,25 @@ inline size_t gj_smem_bytes(int n) { return (size_t)n * n * 4 + 512 * 4 + 768 * 
 // With Nbar = {i_0 = n', i_1, ...} (m members) the CTA forms
 //   T[(k,x)][l] = d Phi_{i_k l} / d r_{n' x}      (3m rows)
 //   M[(k,x)][k'] = sum_l T[(k,x)][l] A[l][i_k']   (3m x m)
-// as a register-blocked product (3 x 4 outputs per thread) over chunks of
-// LC orbitals staged in shared memory, then
+// as a register-blocked product (3 x 4 outputs per thread, MAXT tiles per
+// thread, all tiles in one pass) over chunks of LC = 32 orbitals staged in
+// shared memory, then
 //   d log det / d r_{n'x} = sum_k M[(k,x)][k]
 //   trace_{n'} = sum_x sum_{k,k'} M[(k,x)][k'] M[(k',x)][k].
-template <typename T>
+template <typename T, int MAXT>
 __global__ void __launch_bounds__(256)
 contract_kernel(int Wc, int n, int n_up, int K, int mcap, int dd, int D, const int32_t* __restrict__ idx,
                 const int32_t* __restrict__ cnt, const int32_t* __restrict__ rev,
                 const int64_t* __restrict__ blk_off, const T* __restrict__ O, const T* __restrict__ Fenv,
                 const T* __restrict__ AT, T* __restrict__ gdet, T* __restrict__ ldet, DevStatus* st) {
-  constexpr int LC = 64, LDC = LC + 1, MAXT = 5, NT = 256;
+  // one batch of 3 x 4 tiles: NT * MAXT >= mcap * ceil(mcap / 4) (host-checked)
+  constexpr int LC = 32, LDC = LC + 1, NT = 256;
   extern __shared__ unsigned char ct_smem[];
   T* Tc = reinterpret_cast<T*>(ct_smem);              // [3*mcap][LDC]
   T* Ac = Tc + (int64_t)3 * mcap * LDC;               // [mcap][LDC]
-  int64_t* ro = reinterpret_cast<int64_t*>(Ac + (int64_t)mcap * LDC);   // O row of (k, x = 0)
+  // the staging area [Tc | Ac] also holds M [3m][m] at the end
+  const int64_t region = max((int64_t)4 * mcap * LDC, (int64_t)3 * mcap * mcap);
+  int64_t* ro = reinterpret_cast<int64_t*>(Tc + ((region + 1) & ~(int64_t)1));   // O row of (k, x = 0)
   int64_t* fo = ro + mcap;                                              // Fenv value row of member k
   int* mi = reinterpret_cast<int*>(fo + mcap);
   int* ms = mi + mcap;
@@ -420,7 +437,7 @@ contract_kernel(int Wc, int n, int n_up, int K, int mcap, int dd, int D, const i
   const int ntile = m * nq;
   T g0 = T(0), g1 = T(0), g2 = T(0), tr = T(0), lt = T(0);
   T* Ms = Tc;                                         // [3m][m], reuses the staging area
-  for (int tb = 0; tb < ntile; tb += NT * MAXT) {    // one pass for m <= 55
+  for (int tb = 0; tb < ntile; tb += NT * MAXT) {    // a single pass (see above)
     T acc[MAXT][12];
 #pragma unroll
     for (int t = 0; t < MAXT; ++t)
@@ -429,10 +446,12 @@ contract_kernel(int Wc, int n, int n_up, int K, int mcap, int dd, int D, const i
     for (int l0 = 0; l0 < n; l0 += LC) {
       const int lc = min(LC, n - l0);
       __syncthreads();
+#pragma unroll 4
       for (int e = tid; e < m * lc; e += NT) {
         const int k = e / lc, l = e % lc;
         Ac[k * LDC + l] = Aw[(int64_t)mi[k] * n + l0 + l];
       }
+#pragma unroll 4
       for (int e = tid; e < 3 * m * lc; e += NT) {
         const int row = e / lc, l = e % lc;
         const int k = row / 3, x = row - 3 * k;

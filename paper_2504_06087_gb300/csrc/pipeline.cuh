@@ -268,13 +268,19 @@ struct Runner {
       nbr_reverse_kernel<<<wc, 256, 0, s>>>(n, n_up, K, idx, cnt, rev);
       blk_scan_kernel<<<1, 1024, 0, s>>>(nb, wc * n_up, brow, boff, rng, st);
       check("nbr");
-      const int64_t cap = (int64_t)nb * pl.rows_per_el;
-      const int64_t* full = rng;          // {0, total} is rng[0], rng[3]: use a 2-element view
+      // the chunk's row total and largest neighbour count, read back once:
+      // they size the grids and the contraction tiles exactly
+      int64_t rows_chunk = 0;
+      int32_t kreq = 0;
+      cudaMemcpyAsync(&rows_chunk, rng + 3, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+      cudaMemcpyAsync(&kreq, &st->k_required, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+      if (cudaStreamSynchronize(s) != cudaSuccess) return FIRE_ERR_CUDA;
+      const int64_t cap = rows_chunk > 0 ? rows_chunk : 1;
       int64_t* fullr = at<int64_t>(pl.ranges) + 4;
       // fullr = {0, total}: written by a tiny copy below
       cudaMemcpyAsync(fullr, rng, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
       cudaMemcpyAsync(fullr + 1, rng + 3, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
-      (void)full;
+
       // 2. initial embeddings h^0 (5 rows per electron)
       T* S5 = at<T>(pl.S5);
       T* Y5 = at<T>(pl.Y5);
@@ -434,8 +440,11 @@ struct Runner {
         // 8. log-det gradient and Laplacian, determinant by determinant
         T* O = big;  // aliases Z | Y | SU, which are dead by now
         vr_off = nullptr;   // orbital values come from the Ov product
-        const int mcap = 1 + (K < n - 1 ? K : n - 1);
-        const size_t ctsm = (size_t)(4 * mcap) * 65 * sizeof(T) + 2 * mcap * sizeof(int) + 2 * mcap * sizeof(int64_t) + 16;
+        const int kmax = kreq < K ? kreq : K;
+        const int mcap = 1 + (kmax < n - 1 ? kmax : n - 1);
+        const int maxt = contract_maxt(mcap);
+        if (maxt == 0) { set_last_error("contract", "neighbourhood larger than 95 members"); return FIRE_ERR_UNSUPPORTED; }
+        const size_t ctsm = contract_smem_bytes(mcap, sizeof(T));
         for (int dd = 0; dd < D; ++dd) {
           mark("orb_gemm", 2);
           for (int sp = 0; sp < 2; ++sp)
@@ -443,8 +452,12 @@ struct Runner {
                      wbm(3, pl.wb_orb + kMaxSplit * ((int64_t)sp * D + dd) * n * d), n, O, n, rng + 2 * sp, 0, 0,
                      cap, n, d, nc_orb);
           mark("contract", 1);
-          contract_kernel<T><<<nb, 256, ctsm, s>>>(wc, n, n_up, K, mcap, dd, D, idx, cnt, rev, boff, O, Fenv, Ainv,
-                                                   gdet, ldet, st);
+          auto ck = contract_kernel<T, 1>;
+          if (maxt == 2) ck = contract_kernel<T, 2>;
+          else if (maxt == 3) ck = contract_kernel<T, 3>;
+          else if (maxt == 5) ck = contract_kernel<T, 5>;
+          else if (maxt == 9) ck = contract_kernel<T, 9>;
+          ck<<<nb, 256, ctsm, s>>>(wc, n, n_up, K, mcap, dd, D, idx, cnt, rev, boff, O, Fenv, Ainv, gdet, ldet, st);
       check("contract");
         }
       }
@@ -487,7 +500,11 @@ inline int set_smem_limits() {
     const int dyn = maxopt - (int)at.sharedSizeBytes;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) != cudaSuccess) rc = FIRE_ERR_CUDA;
   };
-  raise((const void*)contract_kernel<T>);
+  raise((const void*)contract_kernel<T, 1>);
+  raise((const void*)contract_kernel<T, 2>);
+  raise((const void*)contract_kernel<T, 3>);
+  raise((const void*)contract_kernel<T, 5>);
+  raise((const void*)contract_kernel<T, 9>);
   raise((const void*)lu_inverse_kernel<LT, T>);
   raise((const void*)lu_kernel<LT, 16>);
   raise((const void*)att_pool_kernel<T>);

@@ -52,7 +52,9 @@ static int launch(cudaStream_t s, const CUtensorMap& ma, const CUtensorMap& mb, 
   if (cudaFuncSetAttribute(tc_gemm_kernel<STAGES, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
       cudaSuccess)
     return FIRE_ERR_CUDA;
-  dim3 grid((unsigned)((m_cap + BM - 1) / BM), (unsigned)nt);
+  const int64_t mt = (m_cap + BM - 1) / BM;
+  if (mt > 65535) return FIRE_ERR_UNSUPPORTED;
+  dim3 grid((unsigned)nt, (unsigned)mt);
   tc_gemm_kernel<STAGES, NC><<<grid, 128, sm, s>>>(ma, mb, g);
   return cudaGetLastError() == cudaSuccess ? FIRE_OK : FIRE_ERR_CUDA;
 }

@@ -166,9 +166,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
 
   int64_t mb = g.m_begin, me = g.m_end;
   if (g.m_range) { mb = g.m_range[0]; me = g.m_range[1]; }
-  const int64_t m0 = mb + (int64_t)blockIdx.x * BM;
+  // N tiles vary fastest, so the CTAs that share an A tile run together and
+  // the second reads it from L2
+  const int64_t m0 = mb + (int64_t)blockIdx.y * BM;
   if (m0 >= me) return;                       // uniform across the CTA
-  const int n0 = blockIdx.y * g.BN;
+  const int n0 = blockIdx.x * g.BN;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int BN = g.BN;
   const uint32_t a_bytes = BM * BK * 2, b_bytes = (uint32_t)BN * BK * 2;

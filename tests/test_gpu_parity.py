@@ -186,3 +186,19 @@ def test_c26h24_matches_oracle(prec, tol_e):
     np.testing.assert_array_equal(out["sign"].cpu().numpy(), g["sign"])
     assert rel(out["logabs"].cpu().numpy(), g["logabs"]).max() < 1e-4
     assert rel(out["e_loc"].cpu().numpy(), g["e_loc"]).max() < tol_e
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_dense_limit_large_neighbourhoods(prec):
+    """c beyond the molecule: every electron has n-1 = 57 neighbours, the
+    largest contraction tiles; results must still match the oracle."""
+    s = synth.zigzag_polyene(8, cutoff=100.0)
+    arch = synth.Arch(width=128, n_layers=2, n_det=2)
+    p = synth.init_params(s, arch, 21)
+    r = synth.walkers(s, 2, 2121)
+    e, la, sg = O.local_energy(s, arch, p, r)
+    out = fire.Fire(s, arch, p, prec).local_energy(r)
+    np.testing.assert_array_equal(out["sign"].cpu().numpy(), sg)
+    assert out["info"]["k_required"] == 57
+    assert rel(out["logabs"].cpu().numpy(), la).max() < 1e-5
+    assert np.median(rel(out["e_loc"].cpu().numpy(), e)) < 1e-4
