@@ -162,8 +162,9 @@ static size_t layout(Plan& pl, int64_t Wc) {
 
 static size_t budget_bytes() {
   const char* e = getenv("FIRE_WORKSPACE_BUDGET_MB");
-  double mb = e ? atof(e) : 24576.0;
-  if (!(mb > 0)) mb = 24576.0;
+  // default: 64 GiB of the 280 GB of HBM3e; FIRE_WORKSPACE_BUDGET_MB overrides
+  double mb = e ? atof(e) : 65536.0;
+  if (!(mb > 0)) mb = 65536.0;
   return (size_t)(mb * 1024.0 * 1024.0);
 }
 
