@@ -197,6 +197,18 @@ int fire_logpsi(const fire_system_t* sys, const fire_arch_t* arch,
                 int32_t k_cap, int32_t precision, double* logabs, double* sign,
                 fire_info_t* info, void* ws, size_t ws_bytes, void* stream);
 
+/* Per-walker gradient d log|Psi| / d theta (Methods, eq. spring: the rows
+ * O_i of the SPRING update), by hand-written adjoint kernels over the value
+ * path, whose embeddings are recomputed in the call.  grad is [W][P] (device,
+ * P = fire_param_count(), layout of fire_param_layout()) in the dtype of theta
+ * (float64 for FIRE_PREC_FP64, float32 otherwise; the BF16_FP64 form
+ * computes its gradient in float32 with a float64 LU).  logabs and sign [W]
+ * as in fire_logpsi.  Walkers on a node give non-finite rows. */
+int fire_grad_logpsi(const fire_system_t* sys, const fire_arch_t* arch,
+                     const fire_params_t* params, int64_t n_walkers, const double* r,
+                     int32_t k_cap, int32_t precision, void* grad, double* logabs, double* sign,
+                     fire_info_t* info, void* ws, size_t ws_bytes, void* stream);
+
 /* Local energy E_L (Methods, eq. of E_L) with the exact Laplacian of
  * log|Psi| from the sparse forward Laplacian (Methods, "Efficient
  * Laplacian").  Outputs [W] float64 (device): e_loc, logabs, sign; e_kin and

@@ -5,6 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include "grad_bufs.h"
 #include "nbr.cuh"
 #include "pipeline.cuh"
 #include "plan.h"
@@ -154,6 +155,16 @@ static size_t layout(Plan& pl, int64_t Wc) {
     TAKE(wbf16, e * 2);
   } else {
     pl.wbf16 = 0;
+  }
+  if (dm.op == FIRE_OP_GRAD_LOGPSI) {
+    TAKE(poff_dev, P_COUNT * 8);
+    const size_t gb = ts == 8 ? GradBufs<double>::carve(nullptr, nullptr, Wc, (int)n, (int)d, dm.L, (int)D, (int)J,
+                                                         dm.R, (int)RD, (int)NE)
+                              : GradBufs<float>::carve(nullptr, nullptr, Wc, (int)n, (int)d, dm.L, (int)D, (int)J,
+                                                        dm.R, (int)RD, (int)NE);
+    TAKE(gradws, gb);
+  } else {
+    pl.poff_dev = pl.gradws = 0;
   }
 #undef TAKE
   pl.total = o;
@@ -368,9 +379,10 @@ int fire_neighbors(const fire_system_t* sys, int64_t W, const double* r, int32_t
 static int run_call(const fire_system_t* sys, const fire_arch_t* arch, const fire_params_t* params,
                     int64_t W, const double* r, int32_t k_cap, int32_t prec, int op, double* e_loc,
                     double* logabs, double* sign, double* e_kin, double* e_pot, fire_info_t* info,
-                    void* ws, size_t ws_bytes, void* stream) {
+                    void* ws, size_t ws_bytes, void* stream, void* grad = nullptr) {
   if (!params || !params->theta || !r || !logabs || !sign) return FIRE_ERR_INVALID_ARG;
   if (op == FIRE_OP_LOCAL_ENERGY && !e_loc) return FIRE_ERR_INVALID_ARG;
+  if (op == FIRE_OP_GRAD_LOGPSI && !grad) return FIRE_ERR_INVALID_ARG;
   Plan pl;
   int rc = make_plan(sys, arch, W, prec, k_cap, op, &pl);
   if (rc) return rc;
@@ -387,8 +399,9 @@ static int run_call(const fire_system_t* sys, const fire_arch_t* arch, const fir
   DevStatus hs;
   memset(&hs, 0, sizeof(hs));
   int64_t nl = 0;
+  pl.nparams = off;
   CallArgs a{sys, arch, params->theta, poff, W, r, e_loc, logabs, sign, e_kin, e_pot, ws,
-             (cudaStream_t)stream, &hs, &nl};
+             (cudaStream_t)stream, &hs, &nl, grad};
   if (prec == FIRE_PREC_FP64) rc = run_fp64(pl, a);
   else if (prec == FIRE_PREC_FP32) rc = run_fp32(pl, a);
   else rc = run_bf16(pl, a);
@@ -413,6 +426,13 @@ int fire_logpsi(const fire_system_t* sys, const fire_arch_t* arch, const fire_pa
                 fire_info_t* info, void* ws, size_t ws_bytes, void* stream) {
   return run_call(sys, arch, params, W, r, k_cap, precision, FIRE_OP_LOGPSI, nullptr, logabs, sign, nullptr,
                   nullptr, info, ws, ws_bytes, stream);
+}
+
+int fire_grad_logpsi(const fire_system_t* sys, const fire_arch_t* arch, const fire_params_t* params,
+                     int64_t W, const double* r, int32_t k_cap, int32_t precision, void* grad, double* logabs,
+                     double* sign, fire_info_t* info, void* ws, size_t ws_bytes, void* stream) {
+  return run_call(sys, arch, params, W, r, k_cap, precision, FIRE_OP_GRAD_LOGPSI, nullptr, logabs, sign, nullptr,
+                  nullptr, info, ws, ws_bytes, stream, grad);
 }
 
 int fire_local_energy(const fire_system_t* sys, const fire_arch_t* arch, const fire_params_t* params,

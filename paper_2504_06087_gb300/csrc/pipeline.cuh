@@ -31,6 +31,14 @@ enum ParamIndex {
   P_COUNT
 };
 
+}  // namespace fire
+
+#include "grad.cuh"
+#include "grad_bufs.h"
+#include "grad_util.cuh"
+
+namespace fire {
+
 struct CallArgs {
   const fire_system_t* sys;
   const fire_arch_t* arch;
@@ -43,6 +51,7 @@ struct CallArgs {
   cudaStream_t stream;
   DevStatus* host_status;    // filled after the call
   int64_t* n_launches;       // kernels launched (host out)
+  void* grad;                // [W][P] parameter gradient (gradient call only)
 };
 
 void set_last_error(const char* stage, const char* msg);
@@ -208,6 +217,312 @@ struct Runner {
     fl_act_kernel<T, T><<<nblk, 256, 0, s>>>(J, off, stride, Z, ldz, b2, Y, ldy, 0);
     const int64_t nrows_grid = cap;
     rowdot_kernel<T, T><<<(unsigned)((nrows_grid + 7) / 8), 256, 0, s>>>(Y, ldy, J, w3, F, range, rb, re);
+  }
+
+
+  // ---------------------------------------------------------------------
+  // d log|Psi| / d theta per walker: the value path with its intermediates
+  // kept, then the adjoint in reverse order.  Embeddings are recomputed here
+  // (no state is carried between calls).
+  // ---------------------------------------------------------------------
+  int run_grad() {
+    const fire_system_t* sys = a.sys;
+    const int n = dm.n, n_up = dm.n_up, n_dn = n - n_up, N = dm.N, d = dm.d, D = dm.D, K = dm.K, L = dm.L;
+    const int J = dm.J, R = dm.R, dr = dm.dr, RD = R * dr, E = dm.E, NE = N * E;
+    const int64_t Dn = (int64_t)D * n;
+    const int64_t P = pl.nparams;
+    const int64_t* po = a.poff;
+    DevStatus* st = at<DevStatus>(pl.status);
+    cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
+    int64_t* pod = at<int64_t>(pl.poff_dev);
+    cudaMemcpyAsync(pod, po, sizeof(int64_t) * P_COUNT, cudaMemcpyHostToDevice, s);
+    T* G = reinterpret_cast<T*>(a.grad);
+    for (int64_t ch = 0; ch < pl.nchunks; ++ch) {
+      const int64_t w0 = ch * pl.Wc;
+      const int wc = (int)((a.W - w0) < pl.Wc ? (a.W - w0) : pl.Wc);
+      const double* r = a.r + w0 * n * 3;
+      const int nb = wc * n;
+      T* g = G + w0 * P;
+      cudaMemsetAsync(g, 0, sizeof(T) * (size_t)wc * P, s);
+      GradBufs<T> B;
+      GradBufs<T>::carve(at<unsigned char>(pl.gradws), &B, pl.Wc, n, d, L, D, J, R, RD, NE);
+      int32_t* idx = at<int32_t>(pl.idx);
+      int32_t* cnt = at<int32_t>(pl.cnt);
+      int32_t* rev = at<int32_t>(pl.rev);
+      int64_t* brow = at<int64_t>(pl.blk_rows);
+      int64_t* boff = at<int64_t>(pl.blk_off);
+      int64_t* rng = at<int64_t>(pl.ranges);
+      const double c = sys->cutoff;
+      // segments of a walker's electrons in block order: up [w n_up, +n_up), down [Wc n_up + w n_dn, +n_dn)
+      auto tn_w = [&](const T* X, int64_t ldx, int Na, const T* Y, int64_t ldy, int Nb, int64_t goff, int64_t ldc,
+                      bool acc) {
+        tn_batched<T>(s, wc, Na, Nb, n_up, X, ldx, n_up * ldx, Y, ldy, n_up * ldy, g + goff, ldc, P, acc);
+        tn_batched<T>(s, wc, Na, Nb, n_dn, X + (int64_t)wc * n_up * ldx, ldx, n_dn * ldx,
+                      Y + (int64_t)wc * n_up * ldy, ldy, n_dn * ldy, g + goff, ldc, P, true);
+        launches += 2;
+      };
+      auto colsum_w = [&](const T* Y, int64_t ldy, int Nb, int64_t goff) {
+        colsum_batched<T>(s, wc, Nb, n_up, Y, ldy, n_up * ldy, g + goff, P, true);
+        colsum_batched<T>(s, wc, Nb, n_dn, Y + (int64_t)wc * n_up * ldy, ldy, n_dn * ldy, g + goff, P, true);
+        launches += 2;
+      };
+      // ---- forward (value rows: one row per electron block) ----
+      mark("neighbors", 3);
+      nbr_build_kernel<<<wc, 256, (size_t)n * 3 * sizeof(double), s>>>(wc, n, n_up, r, c * c, K, idx, cnt, brow, st, 0);
+      nbr_reverse_kernel<<<wc, 256, 0, s>>>(n, n_up, K, idx, cnt, rev);
+      blk_scan_kernel<<<1, 1024, 0, s>>>(nb, wc * n_up, brow, boff, rng, st);
+      T* S5 = at<T>(pl.S5);
+      T* Y5 = at<T>(pl.Y5);
+      T* Z5 = at<T>(pl.Z5);
+      T* P5 = at<T>(pl.P5);
+      T* H0 = at<T>(pl.H0);
+      T* PQ = at<T>(pl.PQ);
+      mark("fwd_embed", 8);
+      en_filter_kernel<T, T><<<nb, d, 0, s>>>(wc, n, n_up, N, d, r, sys->nuc_pos, sys->cutoff_nuc, p, S5, 1);
+      ln_fl_kernel<T, T><<<nb, d, 0, s>>>(d, S5, Y5, p.ln_gamma, p.ln_beta, 1);
+      gemm<T>(s, Y5, d, p.glu_wg, d, false, Z5, 2 * d, 0, nb, nullptr, nb, d, d);
+      gemm<T>(s, Y5, d, p.glu_wv, d, false, Z5 + d, 2 * d, 0, nb, nullptr, nb, d, d);
+      glu_gate_kernel<T><<<nb, d, 0, s>>>(d, Z5, P5, 1);
+      gemm<T>(s, P5, d, p.glu_wo, d, false, H0, d, 0, nb, nullptr, nb, d, d);
+      for (int part = 0; part < 2; ++part)
+        gemm<T>(s, H0, d, p.msg_w + (int64_t)part * d * d, d, false, PQ + (int64_t)part * 2 * d, 4 * d, 0, nb,
+                nullptr, nb, d, d, 2, 0, (int64_t)(2 * d + 4) * d, d);
+      T* H1 = B.HL;
+      msg_kernel<T, T><<<nb, d, 0, s>>>(wc, n, n_up, d, K, r, c, p, idx, cnt, boff, H0, PQ, H1, nullptr, 1, 0, 0);
+      mark("fwd_mlp", 3 * L);
+      for (int l = 0; l < L; ++l) {
+        T* hin = B.HL + (int64_t)l * nb * d;
+        T* hout = B.HL + (int64_t)(l + 1) * nb * d;
+        T* z = B.ZL + (int64_t)l * nb * d;
+        gemm<T>(s, hin, d, p.mlp_w + (int64_t)l * d * d, d, false, z, d, 0, nb, nullptr, nb, d, d);
+        cudaMemcpyAsync(hout, hin, sizeof(T) * (size_t)nb * d, cudaMemcpyDeviceToDevice, s);
+        fl_act_kernel<T, T><<<nb, 256, 0, s>>>(d, nullptr, 1, z, d, p.mlp_b + (int64_t)l * d, hout, d, 1);
+      }
+      const T* h = B.HL + (int64_t)L * nb * d;
+      T* jval = at<T>(pl.jval); T* jsign = at<T>(pl.jsign);
+      T* aval = at<T>(pl.aval); T* asign = at<T>(pl.asign);
+      T* cval = at<T>(pl.cval); T* vpot = at<T>(pl.vpot);
+      T* F[2] = {at<T>(pl.F1), at<T>(pl.F2)};
+      const T* jw1[2] = {p.jm1_w1, p.jm2_w1};
+      const T* jb1[2] = {p.jm1_b1, p.jm2_b1};
+      const T* jw2[2] = {p.jm1_w2, p.jm2_w2};
+      const T* jb2[2] = {p.jm1_b2, p.jm2_b2};
+      const T* jw3[2] = {p.jm1_w3, p.jm2_w3};
+      if (dm.flags & FIRE_J_MLP) {
+        mark("fwd_jastrow", 11);
+        for (int k = 0; k < 2; ++k) {
+          gemm<T>(s, h, d, jw1[k], J, false, B.JZ1[k], J, 0, nb, nullptr, nb, J, d);
+          fl_act_kernel<T, T><<<nb, 256, 0, s>>>(J, nullptr, 1, B.JZ1[k], J, jb1[k], B.JA1[k], J, 0);
+          gemm<T>(s, B.JA1[k], J, jw2[k], J, false, B.JZ2[k], J, 0, nb, nullptr, nb, J, J);
+          fl_act_kernel<T, T><<<nb, 256, 0, s>>>(J, nullptr, 1, B.JZ2[k], J, jb2[k], B.JA2[k], J, 0);
+          rowdot_kernel<T, T><<<(unsigned)((nb + 7) / 8), 256, 0, s>>>(B.JA2[k], J, J, jw3[k], F[k], nullptr, 0, nb);
+        }
+        jmlp_reduce_kernel<T, T><<<wc, 256, 0, s>>>(wc, n, n_up, K, idx, cnt, rev, boff, F[0], F[1], p.jm1_b3,
+                                                    p.jm2_b3, jval, jsign, nullptr, nullptr, 0);
+      }
+      const int64_t ldsu = R + RD;
+      T* V = at<T>(pl.V);
+      T* Gv[2] = {at<T>(pl.G1), at<T>(pl.G2)};
+      const T* vw1[2] = {p.ja1_w1, p.ja2_w1};
+      const T* vb1[2] = {p.ja1_b1, p.ja2_b1};
+      const T* vw2[2] = {p.ja1_w2, p.ja2_w2};
+      const T* vb2[2] = {p.ja1_b2, p.ja2_b2};
+      const T* vw3[2] = {p.ja1_w3, p.ja2_w3};
+      if (dm.flags & FIRE_J_ATT) {
+        mark("fwd_att", 14);
+        gemm<T>(s, h, d, p.att_q, d, true, B.SU, ldsu, 0, nb, nullptr, nb, R, d);
+        gemm<T>(s, h, d, p.att_wv, dr, false, B.SU + R, ldsu, 0, nb, nullptr, nb, dr, d, R, 0, (int64_t)d * dr, dr);
+        const int bt = ((RD + 31) / 32) * 32;
+        att_pool_kernel<T><<<wc, bt, (size_t)(R + n * R) * sizeof(T), s>>>(wc, n, n_up, K, R, dr, idx, cnt, rev,
+                                                                          boff, B.SU, ldsu, V, 0);
+        for (int k = 0; k < 2; ++k) {
+          gemm<T>(s, V, RD, vw1[k], J, false, B.VZ1[k], J, 0, wc, nullptr, wc, J, RD);
+          fl_act_kernel<T, T><<<wc, 256, 0, s>>>(J, nullptr, 1, B.VZ1[k], J, vb1[k], B.VA1[k], J, 0);
+          gemm<T>(s, B.VA1[k], J, vw2[k], J, false, B.VZ2[k], J, 0, wc, nullptr, wc, J, J);
+          fl_act_kernel<T, T><<<wc, 256, 0, s>>>(J, nullptr, 1, B.VZ2[k], J, vb2[k], B.VA2[k], J, 0);
+          rowdot_kernel<T, T><<<(unsigned)((wc + 7) / 8), 256, 0, s>>>(B.VA2[k], J, J, vw3[k], Gv[k], nullptr, 0, wc);
+        }
+        att_reduce_kernel<T, T><<<wc, 256, 0, s>>>(n, Gv[0], Gv[1], p.ja1_b3, p.ja2_b3, aval, asign, nullptr, nullptr, 0);
+      }
+      mark("fwd_orbitals", 8);
+      coulomb_cusp_kernel<T, T><<<wc, 256, 0, s>>>(n, n_up, N, r, sys->nuc_pos, sys->nuc_charge, p.cusp, vpot, cval,
+                                                   nullptr, nullptr, 0);
+      T* Qf = at<T>(pl.Qf);
+      T* Fenv = at<T>(pl.Fenv);
+      T* Ov = at<T>(pl.Ov);
+      env_feat_kernel<T, T><<<nb, 128, 0, s>>>(wc, n, n_up, N, E, r, sys->nuc_pos, p.env_sigma, Qf, 1);
+      const int64_t upv = (int64_t)wc * n_up;
+      for (int sp = 0; sp < 2; ++sp) {
+        const int64_t rb = sp ? upv : 0, re = sp ? nb : upv;
+        if (re <= rb) continue;
+        gemm<T>(s, Qf, NE, p.env_pi + (int64_t)sp * Dn * NE, NE, true, Fenv, Dn, rb, re, nullptr, re - rb, (int)Dn, NE);
+        gemm<T>(s, h, d, p.orb_w + (int64_t)sp * D * d * n, n, false, Ov, Dn, rb, re, nullptr, re - rb, n, d, D, 0,
+                (int64_t)d * n, n);
+      }
+      LT* LUb = at<LT>(pl.LU);
+      int32_t* piv = at<int32_t>(pl.piv);
+      double* ldabs = at<double>(pl.ldabs);
+      double* lsign = at<double>(pl.lsign);
+      const bool gj = sizeof(T) == 4 && n <= 192;
+      phi_assemble_kernel<T, LT><<<wc * D, 256, 0, s>>>(wc, n, n_up, D, Ov, Fenv, 1, LUb, gj ? B.Phif : nullptr);
+      lu_kernel<LT, 16><<<wc * D, 256, (size_t)2 * n * 16 * sizeof(LT), s>>>(n, LUb, piv, ldabs, lsign);
+      if (gj) {
+        const int Gq = (n + 7) / 8;
+        gj_inverse_kernel<float, T><<<wc * D, ((Gq * Gq + 31) / 32) * 32, gj_smem_bytes(n), s>>>(n, B.Phif, B.AT);
+      } else {
+        lu_inverse_kernel<LT, T><<<wc * D, 256, (size_t)n * n * sizeof(T) + 2 * n * sizeof(int), s>>>(n, LUb, piv, B.AT);
+      }
+      FinalIn<T, RT> fi{ldabs, lsign, nullptr, nullptr, cval, nullptr, nullptr, jval, jsign, nullptr, nullptr,
+                        aval, asign, nullptr, nullptr, vpot};
+      final_kernel<T, RT><<<wc, 256, 0, s>>>(n, D, dm.flags, fi, 0, nullptr, a.logabs + w0, a.sign + w0, nullptr,
+                                             nullptr, st);
+      check("grad forward");
+      // ---- backward ----
+      mark("bwd_orbitals", 0);
+      det_bwd_kernel<T><<<wc * D, 256, 0, s>>>(wc, n, n_up, D, ldabs, lsign, B.AT, Ov, Fenv, B.dO, B.dF);
+      ++launches;
+      cudaMemsetAsync(B.dH, 0, sizeof(T) * (size_t)nb * d, s);
+      for (int sp = 0; sp < 2; ++sp) {
+        const int64_t rb = sp ? upv : 0, re = sp ? nb : upv;
+        if (re <= rb) continue;
+        const int ns = sp ? n_dn : n_up;
+        for (int dd = 0; dd < D; ++dd) {
+          const int64_t wo = po[P_ORB_W] + ((int64_t)sp * D + dd) * d * n;
+          const int64_t pi_o = po[P_ENV_PI] + ((int64_t)sp * D + dd) * n * NE;
+          const T* Xs = h + rb * d;
+          tn_batched<T>(s, wc, d, n, ns, Xs, d, (int64_t)ns * d, B.dO + rb * Dn + dd * n, Dn, (int64_t)ns * Dn,
+                        g + wo, n, P, false);
+          tn_batched<T>(s, wc, n, NE, ns, B.dF + rb * Dn + dd * n, Dn, (int64_t)ns * Dn, Qf + rb * NE, NE,
+                        (int64_t)ns * NE, g + pi_o, NE, P, false);
+          gemm<T>(s, B.dO + dd * n, Dn, p.orb_w + ((int64_t)sp * D + dd) * d * n, n, true, B.dH, d, rb, re, nullptr,
+                  re - rb, d, n, 1, 0, 0, 0, true);
+          launches += 3;
+        }
+        gemm<T>(s, B.dF, Dn, p.env_pi + (int64_t)sp * Dn * NE, NE, false, B.dQf, NE, rb, re, nullptr, re - rb, NE,
+                (int)Dn);
+        ++launches;
+      }
+      env_sigma_bwd_kernel<T><<<wc, 128, 0, s>>>(wc, n, n_up, N, E, r, sys->nuc_pos, Qf, B.dQf, g, P, po[P_ENV_SIGMA]);
+      ++launches;
+      check("bwd orbitals");
+      if (dm.flags & FIRE_J_MLP) {
+        mark("bwd_jastrow", 0);
+        const int64_t jo[2][6] = {{po[P_JM1_W1], po[P_JM1_B1], po[P_JM1_W2], po[P_JM1_B2], po[P_JM1_W3], po[P_JM1_B3]},
+                                  {po[P_JM2_W1], po[P_JM2_B1], po[P_JM2_W2], po[P_JM2_B2], po[P_JM2_W3], po[P_JM2_B3]}};
+        for (int k = 0; k < 2; ++k) {
+          jseed_kernel<T><<<wc, 256, 0, s>>>(wc, n, n_up, J, F[1], p.jm2_b3, jw3[k], k, B.df, B.dY2);
+          tn_w(B.df, 1, 1, B.JA2[k], J, J, jo[k][4], J, true);
+          colsum_w(B.df, 1, 1, jo[k][5]);
+          silu_bwd_kernel<T, T><<<(unsigned)(((int64_t)nb * J + 255) / 256), 256, 0, s>>>(nb, J, B.dY2, J, B.JZ2[k], J,
+                                                                                         jb2[k], B.dZ2, J);
+          tn_w(B.JA1[k], J, J, B.dZ2, J, J, jo[k][2], J, true);
+          colsum_w(B.dZ2, J, J, jo[k][3]);
+          gemm<T>(s, B.dZ2, J, jw2[k], J, true, B.dA1, J, 0, nb, nullptr, nb, J, J);
+          silu_bwd_kernel<T, T><<<(unsigned)(((int64_t)nb * J + 255) / 256), 256, 0, s>>>(nb, J, B.dA1, J, B.JZ1[k], J,
+                                                                                         jb1[k], B.dZ1, J);
+          tn_w(h, d, d, B.dZ1, J, J, jo[k][0], J, true);
+          colsum_w(B.dZ1, J, J, jo[k][1]);
+          gemm<T>(s, B.dZ1, J, jw1[k], J, true, B.dH, d, 0, nb, nullptr, nb, d, J, 1, 0, 0, 0, true);
+          launches += 5;
+        }
+      }
+      if (dm.flags & FIRE_J_ATT) {
+        mark("bwd_att", 0);
+        const int64_t vo[2][6] = {{po[P_JA1_W1], po[P_JA1_B1], po[P_JA1_W2], po[P_JA1_B2], po[P_JA1_W3], po[P_JA1_B3]},
+                                  {po[P_JA2_W1], po[P_JA2_B1], po[P_JA2_W2], po[P_JA2_B2], po[P_JA2_W3], po[P_JA2_B3]}};
+        cudaMemsetAsync(B.dV, 0, sizeof(T) * (size_t)wc * RD, s);
+        for (int k = 0; k < 2; ++k) {
+          vseed_kernel<T><<<wc, 256, 0, s>>>(J, Gv[1], p.ja2_b3, vw3[k], k, B.dfv, B.dVY2);
+          tn_batched<T>(s, wc, 1, J, 1, B.dfv, 1, 1, B.VA2[k], J, J, g + vo[k][4], J, P, true);
+          colsum_batched<T>(s, wc, 1, 1, B.dfv, 1, 1, g + vo[k][5], P, true);
+          silu_bwd_kernel<T, T><<<(unsigned)(((int64_t)wc * J + 255) / 256), 256, 0, s>>>(wc, J, B.dVY2, J, B.VZ2[k],
+                                                                                         J, vb2[k], B.dVZ2, J);
+          tn_batched<T>(s, wc, J, J, 1, B.VA1[k], J, J, B.dVZ2, J, J, g + vo[k][2], J, P, true);
+          colsum_batched<T>(s, wc, J, 1, B.dVZ2, J, J, g + vo[k][3], P, true);
+          gemm<T>(s, B.dVZ2, J, vw2[k], J, true, B.dVA1, J, 0, wc, nullptr, wc, J, J);
+          silu_bwd_kernel<T, T><<<(unsigned)(((int64_t)wc * J + 255) / 256), 256, 0, s>>>(wc, J, B.dVA1, J, B.VZ1[k],
+                                                                                         J, vb1[k], B.dVZ1, J);
+          tn_batched<T>(s, wc, RD, J, 1, V, RD, RD, B.dVZ1, J, J, g + vo[k][0], J, P, true);
+          colsum_batched<T>(s, wc, J, 1, B.dVZ1, J, J, g + vo[k][1], P, true);
+          gemm<T>(s, B.dVZ1, J, vw1[k], J, true, B.dV, RD, 0, wc, nullptr, wc, RD, J, 1, 0, 0, 0, true);
+          launches += 11;
+        }
+        const size_t absm = (size_t)(2 * n * R + 3 * R) * sizeof(T);
+        const int bt = ((RD + 31) / 32) * 32;
+        att_bwd_kernel<T><<<wc, bt, absm, s>>>(wc, n, n_up, R, dr, B.SU, ldsu, B.dV, B.dSU);
+        tn_w(B.dSU, ldsu, R, h, d, d, po[P_ATT_Q], d, true);
+        for (int rr = 0; rr < R; ++rr)
+          tn_w(h, d, d, B.dSU + R + rr * dr, ldsu, dr, po[P_ATT_WV] + (int64_t)rr * d * dr, dr, true);
+        gemm<T>(s, B.dSU, ldsu, p.att_q, d, false, B.dH, d, 0, nb, nullptr, nb, d, R, 1, 0, 0, 0, true);
+        for (int rr = 0; rr < R; ++rr)
+          gemm<T>(s, B.dSU + R + rr * dr, ldsu, p.att_wv + (int64_t)rr * d * dr, dr, true, B.dH, d, 0, nb, nullptr, nb,
+                  d, dr, 1, 0, 0, 0, true);
+        launches += 2 + 2 * R;
+      }
+      if (dm.flags & FIRE_J_CUSP) {
+        cusp_bwd_kernel<T><<<wc, 256, 0, s>>>(n, n_up, r, p.cusp, g, P, po[P_CUSP]);
+        ++launches;
+      }
+      check("bwd jastrow");
+      // embedding MLP, layer by layer
+      mark("bwd_mlp", 0);
+      for (int l = L - 1; l >= 0; --l) {
+        const T* hin = B.HL + (int64_t)l * nb * d;
+        const T* z = B.ZL + (int64_t)l * nb * d;
+        silu_bwd_kernel<T, T><<<(unsigned)(((int64_t)nb * d + 255) / 256), 256, 0, s>>>(nb, d, B.dH, d, z, d,
+                                                                                       p.mlp_b + (int64_t)l * d, B.dZ, d);
+        tn_w(hin, d, d, B.dZ, d, d, po[P_MLP_W] + (int64_t)l * d * d, d, true);
+        colsum_w(B.dZ, d, d, po[P_MLP_B] + (int64_t)l * d);
+        gemm<T>(s, B.dZ, d, p.mlp_w + (int64_t)l * d * d, d, true, B.dH, d, 0, nb, nullptr, nb, d, d, 1, 0, 0, 0, true);
+        launches += 2;
+      }
+      // message passing (dH now holds d/dh^1)
+      mark("bwd_msg", 0);
+      cudaMemsetAsync(B.dQm, 0, sizeof(T) * (size_t)nb * 2 * d, s);
+      msg_bwd_kernel<T, T><<<nb, d, 0, s>>>(wc, n, n_up, d, K, r, c, p, idx, cnt, PQ, B.dH, B.dPm, B.dQm, g, P, pod);
+      cudaMemcpyAsync(B.dH0, B.dH, sizeof(T) * (size_t)nb * d, cudaMemcpyDeviceToDevice, s);
+      for (int al = 0; al < 2; ++al) {
+        const int64_t wa = po[P_MSG_W] + (int64_t)al * (2 * d + 4) * d;
+        tn_w(H0, d, d, B.dPm + (int64_t)al * d, 2 * d, d, wa, d, true);
+        tn_w(H0, d, d, B.dQm + (int64_t)al * d, 2 * d, d, wa + (int64_t)d * d, d, true);
+        gemm<T>(s, B.dPm + (int64_t)al * d, 2 * d, p.msg_w + (int64_t)al * (2 * d + 4) * d, d, true, B.dH0, d, 0, nb,
+                nullptr, nb, d, d, 1, 0, 0, 0, true);
+        gemm<T>(s, B.dQm + (int64_t)al * d, 2 * d, p.msg_w + (int64_t)al * (2 * d + 4) * d + (int64_t)d * d, d, true,
+                B.dH0, d, 0, nb, nullptr, nb, d, d, 1, 0, 0, 0, true);
+      }
+      launches += 6;
+      check("bwd msg");
+      // GLU and LayerNorm
+      mark("bwd_glu", 0);
+      gemm<T>(s, B.dH0, d, p.glu_wo, d, true, B.dP5, d, 0, nb, nullptr, nb, d, d);
+      tn_w(P5, d, d, B.dH0, d, d, po[P_GLU_WO], d, true);
+      gate_bwd_kernel<T><<<(unsigned)(((int64_t)nb * d + 255) / 256), 256, 0, s>>>(nb, d, Z5, B.dP5, B.dZ5);
+      tn_w(Y5, d, d, B.dZ5, 2 * d, d, po[P_GLU_WG], d, true);
+      tn_w(Y5, d, d, B.dZ5 + d, 2 * d, d, po[P_GLU_WV], d, true);
+      gemm<T>(s, B.dZ5, 2 * d, p.glu_wg, d, true, B.dY5, d, 0, nb, nullptr, nb, d, d);
+      gemm<T>(s, B.dZ5 + d, 2 * d, p.glu_wv, d, true, B.dY5, d, 0, nb, nullptr, nb, d, d, 1, 0, 0, 0, true);
+      ln_bwd_kernel<T, T><<<nb, d, 0, s>>>(d, S5, B.dY5, p.ln_gamma, B.dS5, B.dyx);
+      colsum_w(B.dyx, d, d, po[P_LN_GAMMA]);
+      colsum_w(B.dY5, d, d, po[P_LN_BETA]);
+      launches += 6;
+      // electron-nucleus filters
+      mark("bwd_en", 1);
+      en_bwd_kernel<T, T><<<nb, d, 0, s>>>(wc, n, n_up, N, d, r, sys->nuc_pos, sys->cutoff_nuc, p, B.dS5, g, P, pod);
+      check("bwd en");
+    }
+    mark("end", 0);
+    check("final");
+    flush_marks();
+    if (a.n_launches) *a.n_launches = launches;
+    if (failed) return FIRE_ERR_CUDA;
+    {
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) { set_last_error("launch", cudaGetErrorString(e)); return FIRE_ERR_CUDA; }
+    }
+    if (cudaMemcpyAsync(a.host_status, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return FIRE_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return FIRE_ERR_CUDA;
+    return FIRE_OK;
   }
 
   int run() {

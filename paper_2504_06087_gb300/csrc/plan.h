@@ -34,6 +34,9 @@ struct Plan {
   size_t jval, jsign, jgrad, jlap, aval, asign, agrad, alap, cval, cgrad, clap, vpot;
   size_t V, VZ, VY, G1, G2;
   size_t wbf16;            // packed BF16 weights (tensor-core form)
+  size_t poff_dev;         // device copy of the parameter offsets (gradient call)
+  size_t gradws;           // gradient scratch region (GradBufs)
+  int64_t nparams;
   size_t total;
   // column layout of `big`
   int64_t ld_big, zcol, ycol, sucol;

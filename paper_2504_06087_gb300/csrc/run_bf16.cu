@@ -8,7 +8,8 @@ int run_bf16(const Plan& pl, const CallArgs& a) {
   int rc = set_smem_limits<float, double>();
   if (rc) return rc;
   Runner<float, double, double> rn(pl, a);
-  return rn.run();
+  // the gradient of the BF16_FP64 form runs in fp32 (FP64 LU)
+  return pl.dm.op == FIRE_OP_GRAD_LOGPSI ? rn.run_grad() : rn.run();
 }
 
 }  // namespace fire

@@ -102,6 +102,8 @@ SIGNATURES = {
                                    ctypes.c_int32, VP, VP, P(Info), VP, ctypes.c_size_t, VP]),
     "fire_local_energy": (ctypes.c_int, [P(System), P(Arch), P(Params), ctypes.c_int64, VP, ctypes.c_int32,
                                          ctypes.c_int32, VP, VP, VP, VP, VP, P(Info), VP, ctypes.c_size_t, VP]),
+    "fire_grad_logpsi": (ctypes.c_int, [P(System), P(Arch), P(Params), ctypes.c_int64, VP, ctypes.c_int32,
+                                        ctypes.c_int32, VP, VP, VP, P(Info), VP, ctypes.c_size_t, VP]),
     "fire_local_energy_static": (ctypes.c_int, [P(System), P(Arch), P(Params), ctypes.c_int64, VP,
                                                 ctypes.c_int32, ctypes.c_int32, VP, VP, VP, VP, VP, P(Info), VP]),
 }
@@ -316,6 +318,31 @@ class Fire:
         if check and rc != 0:
             raise FireError(rc, "fire_logpsi", out["info"])
         return out
+
+    def grad_logpsi(self, r, check: bool = True):
+        """Per-walker d log|Psi| / d theta: {"grad": [W, P], "logabs", "sign"}."""
+        r = self._r(r)
+        W = r.shape[0]
+        dt = torch.float64 if self.prec == 0 else torch.float32
+        out = {"grad": torch.empty((W, self.n_params), dtype=dt, device=self.device),
+               "logabs": torch.empty(W, dtype=torch.float64, device=self.device),
+               "sign": torch.empty(W, dtype=torch.float64, device=self.device)}
+        ws = self.workspace(W, OP_GRAD_LOGPSI)
+        info = Info()
+        rc = lib().fire_grad_logpsi(ctypes.byref(self.sys_c), ctypes.byref(self.arch_c),
+                                    ctypes.byref(self.params_c), W, _ptr(r), self.k_cap, self.prec,
+                                    _ptr(out["grad"]), _ptr(out["logabs"]), _ptr(out["sign"]), ctypes.byref(info),
+                                    _ptr(ws), ws.numel(), self._stream())
+        out["info"] = info.as_dict()
+        out["status"] = rc
+        if check and rc != 0:
+            raise FireError(rc, "fire_grad_logpsi", out["info"])
+        return out
+
+    def unflatten(self, flat):
+        """{name: array [..., *shape]} views of a flat parameter-sized last axis."""
+        return {name: flat[..., off:off + int(np.prod(shape))].reshape(*flat.shape[:-1], *shape)
+                for name, off, shape in self.layout}
 
     def neighbors(self, r):
         r = self._r(r)

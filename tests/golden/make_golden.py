@@ -6,6 +6,7 @@ so a test can confirm that it regenerates the same walkers and parameters.
 
     python tests/golden/make_golden.py c8h10 8
     python tests/golden/make_golden.py c26h24 2
+    python tests/golden/make_golden.py c26h24 16 grad
 """
 import hashlib
 import json
@@ -63,5 +64,31 @@ def main(key: str, nw: int):
     print(path, out["seconds"])
 
 
+
+
+def main_grad(key: str, nw: int, nidx: int = 64):
+    """Oracle d log|Psi| / d theta at nidx seeded flat indices, per walker."""
+    w = synth.workload(key)
+    r, p = synth.make_inputs(w, nw)
+    spec = synth.param_spec(w.system, w.arch)
+    sizes = [int(np.prod(s)) for _, s in spec]
+    offs = np.cumsum([0] + sizes[:-1])
+    idx = np.sort(np.random.default_rng(4).choice(int(sum(sizes)), size=nidx, replace=False))
+    t0 = time.time()
+    g = O.grad_logpsi(w.system, w.arch, p, r)
+    flat = np.concatenate([g[name].reshape(nw, -1) for name, _ in spec], axis=1)
+    out = {"workload": key, "n_walkers": nw, "input_sha256": input_hash(r, p),
+           "input_summary": input_summary(r, p),
+           "source": "oracle/fire_oracle.py grad_logpsi (FP64, autograd)", "seconds": time.time() - t0,
+           "flat_index": idx.tolist(), "grad": flat[:, idx].tolist()}
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"{key}_grad_oracle.json")
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+    print(path, out["seconds"])
+
+
 if __name__ == "__main__":
-    main(sys.argv[1], int(sys.argv[2]))
+    if len(sys.argv) > 3 and sys.argv[3] == "grad":
+        main_grad(sys.argv[1], int(sys.argv[2]))
+    else:
+        main(sys.argv[1], int(sys.argv[2]))
