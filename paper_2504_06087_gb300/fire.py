@@ -226,6 +226,14 @@ class Fire:
         self.theta = torch.as_tensor(flat, device=self.device)
         self.params_c = Params(self.theta.data_ptr(), self.n_params, 0 if self.prec == 0 else 1, 0)
 
+    def set_theta(self, theta: torch.Tensor):
+        """Use a flat device parameter tensor (layout of fire_param_layout) as theta."""
+        dt = torch.float64 if self.prec == 0 else torch.float32
+        t = theta.detach().to(device=self.device, dtype=dt).contiguous()
+        assert t.numel() == self.n_params
+        self.theta = t
+        self.params_c = Params(self.theta.data_ptr(), self.n_params, 0 if self.prec == 0 else 1, 0)
+
     def workspace(self, W: int, op: int) -> torch.Tensor:
         key = (W, op)
         if key not in self._ws:
@@ -354,3 +362,30 @@ class Fire:
         rc = lib().fire_neighbors(ctypes.byref(self.sys_c), W, _ptr(r), self.k_cap, _ptr(idx), _ptr(cnt),
                                   ctypes.byref(kreq), _ptr(ws), ws.numel(), self._stream())
         return {"idx": idx, "cnt": cnt, "k_required": kreq.value, "status": rc}
+
+
+class LogPsi(torch.autograd.Function):
+    """log|Psi(r; theta)| as a differentiable function of the flat parameter
+    tensor theta.  Forward: fire_logpsi.  Backward: fire_grad_logpsi (the
+    adjoint kernels, embeddings recomputed) contracted with the incoming
+    gradient: d/dtheta sum_w g_w log|Psi_w| = sum_w g_w O_w.  Positions get
+    no gradient."""
+
+    @staticmethod
+    def forward(ctx, theta: torch.Tensor, r: torch.Tensor, model: "Fire"):
+        model.set_theta(theta)
+        out = model.logpsi(r)
+        ctx.model = model
+        ctx.save_for_backward(theta, r)
+        return out["logabs"]
+
+    @staticmethod
+    def backward(ctx, g):
+        theta, r = ctx.saved_tensors
+        ctx.model.set_theta(theta)
+        rows = ctx.model.grad_logpsi(r)["grad"]
+        return (g.to(rows.dtype) @ rows).to(theta.dtype), None, None
+
+
+def logpsi(theta: torch.Tensor, r: torch.Tensor, model: "Fire") -> torch.Tensor:
+    return LogPsi.apply(theta, r, model)

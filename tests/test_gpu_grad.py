@@ -77,3 +77,20 @@ def test_c26h24_fp32_gradient_matches_stored_oracle():
     assert norm.max() < 1e-4, norm
     err = np.abs(got - ref) / np.maximum(np.abs(ref), 1.0)
     assert err.max() < 5e-3, float(err.max())
+
+
+def test_autograd_function_contracts_the_walker_rows():
+    """torch.autograd through fire.LogPsi: the gradient of sum_w c_w log|Psi_w|
+    equals the oracle's sum_w c_w d log|Psi_w| / d theta."""
+    w = synth.workload("water")
+    r, p = synth.make_inputs(w, 3)
+    f = fire.Fire(w.system, w.arch, p, "fp64")
+    theta = f.theta.clone().requires_grad_(True)
+    coef = torch.tensor([0.5, -1.25, 2.0], dtype=torch.float64, device=theta.device)
+    la = fire.logpsi(theta, torch.as_tensor(r, device=theta.device), f)
+    (gt,) = torch.autograd.grad((coef * la).sum(), theta)
+    ref = O.grad_logpsi(w.system, w.arch, p, r)
+    flat_ref = np.concatenate([np.tensordot(coef.cpu().numpy(), ref[name].reshape(3, -1), axes=1)
+                               for name, _, _ in f.layout])
+    err = np.abs(gt.cpu().numpy() - flat_ref) / np.maximum(np.abs(flat_ref), 1.0)
+    assert err.max() < 1e-9
