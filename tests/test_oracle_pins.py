@@ -13,23 +13,7 @@ import torch
 
 from paper_2504_06087_gb300 import synth
 from oracle import fire_oracle as O
-
-
-def const_h_params(system, arch, seed=0, bias=1.0):
-    """Parameters that make every embedding h_i the same constant vector.
-
-    nuc_emb = 0 and the feature weights 0 make the filter sum vanish, so
-    LN(0) = beta = 0 and h^0 = GLU(0) = 0; zero message weights keep h^1 = 0;
-    zero MLP matrices with bias b give h = L * SiLU(b) in every component.
-    """
-    p = synth.init_params(system, arch, seed)
-    p["nuc_emb"][:] = 0.0
-    p["en_wfeat"][:] = 0.0
-    p["msg_w"][:] = 0.0
-    p["msg_b"][:] = 0.0
-    p["mlp_w"][:] = 0.0
-    p["mlp_b"][:] = bias
-    return p
+from recipes import const_h_params
 
 
 # ---------------------------------------------------------------------------
