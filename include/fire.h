@@ -219,6 +219,47 @@ int fire_local_energy(const fire_system_t* sys, const fire_arch_t* arch,
                       double* sign, double* e_kin, double* e_pot, fire_info_t* info,
                       void* ws, size_t ws_bytes, void* stream);
 
+/* Metropolis sweeps of single-electron moves with local recompute and
+ * low-rank updates (Methods, "Improved Monte Carlo sampling" and "Low-rank
+ * updates"; Supplementary "Hyperparameters": Gaussian single-electron moves).
+ *
+ * One sweep moves electron k = 0 .. n_el-1 in turn in every walker:
+ * r'_k = r_k + sigma xi, xi ~ N(0, I_3), accepted iff ln u < 2 ln|Psi'/Psi|.
+ * The update set U = {k} and every electron within c of r_k or r'_k is
+ * recomputed (h^0 of k, messages, MLP, orbital rows, Jastrow terms of U);
+ * the determinant ratios come from the |U| x |U| matrix determinant lemma
+ * with the cached inverse (float64 LU of the small matrix) and an accepted
+ * move updates the inverse by the Woodbury identity.
+ *
+ * Random numbers: Philox4x32-10 with key (seed low word, seed high word) and
+ * counter (move low word, move high word, walker, stream), move =
+ * *counter + sweep * n_el + k; stream 0 gives xi by Box-Muller in float64,
+ * stream 1 the uniform u; uniforms are (x + 1/2) / 2^32.  *counter (host,
+ * in/out) advances by n_sweeps * n_el.
+ *
+ * r [W][n_el][3] float64 (device, in/out).  The cached state lives in the
+ * workspace (fire_workspace_size() with FIRE_OP_MCMC; the call holds every
+ * walker at once, it does not chunk) and is built by a value forward at the
+ * start of the call, rebuilt every refresh_every moves (0: only at the end)
+ * and at the end; max_drift (host out, may be NULL) is the largest
+ * |log|Psi|| difference between the carried value and a rebuild.
+ * Precision: FIRE_PREC_FP64 keeps the state in float64; FIRE_PREC_FP32 and
+ * FIRE_PREC_BF16_FP64 keep it in float32 with float64 determinant lemmas,
+ * LU factorisations and refresh inverses (no tensor cores).
+ * Outputs: logabs, sign [W] float64 (device, may be NULL) at the final
+ * positions (from the final rebuild); accepted [W] int32 (device, may be
+ * NULL): accepted moves per walker; *n_accepted (host, may be NULL) their
+ * total.  Errors: FIRE_ERR_INVALID_ARG for sigma <= 0, n_sweeps < 0,
+ * refresh_every < 0 or a missing pointer (before any launch);
+ * FIRE_ERR_CAPACITY if an update set or a neighbour list exceeded its
+ * capacity (|U| <= min(n_el, 2 k_cap + 1)); FIRE_ERR_NONFINITE as in
+ * fire_logpsi. */
+int fire_mcmc_step(const fire_system_t* sys, const fire_arch_t* arch, const fire_params_t* params,
+                   int64_t n_walkers, double* r, int32_t k_cap, int32_t precision, double sigma,
+                   int32_t n_sweeps, int32_t refresh_every, uint64_t seed, uint64_t* counter,
+                   double* logabs, double* sign, int32_t* accepted, int64_t* n_accepted,
+                   double* max_drift, fire_info_t* info, void* ws, size_t ws_bytes, void* stream);
+
 /* Layout of the workspace of a call (diagnostics and tests): for each named
  * intermediate buffer its byte offset inside ws and its size in bytes, for
  * the first walker chunk (chunk_walkers walkers).  With out == NULL only *n is

@@ -90,7 +90,7 @@ static size_t layout(Plan& pl, int64_t Wc) {
   auto take = [&](size_t bytes) {
     size_t r = o;
     o = align_up(o + bytes);
-    if (pl.nent < 96) pl.ent[pl.nent++] = Plan::Ent{nm, r, bytes};
+    if (pl.nent < 160) pl.ent[pl.nent++] = Plan::Ent{nm, r, bytes};
     return r;
   };
 #define TAKE(field, bytes) (nm = #field, pl.field = take(bytes))
@@ -131,7 +131,8 @@ static size_t layout(Plan& pl, int64_t Wc) {
   TAKE(piv, Wc * D * n * 4);
   TAKE(ldabs, Wc * D * 8);
   TAKE(lsign, Wc * D * 8);
-  if (dm.deriv) TAKE(Ainv, Wc * D * n * n * ts); else pl.Ainv = 0;
+  const bool mc = dm.op == FIRE_OP_MCMC;
+  if (dm.deriv || mc) TAKE(Ainv, Wc * D * n * n * ts); else pl.Ainv = 0;
   if (dm.deriv && ts == 4) TAKE(Phif, Wc * D * n * n * 4); else pl.Phif = 0;
   TAKE(gdet, Wc * D * n * 3 * ts);
   TAKE(ldet, Wc * D * n * ts);
@@ -166,6 +167,48 @@ static size_t layout(Plan& pl, int64_t Wc) {
   } else {
     pl.poff_dev = pl.gradws = 0;
   }
+  if (mc) {
+    // cached Phi and the per-move scratch of the Metropolis call
+    const int64_t Um = pl.Umax, capU = Wc * Um, Dn = D * n, RD1 = dm.R + RD;
+    const int64_t zc = d > J ? d : J;
+    TAKE(PhiS, Wc * D * n * n * ts);
+    TAKE(mc_rk, Wc * 3 * 8);
+    TAKE(mc_u, Wc * 8);
+    TAKE(mc_Ul, capU * 4);
+    TAKE(mc_Uc, Wc * 4);
+    TAKE(mc_Ucu, Wc * 4);
+    TAKE(mc_Urow, capU * 4);
+    TAKE(mc_rng, 16 * 8);
+    TAKE(mc_h0k, Wc * d * ts);
+    TAKE(mc_PQk, Wc * 4 * d * ts);
+    TAKE(mc_Qk, Wc * NE * ts);
+    TAKE(mc_Fk, Wc * Dn * ts);
+    TAKE(mc_X, capU * d * ts);
+    TAKE(mc_Z, capU * zc * ts);
+    TAKE(mc_Y, capU * J * ts);
+    TAKE(mc_F1n, capU * ts);
+    TAKE(mc_F2n, capU * ts);
+    TAKE(mc_SUn, capU * RD1 * ts);
+    TAKE(mc_On, capU * Dn * ts);
+    TAKE(mc_Vn, Wc * RD * ts);
+    TAKE(mc_VZ, Wc * J * ts);
+    TAKE(mc_VY, Wc * J * ts);
+    TAKE(mc_G1n, Wc * ts);
+    TAKE(mc_G2n, Wc * ts);
+    TAKE(mc_Dl, Wc * D * Um * n * ts);
+    TAKE(mc_Mt, Wc * D * Um * Um * ts);
+    TAKE(mc_Mlu, Wc * D * Um * Um * 8);
+    TAKE(mc_piv, Wc * D * Um * 4);
+    TAKE(mc_lrat, Wc * D * 8);
+    TAKE(mc_srat, Wc * D * 8);
+    TAKE(mc_acc, Wc * 4);
+    TAKE(mc_Tu, Wc * D * Um * n * ts);
+    TAKE(mc_Bw, Wc * D * Um * n * ts);
+    TAKE(mc_lp, Wc * 8);
+    TAKE(mc_lpf, Wc * 8);
+    TAKE(mc_sgf, Wc * 8);
+    TAKE(mc_stat, sizeof(McmcStat));
+  }
 #undef TAKE
   pl.total = o;
   return o;
@@ -185,6 +228,8 @@ int make_plan(const fire_system_t* sys, const fire_arch_t* ar, int64_t W, int pr
   if (rc) return rc;
   if (W < 1 || k_cap < 1 || k_cap > 1024) return FIRE_ERR_INVALID_ARG;
   if (prec < 0 || prec > 2) return FIRE_ERR_INVALID_ARG;
+  // Metropolis moves of both reduced forms run in float32
+  if (op == FIRE_OP_MCMC && prec == FIRE_PREC_BF16_FP64) prec = FIRE_PREC_FP32;
   memset(pl, 0, sizeof(Plan));
   Dims& dm = pl->dm;
   dm.n = sys->n_el; dm.n_up = sys->n_up; dm.N = sys->n_nuc; dm.d = ar->width; dm.L = ar->n_layers;
@@ -195,7 +240,9 @@ int make_plan(const fire_system_t* sys, const fire_arch_t* ar, int64_t W, int pr
   const int keff = k_cap < dm.n - 1 ? k_cap : (dm.n - 1 > 0 ? dm.n - 1 : 0);
   pl->rows_per_el = dm.deriv ? 2 + 3 * (1 + keff) : 1;
   pl->tsz = prec == FIRE_PREC_FP64 ? 8 : 4;
-  pl->lsz = prec == FIRE_PREC_FP32 ? 4 : 8;
+  // the Metropolis refresh factorises in float64 in every form
+  pl->lsz = (prec == FIRE_PREC_FP32 && op != FIRE_OP_MCMC) ? 4 : 8;
+  pl->Umax = keff * 2 + 1 < dm.n ? keff * 2 + 1 : dm.n;
   pl->W = W;
   const size_t s1 = layout(*pl, 1), s2 = layout(*pl, 2);
   const size_t per = s2 > s1 ? s2 - s1 : 1;
@@ -203,7 +250,7 @@ int make_plan(const fire_system_t* sys, const fire_arch_t* ar, int64_t W, int pr
   const size_t bud = budget_bytes();
   int64_t wc = bud > base ? (int64_t)((bud - base) / per) : 1;
   if (wc < 1) wc = 1;
-  if (wc > W) wc = W;
+  if (wc > W || op == FIRE_OP_MCMC) wc = W;   // the Metropolis state covers every walker
   // shared-memory limits of the determinant kernels
   const int n = dm.n, mcap = 1 + (k_cap < dm.n - 1 ? k_cap : dm.n - 1);
   const size_t ctsm = contract_smem_bytes(mcap, pl->tsz);
@@ -401,7 +448,7 @@ static int run_call(const fire_system_t* sys, const fire_arch_t* arch, const fir
   int64_t nl = 0;
   pl.nparams = off;
   CallArgs a{sys, arch, params->theta, poff, W, r, e_loc, logabs, sign, e_kin, e_pot, ws,
-             (cudaStream_t)stream, &hs, &nl, grad};
+             (cudaStream_t)stream, &hs, &nl, grad, nullptr};
   if (prec == FIRE_PREC_FP64) rc = run_fp64(pl, a);
   else if (prec == FIRE_PREC_FP32) rc = run_fp32(pl, a);
   else rc = run_bf16(pl, a);
@@ -441,6 +488,62 @@ int fire_local_energy(const fire_system_t* sys, const fire_arch_t* arch, const f
                       void* ws, size_t ws_bytes, void* stream) {
   return run_call(sys, arch, params, W, r, k_cap, precision, FIRE_OP_LOCAL_ENERGY, e_loc, logabs, sign, e_kin,
                   e_pot, info, ws, ws_bytes, stream);
+}
+
+int fire_mcmc_step(const fire_system_t* sys, const fire_arch_t* arch, const fire_params_t* params,
+                   int64_t W, double* r, int32_t k_cap, int32_t precision, double sigma, int32_t n_sweeps,
+                   int32_t refresh_every, uint64_t seed, uint64_t* counter, double* logabs, double* sign,
+                   int32_t* accepted, int64_t* n_accepted, double* max_drift, fire_info_t* info, void* ws,
+                   size_t ws_bytes, void* stream) {
+  if (!params || !params->theta || !r || !counter) return FIRE_ERR_INVALID_ARG;
+  if (!(sigma > 0.0) || !(sigma < 1e300) || n_sweeps < 0 || refresh_every < 0) return FIRE_ERR_INVALID_ARG;
+  if (precision < 0 || precision > 2) return FIRE_ERR_INVALID_ARG;
+  // the moves run in float32 for both reduced forms
+  const int prec = precision == FIRE_PREC_FP64 ? FIRE_PREC_FP64 : FIRE_PREC_FP32;
+  Plan pl;
+  int rc = make_plan(sys, arch, W, prec, k_cap, FIRE_OP_MCMC, &pl);
+  if (rc) return rc;
+  if (!sys->nuc_pos || !sys->nuc_charge) return FIRE_ERR_INVALID_ARG;
+  if (params->n_params != fire_param_count(sys, arch)) return FIRE_ERR_INVALID_ARG;
+  if (params->dtype != (prec == FIRE_PREC_FP64 ? 0 : 1)) return FIRE_ERR_INVALID_ARG;
+  if (!ws || ws_bytes < pl.total) return FIRE_ERR_WORKSPACE;
+  PDesc t[P_COUNT];
+  param_table(sys, arch, t);
+  int64_t poff[P_COUNT];
+  int64_t off = 0;
+  for (int k = 0; k < P_COUNT; ++k) { poff[k] = off; off += numel(t[k]); }
+  pl.nparams = off;
+  DevStatus hs;
+  memset(&hs, 0, sizeof(hs));
+  int64_t nl = 0;
+  McmcCall mc{sigma, n_sweeps, refresh_every, seed, *counter, accepted, 0, 0.0};
+  unsigned char* wsb = reinterpret_cast<unsigned char*>(ws);
+  double* lpf = reinterpret_cast<double*>(wsb + pl.mc_lpf);
+  double* sgf = reinterpret_cast<double*>(wsb + pl.mc_sgf);
+  CallArgs a{sys, arch, params->theta, poff, W, r, nullptr, lpf, sgf, nullptr, nullptr, ws,
+             (cudaStream_t)stream, &hs, &nl, nullptr, &mc};
+  rc = prec == FIRE_PREC_FP64 ? run_fp64(pl, a) : run_bf16(pl, a);
+  if (info) {
+    info->k_required = hs.k_required;
+    info->n_nodes = hs.n_nodes;
+    info->n_nonfinite = hs.n_nonfinite;
+    info->n_chunks = 1;
+    info->rows_total = hs.rows_total;
+    info->n_launches = nl;
+    info->mean_neighbors = (double)hs.nbr_total / ((double)W * sys->n_el);
+  }
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (logabs && cudaMemcpyAsync(logabs, lpf, sizeof(double) * (size_t)W, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return FIRE_ERR_CUDA;
+  if (sign && cudaMemcpyAsync(sign, sgf, sizeof(double) * (size_t)W, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return FIRE_ERR_CUDA;
+  *counter = mc.counter;
+  if (n_accepted) *n_accepted = mc.n_accepted;
+  if (max_drift) *max_drift = mc.max_drift;
+  if (hs.overflow) return FIRE_ERR_CAPACITY;
+  if (hs.n_nonfinite) return FIRE_ERR_NONFINITE;
+  return FIRE_OK;
 }
 
 }  // extern "C"

@@ -1,0 +1,723 @@
+// Metropolis sampling with single-electron moves and low-rank wave-function
+// updates (Methods, "Improved Monte Carlo sampling" and "Low-rank updates").
+//
+// Moving electron k from r_k to r'_k changes the embeddings of the update set
+// U = {k} u {i : |r_i - r_k| <= c} u {i : |r_i - r'_k| <= c} only: h^0_i
+// depends on r_i alone and the single message-passing round only sees
+// electrons within c.  Those rows of h and of every orbital matrix are
+// recomputed; with A = Phi^-1 cached, the determinant ratio is
+//   det(Phi') / det(Phi) = det(M),  M = I + Delta A[:, U]   (|U| x |U|)
+// (matrix determinant lemma, Delta = Phi'_U - Phi_U), and an accepted move
+// updates A by the Woodbury identity
+//   A' = A - A[:, U] M^-1 Delta A.
+// A is kept transposed (AT[k][l] = A[l][k]) so that a column of A is a row.
+//
+// The members of U of every walker are compacted into one row list, spin-up
+// rows first, so each product of the move is one matrix product over the
+// rows of all walkers.
+#pragma once
+
+#include "common.cuh"
+#include "philox.cuh"
+
+namespace fire {
+
+// ---------------------------------------------------------------------------
+// CTA-wide tiled products (256 threads, 32 x 32 tiles, 2 x 2 per thread).
+//   nt: C[i][j] (+)= alpha sum_k A[i][k] B[brow(j)][k]
+//   tn: C[i][j] (+)= alpha sum_k A[k][i] B[k][j]
+// sm holds 2 x 32 x 33 elements.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ void cta_gemm_nt(int M, int N, int K, const T* __restrict__ A, int64_t lda, const T* __restrict__ B,
+                            int64_t ldb, const int32_t* __restrict__ brow, T* __restrict__ C, int64_t ldc,
+                            T alpha, bool accumulate, T* sm) {
+  T(*as)[33] = reinterpret_cast<T(*)[33]>(sm);
+  T(*bs)[33] = reinterpret_cast<T(*)[33]>(sm + 32 * 33);
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  for (int i0 = 0; i0 < M; i0 += 32)
+    for (int j0 = 0; j0 < N; j0 += 32) {
+      T acc[2][2] = {{T(0), T(0)}, {T(0), T(0)}};
+      for (int k0 = 0; k0 < K; k0 += 32) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+          const int r = e / 32, c = e % 32;   // r: row of A or B, c: k
+          const int kk = k0 + c;
+          as[c][r] = (i0 + r < M && kk < K) ? A[(int64_t)(i0 + r) * lda + kk] : T(0);
+          const int jj = j0 + r;
+          bs[c][r] = (jj < N && kk < K) ? B[(int64_t)(brow ? brow[jj] : jj) * ldb + kk] : T(0);
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int c = 0; c < 32; ++c) {
+          const T a0 = as[c][2 * ty], a1 = as[c][2 * ty + 1];
+          const T b0 = bs[c][2 * tx], b1 = bs[c][2 * tx + 1];
+          acc[0][0] += a0 * b0; acc[0][1] += a0 * b1;
+          acc[1][0] += a1 * b0; acc[1][1] += a1 * b1;
+        }
+      }
+#pragma unroll
+      for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int i = i0 + 2 * ty + p, j = j0 + 2 * tx + q;
+          if (i < M && j < N) {
+            T* o = C + (int64_t)i * ldc + j;
+            *o = accumulate ? *o + alpha * acc[p][q] : alpha * acc[p][q];
+          }
+        }
+    }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ void cta_gemm_tn(int M, int N, int K, const T* __restrict__ A, int64_t lda, const T* __restrict__ B,
+                            int64_t ldb, T* __restrict__ C, int64_t ldc, T alpha, bool accumulate, T* sm) {
+  T(*as)[33] = reinterpret_cast<T(*)[33]>(sm);
+  T(*bs)[33] = reinterpret_cast<T(*)[33]>(sm + 32 * 33);
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  for (int i0 = 0; i0 < M; i0 += 32)
+    for (int j0 = 0; j0 < N; j0 += 32) {
+      T acc[2][2] = {{T(0), T(0)}, {T(0), T(0)}};
+      for (int k0 = 0; k0 < K; k0 += 32) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+          const int r = e / 32, c = e % 32;   // r: k, c: column of A or B
+          const int kk = k0 + r;
+          as[r][c] = (kk < K && i0 + c < M) ? A[(int64_t)kk * lda + i0 + c] : T(0);
+          bs[r][c] = (kk < K && j0 + c < N) ? B[(int64_t)kk * ldb + j0 + c] : T(0);
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int r = 0; r < 32; ++r) {
+          const T a0 = as[r][2 * ty], a1 = as[r][2 * ty + 1];
+          const T b0 = bs[r][2 * tx], b1 = bs[r][2 * tx + 1];
+          acc[0][0] += a0 * b0; acc[0][1] += a0 * b1;
+          acc[1][0] += a1 * b0; acc[1][1] += a1 * b1;
+        }
+      }
+#pragma unroll
+      for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int i = i0 + 2 * ty + p, j = j0 + 2 * tx + q;
+          if (i < M && j < N) {
+            T* o = C + (int64_t)i * ldc + j;
+            *o = accumulate ? *o + alpha * acc[p][q] : alpha * acc[p][q];
+          }
+        }
+    }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Proposal r'_k = r_k + sigma xi and the acceptance uniform from Philox4x32-10:
+// key (seed low, seed high); counter (move low, move high, walker, 0) gives
+// four uniforms and, by Box-Muller in float64, xi; counter (..., 1) gives u.
+// Then the update set U of the walker, ascending (so its spin-up members come
+// first); Ucu = number of spin-up members.  One warp per walker.
+// ---------------------------------------------------------------------------
+static __global__ void mcmc_propose_kernel(int n, int n_up, int k, const double* __restrict__ r, double sigma,
+                                    uint64_t seed, uint64_t move, int64_t w0, double c2, int Umax,
+                                    double* __restrict__ rk, double* __restrict__ uacc, int32_t* __restrict__ Ul,
+                                    int32_t* __restrict__ Uc, int32_t* __restrict__ Ucu, DevStatus* st) {
+  const int w = blockIdx.x;
+  const int lane = threadIdx.x;
+  const double* rw = r + (int64_t)w * n * 3;
+  __shared__ double rn[3];
+  if (lane == 0) {
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const uint32_t m0 = (uint32_t)move, m1 = (uint32_t)(move >> 32), wg = (uint32_t)(w0 + w);
+    const Philox4 a = philox4x32_10(m0, m1, wg, 0u, k0, k1);
+    const Philox4 b = philox4x32_10(m0, m1, wg, 1u, k0, k1);
+    const double two_pi = 6.283185307179586476925286766559;
+    const double ra = sqrt(-2.0 * log(u01(a.v[0]))), rb = sqrt(-2.0 * log(u01(a.v[2])));
+    const double t1 = two_pi * u01(a.v[1]), t3 = two_pi * u01(a.v[3]);
+    const double xi[3] = {ra * cos(t1), ra * sin(t1), rb * cos(t3)};
+    for (int t = 0; t < 3; ++t) {
+      rn[t] = rw[3 * k + t] + sigma * xi[t];
+      rk[(int64_t)w * 3 + t] = rn[t];
+    }
+    uacc[w] = u01(b.v[0]);
+  }
+  __syncwarp();
+  int cntU = 0, cntUp = 0;
+  for (int j0 = 0; j0 < n; j0 += 32) {
+    const int j = j0 + lane;
+    bool in = false;
+    if (j < n) {
+      if (j == k) {
+        in = true;
+      } else {
+        double a2 = 0.0, b2 = 0.0;
+        for (int t = 0; t < 3; ++t) {
+          const double da = rw[3 * j + t] - rw[3 * k + t], db = rw[3 * j + t] - rn[t];
+          a2 += da * da;
+          b2 += db * db;
+        }
+        in = (a2 <= c2) || (b2 <= c2);
+      }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, in);
+    if (in) {
+      const int pos = cntU + __popc(m & ((1u << lane) - 1u));
+      if (pos < Umax) Ul[(int64_t)w * Umax + pos] = j;
+    }
+    cntU += __popc(m);
+    const unsigned mu = __ballot_sync(0xffffffffu, in && j < n_up);
+    cntUp += __popc(mu);
+  }
+  if (lane == 0) {
+    if (cntU > Umax) {
+      atomicExch(&st->overflow, 1);
+      atomicMax(&st->k_required, cntU);
+    }
+    Uc[w] = cntU < Umax ? cntU : Umax;
+    Ucu[w] = cntUp < Umax ? cntUp : Umax;
+  }
+}
+
+// Compact row index of every member of U: spin-up members of all walkers
+// first (walker-major), then the spin-down ones.  rng = {0, up, up, total,
+// 0, total}.  One CTA of 1024 threads.
+static __global__ void __launch_bounds__(1024) mcmc_scan_kernel(int W, int Umax, const int32_t* __restrict__ Uc,
+                                                         const int32_t* __restrict__ Ucu, int32_t* __restrict__ Urow,
+                                                         int64_t* __restrict__ rng) {
+  __shared__ int64_t sa[1024], sb[1024];
+  __shared__ int64_t carry[2], tot_up;
+  const int t = threadIdx.x;
+  int64_t s = 0;
+  for (int w = t; w < W; w += 1024) s += Ucu[w];
+  sa[t] = s;
+  __syncthreads();
+  for (int o = 512; o > 0; o >>= 1) {
+    if (t < o) sa[t] += sa[t + o];
+    __syncthreads();
+  }
+  if (t == 0) {
+    tot_up = sa[0];
+    carry[0] = 0;
+    carry[1] = 0;
+  }
+  __syncthreads();
+  const int64_t up_total = tot_up;
+  for (int base = 0; base < W; base += 1024) {
+    const int w = base + t;
+    const int64_t cu = w < W ? Ucu[w] : 0, cd = w < W ? Uc[w] - Ucu[w] : 0;
+    sa[t] = cu;
+    sb[t] = cd;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {   // inclusive Hillis-Steele scans
+      const int64_t xa = t >= o ? sa[t - o] : 0, xb = t >= o ? sb[t - o] : 0;
+      __syncthreads();
+      sa[t] += xa;
+      sb[t] += xb;
+      __syncthreads();
+    }
+    if (w < W) {
+      const int64_t uo = carry[0] + sa[t] - cu, dof = up_total + carry[1] + sb[t] - cd;
+      const int nu = (int)cu, nt = Uc[w];
+      for (int a = 0; a < nt; ++a) Urow[(int64_t)w * Umax + a] = (int32_t)(a < nu ? uo + a : dof + (a - nu));
+    }
+    __syncthreads();
+    if (t == 1023) {
+      carry[0] += sa[t];
+      carry[1] += sb[t];
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    rng[0] = 0; rng[1] = up_total; rng[2] = up_total; rng[3] = up_total + carry[1];
+    rng[4] = 0; rng[5] = up_total + carry[1];
+  }
+}
+
+// h^1 of every member i of U under the proposed positions (value only):
+//   h^1_i = h^0_i + sum_{j in N_i} Gamma(e_ij) SiLU(h^0_i W^a + h^0_j W^a' + e-bar_ij W^a_c + b^a)
+// with the neighbour list rebuilt on the fly (same spin ascending, then the
+// opposite spin).  h^0 and its projections of electron k come from h0k / PQk.
+// One CTA per (walker, slot), blockDim == d; dynamic shared memory n ints.
+template <typename T, typename W>
+__global__ void mcmc_msg_kernel(int Wn, int n, int n_up, int d, int k, int Umax, const double* __restrict__ r,
+                                const double* __restrict__ rk, double cut, Params<W> p,
+                                const int32_t* __restrict__ Ul, const int32_t* __restrict__ Uc,
+                                const int32_t* __restrict__ Urow, const T* __restrict__ H0,
+                                const T* __restrict__ PQ, const T* __restrict__ h0k, const T* __restrict__ PQk,
+                                T* __restrict__ X) {
+  constexpr int H = kEdgeHidden, G = kGauss;
+  __shared__ FL3<T> feat[H + G + 4];
+  extern __shared__ int mm_nbr[];
+  __shared__ int s_cnt[2];
+  const int w = blockIdx.x / Umax, u = blockIdx.x % Umax;
+  if (u >= Uc[w]) return;
+  const int i = Ul[(int64_t)w * Umax + u];
+  const int c = threadIdx.x;
+  const int64_t ld4 = 4 * (int64_t)d;
+  const double* rw = r + (int64_t)w * n * 3;
+  const double* rkw = rk + (int64_t)w * 3;
+  auto pos = [&](int j, int t) -> double { return j == k ? rkw[t] : rw[3 * j + t]; };
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    const bool up = i < n_up;
+    int cntN = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+      const bool same = pass == 0;
+      const int lo = (up == same) ? 0 : n_up, hi = (up == same) ? n_up : n;
+      for (int j0 = lo; j0 < hi; j0 += 32) {
+        const int j = j0 + lane;
+        bool in = false;
+        if (j < hi && j != i) {
+          double a2 = 0.0;
+          for (int t = 0; t < 3; ++t) {
+            const double dd = pos(i, t) - pos(j, t);
+            a2 += dd * dd;
+          }
+          in = a2 <= cut * cut;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, in);
+        if (in) mm_nbr[cntN + __popc(m & ((1u << lane) - 1u))] = j;
+        cntN += __popc(m);
+      }
+      if (lane == 0) s_cnt[pass] = cntN;
+    }
+  }
+  __syncthreads();
+  const int cpar = s_cnt[0], ctot = s_cnt[1];
+  T w2[H], we[G], wc[2][4], bb[2];
+#pragma unroll
+  for (int h = 0; h < H; ++h) w2[h] = T(p.ee_w2[h * d + c]);
+#pragma unroll
+  for (int g = 0; g < G; ++g) we[g] = T(p.ee_wenv[g * d + c]);
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    bb[a] = T(p.msg_b[a * d + c]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) wc[a][q] = T(p.msg_w[((int64_t)a * (2 * d + 4) + 2 * d + q) * d + c]);
+  }
+  const int bi = block_index(w, i, Wn, n, n_up);
+  const T* Pi = (i == k) ? PQk + (int64_t)w * ld4 : PQ + (int64_t)bi * ld4;
+  T acc = (i == k) ? h0k[(int64_t)w * d + c] : H0[(int64_t)bi * d + c];
+  for (int s = 0; s < ctot; ++s) {
+    const int j = mm_nbr[s];
+    const int a = (s < cpar) ? 0 : 1;
+    const double ddv[3] = {pos(i, 0) - pos(j, 0), pos(i, 1) - pos(j, 1), pos(i, 2) - pos(j, 2)};
+    const double rr = sqrt(ddv[0] * ddv[0] + ddv[1] * ddv[1] + ddv[2] * ddv[2]);
+    T dv[3] = {T(ddv[0]), T(ddv[1]), T(ddv[2])};
+    __syncthreads();
+    pair_features_to_smem<T, W>(dv, T(rr), p.ee_w1, p.ee_b1, p.ee_sigma, T(cut), feat);
+    __syncthreads();
+    T gv = T(0), ev = T(0), eb = T(0);
+#pragma unroll
+    for (int h = 0; h < H; ++h) gv += feat[h].v * w2[h];
+#pragma unroll
+    for (int g = 0; g < G; ++g) ev += feat[H + g].v * we[g];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) eb += feat[H + G + q].v * wc[a][q];
+    const T* Qj = (j == k) ? PQk + (int64_t)w * ld4 : PQ + (int64_t)block_index(w, j, Wn, n, n_up) * ld4;
+    const T z = Pi[(int64_t)a * d + c] + Qj[2 * (int64_t)d + (int64_t)a * d + c] + eb + bb[a];
+    T f, f1, f2;
+    silu3<T>(z, f, f1, f2);
+    acc += (gv * ev) * f;
+  }
+  X[(int64_t)Urow[(int64_t)w * Umax + u] * d + c] = acc;
+}
+
+// Y[row][c] = (residual ? Y[row][c] : 0) + SiLU(Z[row][c] + b[c]) for rows in
+// [rng[0], rng[1]); grid-stride over rows x columns.
+template <typename T, typename W>
+__global__ void mcmc_act_kernel(const int64_t* __restrict__ rng, int ncol, const T* __restrict__ Z, int64_t ldz,
+                                const W* bias, T* __restrict__ Y, int64_t ldy, int residual) {
+  const int64_t r0 = rng[0], r1 = rng[1];
+  const int64_t total = (r1 - r0) * ncol;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = r0 + e / ncol;
+    const int c = (int)(e % ncol);
+    T f, f1, f2;
+    silu3<T>(Z[row * ldz + c] + T(bias[c]), f, f1, f2);
+    Y[row * ldy + c] = residual ? Y[row * ldy + c] + f : f;
+  }
+}
+
+// Determinant lemma for one (walker, det): Delta rows of U (new orbital row
+// times envelope minus the cached Phi row), M = I + Delta A[:, U], its LU with
+// partial pivoting in float64 and log|det M|, sign.  Delta, the LU and the
+// pivots are kept for the Woodbury update.  One CTA (256 threads) per
+// (walker, det).  Mt is [Umax][Umax] scratch in T per (walker, det).
+template <typename T>
+__global__ void __launch_bounds__(256) mcmc_ratio_kernel(
+    int Wn, int n, int n_up, int D, int k, int Umax, const int32_t* __restrict__ Ul, const int32_t* __restrict__ Uc,
+    const int32_t* __restrict__ Urow, const T* __restrict__ On, const T* __restrict__ Fenv, const T* __restrict__ Fk,
+    const T* __restrict__ Phi, const T* __restrict__ AT, T* __restrict__ Dl, T* __restrict__ Mt,
+    double* __restrict__ Mlu, int32_t* __restrict__ Mpiv, double* __restrict__ lrat, double* __restrict__ srat) {
+  __shared__ T sm[2 * 32 * 33];
+  __shared__ int s_p;
+  const int w = blockIdx.x / D, dd = blockIdx.x % D;
+  const int u = Uc[w];
+  const int64_t Dn = (int64_t)D * n;
+  const int64_t md = (int64_t)w * D + dd;
+  const int32_t* U = Ul + (int64_t)w * Umax;
+  const T* Pw = Phi + md * n * n;
+  const T* Aw = AT + md * n * n;
+  T* Dw = Dl + md * Umax * n;
+  for (int e = threadIdx.x; e < u * n; e += blockDim.x) {
+    const int aa = e / n, l = e % n;
+    const int i = U[aa];
+    const T o = On[(int64_t)Urow[(int64_t)w * Umax + aa] * Dn + dd * n + l];
+    const T ph = (i == k) ? Fk[(int64_t)w * Dn + dd * n + l]
+                          : Fenv[(int64_t)block_index(w, i, Wn, n, n_up) * Dn + dd * n + l];
+    Dw[(int64_t)aa * n + l] = o * ph - Pw[(int64_t)i * n + l];
+  }
+  // Delta A[:, U] = Delta (u x n) times the rows U of A^T
+  T* Mw = Mt + md * Umax * Umax;
+  cta_gemm_nt<T>(u, u, n, Dw, n, Aw, n, U, Mw, Umax, T(1), false, sm);
+  double* M = Mlu + md * Umax * Umax;
+  for (int e = threadIdx.x; e < u * u; e += blockDim.x) {
+    const int a = e / u, b = e % u;
+    M[a * Umax + b] = (double)Mw[a * Umax + b] + (a == b ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  double la = 0.0;
+  int neg = 0;
+  bool zero = false;
+  for (int c = 0; c < u; ++c) {
+    if (threadIdx.x == 0) {
+      int pv = c;
+      double best = fabs(M[c * Umax + c]);
+      for (int q = c + 1; q < u; ++q)
+        if (fabs(M[q * Umax + c]) > best) {
+          best = fabs(M[q * Umax + c]);
+          pv = q;
+        }
+      s_p = pv;
+      Mpiv[md * Umax + c] = pv;
+    }
+    __syncthreads();
+    const int pv = s_p;
+    if (pv != c) {
+      for (int q = threadIdx.x; q < u; q += blockDim.x) {
+        const double t = M[c * Umax + q];
+        M[c * Umax + q] = M[pv * Umax + q];
+        M[pv * Umax + q] = t;
+      }
+      neg ^= 1;
+    }
+    __syncthreads();
+    const double piv = M[c * Umax + c];
+    if (piv == 0.0) {
+      zero = true;
+    } else {
+      la += log(fabs(piv));
+      if (piv < 0.0) neg ^= 1;
+      const int wdt = u - c - 1;
+      for (int e = threadIdx.x; e < wdt * wdt; e += blockDim.x) {
+        const int q = c + 1 + e / wdt, cc = c + 1 + e % wdt;
+        M[q * Umax + cc] -= (M[q * Umax + c] / piv) * M[c * Umax + cc];
+      }
+      __syncthreads();
+      for (int q = c + 1 + threadIdx.x; q < u; q += blockDim.x) M[q * Umax + c] /= piv;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    lrat[md] = zero ? -INFINITY : la;
+    srat[md] = zero ? 0.0 : (neg ? -1.0 : 1.0);
+  }
+}
+
+// Attention registers with the rows of U replaced (value only):
+// V_r = sum_i softmax_i(s_ir) v_ir, the scores and values of U from SUn.
+// One CTA per walker, one thread per column of V.
+template <typename T>
+__global__ void mcmc_att_kernel(int Wn, int n, int n_up, int R, int dr, int Umax, const int32_t* __restrict__ Ul,
+                                const int32_t* __restrict__ Uc, const int32_t* __restrict__ Urow,
+                                const T* __restrict__ SU, int64_t ld, const T* __restrict__ SUn, int64_t ldn,
+                                T* __restrict__ Vn) {
+  extern __shared__ unsigned char ma_smem[];
+  int* slot = reinterpret_cast<int*>(ma_smem);    // [n]: compact row of i in U, or -1
+  T* smax = reinterpret_cast<T*>(ma_smem + (((size_t)n * sizeof(int) + 15) & ~(size_t)15));
+  const int w = blockIdx.x;
+  const int RD = R * dr;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) slot[i] = -1;
+  __syncthreads();
+  for (int a = threadIdx.x; a < Uc[w]; a += blockDim.x) slot[Ul[(int64_t)w * Umax + a]] = Urow[(int64_t)w * Umax + a];
+  __syncthreads();
+  auto row = [&](int i) -> const T* {
+    return slot[i] >= 0 ? SUn + (int64_t)slot[i] * ldn : SU + (int64_t)block_index(w, i, Wn, n, n_up) * ld;
+  };
+  for (int q = threadIdx.x; q < R; q += blockDim.x) {
+    T m = -INFINITY;
+    for (int i = 0; i < n; ++i) m = fmax(m, row(i)[q]);
+    smax[q] = m;
+  }
+  __syncthreads();
+  for (int col = threadIdx.x; col < RD; col += blockDim.x) {
+    const int rg = col / dr;
+    T Z = T(0), Nv = T(0);
+    for (int i = 0; i < n; ++i) {
+      const T* rr = row(i);
+      const T e = dexp<T>(rr[rg] - smax[rg]);
+      Z += e;
+      Nv += e * rr[R + col];
+    }
+    Vn[(int64_t)w * RD + col] = Nv / Z;
+  }
+}
+
+// Jastrow parameters the acceptance test reads (type T).
+struct McmcJastrow {
+  const void *cusp, *jb32, *ab32;
+};
+
+// Accept / reject.  ln|Psi'/Psi| = determinant part (from the ratios of all
+// determinants) + cusp change of electron k + change of the MLP-Jastrow sums
+// + change of the attention-Jastrow readout.  Accept iff ln u < 2 ln|Psi'/Psi|
+// and the ratio is finite.  One warp per walker; an accepted walker moves r_k
+// and updates its determinant logs and its running log|Psi|.
+template <typename T>
+__global__ void mcmc_accept_kernel(int Wn, int n, int n_up, int D, int k, int Umax, uint32_t flags,
+                                   double* __restrict__ r, const double* __restrict__ rk,
+                                   const double* __restrict__ uacc, const int32_t* __restrict__ Ul,
+                                   const int32_t* __restrict__ Uc, const int32_t* __restrict__ Urow, McmcJastrow jp,
+                                   const T* __restrict__ F1, const T* __restrict__ F2, const T* __restrict__ F1n,
+                                   const T* __restrict__ F2n, const T* __restrict__ G1, const T* __restrict__ G2,
+                                   const T* __restrict__ G1n, const T* __restrict__ G2n,
+                                   double* __restrict__ ldabs, double* __restrict__ lsign,
+                                   const double* __restrict__ lrat, const double* __restrict__ srat,
+                                   double* __restrict__ lp, int32_t* __restrict__ acc,
+                                   int32_t* __restrict__ acc_count, unsigned long long* __restrict__ nacc) {
+  const int w = blockIdx.x;
+  const int lane = threadIdx.x;
+  double* rw = r + (int64_t)w * n * 3;
+  const double* rn = rk + (int64_t)w * 3;
+  const T* cusp = reinterpret_cast<const T*>(jp.cusp);
+  double dc = 0.0, s2 = 0.0, ds1 = 0.0, ds2 = 0.0;
+  const double wp = (double)cusp[0], wa = (double)cusp[1], ap = (double)cusp[2], aa = (double)cusp[3];
+  for (int j = lane; j < n; j += 32) {
+    if (j != k) {
+      const bool same = (j < n_up) == (k < n_up);
+      const double om = same ? wp : wa, al = same ? ap : aa;
+      double o2 = 0.0, n2 = 0.0;
+      for (int t = 0; t < 3; ++t) {
+        const double a = rw[3 * k + t] - rw[3 * j + t], b = rn[t] - rw[3 * j + t];
+        o2 += a * a;
+        n2 += b * b;
+      }
+      dc += om * al * al / (al + sqrt(n2)) - om * al * al / (al + sqrt(o2));
+    }
+    if (flags & FIRE_J_MLP) s2 += (double)F2[block_index(w, j, Wn, n, n_up)];
+  }
+  if (flags & FIRE_J_MLP)
+    for (int a = lane; a < Uc[w]; a += 32) {
+      const int i = Ul[(int64_t)w * Umax + a];
+      const int64_t b = block_index(w, i, Wn, n, n_up);
+      const int64_t q = Urow[(int64_t)w * Umax + a];
+      ds1 += (double)F1n[q] - (double)F1[b];
+      ds2 += (double)F2n[q] - (double)F2[b];
+    }
+  for (int o = 16; o > 0; o >>= 1) {
+    dc += __shfl_xor_sync(0xffffffffu, dc, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    ds1 += __shfl_xor_sync(0xffffffffu, ds1, o);
+    ds2 += __shfl_xor_sync(0xffffffffu, ds2, o);
+  }
+  if (lane != 0) return;
+  // determinants: ln|sum_d s_d rho_d e^{l_d}| - ln|sum_d s_d e^{l_d}|
+  const double* lw = ldabs + (int64_t)w * D;
+  const double* sw = lsign + (int64_t)w * D;
+  const double* lr = lrat + (int64_t)w * D;
+  const double* sr = srat + (int64_t)w * D;
+  double lmax = -INFINITY, lmaxn = -INFINITY;
+  for (int q = 0; q < D; ++q) {
+    if (sw[q] != 0.0 && lw[q] > lmax) lmax = lw[q];
+    if (sw[q] * sr[q] != 0.0 && lw[q] + lr[q] > lmaxn) lmaxn = lw[q] + lr[q];
+  }
+  double So = 0.0, Sn = 0.0;
+  for (int q = 0; q < D; ++q) {
+    if (sw[q] != 0.0) So += sw[q] * exp(lw[q] - lmax);
+    if (sw[q] * sr[q] != 0.0) Sn += sw[q] * sr[q] * exp(lw[q] + lr[q] - lmaxn);
+  }
+  double logr = (lmaxn + log(fabs(Sn))) - (lmax + log(fabs(So)));
+  if (flags & FIRE_J_CUSP) logr += dc;
+  if (flags & FIRE_J_MLP) {
+    const double S2o = s2 + n * (double)reinterpret_cast<const T*>(jp.jb32)[0];
+    logr += ds1 + log(fabs(S2o + ds2)) - log(fabs(S2o));
+  }
+  if (flags & FIRE_J_ATT) {
+    const double b32 = (double)reinterpret_cast<const T*>(jp.ab32)[0];
+    logr += ((double)G1n[w] - (double)G1[w]) + log(fabs((double)G2n[w] + b32)) - log(fabs((double)G2[w] + b32));
+  }
+  const bool ok = isfinite(logr) && (log(uacc[w]) < 2.0 * logr);
+  acc[w] = ok ? 1 : 0;
+  if (ok) {
+    for (int t = 0; t < 3; ++t) rw[3 * k + t] = rn[t];
+    for (int q = 0; q < D; ++q) {
+      ldabs[(int64_t)w * D + q] += lr[q];
+      lsign[(int64_t)w * D + q] *= sr[q];
+    }
+    lp[w] += logr;
+    if (acc_count) acc_count[w] += 1;
+    atomicAdd(nacc, 1ull);
+  }
+}
+
+// Copies the recomputed rows of an accepted move into the cached state:
+// MLP-Jastrow outputs and attention scores/values of every member of U, the
+// initial embedding, projections and envelope row of electron k, and the
+// walker's attention registers and readouts.  One CTA per (walker, slot).
+template <typename T>
+__global__ void mcmc_rows_kernel(int Wn, int n, int n_up, int d, int Dn, int RD, int k, int Umax, int64_t ldsu,
+                                 int64_t ldsun, int has_mlp, int has_att, const int32_t* __restrict__ acc,
+                                 const int32_t* __restrict__ Ul, const int32_t* __restrict__ Uc,
+                                 const int32_t* __restrict__ Urow, const T* __restrict__ F1n,
+                                 const T* __restrict__ F2n, T* __restrict__ F1, T* __restrict__ F2,
+                                 const T* __restrict__ SUn, T* __restrict__ SU, const T* __restrict__ h0k,
+                                 T* __restrict__ H0, const T* __restrict__ PQk, T* __restrict__ PQ,
+                                 const T* __restrict__ Fk, T* __restrict__ Fenv, const T* __restrict__ Vn,
+                                 T* __restrict__ V, const T* __restrict__ G1n, const T* __restrict__ G2n,
+                                 T* __restrict__ G1, T* __restrict__ G2) {
+  const int w = blockIdx.x / Umax, a = blockIdx.x % Umax;
+  if (!acc[w] || a >= Uc[w]) return;
+  const int i = Ul[(int64_t)w * Umax + a];
+  const int64_t b = block_index(w, i, Wn, n, n_up);
+  const int64_t q = Urow[(int64_t)w * Umax + a];
+  if (has_att)
+    for (int c = threadIdx.x; c < ldsun; c += blockDim.x) SU[b * ldsu + c] = SUn[q * ldsun + c];
+  if (has_mlp && threadIdx.x == 0) {
+    F1[b] = F1n[q];
+    F2[b] = F2n[q];
+  }
+  if (i == k) {
+    for (int c = threadIdx.x; c < d; c += blockDim.x) H0[b * d + c] = h0k[(int64_t)w * d + c];
+    for (int c = threadIdx.x; c < 4 * d; c += blockDim.x) PQ[b * 4 * d + c] = PQk[(int64_t)w * 4 * d + c];
+    for (int c = threadIdx.x; c < Dn; c += blockDim.x) Fenv[b * Dn + c] = Fk[(int64_t)w * Dn + c];
+  }
+  if (a == 0 && has_att) {
+    for (int c = threadIdx.x; c < RD; c += blockDim.x) V[(int64_t)w * RD + c] = Vn[(int64_t)w * RD + c];
+    if (threadIdx.x == 0) {
+      G1[w] = G1n[w];
+      G2[w] = G2n[w];
+    }
+  }
+}
+
+// Woodbury update of A^T and the rows U of Phi for accepted walkers:
+//   B = Delta A (u x n), C = M^-1 B,
+//   A'^T[m][l] = A^T[m][l] - sum_a C[a][m] A^T[U_a][l],   Phi_U += Delta.
+// One CTA (256 threads) per (walker, det).  Tu, Bw: [Umax][n] scratch each.
+template <typename T>
+__global__ void __launch_bounds__(256) mcmc_woodbury_kernel(
+    int n, int D, int Umax, const int32_t* __restrict__ acc, const int32_t* __restrict__ Ul,
+    const int32_t* __restrict__ Uc, const T* __restrict__ Dl, const double* __restrict__ Mlu,
+    const int32_t* __restrict__ Mpiv, T* __restrict__ AT, T* __restrict__ Phi, T* __restrict__ Tu,
+    T* __restrict__ Bw) {
+  __shared__ T sm[2 * 32 * 33];
+  const int w = blockIdx.x / D, dd = blockIdx.x % D;
+  if (!acc[w]) return;
+  const int u = Uc[w];
+  const int64_t md = (int64_t)w * D + dd;
+  const int32_t* U = Ul + (int64_t)w * Umax;
+  T* A = AT + md * n * n;
+  const T* Dw = Dl + md * Umax * n;
+  T* Tw = Tu + md * Umax * n;
+  T* Bm = Bw + md * Umax * n;
+  const double* M = Mlu + md * Umax * Umax;
+  const int32_t* pv = Mpiv + md * Umax;
+  for (int e = threadIdx.x; e < u * n; e += blockDim.x) Tw[e] = A[(int64_t)U[e / n] * n + e % n];
+  // B[a][m] = sum_l Delta[a][l] A^T[m][l]
+  cta_gemm_nt<T>(u, n, n, Dw, n, A, n, nullptr, Bm, n, T(1), false, sm);
+  // C = M^-1 B, column by column (row swaps, unit-lower and upper solves)
+  for (int m = threadIdx.x; m < n; m += blockDim.x) {
+    for (int c = 0; c < u; ++c) {
+      const int p = pv[c];
+      if (p != c) {
+        const T t = Bm[(int64_t)c * n + m];
+        Bm[(int64_t)c * n + m] = Bm[(int64_t)p * n + m];
+        Bm[(int64_t)p * n + m] = t;
+      }
+    }
+    for (int c = 0; c < u; ++c) {
+      double s = (double)Bm[(int64_t)c * n + m];
+      for (int q = 0; q < c; ++q) s -= M[c * Umax + q] * (double)Bm[(int64_t)q * n + m];
+      Bm[(int64_t)c * n + m] = (T)s;
+    }
+    for (int c = u - 1; c >= 0; --c) {
+      double s = (double)Bm[(int64_t)c * n + m];
+      for (int q = c + 1; q < u; ++q) s -= M[c * Umax + q] * (double)Bm[(int64_t)q * n + m];
+      Bm[(int64_t)c * n + m] = (T)(s / M[c * Umax + c]);
+    }
+  }
+  __syncthreads();
+  // A^T -= C^T Tw
+  cta_gemm_tn<T>(n, n, u, Bm, n, Tw, n, A, n, T(-1), true, sm);
+  T* P = Phi + md * n * n;
+  for (int e = threadIdx.x; e < u * n; e += blockDim.x) P[(int64_t)U[e / n] * n + e % n] += Dw[e];
+}
+
+// ---------------------------------------------------------------------------
+// Refresh helpers
+// ---------------------------------------------------------------------------
+
+template <typename S, typename T>
+__global__ void convert_kernel(int64_t count, const S* __restrict__ src, T* __restrict__ dst) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = (T)src[e];
+}
+
+// A = Phi^-1 from the LU factors, for matrices [m0, m0 + gridDim.x): column
+// j of A solves L U x = e_{pinv[j]} in LT; Xs is [n][n] LT scratch per matrix
+// of the launch; the result is written transposed in AT's type.  One CTA per
+// matrix, one thread per column; no shared-memory limit on n.
+template <typename LT, typename AT>
+__global__ void inverse_global_kernel(int n, int64_t m0, const LT* __restrict__ LU, const int32_t* __restrict__ piv,
+                                      LT* __restrict__ Xs, AT* __restrict__ Ainv) {
+  extern __shared__ int ig_smem[];
+  int* perm = ig_smem;
+  int* pinv = perm + n;
+  const int64_t mat = m0 + blockIdx.x;
+  const LT* A = LU + mat * n * n;
+  const int32_t* pv = piv + mat * n;
+  LT* X = Xs + (int64_t)blockIdx.x * n * n;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < n; ++i) perm[i] = i;
+    for (int k = 0; k < n; ++k) {
+      const int t = perm[k];
+      perm[k] = perm[pv[k]];
+      perm[pv[k]] = t;
+    }
+    for (int i = 0; i < n; ++i) pinv[perm[i]] = i;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const int p = pinv[j];
+    for (int i = 0; i < n; ++i) {
+      LT s = (i == p) ? LT(1) : LT(0);
+      for (int k = 0; k < i; ++k) s -= A[(int64_t)i * n + k] * X[(int64_t)k * n + j];
+      X[(int64_t)i * n + j] = s;
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      LT s = X[(int64_t)i * n + j];
+      for (int k = i + 1; k < n; ++k) s -= A[(int64_t)i * n + k] * X[(int64_t)k * n + j];
+      X[(int64_t)i * n + j] = s / A[(int64_t)i * n + i];
+    }
+  }
+  __syncthreads();
+  AT* out = Ainv + mat * n * n;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) out[e] = (AT)X[(int64_t)(e % n) * n + e / n];
+}
+
+// drift = max_w |lp_inc - lp_fresh| (the bits of a non-negative double order
+// like the values); then lp_inc = lp_fresh.
+static __global__ void mcmc_drift_kernel(int W, double* __restrict__ lp_inc, const double* __restrict__ lp_fresh,
+                                  unsigned long long* __restrict__ drift_bits, int measure) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= W) return;
+  if (measure) {
+    const double a = lp_inc[w], b = lp_fresh[w];
+    if (isfinite(a) && isfinite(b))
+      atomicMax(drift_bits, (unsigned long long)__double_as_longlong(fabs(a - b)));
+  }
+  lp_inc[w] = lp_fresh[w];
+}
+
+}  // namespace fire

@@ -12,6 +12,7 @@
 #include "embed.cuh"
 #include "gemm.cuh"
 #include "jastrow.cuh"
+#include "mcmc.cuh"
 #include "nbr.cuh"
 #include "plan.h"
 #include "tc_api.h"
@@ -39,6 +40,16 @@ enum ParamIndex {
 
 namespace fire {
 
+// Host-side arguments and results of a Metropolis call.
+struct McmcCall {
+  double sigma;
+  int n_sweeps, refresh_every;
+  uint64_t seed, counter;
+  int32_t* acc_count;        // device [W] accepted moves per walker, or null
+  int64_t n_accepted;        // out
+  double max_drift;          // out
+};
+
 struct CallArgs {
   const fire_system_t* sys;
   const fire_arch_t* arch;
@@ -52,6 +63,7 @@ struct CallArgs {
   DevStatus* host_status;    // filled after the call
   int64_t* n_launches;       // kernels launched (host out)
   void* grad;                // [W][P] parameter gradient (gradient call only)
+  McmcCall* mcmc;            // Metropolis call only
 };
 
 void set_last_error(const char* stage, const char* msg);
@@ -525,13 +537,15 @@ struct Runner {
     return FIRE_OK;
   }
 
+  bool reset_status = true;   // false for the refreshes inside a Metropolis call
+
   int run() {
     const fire_system_t* sys = a.sys;
     const int n = dm.n, n_up = dm.n_up, N = dm.N, d = dm.d, D = dm.D, K = dm.K;
     const int deriv = dm.deriv;
     const int R5 = deriv ? 5 : 1;
     DevStatus* st = at<DevStatus>(pl.status);
-    cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
+    if (reset_status) cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
     if constexpr (sizeof(T) == 4) {
       if (pl.wbf16) {
         // bf16 K-major copies of the weights of every tensor-core product
@@ -734,10 +748,33 @@ struct Runner {
       const bool gj = deriv && sizeof(T) == 4 && n <= 192;
       float* Phif = gj ? at<float>(pl.Phif) : nullptr;
       phi_assemble_kernel<T, LT><<<wc * D, 256, 0, s>>>(wc, n, n_up, D, Ov, Fenv, R5, LUb, Phif);
+      const bool mc = dm.op == FIRE_OP_MCMC;
+      if (mc) {
+        // the Metropolis state keeps Phi itself next to its factors
+        convert_kernel<LT, T><<<1024, 256, 0, s>>>((int64_t)wc * D * n * n, LUb, at<T>(pl.PhiS));
+        launches += 1;
+      }
       const size_t lusm = (size_t)2 * n * 16 * sizeof(LT);
       mark("lu", 1);
       lu_kernel<LT, 16><<<wc * D, 256, lusm, s>>>(n, LUb, piv, ldabs, lsign);
       check("lu");
+      if (mc) {
+        // A^T = (Phi^-1)^T from the float64 factors, in batches that fit the
+        // dead orbital-value buffer as float64 scratch
+        mark("inverse", 1);
+        const int64_t nmat = (int64_t)wc * D;
+        const size_t ov_bytes = (size_t)nb * (size_t)Dn * sizeof(T);
+        int64_t per = (int64_t)(ov_bytes / ((size_t)n * n * sizeof(LT)));
+        if (per < 1) per = 1;
+        if (per > 65535) per = 65535;
+        for (int64_t m0 = 0; m0 < nmat; m0 += per) {
+          const int64_t cnt = nmat - m0 < per ? nmat - m0 : per;
+          inverse_global_kernel<LT, T><<<(unsigned)cnt, 256, (size_t)2 * n * sizeof(int), s>>>(
+              n, m0, LUb, piv, reinterpret_cast<LT*>(Ov), at<T>(pl.Ainv));
+          launches += 1;
+        }
+        check("inverse");
+      }
       T* gdet = at<T>(pl.gdet);
       T* ldet = at<T>(pl.ldet);
       if (deriv) {
@@ -799,6 +836,216 @@ struct Runner {
     if (cudaStreamSynchronize(s) != cudaSuccess) return FIRE_ERR_CUDA;
     return FIRE_OK;
   }
+
+  // ---------------------------------------------------------------------
+  // Metropolis sweeps with local recompute and low-rank updates.  The state
+  // (embeddings h^0 and their projections, envelope rows, Phi, A^T,
+  // determinant logs, Jastrow sums, attention scores) is built by a value
+  // forward at the start, rebuilt every refresh_every moves and at the end;
+  // the drift of the carried log|Psi| against each rebuild is recorded.
+  // ---------------------------------------------------------------------
+  int run_mcmc() {
+    McmcCall& mc = *a.mcmc;
+    const fire_system_t* sys = a.sys;
+    const int n = dm.n, n_up = dm.n_up, N = dm.N, d = dm.d, D = dm.D, E = dm.E, NE = N * E;
+    const int J = dm.J, R = dm.R, dr = dm.dr, RD = R * dr, RD1 = R + RD;
+    const int Wn = (int)a.W;
+    const int Umax = pl.Umax;
+    const int64_t capU = (int64_t)Wn * Umax, Dn = (int64_t)D * n;
+    const int64_t ldz = d > J ? d : J;
+    double* r = const_cast<double*>(a.r);
+    DevStatus* st = at<DevStatus>(pl.status);
+    McmcStat* ms = at<McmcStat>(pl.mc_stat);
+    double* rk = at<double>(pl.mc_rk);
+    double* uacc = at<double>(pl.mc_u);
+    int32_t* Ul = at<int32_t>(pl.mc_Ul);
+    int32_t* Uc = at<int32_t>(pl.mc_Uc);
+    int32_t* Ucu = at<int32_t>(pl.mc_Ucu);
+    int32_t* Urow = at<int32_t>(pl.mc_Urow);
+    int64_t* rngu = at<int64_t>(pl.mc_rng);        // {0, up, up, total, 0, total, 0, W}
+    T* h0k = at<T>(pl.mc_h0k);
+    T* PQk = at<T>(pl.mc_PQk);
+    T* Qk = at<T>(pl.mc_Qk);
+    T* Fk = at<T>(pl.mc_Fk);
+    T* X1 = at<T>(pl.mc_X);
+    T* Zm = at<T>(pl.mc_Z);
+    T* Ym = at<T>(pl.mc_Y);
+    T* F1n = at<T>(pl.mc_F1n);
+    T* F2n = at<T>(pl.mc_F2n);
+    T* SUn = at<T>(pl.mc_SUn);
+    T* On = at<T>(pl.mc_On);
+    T* Vn = at<T>(pl.mc_Vn);
+    T* VZ = at<T>(pl.mc_VZ);
+    T* VY = at<T>(pl.mc_VY);
+    T* G1n = at<T>(pl.mc_G1n);
+    T* G2n = at<T>(pl.mc_G2n);
+    T* Dl = at<T>(pl.mc_Dl);
+    T* Mt = at<T>(pl.mc_Mt);
+    double* Mlu = at<double>(pl.mc_Mlu);
+    int32_t* Mpiv = at<int32_t>(pl.mc_piv);
+    double* lrat = at<double>(pl.mc_lrat);
+    double* srat = at<double>(pl.mc_srat);
+    int32_t* acc = at<int32_t>(pl.mc_acc);
+    T* Tu = at<T>(pl.mc_Tu);
+    T* Bw = at<T>(pl.mc_Bw);
+    double* lp = at<double>(pl.mc_lp);
+    double* lpf = at<double>(pl.mc_lpf);
+    // the state, in the value-forward buffers
+    T* H0 = at<T>(pl.H0);
+    T* PQ = at<T>(pl.PQ);
+    T* Fenv = at<T>(pl.Fenv);
+    T* F1 = at<T>(pl.F1);
+    T* F2 = at<T>(pl.F2);
+    T* SU = at<T>(pl.big) + pl.sucol;
+    T* V = at<T>(pl.V);
+    T* G1 = at<T>(pl.G1);
+    T* G2 = at<T>(pl.G2);
+    T* PhiS = at<T>(pl.PhiS);
+    T* AT = at<T>(pl.Ainv);
+    double* ldabs = at<double>(pl.ldabs);
+    double* lsign = at<double>(pl.lsign);
+    T* S5 = at<T>(pl.S5);
+    T* Y5 = at<T>(pl.Y5);
+    T* Z5 = at<T>(pl.Z5);
+    T* P5 = at<T>(pl.P5);
+
+    cudaMemsetAsync(ms, 0, sizeof(McmcStat), s);
+    if (mc.acc_count) cudaMemsetAsync(mc.acc_count, 0, sizeof(int32_t) * (size_t)Wn, s);
+    {
+      const int64_t wr[2] = {0, (int64_t)Wn};
+      cudaMemcpyAsync(rngu + 6, wr, sizeof(wr), cudaMemcpyHostToDevice, s);
+      // the host array is a stack temporary: finish the copy before it goes
+      if (cudaStreamSynchronize(s) != cudaSuccess) return FIRE_ERR_CUDA;
+    }
+    const int64_t* fullu = rngu + 4;
+    const int64_t* rowsW = rngu + 6;
+    auto refresh = [&](bool measure) -> int {
+      int rc = run();
+      reset_status = false;
+      if (rc != FIRE_OK) return rc;
+      mcmc_drift_kernel<<<(Wn + 255) / 256, 256, 0, s>>>(Wn, lp, lpf, &ms->drift_bits, measure ? 1 : 0);
+      launches += 1;
+      return FIRE_OK;
+    };
+    int rc = refresh(false);
+    if (rc != FIRE_OK) return rc;
+
+    const double c = sys->cutoff;
+    const unsigned actg = 152 * 8;
+    const McmcJastrow jp{p.cusp, p.jm2_b3, p.ja2_b3};
+    const size_t msm = (size_t)n * sizeof(int);
+    const size_t asm_ = (((size_t)n * sizeof(int) + 15) & ~(size_t)15) + (size_t)R * sizeof(T);
+    const int abt = RD < 1024 ? ((RD + 31) / 32) * 32 : 1024;
+    // two-hidden-layer SiLU readout over rows [rng[0], rng[1]); Zb has row stride ldzb
+    auto readout = [&](const T* Xin, int din, const int64_t* rng, int64_t cap, const T* w1, const T* b1,
+                       const T* w2, const T* b2, const T* w3, T* Zb, int64_t ldzb, T* Yb, T* F) {
+      gemm<T>(s, Xin, din, w1, J, false, Zb, ldzb, 0, 0, rng, cap, J, din);
+      mcmc_act_kernel<T, T><<<actg, 256, 0, s>>>(rng, J, Zb, ldzb, b1, Yb, J, 0);
+      gemm<T>(s, Yb, J, w2, J, false, Zb, ldzb, 0, 0, rng, cap, J, J);
+      mcmc_act_kernel<T, T><<<actg, 256, 0, s>>>(rng, J, Zb, ldzb, b2, Yb, J, 0);
+      rowdot_kernel<T, T><<<(unsigned)((cap + 7) / 8), 256, 0, s>>>(Yb, J, J, w3, F, rng, 0, 0);
+      launches += 5;
+    };
+    int64_t moves = 0;
+    const int64_t total_moves = (int64_t)mc.n_sweeps * n;
+    for (int sweep = 0; sweep < mc.n_sweeps; ++sweep) {
+      for (int k = 0; k < n; ++k) {
+        const uint64_t move = mc.counter + (uint64_t)sweep * n + k;
+        mark("mc_propose", 2);
+        mcmc_propose_kernel<<<Wn, 32, 0, s>>>(n, n_up, k, r, mc.sigma, mc.seed, move, 0, c * c, Umax, rk, uacc, Ul,
+                                              Uc, Ucu, st);
+        mcmc_scan_kernel<<<1, 1024, 0, s>>>(Wn, Umax, Uc, Ucu, Urow, rngu);
+        // h^0, its projections and the envelope row of electron k at r'_k
+        // (the proposals form a one-electron batch of Wn walkers)
+        const int nup1 = k < n_up ? 1 : 0;
+        mark("mc_embed_k", 9);
+        en_filter_kernel<T, T><<<Wn, d, 0, s>>>(Wn, 1, nup1, N, d, rk, sys->nuc_pos, sys->cutoff_nuc, p, S5, 1);
+        ln_fl_kernel<T, T><<<Wn, d, 0, s>>>(d, S5, Y5, p.ln_gamma, p.ln_beta, 1);
+        gemm<T>(s, Y5, d, p.glu_wg, d, false, Z5, 2 * d, 0, Wn, nullptr, Wn, d, d);
+        gemm<T>(s, Y5, d, p.glu_wv, d, false, Z5 + d, 2 * d, 0, Wn, nullptr, Wn, d, d);
+        glu_gate_kernel<T><<<Wn, d, 0, s>>>(d, Z5, P5, 1);
+        gemm<T>(s, P5, d, p.glu_wo, d, false, h0k, d, 0, Wn, nullptr, Wn, d, d);
+        for (int part = 0; part < 2; ++part)
+          gemm<T>(s, h0k, d, p.msg_w + (int64_t)part * d * d, d, false, PQk + (int64_t)part * 2 * d, 4 * d, 0, Wn,
+                  nullptr, Wn, d, d, 2, 0, (int64_t)(2 * d + 4) * d, d);
+        env_feat_kernel<T, T><<<Wn, 128, 0, s>>>(Wn, 1, nup1, N, E, rk, sys->nuc_pos, p.env_sigma, Qk, 1);
+        gemm<T>(s, Qk, NE, p.env_pi + (int64_t)(k < n_up ? 0 : 1) * Dn * NE, NE, true, Fk, Dn, 0, Wn, nullptr, Wn,
+                (int)Dn, NE);
+        check("mc embed k");
+        // h^1 and h of the members of U (compact rows)
+        mark("mc_msg", 1);
+        mcmc_msg_kernel<T, T><<<(unsigned)capU, d, msm, s>>>(Wn, n, n_up, d, k, Umax, r, rk, c, p, Ul, Uc, Urow, H0,
+                                                             PQ, h0k, PQk, X1);
+        check("mc msg");
+        mark("mc_mlp", 2 * dm.L);
+        for (int l = 0; l < dm.L; ++l) {
+          gemm<T>(s, X1, d, p.mlp_w + (int64_t)l * d * d, d, false, Zm, ldz, 0, 0, fullu, capU, d, d);
+          mcmc_act_kernel<T, T><<<actg, 256, 0, s>>>(fullu, d, Zm, ldz, p.mlp_b + (int64_t)l * d, X1, d, 1);
+        }
+        if (dm.flags & FIRE_J_MLP) {
+          mark("mc_jastrow", 0);
+          readout(X1, d, fullu, capU, p.jm1_w1, p.jm1_b1, p.jm1_w2, p.jm1_b2, p.jm1_w3, Zm, ldz, Ym, F1n);
+          readout(X1, d, fullu, capU, p.jm2_w1, p.jm2_b1, p.jm2_w2, p.jm2_b2, p.jm2_w3, Zm, ldz, Ym, F2n);
+        }
+        if (dm.flags & FIRE_J_ATT) {
+          mark("mc_att", 3);
+          gemm<T>(s, X1, d, p.att_q, d, true, SUn, RD1, 0, 0, fullu, capU, R, d);
+          gemm<T>(s, X1, d, p.att_wv, dr, false, SUn + R, RD1, 0, 0, fullu, capU, dr, d, R, 0, (int64_t)d * dr, dr);
+          mcmc_att_kernel<T><<<Wn, abt, asm_, s>>>(Wn, n, n_up, R, dr, Umax, Ul, Uc, Urow, SU, pl.ld_big, SUn, RD1,
+                                                    Vn);
+          readout(Vn, RD, rowsW, Wn, p.ja1_w1, p.ja1_b1, p.ja1_w2, p.ja1_b2, p.ja1_w3, VZ, J, VY, G1n);
+          readout(Vn, RD, rowsW, Wn, p.ja2_w1, p.ja2_b1, p.ja2_w2, p.ja2_b2, p.ja2_w3, VZ, J, VY, G2n);
+        }
+        // orbital rows of U, spin-up rows with the up-spin weights
+        mark("mc_orb", 2);
+        for (int sp = 0; sp < 2; ++sp)
+          gemm<T>(s, X1, d, p.orb_w + (int64_t)sp * D * d * n, n, false, On, Dn, 0, 0, rngu + 2 * sp, capU, n, d, D,
+                  0, (int64_t)d * n, n);
+        check("mc orbitals");
+        mark("mc_ratio", 1);
+        mcmc_ratio_kernel<T><<<(unsigned)(Wn * D), 256, 0, s>>>(Wn, n, n_up, D, k, Umax, Ul, Uc, Urow, On, Fenv, Fk,
+                                                               PhiS, AT, Dl, Mt, Mlu, Mpiv, lrat, srat);
+        check("mc ratio");
+        mark("mc_accept", 2);
+        mcmc_accept_kernel<T><<<Wn, 32, 0, s>>>(Wn, n, n_up, D, k, Umax, dm.flags, r, rk, uacc, Ul, Uc, Urow, jp, F1,
+                                                F2, F1n, F2n, G1, G2, G1n, G2n, ldabs, lsign, lrat, srat, lp, acc,
+                                                mc.acc_count, &ms->n_accepted);
+        mcmc_rows_kernel<T><<<(unsigned)capU, 128, 0, s>>>(
+            Wn, n, n_up, d, (int)Dn, RD, k, Umax, pl.ld_big, RD1, (dm.flags & FIRE_J_MLP) ? 1 : 0,
+            (dm.flags & FIRE_J_ATT) ? 1 : 0, acc, Ul, Uc, Urow, F1n, F2n, F1, F2, SUn, SU, h0k, H0, PQk, PQ, Fk,
+            Fenv, Vn, V, G1n, G2n, G1, G2);
+        mark("mc_woodbury", 1);
+        mcmc_woodbury_kernel<T><<<(unsigned)(Wn * D), 256, 0, s>>>(n, D, Umax, acc, Ul, Uc, Dl, Mlu, Mpiv, AT, PhiS,
+                                                                   Tu, Bw);
+        check("mc update");
+        ++moves;
+        if (mc.refresh_every > 0 && moves % mc.refresh_every == 0 && moves < total_moves) {
+          mark("mc_refresh", 0);
+          rc = refresh(true);
+          if (rc != FIRE_OK) return rc;
+        }
+      }
+    }
+    mark("mc_refresh", 0);
+    rc = refresh(moves > 0);
+    if (rc != FIRE_OK) return rc;
+    McmcStat hm;
+    if (cudaMemcpyAsync(&hm, ms, sizeof(McmcStat), cudaMemcpyDeviceToHost, s) != cudaSuccess) return FIRE_ERR_CUDA;
+    if (cudaMemcpyAsync(a.host_status, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return FIRE_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return FIRE_ERR_CUDA;
+    {
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) { set_last_error("mcmc", cudaGetErrorString(e)); return FIRE_ERR_CUDA; }
+    }
+    mc.n_accepted = (int64_t)hm.n_accepted;
+    double dr_ = 0.0;
+    memcpy(&dr_, &hm.drift_bits, sizeof(double));
+    mc.max_drift = dr_;
+    mc.counter += (uint64_t)total_moves;
+    if (a.n_launches) *a.n_launches = launches;
+    return failed ? FIRE_ERR_CUDA : FIRE_OK;
+  }
 };
 
 // Raises the dynamic shared-memory limit of every kernel that needs more than
@@ -824,6 +1071,7 @@ inline int set_smem_limits() {
   raise((const void*)lu_kernel<LT, 16>);
   raise((const void*)att_pool_kernel<T>);
   raise((const void*)gj_inverse_kernel<float, T>);
+  raise((const void*)mcmc_att_kernel<T>);
   cudaError_t e = cudaGetLastError();
   if (rc != FIRE_OK || e != cudaSuccess) set_last_error("smem limits", cudaGetErrorString(e));
   return rc;

@@ -36,13 +36,26 @@ struct Plan {
   size_t wbf16;            // packed BF16 weights (tensor-core form)
   size_t poff_dev;         // device copy of the parameter offsets (gradient call)
   size_t gradws;           // gradient scratch region (GradBufs)
+  // Metropolis moves (op FIRE_OP_MCMC): the cached state lives in the value
+  // buffers above (H0, PQ, Fenv, F1, F2, SU in big, V, G1, G2, ldabs, lsign)
+  // plus PhiS and Ainv; the rest is per-move scratch.
+  int Umax;                // largest update set |U|
+  size_t PhiS, mc_rk, mc_u, mc_Ul, mc_Uc, mc_Ucu, mc_Urow, mc_rng, mc_h0k, mc_PQk, mc_Qk, mc_Fk;
+  size_t mc_X, mc_Z, mc_Y, mc_F1n, mc_F2n, mc_SUn, mc_On, mc_Vn, mc_VZ, mc_VY, mc_G1n, mc_G2n;
+  size_t mc_Dl, mc_Mt, mc_Mlu, mc_piv, mc_lrat, mc_srat, mc_acc, mc_Tu, mc_Bw, mc_lp, mc_lpf, mc_sgf, mc_stat;
   int64_t nparams;
   size_t total;
   // column layout of `big`
   int64_t ld_big, zcol, ycol, sucol;
   // named buffers (diagnostics)
-  struct Ent { const char* name; size_t off, bytes; } ent[96];
+  struct Ent { const char* name; size_t off, bytes; } ent[160];
   int nent;
+};
+
+// Device counters of a Metropolis call.
+struct McmcStat {
+  unsigned long long n_accepted;
+  unsigned long long drift_bits;   // bits of the largest |log|Psi| drift| (a non-negative double)
 };
 
 int make_plan(const fire_system_t* sys, const fire_arch_t* arch, int64_t W, int prec, int k_cap,

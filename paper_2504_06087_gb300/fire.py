@@ -106,6 +106,10 @@ SIGNATURES = {
                                         ctypes.c_int32, VP, VP, VP, P(Info), VP, ctypes.c_size_t, VP]),
     "fire_local_energy_static": (ctypes.c_int, [P(System), P(Arch), P(Params), ctypes.c_int64, VP,
                                                 ctypes.c_int32, ctypes.c_int32, VP, VP, VP, VP, VP, P(Info), VP]),
+    "fire_mcmc_step": (ctypes.c_int, [P(System), P(Arch), P(Params), ctypes.c_int64, VP, ctypes.c_int32,
+                                      ctypes.c_int32, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_uint64, P(ctypes.c_uint64), VP, VP, VP, P(ctypes.c_int64),
+                                      P(ctypes.c_double), P(Info), VP, ctypes.c_size_t, VP]),
 }
 
 # Bytes of the library-owned workspace of fire_local_energy_static (include/fire.h).
@@ -345,6 +349,33 @@ class Fire:
         out["status"] = rc
         if check and rc != 0:
             raise FireError(rc, "fire_grad_logpsi", out["info"])
+        return out
+
+    def mcmc_step(self, r: torch.Tensor, sigma: float, n_sweeps: int, refresh_every: int = 32, seed: int = 0,
+                  counter: int = 0, check: bool = True):
+        """fire_mcmc_step: n_sweeps Metropolis sweeps of single-electron moves on
+        the device positions r [W, n_el, 3] float64, updated in place.
+        Returns {"logabs", "sign", "accepted" [W], "n_accepted", "max_drift",
+        "counter" (the advanced move counter), "info", "status"}."""
+        assert isinstance(r, torch.Tensor) and r.dtype == torch.float64 and r.is_contiguous()
+        assert r.device == torch.device(self.device) and r.dim() == 3 and r.shape[1] == self.system.n_el
+        W = r.shape[0]
+        out = {k: torch.empty(W, dtype=torch.float64, device=self.device) for k in ("logabs", "sign")}
+        out["accepted"] = torch.empty(W, dtype=torch.int32, device=self.device)
+        ws = self.workspace(W, OP_MCMC)
+        info = Info()
+        ctr = ctypes.c_uint64(counter)
+        nacc = ctypes.c_int64(0)
+        drift = ctypes.c_double(0.0)
+        rc = lib().fire_mcmc_step(ctypes.byref(self.sys_c), ctypes.byref(self.arch_c), ctypes.byref(self.params_c),
+                                  W, _ptr(r), self.k_cap, self.prec, float(sigma), int(n_sweeps),
+                                  int(refresh_every), ctypes.c_uint64(seed), ctypes.byref(ctr), _ptr(out["logabs"]),
+                                  _ptr(out["sign"]), _ptr(out["accepted"]), ctypes.byref(nacc),
+                                  ctypes.byref(drift), ctypes.byref(info), _ptr(ws), ws.numel(), self._stream())
+        out.update({"n_accepted": int(nacc.value), "max_drift": float(drift.value), "counter": int(ctr.value),
+                    "info": info.as_dict(), "status": rc})
+        if check and rc != 0:
+            raise FireError(rc, "fire_mcmc_step", out["info"])
         return out
 
     def unflatten(self, flat):

@@ -18,6 +18,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__)
 sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
+import torch  # noqa: E402
 
 from oracle import fire_oracle as O  # noqa: E402
 from paper_2504_06087_gb300 import synth  # noqa: E402
@@ -80,14 +81,43 @@ def main_grad(key: str, nw: int, nidx: int = 64):
     out = {"workload": key, "n_walkers": nw, "input_sha256": input_hash(r, p),
            "input_summary": input_summary(r, p),
            "source": "oracle/fire_oracle.py grad_logpsi (FP64, autograd)", "seconds": time.time() - t0,
-           "flat_index": idx.tolist(), "grad": flat[:, idx].tolist()}
+           "flat_index": idx.tolist(), "grad": flat[:, idx].tolist(),
+           "cond_dominant": dominant_conditioning(w, r, p).tolist()}
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"{key}_grad_oracle.json")
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
     print(path, out["seconds"])
 
 
+def dominant_conditioning(w, r, p) -> np.ndarray:
+    """2-norm condition number of each walker's orbital matrix with the
+    largest |det| (the one that dominates log|Psi| and its gradient)."""
+    pt = O.params_to_torch(p)
+    with torch.no_grad():
+        rt = torch.as_tensor(r, dtype=torch.float64)
+        _, _, h = O.embeddings(w.system, w.arch, pt, rt)
+        phi = O.orbitals(w.system, w.arch, pt, rt, h).numpy()       # [W, D, n, n]
+    dom = np.linalg.slogdet(phi)[1].argmax(axis=1)
+    return np.array([np.linalg.cond(phi[b, dom[b]]) for b in range(phi.shape[0])])
+
+
+def add_conditioning(key: str):
+    """Adds cond_dominant to an existing {key}_grad_oracle.json (same inputs)."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"{key}_grad_oracle.json")
+    out = json.load(open(path))
+    w = synth.workload(key)
+    r, p = synth.make_inputs(w, out["n_walkers"])
+    assert input_hash(r, p) == out["input_sha256"]
+    out["cond_dominant"] = dominant_conditioning(w, r, p).tolist()
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+    print(path, out["cond_dominant"])
+
+
 if __name__ == "__main__":
+    if len(sys.argv) > 2 and sys.argv[2] == "cond":
+        add_conditioning(sys.argv[1])
+        sys.exit(0)
     if len(sys.argv) > 3 and sys.argv[3] == "grad":
         main_grad(sys.argv[1], int(sys.argv[2]))
     else:

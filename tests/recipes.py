@@ -22,11 +22,12 @@ def const_h_params(system, arch, seed=0, bias=1.0):
     return p
 
 
-def hydrogen_like(sigma=1.0, z=1.0):
+def hydrogen_like(sigma=1.0, z=1.0, width=8):
     """One electron on a charge-z nucleus with Psi = exp(-sigma r) exactly:
-    constant embeddings, one determinant of one envelope orbital, no Jastrow."""
+    constant embeddings, one determinant of one envelope orbital, no Jastrow.
+    (The CUDA path takes widths that are multiples of 32.)"""
     system = synth.System(np.zeros((1, 3)), np.array([z]), 1, 1, 5.0, 20.0, "H")
-    arch = synth.Arch(width=8, n_layers=1, n_det=1, n_env=1, jastrow_width=8, flags=0)
+    arch = synth.Arch(width=width, n_layers=1, n_det=1, n_env=1, jastrow_width=width, flags=0)
     p = const_h_params(system, arch)
     p["orb_w"][:] = 1.0
     p["env_pi"][:] = 1.0

@@ -88,3 +88,35 @@ def test_host_side_argument_errors():
     n = ctypes.c_int32(0)
     assert L.fire_param_layout(ctypes.byref(sys_c), ctypes.byref(odd), None, ctypes.byref(n)) == 7
     assert L.fire_status_string(2).decode().startswith("neighbour")
+
+
+def test_mcmc_host_side_argument_errors():
+    """fire_mcmc_step rejects bad step sizes, sweep counts and missing
+    pointers on the host, before any launch; its workspace holds every walker
+    (no chunking) and the cached state on top of the value forward."""
+    _lib_or_skip()
+    w, sys_c, arch_c = _c_structs("water")
+    L = fire.lib()
+    prm = fire.Params(ctypes.c_void_p(16), 1, 0, 0)      # never dereferenced: rejected first
+    ctr = ctypes.c_uint64(0)
+    r = ctypes.c_void_p(16)
+    nacc, drift, info = ctypes.c_int64(0), ctypes.c_double(0), fire.Info()
+
+    def call(sigma=0.3, sweeps=1, refresh=32, counter=ctypes.byref(ctr), rr=r):
+        return L.fire_mcmc_step(ctypes.byref(sys_c), ctypes.byref(arch_c), ctypes.byref(prm), 4, rr, 64, 0,
+                                sigma, sweeps, refresh, 1, counter, None, None, None, ctypes.byref(nacc),
+                                ctypes.byref(drift), ctypes.byref(info), None, 0, None)
+    assert call(sigma=0.0) == 1
+    assert call(sigma=-1.0) == 1
+    assert call(sigma=float("nan")) == 1
+    assert call(sweeps=-1) == 1
+    assert call(refresh=-2) == 1
+    assert call(counter=None) == 1
+    assert call(rr=None) == 1
+    assert ctr.value == 0
+    big = L.fire_workspace_size(ctypes.byref(sys_c), ctypes.byref(arch_c), 4096, 1, 64, fire.OP_MCMC)
+    val = L.fire_workspace_size(ctypes.byref(sys_c), ctypes.byref(arch_c), 4096, 1, 64, fire.OP_LOGPSI)
+    assert big > val > 0
+    # the BF16_FP64 form samples in float32: same plan as FP32
+    b16 = L.fire_workspace_size(ctypes.byref(sys_c), ctypes.byref(arch_c), 4096, 2, 64, fire.OP_MCMC)
+    assert b16 == big

@@ -1,0 +1,117 @@
+"""GPU parity of fire_mcmc_step against the full-recompute Metropolis oracle.
+
+Decisions closer to the acceptance threshold than the rounding of the two
+implementations (the oracle's margin |ln u - 2 ln ratio|) are not compared;
+everything else (which moves were accepted, the final positions, log|Psi|)
+must agree.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import fire_oracle as O
+from oracle import mcmc_oracle as M
+from paper_2504_06087_gb300 import fire, synth
+from recipes import hydrogen_like
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(system, arch, p, prec, r_np, sigma, sweeps, seed, counter=0, refresh=32, k_cap=64):
+    f = fire.Fire(system, arch, p, prec, k_cap=k_cap)
+    r = torch.as_tensor(r_np, device=f.device).clone()
+    out = f.mcmc_step(r, sigma, sweeps, refresh_every=refresh, seed=seed, counter=counter)
+    torch.cuda.synchronize()
+    return f, r.cpu().numpy(), out
+
+
+@pytest.mark.parametrize("sigma", [0.3, 1.0])
+def test_water_fp64_decisions_match_oracle(sigma):
+    w = synth.workload("water")
+    r0, p = synth.make_inputs(w, 16)
+    seed, counter = 1234567890123, 5
+    f, r, out = _run(w.system, w.arch, p, "fp64", r0, sigma, 2, seed, counter, refresh=7)
+    ref = M.mcmc_sweeps(w.system, w.arch, p, r0, sigma, 2, seed, counter)
+    safe = ref["margin"] > 1e-8
+    assert safe.sum() >= 12
+    acc = out["accepted"].cpu().numpy()
+    np.testing.assert_array_equal(acc[safe], ref["accepted"][safe])
+    np.testing.assert_allclose(r[safe], ref["r"][safe], rtol=0, atol=1e-11)
+    la = out["logabs"].cpu().numpy()
+    np.testing.assert_allclose(la[safe], ref["logabs"][safe], rtol=1e-10, atol=1e-10)
+    assert out["counter"] == counter + 2 * w.system.n_el
+    assert out["n_accepted"] == int(acc.sum())
+    assert 0 < out["n_accepted"] < 16 * 2 * w.system.n_el
+    assert out["max_drift"] < 1e-9, out["max_drift"]
+
+
+def test_fp64_woodbury_state_matches_rebuilds():
+    """The same sweeps with the state rebuilt after every move and with the
+    low-rank updates alone (one rebuild at the end) end in the same place."""
+    w = synth.workload("water")
+    r0, p = synth.make_inputs(w, 8)
+    _, ra, oa = _run(w.system, w.arch, p, "fp64", r0, 0.5, 3, 77, refresh=1)
+    _, rb, ob = _run(w.system, w.arch, p, "fp64", r0, 0.5, 3, 77, refresh=0)
+    np.testing.assert_allclose(ra, rb, rtol=0, atol=1e-11)
+    np.testing.assert_array_equal(oa["accepted"].cpu().numpy(), ob["accepted"].cpu().numpy())
+    assert ob["max_drift"] < 1e-9, ob["max_drift"]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_hydrogen_mean_radius(prec):
+    """|Psi|^2 = exp(-2r): <r> = 3/2 bohr within 4 standard errors."""
+    system, arch, p = hydrogen_like(1.0, 1.0, width=32)
+    W = 8192
+    r0 = np.random.default_rng(5).standard_normal((W, 1, 3))
+    _, r, out = _run(system, arch, p, prec, r0, 1.0, 150, 31)
+    rad = np.linalg.norm(r[:, 0], axis=-1)
+    se = math.sqrt(0.75 / W)
+    assert abs(rad.mean() - 1.5) < 4 * se, (rad.mean(), se)
+    assert 0.3 < out["n_accepted"] / (W * 150) < 0.9
+
+
+def test_tiny_steps_are_accepted():
+    w = synth.workload("water")
+    r0, p = synth.make_inputs(w, 8)
+    _, r, out = _run(w.system, w.arch, p, "fp64", r0, 1e-9, 1, 3)
+    assert out["n_accepted"] == 8 * w.system.n_el
+    np.testing.assert_allclose(r, r0, atol=1e-7)
+
+
+def test_c8h10_fp32_against_oracle_and_rebuild():
+    """n_el = 58, float32 state with float64 refreshes: decisions with a
+    margin above the float32 rounding of ln|Psi'/Psi| equal the oracle's, the
+    carried log|Psi| stays within float32 rounding of each rebuild, and the
+    final log|Psi| matches the oracle at the final positions."""
+    w = synth.workload("c8h10")
+    r0, p = synth.make_inputs(w, 24)
+    f, r, out = _run(w.system, w.arch, p, "fp32", r0, 0.3, 1, 2024, refresh=16)
+    ref = M.mcmc_sweeps(w.system, w.arch, p, r0, 0.3, 1, 2024)
+    safe = ref["margin"] > 1e-3
+    assert safe.sum() >= 12
+    acc = out["accepted"].cpu().numpy()
+    np.testing.assert_array_equal(acc[safe], ref["accepted"][safe])
+    np.testing.assert_allclose(r[safe], ref["r"][safe], rtol=0, atol=1e-9)
+    assert out["max_drift"] < 2e-3, out["max_drift"]
+    la_ref, _ = O.logpsi_np(w.system, w.arch, p, r)
+    la = out["logabs"].cpu().numpy()
+    assert np.max(np.abs(la - la_ref) / np.maximum(np.abs(la_ref), 1.0)) < 1e-5
+
+
+def test_c26h24_fp32_sweep_keeps_a_consistent_state():
+    """n_el = 180 (the local-energy workload), one sweep: the carried log|Psi|
+    agrees with each float64 rebuild, and the final log|Psi| with a separate
+    fire_logpsi call at the final positions.  The drift bound is float32
+    rounding amplified by the conditioning of Phi (kappa ~ 1e4 here):
+    ~2e-4 per move, 6e-3 measured over 32 moves."""
+    w = synth.workload("c26h24")
+    r0, p = synth.make_inputs(w, 8)
+    f, r, out = _run(w.system, w.arch, p, "fp32", r0, 0.3, 1, 99, refresh=32)
+    assert out["max_drift"] < 2e-2, out["max_drift"]
+    rate = out["n_accepted"] / (8 * w.system.n_el)
+    assert 0.2 < rate < 0.99, rate
+    g = fire.Fire(w.system, w.arch, p, "fp32", k_cap=64)
+    lp = g.logpsi(torch.as_tensor(r, device=g.device))["logabs"].cpu().numpy()
+    np.testing.assert_allclose(out["logabs"].cpu().numpy(), lp, rtol=1e-6, atol=1e-6)
