@@ -7,6 +7,8 @@ C26H24, 90 up / 90 down, 4096 walkers per GPU, width 256, 4 MLP layers,
 form at the E_L errors each shows against the FP64 oracle.
 
     python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+    python bench.py --op grad            # per-walker d log|Psi|/d theta, C26H24
+    python bench.py --op mcmc [--chain k | --scan]   # Metropolis sweeps, C_kH_{k+2}
 
 One step = one fire_local_energy call over all walkers of the GPU (neighbour
 lists included).  Inputs are resident in HBM for `value`; `e2e` adds the
@@ -138,6 +140,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-coords", type=int, default=8,
                     help="second-derivative passes in one oracle sample (of 3 n_el)")
+    ap.add_argument("--op", default="local_energy", choices=["local_energy", "grad", "mcmc"],
+                    help="local_energy: the headline metric; grad / mcmc: the adjoint and the sampler")
+    ap.add_argument("--chain", type=int, default=26, help="--op mcmc: zigzag chain C_kH_{k+2}")
+    ap.add_argument("--scan", action="store_true", help="--op mcmc: every chain k = 2, 8, ..., 44")
+    ap.add_argument("--sweeps", type=int, default=2, help="--op mcmc: sweeps per timed call")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -146,6 +153,8 @@ def main():
     dist = world > 1
     if args.impl == "reference":
         return reference_arm(args, rank, world)
+    if args.op != "local_energy":
+        return bench_other(args, rank, world, local)
 
     from paper_2504_06087_gb300 import fire, synth
 
@@ -381,6 +390,112 @@ def reference_arm(args, rank, world):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
+
+
+# ---------------------------------------------------------------------------
+# the adjoint and the sampler (not the headline metric)
+# ---------------------------------------------------------------------------
+
+def _timed(fn, steps, warmup, dev):
+    for _ in range(max(warmup, 0)):
+        fn()
+    torch.cuda.synchronize(dev)
+    stream = torch.cuda.current_stream(dev)
+    times, outs = [], []
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        outs.append(fn())
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return times, outs
+
+
+def bench_other(args, rank, world, local):
+    from paper_2504_06087_gb300 import fire, synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    base = {"n_gpus": world, "steps": args.steps, "warmup": args.warmup, "scaling": "weak", "vs_baseline": None,
+            "data": "synthetic"}
+    if args.op == "grad":
+        w = synth.workload("c26h24", args.walkers)
+        r_np, p = synth.make_inputs(w, args.walkers)
+        f = fire.Fire(w.system, w.arch, p, "fp32", k_cap=64, device=str(dev))
+        r = torch.as_tensor(r_np, device=dev)
+        sampler = ClockSampler(local)
+        sampler.start()
+        times, outs = _timed(lambda: f.grad_logpsi(r)["info"], args.steps, args.warmup, dev)
+        clocks = sampler.stop()
+        fire.profile(True)
+        f.grad_logpsi(r)
+        torch.cuda.synchronize(dev)
+        stages = fire.profile_report()
+        fire.profile(False)
+        ms = float(np.mean(times))
+        line = dict(base, metric="per-walker d log|Psi|/d theta evaluations/sec at n_el=180 (FP32 adjoint)",
+                    value=args.walkers / (ms / 1e3), unit="walkers/s", ms_per_step=ms, higher_is_better=True,
+                    dtype="f32+f64", config={"workload": f"zigzag C26H24, n_el=180, {args.walkers} walkers, "
+                                                         f"{f.n_params} parameters, output [W, P] float32",
+                                             "precision": "fp32 (float64 LU)"},
+                    gpu_launches=int(outs[-1]["n_launches"]), clocks=clocks,
+                    stages_ms={k: round(v[1], 3) for k, v in sorted(stages.items(), key=lambda kv: -kv[1][1])})
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
+    chains = [2, 8, 14, 20, 26, 32, 38, 44] if args.scan else [args.chain]
+    pts = []
+    for k in chains:
+        w = synth.workload(f"sample_k{k}", args.walkers)
+        r_np, p = synth.make_inputs(w, args.walkers)
+        f = fire.Fire(w.system, w.arch, p, "fp32", k_cap=64, device=str(dev))
+        r = torch.as_tensor(r_np, device=dev).contiguous()
+        ctr = [0]
+
+        def call():
+            o = f.mcmc_step(r, 0.3, args.sweeps, refresh_every=32, seed=2504, counter=ctr[0])
+            ctr[0] = o["counter"]
+            return {kk: o[kk] for kk in ("n_accepted", "max_drift", "info", "walker_drift")}
+        sampler = ClockSampler(local)
+        sampler.start()
+        times, outs = _timed(call, args.steps, args.warmup, dev)
+        clocks = sampler.stop()
+        fire.profile(True)
+        call()
+        torch.cuda.synchronize(dev)
+        stages = fire.profile_report()
+        fire.profile(False)
+        n = w.system.n_el
+        ms = float(np.mean(times))
+        sweeps_s = args.sweeps / (ms / 1e3)
+        acc = sum(o["n_accepted"] for o in outs) / (len(outs) * args.walkers * n * args.sweeps)
+        drift = max(o["max_drift"] for o in outs)
+        wd = torch.stack([o["walker_drift"] for o in outs]).max(0).values.cpu().numpy()
+        dq = {"p50": float(np.percentile(wd, 50)), "p99": float(np.percentile(wd, 99)),
+              "p999": float(np.percentile(wd, 99.9)), "max": float(wd.max()),
+              "walkers_above_1e-2": int((wd > 1e-2).sum())}
+        pts.append((n, 1.0 / sweeps_s))
+        line = dict(base, metric=f"Metropolis sweeps/sec, zigzag C{k}H{k + 2} (n_el={n}), {args.walkers} walkers",
+                    value=sweeps_s, unit="sweeps/s", ms_per_step=ms, higher_is_better=True, dtype="f32+f64",
+                    config={"workload": f"zigzag C{k}H{k + 2}, n_el={n}, {args.walkers} walkers, width 256, 4 MLP "
+                                        f"layers, 16 determinants, c=5 bohr, sigma=0.3 bohr single-electron moves, "
+                                        f"float64 refresh every 32 moves; one step = one fire_mcmc_step call of "
+                                        f"{args.sweeps} sweeps (with its start and end rebuilds)",
+                            "precision": "fp32 state, float64 LU / ratios / refresh"},
+                    s_per_sweep=1.0 / sweeps_s, acceptance=acc, max_drift=drift, drift_quantiles=dq,
+                    gpu_launches=int(outs[-1]["info"]["n_launches"]), clocks=clocks,
+                    stages_ms={kk: round(v[1], 3) for kk, v in sorted(stages.items(), key=lambda kv: -kv[1][1])})
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        del f, r
+        torch.cuda.empty_cache()
+    if len(pts) > 2 and rank == 0:
+        x = np.log([q[0] for q in pts])
+        y = np.log([q[1] for q in pts])
+        slope = float(np.polyfit(x, y, 1)[0])
+        print(json.dumps({"metric": "fit: seconds per sweep ~ n_el^a", "a": slope,
+                          "points": [{"n_el": q[0], "s_per_sweep": q[1]} for q in pts]}), flush=True)
 
 if __name__ == "__main__":
     main()

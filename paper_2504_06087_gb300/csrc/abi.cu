@@ -168,46 +168,51 @@ static size_t layout(Plan& pl, int64_t Wc) {
     pl.poff_dev = pl.gradws = 0;
   }
   if (mc) {
-    // cached Phi and the per-move scratch of the Metropolis call
+    // cached Phi and the counters that live through the whole call
     const int64_t Um = pl.Umax, capU = Wc * Um, Dn = D * n, RD1 = dm.R + RD;
     const int64_t zc = d > J ? d : J;
     TAKE(PhiS, Wc * D * n * n * ts);
-    TAKE(mc_rk, Wc * 3 * 8);
-    TAKE(mc_u, Wc * 8);
-    TAKE(mc_Ul, capU * 4);
-    TAKE(mc_Uc, Wc * 4);
-    TAKE(mc_Ucu, Wc * 4);
-    TAKE(mc_Urow, capU * 4);
     TAKE(mc_rng, 16 * 8);
-    TAKE(mc_h0k, Wc * d * ts);
-    TAKE(mc_PQk, Wc * 4 * d * ts);
-    TAKE(mc_Qk, Wc * NE * ts);
-    TAKE(mc_Fk, Wc * Dn * ts);
-    TAKE(mc_X, capU * d * ts);
-    TAKE(mc_Z, capU * zc * ts);
-    TAKE(mc_Y, capU * J * ts);
-    TAKE(mc_F1n, capU * ts);
-    TAKE(mc_F2n, capU * ts);
-    TAKE(mc_SUn, capU * RD1 * ts);
-    TAKE(mc_On, capU * Dn * ts);
-    TAKE(mc_Vn, Wc * RD * ts);
-    TAKE(mc_VZ, Wc * J * ts);
-    TAKE(mc_VY, Wc * J * ts);
-    TAKE(mc_G1n, Wc * ts);
-    TAKE(mc_G2n, Wc * ts);
-    TAKE(mc_Dl, Wc * D * Um * n * ts);
-    TAKE(mc_Mt, Wc * D * Um * Um * ts);
-    TAKE(mc_Mlu, Wc * D * Um * Um * 8);
-    TAKE(mc_piv, Wc * D * Um * 4);
-    TAKE(mc_lrat, Wc * D * 8);
-    TAKE(mc_srat, Wc * D * 8);
-    TAKE(mc_acc, Wc * 4);
-    TAKE(mc_Tu, Wc * D * Um * n * ts);
-    TAKE(mc_Bw, Wc * D * Um * n * ts);
     TAKE(mc_lp, Wc * 8);
     TAKE(mc_lpf, Wc * 8);
     TAKE(mc_sgf, Wc * 8);
     TAKE(mc_stat, sizeof(McmcStat));
+    TAKE(mc_wdrift, Wc * 8);
+    TAKE(mc_lref, Wc * D * 8);         // log|det| of each matrix at its last factorisation
+    TAKE(mc_H1, nb * d * ts);          // cached h^1 rows (block order)
+    // per-move scratch: dead during a refresh, so it shares the float64 LU
+    // buffer (dead during the moves) when it fits there
+    struct Sc { size_t* field; const char* name; size_t bytes; };
+    const Sc sc[] = {
+        {&pl.mc_rk, "mc_rk", (size_t)(Wc * 3 * 8)}, {&pl.mc_u, "mc_u", (size_t)(Wc * 8)},
+        {&pl.mc_Ul, "mc_Ul", (size_t)(capU * 4)}, {&pl.mc_Uc, "mc_Uc", (size_t)(Wc * 4)},
+        {&pl.mc_Ucu, "mc_Ucu", (size_t)(Wc * 4)}, {&pl.mc_Urow, "mc_Urow", (size_t)(capU * 4)},
+        {&pl.mc_h0k, "mc_h0k", (size_t)(Wc * d) * ts}, {&pl.mc_PQk, "mc_PQk", (size_t)(Wc * 4 * d) * ts},
+        {&pl.mc_Qk, "mc_Qk", (size_t)(Wc * NE) * ts}, {&pl.mc_Fk, "mc_Fk", (size_t)(Wc * Dn) * ts},
+        {&pl.mc_X, "mc_X", (size_t)(capU * d) * ts}, {&pl.mc_H1n, "mc_H1n", (size_t)(capU * d) * ts},
+        {&pl.mc_Z, "mc_Z", (size_t)(capU * zc) * ts},
+        {&pl.mc_Y, "mc_Y", (size_t)(capU * J) * ts}, {&pl.mc_F1n, "mc_F1n", (size_t)capU * ts},
+        {&pl.mc_F2n, "mc_F2n", (size_t)capU * ts}, {&pl.mc_SUn, "mc_SUn", (size_t)(capU * RD1) * ts},
+        {&pl.mc_On, "mc_On", (size_t)(capU * Dn) * ts}, {&pl.mc_Vn, "mc_Vn", (size_t)(Wc * RD) * ts},
+        {&pl.mc_VZ, "mc_VZ", (size_t)(Wc * J) * ts}, {&pl.mc_VY, "mc_VY", (size_t)(Wc * J) * ts},
+        {&pl.mc_G1n, "mc_G1n", (size_t)Wc * ts}, {&pl.mc_G2n, "mc_G2n", (size_t)Wc * ts},
+        {&pl.mc_Dl, "mc_Dl", (size_t)(Wc * D * Um * n) * ts}, {&pl.mc_Mt, "mc_Mt", (size_t)(Wc * D * Um * Um) * ts},
+        {&pl.mc_Mlu, "mc_Mlu", (size_t)(Wc * D * Um * Um * 8)}, {&pl.mc_piv, "mc_piv", (size_t)(Wc * D * Um * 4)},
+        {&pl.mc_lrat, "mc_lrat", (size_t)(Wc * D * 8)}, {&pl.mc_srat, "mc_srat", (size_t)(Wc * D * 8)},
+        {&pl.mc_acc, "mc_acc", (size_t)(Wc * 4)}, {&pl.mc_flag, "mc_flag", (size_t)(Wc * D * 4)},
+        {&pl.mc_rep, "mc_rep", (size_t)kWoodburySlots * n * n * 8}, {&pl.mc_rpiv, "mc_rpiv", (size_t)kWoodburySlots * n * 4},
+        {&pl.mc_Tu, "mc_Tu", (size_t)(kWoodburySlots * Um * n) * ts},
+        {&pl.mc_Bw, "mc_Bw", (size_t)(kWoodburySlots * Um * n) * ts}};
+    size_t need = 0;
+    for (const Sc& e : sc) need = align_up(need + e.bytes);
+    const size_t lu_bytes = (size_t)(Wc * D * n * n) * ls;
+    size_t q = need <= lu_bytes ? pl.LU : o;
+    for (const Sc& e : sc) {
+      *e.field = q;
+      if (pl.nent < 160) pl.ent[pl.nent++] = Plan::Ent{e.name, q, e.bytes};
+      q = align_up(q + e.bytes);
+    }
+    if (q > o) o = q;
   }
 #undef TAKE
   pl.total = o;

@@ -232,18 +232,22 @@ static __global__ void __launch_bounds__(1024) mcmc_scan_kernel(int W, int Umax,
   }
 }
 
-// h^1 of every member i of U under the proposed positions (value only):
-//   h^1_i = h^0_i + sum_{j in N_i} Gamma(e_ij) SiLU(h^0_i W^a + h^0_j W^a' + e-bar_ij W^a_c + b^a)
-// with the neighbour list rebuilt on the fly (same spin ascending, then the
-// opposite spin).  h^0 and its projections of electron k come from h0k / PQk.
-// One CTA per (walker, slot), blockDim == d; dynamic shared memory n ints.
+// h^1 of every member i of U under the proposed positions (value only),
+//   h^1_i = h^0_i + sum_{j in N_i} Gamma(e_ij) SiLU(h^0_i W^a + h^0_j W^a' + e-bar_ij W^a_c + b^a).
+// For i = k every term changes: the neighbour list is rebuilt on the fly
+// (same spin ascending, then the opposite spin) with h^0 and projections of
+// k from h0k / PQk.  For i != k only the term of the pair (i, k) changes:
+// h^1_i = cached h^1_i - [old (i, k) term] + [new (i, k) term], each present
+// when that distance is within c.  One CTA per (walker, slot), blockDim == d;
+// dynamic shared memory n ints.  Writes h^1 to X (overwritten by the MLP) and
+// to H1n (kept for the cache).
 template <typename T, typename W>
 __global__ void mcmc_msg_kernel(int Wn, int n, int n_up, int d, int k, int Umax, const double* __restrict__ r,
                                 const double* __restrict__ rk, double cut, Params<W> p,
                                 const int32_t* __restrict__ Ul, const int32_t* __restrict__ Uc,
                                 const int32_t* __restrict__ Urow, const T* __restrict__ H0,
-                                const T* __restrict__ PQ, const T* __restrict__ h0k, const T* __restrict__ PQk,
-                                T* __restrict__ X) {
+                                const T* __restrict__ PQ, const T* __restrict__ H1, const T* __restrict__ h0k,
+                                const T* __restrict__ PQk, T* __restrict__ X, T* __restrict__ H1n) {
   constexpr int H = kEdgeHidden, G = kGauss;
   __shared__ FL3<T> feat[H + G + 4];
   extern __shared__ int mm_nbr[];
@@ -255,34 +259,6 @@ __global__ void mcmc_msg_kernel(int Wn, int n, int n_up, int d, int k, int Umax,
   const int64_t ld4 = 4 * (int64_t)d;
   const double* rw = r + (int64_t)w * n * 3;
   const double* rkw = rk + (int64_t)w * 3;
-  auto pos = [&](int j, int t) -> double { return j == k ? rkw[t] : rw[3 * j + t]; };
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    const bool up = i < n_up;
-    int cntN = 0;
-    for (int pass = 0; pass < 2; ++pass) {
-      const bool same = pass == 0;
-      const int lo = (up == same) ? 0 : n_up, hi = (up == same) ? n_up : n;
-      for (int j0 = lo; j0 < hi; j0 += 32) {
-        const int j = j0 + lane;
-        bool in = false;
-        if (j < hi && j != i) {
-          double a2 = 0.0;
-          for (int t = 0; t < 3; ++t) {
-            const double dd = pos(i, t) - pos(j, t);
-            a2 += dd * dd;
-          }
-          in = a2 <= cut * cut;
-        }
-        const unsigned m = __ballot_sync(0xffffffffu, in);
-        if (in) mm_nbr[cntN + __popc(m & ((1u << lane) - 1u))] = j;
-        cntN += __popc(m);
-      }
-      if (lane == 0) s_cnt[pass] = cntN;
-    }
-  }
-  __syncthreads();
-  const int cpar = s_cnt[0], ctot = s_cnt[1];
   T w2[H], we[G], wc[2][4], bb[2];
 #pragma unroll
   for (int h = 0; h < H; ++h) w2[h] = T(p.ee_w2[h * d + c]);
@@ -294,13 +270,8 @@ __global__ void mcmc_msg_kernel(int Wn, int n, int n_up, int d, int k, int Umax,
 #pragma unroll
     for (int q = 0; q < 4; ++q) wc[a][q] = T(p.msg_w[((int64_t)a * (2 * d + 4) + 2 * d + q) * d + c]);
   }
-  const int bi = block_index(w, i, Wn, n, n_up);
-  const T* Pi = (i == k) ? PQk + (int64_t)w * ld4 : PQ + (int64_t)bi * ld4;
-  T acc = (i == k) ? h0k[(int64_t)w * d + c] : H0[(int64_t)bi * d + c];
-  for (int s = 0; s < ctot; ++s) {
-    const int j = mm_nbr[s];
-    const int a = (s < cpar) ? 0 : 1;
-    const double ddv[3] = {pos(i, 0) - pos(j, 0), pos(i, 1) - pos(j, 1), pos(i, 2) - pos(j, 2)};
+  // one message term: Gamma(delta) SiLU(Pi^a + Qj^a + e-bar W_c^a + b^a)
+  auto term = [&](const double ddv[3], const T* Pi, const T* Qj, int a) -> T {
     const double rr = sqrt(ddv[0] * ddv[0] + ddv[1] * ddv[1] + ddv[2] * ddv[2]);
     T dv[3] = {T(ddv[0]), T(ddv[1]), T(ddv[2])};
     __syncthreads();
@@ -313,13 +284,65 @@ __global__ void mcmc_msg_kernel(int Wn, int n, int n_up, int d, int k, int Umax,
     for (int g = 0; g < G; ++g) ev += feat[H + g].v * we[g];
 #pragma unroll
     for (int q = 0; q < 4; ++q) eb += feat[H + G + q].v * wc[a][q];
-    const T* Qj = (j == k) ? PQk + (int64_t)w * ld4 : PQ + (int64_t)block_index(w, j, Wn, n, n_up) * ld4;
     const T z = Pi[(int64_t)a * d + c] + Qj[2 * (int64_t)d + (int64_t)a * d + c] + eb + bb[a];
     T f, f1, f2;
     silu3<T>(z, f, f1, f2);
-    acc += (gv * ev) * f;
+    return (gv * ev) * f;
+  };
+  T acc;
+  if (i == k) {
+    auto pos = [&](int j, int t) -> double { return j == k ? rkw[t] : rw[3 * j + t]; };
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      const bool up = i < n_up;
+      int cntN = 0;
+      for (int pass = 0; pass < 2; ++pass) {
+        const bool same = pass == 0;
+        const int lo = (up == same) ? 0 : n_up, hi = (up == same) ? n_up : n;
+        for (int j0 = lo; j0 < hi; j0 += 32) {
+          const int j = j0 + lane;
+          bool in = false;
+          if (j < hi && j != i) {
+            double a2 = 0.0;
+            for (int t = 0; t < 3; ++t) {
+              const double dd = pos(i, t) - pos(j, t);
+              a2 += dd * dd;
+            }
+            in = a2 <= cut * cut;
+          }
+          const unsigned m = __ballot_sync(0xffffffffu, in);
+          if (in) mm_nbr[cntN + __popc(m & ((1u << lane) - 1u))] = j;
+          cntN += __popc(m);
+        }
+        if (lane == 0) s_cnt[pass] = cntN;
+      }
+    }
+    __syncthreads();
+    const int cpar = s_cnt[0], ctot = s_cnt[1];
+    const T* Pi = PQk + (int64_t)w * ld4;
+    acc = h0k[(int64_t)w * d + c];
+    for (int s = 0; s < ctot; ++s) {
+      const int j = mm_nbr[s];
+      const double ddv[3] = {pos(i, 0) - pos(j, 0), pos(i, 1) - pos(j, 1), pos(i, 2) - pos(j, 2)};
+      acc += term(ddv, Pi, PQ + (int64_t)block_index(w, j, Wn, n, n_up) * ld4, s < cpar ? 0 : 1);
+    }
+  } else {
+    const int bi = block_index(w, i, Wn, n, n_up);
+    const T* Pi = PQ + (int64_t)bi * ld4;
+    const int a = ((i < n_up) == (k < n_up)) ? 0 : 1;
+    acc = H1[(int64_t)bi * d + c];
+    for (int side = 0; side < 2; ++side) {   // 0: remove the old (i, k) term, 1: add the new one
+      const double* q = side == 0 ? rw + 3 * k : rkw;
+      const double ddv[3] = {rw[3 * i] - q[0], rw[3 * i + 1] - q[1], rw[3 * i + 2] - q[2]};
+      if (!(ddv[0] * ddv[0] + ddv[1] * ddv[1] + ddv[2] * ddv[2] <= cut * cut)) continue;
+      const T* Qk = side == 0 ? PQ + (int64_t)block_index(w, k, Wn, n, n_up) * ld4 : PQk + (int64_t)w * ld4;
+      const T t = term(ddv, Pi, Qk, a);
+      acc += side == 0 ? -t : t;
+    }
   }
-  X[(int64_t)Urow[(int64_t)w * Umax + u] * d + c] = acc;
+  const int64_t row = Urow[(int64_t)w * Umax + u];
+  X[row * d + c] = acc;
+  H1n[row * d + c] = acc;
 }
 
 // Y[row][c] = (residual ? Y[row][c] : 0) + SiLU(Z[row][c] + b[c]) for rows in
@@ -339,18 +362,33 @@ __global__ void mcmc_act_kernel(const int64_t* __restrict__ rng, int ncol, const
   }
 }
 
+// log of the shrink factor beyond which a determinant is refactorised: a
+// determinant that an accepted move leaves more than 100 times smaller than
+// at its last factorisation gets a fresh float64 LU and inverse from the
+// cached Phi instead of its Woodbury update, whose rounding errors grow with
+// that shrink (a single determinant passing near its own node while the
+// others keep Psi away from zero).
+constexpr double kRepairLogShrink = -4.605170185988091;   // ln(1e-2)
+
+// |U| up to which the small determinant-lemma matrix lives in shared memory.
+constexpr int kLemmaSmem = 64;
+
 // Determinant lemma for one (walker, det): Delta rows of U (new orbital row
 // times envelope minus the cached Phi row), M = I + Delta A[:, U], its LU with
-// partial pivoting in float64 and log|det M|, sign.  Delta, the LU and the
-// pivots are kept for the Woodbury update.  One CTA (256 threads) per
-// (walker, det).  Mt is [Umax][Umax] scratch in T per (walker, det).
+// partial pivoting in float64, log|det M| and sign.  Delta, the LU factors
+// (in Mg, [Umax][Umax] per pair) and the pivots are kept for the Woodbury
+// update, which solves with them: M can be far from orthogonal (a nearly
+// singular determinant has a large A, so Delta A[:, U] is large while det M
+// stays moderate), and an explicit M^-1 would lose the digits the solve keeps.
+// One CTA (256 threads) per (walker, det); the LU runs in shared memory when
+// |U| <= kLemmaSmem, else in Mg.
 template <typename T>
 __global__ void __launch_bounds__(256) mcmc_ratio_kernel(
     int Wn, int n, int n_up, int D, int k, int Umax, const int32_t* __restrict__ Ul, const int32_t* __restrict__ Uc,
     const int32_t* __restrict__ Urow, const T* __restrict__ On, const T* __restrict__ Fenv, const T* __restrict__ Fk,
     const T* __restrict__ Phi, const T* __restrict__ AT, T* __restrict__ Dl, T* __restrict__ Mt,
-    double* __restrict__ Mlu, int32_t* __restrict__ Mpiv, double* __restrict__ lrat, double* __restrict__ srat) {
-  __shared__ T sm[2 * 32 * 33];
+    double* __restrict__ Mg, int32_t* __restrict__ Mpiv, double* __restrict__ lrat, double* __restrict__ srat) {
+  __shared__ double su[kLemmaSmem * (kLemmaSmem + 1)];   // the product tiles, then M
   __shared__ int s_p;
   const int w = blockIdx.x / D, dd = blockIdx.x % D;
   const int u = Uc[w];
@@ -370,40 +408,46 @@ __global__ void __launch_bounds__(256) mcmc_ratio_kernel(
   }
   // Delta A[:, U] = Delta (u x n) times the rows U of A^T
   T* Mw = Mt + md * Umax * Umax;
-  cta_gemm_nt<T>(u, u, n, Dw, n, Aw, n, U, Mw, Umax, T(1), false, sm);
-  double* M = Mlu + md * Umax * Umax;
+  cta_gemm_nt<T>(u, u, n, Dw, n, Aw, n, U, Mw, Umax, T(1), false, reinterpret_cast<T*>(su));
+  const bool in_smem = u <= kLemmaSmem;
+  double* M = in_smem ? su : Mg + md * Umax * Umax;
+  const int ldm = in_smem ? kLemmaSmem + 1 : Umax;
   for (int e = threadIdx.x; e < u * u; e += blockDim.x) {
     const int a = e / u, b = e % u;
-    M[a * Umax + b] = (double)Mw[a * Umax + b] + (a == b ? 1.0 : 0.0);
+    M[a * ldm + b] = (double)Mw[a * Umax + b] + (a == b ? 1.0 : 0.0);
   }
   __syncthreads();
+  int32_t* pv = Mpiv + md * Umax;
   double la = 0.0;
   int neg = 0;
   bool zero = false;
   for (int c = 0; c < u; ++c) {
-    if (threadIdx.x == 0) {
-      int pv = c;
-      double best = fabs(M[c * Umax + c]);
-      for (int q = c + 1; q < u; ++q)
-        if (fabs(M[q * Umax + c]) > best) {
-          best = fabs(M[q * Umax + c]);
-          pv = q;
-        }
-      s_p = pv;
-      Mpiv[md * Umax + c] = pv;
+    if (threadIdx.x < 32) {   // pivot: the first row of largest |M[q][c]|, q >= c
+      double best = -1.0;
+      int bq = c;
+      for (int q = c + threadIdx.x; q < u; q += 32) {
+        const double v = fabs(M[q * ldm + c]);
+        if (v > best) { best = v; bq = q; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oq = __shfl_xor_sync(0xffffffffu, bq, o);
+        if (ob > best || (ob == best && oq < bq)) { best = ob; bq = oq; }
+      }
+      if (threadIdx.x == 0) { s_p = bq; pv[c] = bq; }
     }
     __syncthreads();
-    const int pv = s_p;
-    if (pv != c) {
+    const int pq = s_p;
+    if (pq != c) {
       for (int q = threadIdx.x; q < u; q += blockDim.x) {
-        const double t = M[c * Umax + q];
-        M[c * Umax + q] = M[pv * Umax + q];
-        M[pv * Umax + q] = t;
+        const double t = M[c * ldm + q];
+        M[c * ldm + q] = M[pq * ldm + q];
+        M[pq * ldm + q] = t;
       }
       neg ^= 1;
     }
     __syncthreads();
-    const double piv = M[c * Umax + c];
+    const double piv = M[c * ldm + c];
     if (piv == 0.0) {
       zero = true;
     } else {
@@ -412,16 +456,21 @@ __global__ void __launch_bounds__(256) mcmc_ratio_kernel(
       const int wdt = u - c - 1;
       for (int e = threadIdx.x; e < wdt * wdt; e += blockDim.x) {
         const int q = c + 1 + e / wdt, cc = c + 1 + e % wdt;
-        M[q * Umax + cc] -= (M[q * Umax + c] / piv) * M[c * Umax + cc];
+        M[q * ldm + cc] -= (M[q * ldm + c] / piv) * M[c * ldm + cc];
       }
       __syncthreads();
-      for (int q = c + 1 + threadIdx.x; q < u; q += blockDim.x) M[q * Umax + c] /= piv;
+      for (int q = c + 1 + threadIdx.x; q < u; q += blockDim.x) M[q * ldm + c] /= piv;
     }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
     lrat[md] = zero ? -INFINITY : la;
     srat[md] = zero ? 0.0 : (neg ? -1.0 : 1.0);
+  }
+  // the factors go to Mg for the Woodbury solve (already there when M lived in Mg)
+  if (in_smem) {
+    double* G = Mg + md * Umax * Umax;
+    for (int e = threadIdx.x; e < u * u; e += blockDim.x) G[(e / u) * Umax + e % u] = M[(e / u) * ldm + e % u];
   }
 }
 
@@ -485,7 +534,8 @@ __global__ void mcmc_accept_kernel(int Wn, int n, int n_up, int D, int k, int Um
                                    double* __restrict__ ldabs, double* __restrict__ lsign,
                                    const double* __restrict__ lrat, const double* __restrict__ srat,
                                    double* __restrict__ lp, int32_t* __restrict__ acc,
-                                   int32_t* __restrict__ acc_count, unsigned long long* __restrict__ nacc) {
+                                   int32_t* __restrict__ acc_count, unsigned long long* __restrict__ nacc,
+                                   const double* __restrict__ lref, int32_t* __restrict__ flag) {
   const int w = blockIdx.x;
   const int lane = threadIdx.x;
   double* rw = r + (int64_t)w * n * 3;
@@ -528,14 +578,15 @@ __global__ void mcmc_accept_kernel(int Wn, int n, int n_up, int D, int k, int Um
   const double* lr = lrat + (int64_t)w * D;
   const double* sr = srat + (int64_t)w * D;
   double lmax = -INFINITY, lmaxn = -INFINITY;
+  auto live = [&](int q) { return sw[q] * sr[q] != 0.0 && isfinite(lr[q]); };
   for (int q = 0; q < D; ++q) {
     if (sw[q] != 0.0 && lw[q] > lmax) lmax = lw[q];
-    if (sw[q] * sr[q] != 0.0 && lw[q] + lr[q] > lmaxn) lmaxn = lw[q] + lr[q];
+    if (live(q) && lw[q] + lr[q] > lmaxn) lmaxn = lw[q] + lr[q];
   }
   double So = 0.0, Sn = 0.0;
   for (int q = 0; q < D; ++q) {
     if (sw[q] != 0.0) So += sw[q] * exp(lw[q] - lmax);
-    if (sw[q] * sr[q] != 0.0) Sn += sw[q] * sr[q] * exp(lw[q] + lr[q] - lmaxn);
+    if (live(q)) Sn += sw[q] * sr[q] * exp(lw[q] + lr[q] - lmaxn);
   }
   double logr = (lmaxn + log(fabs(Sn))) - (lmax + log(fabs(So)));
   if (flags & FIRE_J_CUSP) logr += dc;
@@ -552,8 +603,16 @@ __global__ void mcmc_accept_kernel(int Wn, int n, int n_up, int D, int k, int Um
   if (ok) {
     for (int t = 0; t < 3; ++t) rw[3 * k + t] = rn[t];
     for (int q = 0; q < D; ++q) {
-      ldabs[(int64_t)w * D + q] += lr[q];
-      lsign[(int64_t)w * D + q] *= sr[q];
+      const int64_t md = (int64_t)w * D + q;
+      if (isfinite(lr[q])) {
+        ldabs[md] += lr[q];
+        lsign[md] *= sr[q];
+      } else {
+        ldabs[md] = -INFINITY;
+        lsign[md] = 0.0;
+      }
+      // refactorise a determinant that shrank too far since its last LU
+      flag[md] = (ldabs[md] >= lref[md] + kRepairLogShrink) ? 0 : 1;
     }
     lp[w] += logr;
     if (acc_count) acc_count[w] += 1;
@@ -562,7 +621,7 @@ __global__ void mcmc_accept_kernel(int Wn, int n, int n_up, int D, int k, int Um
 }
 
 // Copies the recomputed rows of an accepted move into the cached state:
-// MLP-Jastrow outputs and attention scores/values of every member of U, the
+// h^1, MLP-Jastrow outputs and attention scores/values of every member of U, the
 // initial embedding, projections and envelope row of electron k, and the
 // walker's attention registers and readouts.  One CTA per (walker, slot).
 template <typename T>
@@ -575,12 +634,14 @@ __global__ void mcmc_rows_kernel(int Wn, int n, int n_up, int d, int Dn, int RD,
                                  T* __restrict__ H0, const T* __restrict__ PQk, T* __restrict__ PQ,
                                  const T* __restrict__ Fk, T* __restrict__ Fenv, const T* __restrict__ Vn,
                                  T* __restrict__ V, const T* __restrict__ G1n, const T* __restrict__ G2n,
-                                 T* __restrict__ G1, T* __restrict__ G2) {
+                                 T* __restrict__ G1, T* __restrict__ G2, const T* __restrict__ H1n,
+                                 T* __restrict__ H1) {
   const int w = blockIdx.x / Umax, a = blockIdx.x % Umax;
   if (!acc[w] || a >= Uc[w]) return;
   const int i = Ul[(int64_t)w * Umax + a];
   const int64_t b = block_index(w, i, Wn, n, n_up);
   const int64_t q = Urow[(int64_t)w * Umax + a];
+  for (int c = threadIdx.x; c < d; c += blockDim.x) H1[b * d + c] = H1n[q * d + c];
   if (has_att)
     for (int c = threadIdx.x; c < ldsun; c += blockDim.x) SU[b * ldsu + c] = SUn[q * ldsun + c];
   if (has_mlp && threadIdx.x == 0) {
@@ -602,56 +663,98 @@ __global__ void mcmc_rows_kernel(int Wn, int n, int n_up, int d, int Dn, int RD,
 }
 
 // Woodbury update of A^T and the rows U of Phi for accepted walkers:
-//   B = Delta A (u x n), C = M^-1 B,
+//   B = Delta A (u x n), C = M^-1 B (solved with the LU factors of M),
 //   A'^T[m][l] = A^T[m][l] - sum_a C[a][m] A^T[U_a][l],   Phi_U += Delta.
-// One CTA (256 threads) per (walker, det).  Tu, Bw: [Umax][n] scratch each.
+// A persistent grid of 256-thread CTAs walks the (walker, det) pairs; CTA b
+// keeps its scratch (Tw: [Umax][n] in Tu, B then C: [Umax][n] in Bw) in slot
+// b.  Flagged pairs are refactorised by mcmc_repair_kernel instead.
 template <typename T>
 __global__ void __launch_bounds__(256) mcmc_woodbury_kernel(
-    int n, int D, int Umax, const int32_t* __restrict__ acc, const int32_t* __restrict__ Ul,
-    const int32_t* __restrict__ Uc, const T* __restrict__ Dl, const double* __restrict__ Mlu,
-    const int32_t* __restrict__ Mpiv, T* __restrict__ AT, T* __restrict__ Phi, T* __restrict__ Tu,
-    T* __restrict__ Bw) {
-  __shared__ T sm[2 * 32 * 33];
-  const int w = blockIdx.x / D, dd = blockIdx.x % D;
-  if (!acc[w]) return;
-  const int u = Uc[w];
-  const int64_t md = (int64_t)w * D + dd;
-  const int32_t* U = Ul + (int64_t)w * Umax;
-  T* A = AT + md * n * n;
-  const T* Dw = Dl + md * Umax * n;
-  T* Tw = Tu + md * Umax * n;
-  T* Bm = Bw + md * Umax * n;
-  const double* M = Mlu + md * Umax * Umax;
-  const int32_t* pv = Mpiv + md * Umax;
-  for (int e = threadIdx.x; e < u * n; e += blockDim.x) Tw[e] = A[(int64_t)U[e / n] * n + e % n];
-  // B[a][m] = sum_l Delta[a][l] A^T[m][l]
-  cta_gemm_nt<T>(u, n, n, Dw, n, A, n, nullptr, Bm, n, T(1), false, sm);
-  // C = M^-1 B, column by column (row swaps, unit-lower and upper solves)
-  for (int m = threadIdx.x; m < n; m += blockDim.x) {
-    for (int c = 0; c < u; ++c) {
-      const int p = pv[c];
-      if (p != c) {
-        const T t = Bm[(int64_t)c * n + m];
-        Bm[(int64_t)c * n + m] = Bm[(int64_t)p * n + m];
-        Bm[(int64_t)p * n + m] = t;
+    int Wn, int n, int D, int Umax, const int32_t* __restrict__ acc, const int32_t* __restrict__ flag,
+    const int32_t* __restrict__ Ul, const int32_t* __restrict__ Uc, const T* __restrict__ Dl,
+    const double* __restrict__ Mlu, const int32_t* __restrict__ Mpiv, T* __restrict__ AT, T* __restrict__ Phi,
+    T* __restrict__ Tu, T* __restrict__ Bw) {
+  // the product tiles and the LU of M are never live together: one buffer
+  __shared__ double su[kLemmaSmem * (kLemmaSmem + 1)];
+  __shared__ int spv[kLemmaSmem];
+  T* sm = reinterpret_cast<T*>(su);
+  double* sL = su;
+  T* Tw = Tu + (int64_t)blockIdx.x * Umax * n;
+  T* Bm = Bw + (int64_t)blockIdx.x * Umax * n;
+  for (int64_t md = blockIdx.x; md < (int64_t)Wn * D; md += gridDim.x) {
+    const int w = (int)(md / D);
+    if (!acc[w]) continue;
+    const int u = Uc[w];
+    const int32_t* U = Ul + (int64_t)w * Umax;
+    T* A = AT + md * n * n;
+    const T* Dw = Dl + md * Umax * n;
+    T* P = Phi + md * n * n;
+    if (flag[md]) {   // refactorised by mcmc_repair_kernel: only Phi moves here
+      for (int e = threadIdx.x; e < u * n; e += blockDim.x) P[(int64_t)U[e / n] * n + e % n] += Dw[e];
+      continue;
+    }
+    for (int e = threadIdx.x; e < u * n; e += blockDim.x) Tw[e] = A[(int64_t)U[e / n] * n + e % n];
+    // B[a][m] = sum_l Delta[a][l] A^T[m][l]   (starts and ends with a barrier)
+    cta_gemm_nt<T>(u, n, n, Dw, n, A, n, nullptr, Bm, n, T(1), false, sm);
+    const bool in_smem = u <= kLemmaSmem;
+    const double* Mg = Mlu + md * Umax * Umax;
+    const int32_t* pvg = Mpiv + md * Umax;
+    if (in_smem) {
+      for (int e = threadIdx.x; e < u * u; e += blockDim.x)
+        sL[(e / u) * (kLemmaSmem + 1) + e % u] = Mg[(e / u) * Umax + e % u];
+      for (int e = threadIdx.x; e < u; e += blockDim.x) spv[e] = pvg[e];
+    }
+    __syncthreads();
+    const double* L = in_smem ? sL : Mg;
+    const int ldl = in_smem ? kLemmaSmem + 1 : Umax;
+    const int32_t* pv = in_smem ? spv : pvg;
+    // C = M^-1 B: one column per thread, row swaps then unit-lower and upper
+    // solves in float64; the column lives in local memory
+    for (int m = threadIdx.x; m < n; m += blockDim.x) {
+      double x[kLemmaSmem];
+      if (in_smem) {
+        for (int c = 0; c < u; ++c) x[c] = (double)Bm[(int64_t)c * n + m];
+        for (int c = 0; c < u; ++c) {
+          const int p = pv[c];
+          if (p != c) { const double t = x[c]; x[c] = x[p]; x[p] = t; }
+        }
+        for (int c = 0; c < u; ++c) {
+          double s = x[c];
+          for (int q = 0; q < c; ++q) s -= L[c * ldl + q] * x[q];
+          x[c] = s;
+        }
+        for (int c = u - 1; c >= 0; --c) {
+          double s = x[c];
+          for (int q = c + 1; q < u; ++q) s -= L[c * ldl + q] * x[q];
+          x[c] = s / L[c * ldl + c];
+        }
+        for (int c = 0; c < u; ++c) Bm[(int64_t)c * n + m] = (T)x[c];
+      } else {   // large U: the same solve on the column in the scratch
+        for (int c = 0; c < u; ++c) {
+          const int p = pv[c];
+          if (p != c) {
+            const T t = Bm[(int64_t)c * n + m];
+            Bm[(int64_t)c * n + m] = Bm[(int64_t)p * n + m];
+            Bm[(int64_t)p * n + m] = t;
+          }
+        }
+        for (int c = 0; c < u; ++c) {
+          double s = (double)Bm[(int64_t)c * n + m];
+          for (int q = 0; q < c; ++q) s -= L[c * ldl + q] * (double)Bm[(int64_t)q * n + m];
+          Bm[(int64_t)c * n + m] = (T)s;
+        }
+        for (int c = u - 1; c >= 0; --c) {
+          double s = (double)Bm[(int64_t)c * n + m];
+          for (int q = c + 1; q < u; ++q) s -= L[c * ldl + q] * (double)Bm[(int64_t)q * n + m];
+          Bm[(int64_t)c * n + m] = (T)(s / L[c * ldl + c]);
+        }
       }
     }
-    for (int c = 0; c < u; ++c) {
-      double s = (double)Bm[(int64_t)c * n + m];
-      for (int q = 0; q < c; ++q) s -= M[c * Umax + q] * (double)Bm[(int64_t)q * n + m];
-      Bm[(int64_t)c * n + m] = (T)s;
-    }
-    for (int c = u - 1; c >= 0; --c) {
-      double s = (double)Bm[(int64_t)c * n + m];
-      for (int q = c + 1; q < u; ++q) s -= M[c * Umax + q] * (double)Bm[(int64_t)q * n + m];
-      Bm[(int64_t)c * n + m] = (T)(s / M[c * Umax + c]);
-    }
+    __syncthreads();
+    // A^T[m][l] -= sum_a C[a][m] Tw[a][l]  (ends with a barrier: the slot is free)
+    cta_gemm_tn<T>(n, n, u, Bm, n, Tw, n, A, n, T(-1), true, sm);
+    for (int e = threadIdx.x; e < u * n; e += blockDim.x) P[(int64_t)U[e / n] * n + e % n] += Dw[e];
   }
-  __syncthreads();
-  // A^T -= C^T Tw
-  cta_gemm_tn<T>(n, n, u, Bm, n, Tw, n, A, n, T(-1), true, sm);
-  T* P = Phi + md * n * n;
-  for (int e = threadIdx.x; e < u * n; e += blockDim.x) P[(int64_t)U[e / n] * n + e % n] += Dw[e];
 }
 
 // ---------------------------------------------------------------------------
@@ -664,20 +767,18 @@ __global__ void convert_kernel(int64_t count, const S* __restrict__ src, T* __re
     dst[e] = (T)src[e];
 }
 
-// A = Phi^-1 from the LU factors, for matrices [m0, m0 + gridDim.x): column
-// j of A solves L U x = e_{pinv[j]} in LT; Xs is [n][n] LT scratch per matrix
-// of the launch; the result is written transposed in AT's type.  One CTA per
-// matrix, one thread per column; no shared-memory limit on n.
+// A = Phi^-1 from the LU factors (P Phi = L U, unit L) of one n x n matrix,
+// written transposed (AT[k][l] = A[l][k]) in AT's type, by one CTA of 256
+// threads.  Columns go in panels of 32: column j of A solves
+// L U x = e_{pinv[j]}; the panel X[n][33] sits in shared memory (sm), warp g
+// owns columns 4g .. 4g+3 with 8 lanes per column splitting each dot product.
 template <typename LT, typename AT>
-__global__ void inverse_global_kernel(int n, int64_t m0, const LT* __restrict__ LU, const int32_t* __restrict__ piv,
-                                      LT* __restrict__ Xs, AT* __restrict__ Ainv) {
-  extern __shared__ int ig_smem[];
-  int* perm = ig_smem;
-  int* pinv = perm + n;
-  const int64_t mat = m0 + blockIdx.x;
-  const LT* A = LU + mat * n * n;
-  const int32_t* pv = piv + mat * n;
-  LT* X = Xs + (int64_t)blockIdx.x * n * n;
+__device__ void inverse_panel_block(int n, const LT* __restrict__ A, const int32_t* __restrict__ pv,
+                                    AT* __restrict__ out, unsigned char* sm) {
+  LT* X = reinterpret_cast<LT*>(sm);                         // [n][33]
+  int* pinv = reinterpret_cast<int*>(X + (int64_t)n * 33);   // [n]
+  int* perm = pinv + n;                                      // [n]
+  __syncthreads();
   if (threadIdx.x == 0) {
     for (int i = 0; i < n; ++i) perm[i] = i;
     for (int k = 0; k < n; ++k) {
@@ -688,34 +789,166 @@ __global__ void inverse_global_kernel(int n, int64_t m0, const LT* __restrict__ 
     for (int i = 0; i < n; ++i) pinv[perm[i]] = i;
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    const int p = pinv[j];
-    for (int i = 0; i < n; ++i) {
-      LT s = (i == p) ? LT(1) : LT(0);
-      for (int k = 0; k < i; ++k) s -= A[(int64_t)i * n + k] * X[(int64_t)k * n + j];
-      X[(int64_t)i * n + j] = s;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int cl = 4 * wp + (lane >> 3);   // column of the panel
+  const int sub = lane & 7;
+  for (int j0 = 0; j0 < n; j0 += 32) {
+    const int j = j0 + cl;
+    const int p = j < n ? pinv[j] : -1;
+    for (int i = 0; i < n; ++i) {   // forward: unit lower
+      LT s = LT(0);
+      for (int q = sub; q < i; q += 8) s += A[(int64_t)i * n + q] * X[q * 33 + cl];
+      s += __shfl_xor_sync(0xffffffffu, s, 1);
+      s += __shfl_xor_sync(0xffffffffu, s, 2);
+      s += __shfl_xor_sync(0xffffffffu, s, 4);
+      if (sub == 0) X[i * 33 + cl] = ((i == p) ? LT(1) : LT(0)) - s;
+      __syncwarp();
     }
-    for (int i = n - 1; i >= 0; --i) {
-      LT s = X[(int64_t)i * n + j];
-      for (int k = i + 1; k < n; ++k) s -= A[(int64_t)i * n + k] * X[(int64_t)k * n + j];
-      X[(int64_t)i * n + j] = s / A[(int64_t)i * n + i];
+    for (int i = n - 1; i >= 0; --i) {   // backward: upper
+      LT s = LT(0);
+      for (int q = i + 1 + sub; q < n; q += 8) s += A[(int64_t)i * n + q] * X[q * 33 + cl];
+      s += __shfl_xor_sync(0xffffffffu, s, 1);
+      s += __shfl_xor_sync(0xffffffffu, s, 2);
+      s += __shfl_xor_sync(0xffffffffu, s, 4);
+      if (sub == 0) X[i * 33 + cl] = (X[i * 33 + cl] - s) / A[(int64_t)i * n + i];
+      __syncwarp();
     }
+    __syncthreads();
+    // out[j][l] = A[l][j] = X[l][j - j0]: row j of the output is column j of A
+    for (int e = threadIdx.x; e < 32 * n; e += blockDim.x) {
+      const int jj = e / n, l = e % n;
+      if (j0 + jj < n) out[(int64_t)(j0 + jj) * n + l] = (AT)X[l * 33 + jj];
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  AT* out = Ainv + mat * n * n;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) out[e] = (AT)X[(int64_t)(e % n) * n + e / n];
 }
 
+// The inverse of matrices [m0, m0 + gridDim.x) of a batch, one CTA each.
+template <typename LT, typename AT>
+__global__ void __launch_bounds__(256) inverse_panel_kernel(int n, int64_t m0, const LT* __restrict__ LU,
+                                                            const int32_t* __restrict__ piv,
+                                                            AT* __restrict__ Ainv) {
+  extern __shared__ unsigned char ip_smem[];
+  const int64_t mat = m0 + blockIdx.x;
+  inverse_panel_block<LT, AT>(n, LU + mat * n * n, piv + mat * n, Ainv + mat * n * n, ip_smem);
+}
+
+inline size_t inverse_panel_smem(int n, size_t lsz) { return (size_t)n * 33 * lsz + 2 * (size_t)n * sizeof(int); }
+
+
+// Right-looking LU with partial pivoting of one n x n matrix in place, by one
+// CTA (pivot search by warp 0).  Returns log|det| and the sign through
+// shared memory (sign 0 and -inf for an exactly zero pivot).
+template <typename LT>
+__device__ void lu_block(int n, LT* __restrict__ A, int32_t* __restrict__ pv, double* s_la, double* s_sg) {
+  __shared__ int s_p;
+  double la = 0.0;
+  int neg = 0;
+  bool zero = false;
+  for (int c = 0; c < n; ++c) {
+    if (threadIdx.x < 32) {
+      double best = -1.0;
+      int bq = c;
+      for (int q = c + threadIdx.x; q < n; q += 32) {
+        const double v = fabs((double)A[(int64_t)q * n + c]);
+        if (v > best) { best = v; bq = q; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oq = __shfl_xor_sync(0xffffffffu, bq, o);
+        if (ob > best || (ob == best && oq < bq)) { best = ob; bq = oq; }
+      }
+      if (threadIdx.x == 0) { s_p = bq; pv[c] = bq; }
+    }
+    __syncthreads();
+    const int pq = s_p;
+    if (pq != c) {
+      for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        const LT t = A[(int64_t)c * n + q];
+        A[(int64_t)c * n + q] = A[(int64_t)pq * n + q];
+        A[(int64_t)pq * n + q] = t;
+      }
+      neg ^= 1;
+    }
+    __syncthreads();
+    const LT piv = A[(int64_t)c * n + c];
+    if (piv == LT(0)) {
+      zero = true;
+    } else {
+      la += log(fabs((double)piv));
+      if (piv < LT(0)) neg ^= 1;
+      const int wdt = n - c - 1;
+      for (int e = threadIdx.x; e < wdt * wdt; e += blockDim.x) {
+        const int q = c + 1 + e / wdt, cc = c + 1 + e % wdt;
+        A[(int64_t)q * n + cc] -= (A[(int64_t)q * n + c] / piv) * A[(int64_t)c * n + cc];
+      }
+      __syncthreads();
+      for (int q = c + 1 + threadIdx.x; q < n; q += blockDim.x) A[(int64_t)q * n + c] /= piv;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *s_la = zero ? -INFINITY : la;
+    *s_sg = zero ? 0.0 : (neg ? -1.0 : 1.0);
+  }
+  __syncthreads();
+}
+
+// Refactorisation of the flagged (walker, det) pairs of accepted walkers
+// from the cached Phi (already updated by the move): log|det|, sign and A^T.
+// A persistent grid; CTA b uses slot b of the float64 scratch (n x n matrix,
+// n pivots) and dynamic shared memory for the inverse panel.
+template <typename T, typename LT>
+__global__ void __launch_bounds__(256) mcmc_repair_kernel(int Wn, int n, int D, const int32_t* __restrict__ acc,
+                                                          const int32_t* __restrict__ flag,
+                                                          const T* __restrict__ Phi, T* __restrict__ AT,
+                                                          double* __restrict__ ldabs, double* __restrict__ lsign,
+                                                          double* __restrict__ lref, LT* __restrict__ scratch,
+                                                          int32_t* __restrict__ spiv) {
+  extern __shared__ unsigned char rp_smem[];
+  __shared__ double s_la, s_sg;
+  LT* L = scratch + (int64_t)blockIdx.x * n * n;
+  int32_t* pv = spiv + (int64_t)blockIdx.x * n;
+  for (int64_t md = blockIdx.x; md < (int64_t)Wn * D; md += gridDim.x) {
+    if (!acc[md / D] || !flag[md]) continue;
+    const T* P = Phi + md * n * n;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) L[e] = (LT)P[e];
+    __syncthreads();
+    lu_block<LT>(n, L, pv, &s_la, &s_sg);
+    if (threadIdx.x == 0) {
+      ldabs[md] = s_la;
+      lsign[md] = s_sg;
+      lref[md] = s_la;
+    }
+    T* A = AT + md * n * n;
+    if (s_sg == 0.0) {
+      // singular: the determinant stays dead until the next rebuild
+      for (int e = threadIdx.x; e < n * n; e += blockDim.x) A[e] = T(0);
+      __syncthreads();
+      continue;
+    }
+    inverse_panel_block<LT, T>(n, L, pv, A, rp_smem);
+  }
+}
+
+
 // drift = max_w |lp_inc - lp_fresh| (the bits of a non-negative double order
-// like the values); then lp_inc = lp_fresh.
+// like the values), wdrift[w] = the walker's largest drift so far; then
+// lp_inc = lp_fresh.
 static __global__ void mcmc_drift_kernel(int W, double* __restrict__ lp_inc, const double* __restrict__ lp_fresh,
-                                  unsigned long long* __restrict__ drift_bits, int measure) {
+                                         double* __restrict__ wdrift, unsigned long long* __restrict__ drift_bits,
+                                         int measure) {
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= W) return;
   if (measure) {
     const double a = lp_inc[w], b = lp_fresh[w];
-    if (isfinite(a) && isfinite(b))
-      atomicMax(drift_bits, (unsigned long long)__double_as_longlong(fabs(a - b)));
+    if (isfinite(a) && isfinite(b)) {
+      const double dr = fabs(a - b);
+      atomicMax(drift_bits, (unsigned long long)__double_as_longlong(dr));
+      if (dr > wdrift[w]) wdrift[w] = dr;
+    }
+  } else {
+    wdrift[w] = 0.0;
   }
   lp_inc[w] = lp_fresh[w];
 }

@@ -645,6 +645,9 @@ struct Runner {
       msg_kernel<T, T><<<nb, d, 0, s>>>(wc, n, n_up, d, K, r, c, p, idx, cnt, boff, H0, PQ, X, Xb, kMaxSplit,
                                         capA * d, deriv);
       check("msg");
+      if (dm.op == FIRE_OP_MCMC) {   // the Metropolis state keeps h^1 (value rows, block order)
+        cudaMemcpyAsync(at<T>(pl.mc_H1), X, sizeof(T) * (size_t)nb * d, cudaMemcpyDeviceToDevice, s);
+      }
       // 5. embedding MLP h = MLP(h^1): L residual SiLU layers
       T* big = at<T>(pl.big);
       T* Z = big + pl.zcol;
@@ -759,18 +762,13 @@ struct Runner {
       lu_kernel<LT, 16><<<wc * D, 256, lusm, s>>>(n, LUb, piv, ldabs, lsign);
       check("lu");
       if (mc) {
-        // A^T = (Phi^-1)^T from the float64 factors, in batches that fit the
-        // dead orbital-value buffer as float64 scratch
+        // A^T = (Phi^-1)^T from the float64 factors
         mark("inverse", 1);
         const int64_t nmat = (int64_t)wc * D;
-        const size_t ov_bytes = (size_t)nb * (size_t)Dn * sizeof(T);
-        int64_t per = (int64_t)(ov_bytes / ((size_t)n * n * sizeof(LT)));
-        if (per < 1) per = 1;
-        if (per > 65535) per = 65535;
-        for (int64_t m0 = 0; m0 < nmat; m0 += per) {
-          const int64_t cnt = nmat - m0 < per ? nmat - m0 : per;
-          inverse_global_kernel<LT, T><<<(unsigned)cnt, 256, (size_t)2 * n * sizeof(int), s>>>(
-              n, m0, LUb, piv, reinterpret_cast<LT*>(Ov), at<T>(pl.Ainv));
+        const size_t ism = inverse_panel_smem(n, sizeof(LT));
+        for (int64_t m0 = 0; m0 < nmat; m0 += 65535) {
+          const int64_t cnt = nmat - m0 < 65535 ? nmat - m0 : 65535;
+          inverse_panel_kernel<LT, T><<<(unsigned)cnt, 256, ism, s>>>(n, m0, LUb, piv, at<T>(pl.Ainv));
           launches += 1;
         }
         check("inverse");
@@ -890,6 +888,11 @@ struct Runner {
     T* Bw = at<T>(pl.mc_Bw);
     double* lp = at<double>(pl.mc_lp);
     double* lpf = at<double>(pl.mc_lpf);
+    double* wdrift = at<double>(pl.mc_wdrift);
+    T* H1 = at<T>(pl.mc_H1);
+    T* H1n = at<T>(pl.mc_H1n);
+    double* lref = at<double>(pl.mc_lref);
+    int32_t* flag = at<int32_t>(pl.mc_flag);
     // the state, in the value-forward buffers
     T* H0 = at<T>(pl.H0);
     T* PQ = at<T>(pl.PQ);
@@ -923,7 +926,8 @@ struct Runner {
       int rc = run();
       reset_status = false;
       if (rc != FIRE_OK) return rc;
-      mcmc_drift_kernel<<<(Wn + 255) / 256, 256, 0, s>>>(Wn, lp, lpf, &ms->drift_bits, measure ? 1 : 0);
+      cudaMemcpyAsync(lref, at<double>(pl.ldabs), sizeof(double) * (size_t)Wn * D, cudaMemcpyDeviceToDevice, s);
+      mcmc_drift_kernel<<<(Wn + 255) / 256, 256, 0, s>>>(Wn, lp, lpf, wdrift, &ms->drift_bits, measure ? 1 : 0);
       launches += 1;
       return FIRE_OK;
     };
@@ -975,7 +979,7 @@ struct Runner {
         // h^1 and h of the members of U (compact rows)
         mark("mc_msg", 1);
         mcmc_msg_kernel<T, T><<<(unsigned)capU, d, msm, s>>>(Wn, n, n_up, d, k, Umax, r, rk, c, p, Ul, Uc, Urow, H0,
-                                                             PQ, h0k, PQk, X1);
+                                                             PQ, H1, h0k, PQk, X1, H1n);
         check("mc msg");
         mark("mc_mlp", 2 * dm.L);
         for (int l = 0; l < dm.L; ++l) {
@@ -1009,14 +1013,19 @@ struct Runner {
         mark("mc_accept", 2);
         mcmc_accept_kernel<T><<<Wn, 32, 0, s>>>(Wn, n, n_up, D, k, Umax, dm.flags, r, rk, uacc, Ul, Uc, Urow, jp, F1,
                                                 F2, F1n, F2n, G1, G2, G1n, G2n, ldabs, lsign, lrat, srat, lp, acc,
-                                                mc.acc_count, &ms->n_accepted);
+                                                mc.acc_count, &ms->n_accepted, lref, flag);
         mcmc_rows_kernel<T><<<(unsigned)capU, 128, 0, s>>>(
             Wn, n, n_up, d, (int)Dn, RD, k, Umax, pl.ld_big, RD1, (dm.flags & FIRE_J_MLP) ? 1 : 0,
             (dm.flags & FIRE_J_ATT) ? 1 : 0, acc, Ul, Uc, Urow, F1n, F2n, F1, F2, SUn, SU, h0k, H0, PQk, PQ, Fk,
-            Fenv, Vn, V, G1n, G2n, G1, G2);
+            Fenv, Vn, V, G1n, G2n, G1, G2, H1n, H1);
         mark("mc_woodbury", 1);
-        mcmc_woodbury_kernel<T><<<(unsigned)(Wn * D), 256, 0, s>>>(n, D, Umax, acc, Ul, Uc, Dl, Mlu, Mpiv, AT, PhiS,
-                                                                   Tu, Bw);
+        const int64_t npair = (int64_t)Wn * D;
+        mcmc_woodbury_kernel<T><<<(unsigned)(npair < kWoodburySlots ? npair : kWoodburySlots), 256, 0, s>>>(
+            Wn, n, D, Umax, acc, flag, Ul, Uc, Dl, Mlu, Mpiv, AT, PhiS, Tu, Bw);
+        mcmc_repair_kernel<T, LT><<<(unsigned)(npair < kWoodburySlots ? npair : kWoodburySlots), 256,
+                                    inverse_panel_smem(n, sizeof(LT)), s>>>(
+            Wn, n, D, acc, flag, PhiS, AT, ldabs, lsign, lref, at<LT>(pl.mc_rep), at<int32_t>(pl.mc_rpiv));
+        launches += 1;
         check("mc update");
         ++moves;
         if (mc.refresh_every > 0 && moves % mc.refresh_every == 0 && moves < total_moves) {
@@ -1072,6 +1081,8 @@ inline int set_smem_limits() {
   raise((const void*)att_pool_kernel<T>);
   raise((const void*)gj_inverse_kernel<float, T>);
   raise((const void*)mcmc_att_kernel<T>);
+  raise((const void*)inverse_panel_kernel<LT, T>);
+  raise((const void*)mcmc_repair_kernel<T, LT>);
   cudaError_t e = cudaGetLastError();
   if (rc != FIRE_OK || e != cudaSuccess) set_last_error("smem limits", cudaGetErrorString(e));
   return rc;

@@ -374,6 +374,8 @@ class Fire:
                                   ctypes.byref(drift), ctypes.byref(info), _ptr(ws), ws.numel(), self._stream())
         out.update({"n_accepted": int(nacc.value), "max_drift": float(drift.value), "counter": int(ctr.value),
                     "info": info.as_dict(), "status": rc})
+        # per-walker largest drift of this call (a diagnostic buffer of the workspace)
+        out["walker_drift"] = self.ws_view(W, OP_MCMC, "mc_wdrift", torch.float64, (W,)).clone()
         if check and rc != 0:
             raise FireError(rc, "fire_mcmc_step", out["info"])
         return out

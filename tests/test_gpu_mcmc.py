@@ -80,15 +80,34 @@ def test_tiny_steps_are_accepted():
     np.testing.assert_allclose(r, r0, atol=1e-7)
 
 
-def test_c8h10_fp32_against_oracle_and_rebuild():
+@pytest.fixture(scope="module")
+def c8h10_oracle():
+    w = synth.workload("c8h10")
+    r0, p = synth.make_inputs(w, 24)
+    return w, r0, p, M.mcmc_sweeps(w.system, w.arch, p, r0, 0.3, 1, 2024)
+
+
+def test_c8h10_fp64_low_rank_state_stays_exact(c8h10_oracle):
+    """n_el = 58, float64 state, no rebuild inside the sweep: every decision
+    equals the oracle's and the carried log|Psi| equals the rebuild at the
+    end to float64 rounding -- including walkers where single determinants
+    pass near their nodes (refactorised instead of Woodbury-updated)."""
+    w, r0, p, ref = c8h10_oracle
+    f, r, out = _run(w.system, w.arch, p, "fp64", r0, 0.3, 1, 2024, refresh=0)
+    safe = ref["margin"] > 1e-8
+    acc = out["accepted"].cpu().numpy()
+    np.testing.assert_array_equal(acc[safe], ref["accepted"][safe])
+    np.testing.assert_allclose(r[safe], ref["r"][safe], rtol=0, atol=1e-11)
+    assert out["max_drift"] < 1e-8, out["max_drift"]
+
+
+def test_c8h10_fp32_against_oracle_and_rebuild(c8h10_oracle):
     """n_el = 58, float32 state with float64 refreshes: decisions with a
     margin above the float32 rounding of ln|Psi'/Psi| equal the oracle's, the
     carried log|Psi| stays within float32 rounding of each rebuild, and the
     final log|Psi| matches the oracle at the final positions."""
-    w = synth.workload("c8h10")
-    r0, p = synth.make_inputs(w, 24)
+    w, r0, p, ref = c8h10_oracle
     f, r, out = _run(w.system, w.arch, p, "fp32", r0, 0.3, 1, 2024, refresh=16)
-    ref = M.mcmc_sweeps(w.system, w.arch, p, r0, 0.3, 1, 2024)
     safe = ref["margin"] > 1e-3
     assert safe.sum() >= 12
     acc = out["accepted"].cpu().numpy()
