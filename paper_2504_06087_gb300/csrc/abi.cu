@@ -200,6 +200,7 @@ static size_t layout(Plan& pl, int64_t Wc) {
         {&pl.mc_Mlu, "mc_Mlu", (size_t)(Wc * D * Um * Um * 8)}, {&pl.mc_piv, "mc_piv", (size_t)(Wc * D * Um * 4)},
         {&pl.mc_lrat, "mc_lrat", (size_t)(Wc * D * 8)}, {&pl.mc_srat, "mc_srat", (size_t)(Wc * D * 8)},
         {&pl.mc_acc, "mc_acc", (size_t)(Wc * 4)}, {&pl.mc_flag, "mc_flag", (size_t)(Wc * D * 4)},
+        {&pl.mc_xflag, "mc_xflag", (size_t)(Wc * D * 4)},
         {&pl.mc_rep, "mc_rep", (size_t)kWoodburySlots * n * n * 8}, {&pl.mc_rpiv, "mc_rpiv", (size_t)kWoodburySlots * n * 4},
         {&pl.mc_Tu, "mc_Tu", (size_t)(kWoodburySlots * Um * n) * ts},
         {&pl.mc_Bw, "mc_Bw", (size_t)(kWoodburySlots * Um * n) * ts}};

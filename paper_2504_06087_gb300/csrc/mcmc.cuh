@@ -370,6 +370,12 @@ __global__ void mcmc_act_kernel(const int64_t* __restrict__ rng, int ncol, const
 // others keep Psi away from zero).
 constexpr double kRepairLogShrink = -4.605170185988091;   // ln(1e-2)
 
+// A determinant-lemma ratio beyond e^{+-6.9} (a factor 1000) is recomputed
+// exactly, as log|det Phi'| - log|det Phi| from a float64 LU of the new
+// matrix: a float32 inverse of a badly conditioned matrix can turn a modest
+// ratio into a huge one, which would then dominate the determinant sum.
+constexpr double kExactLogRatio = 6.907755278982137;      // ln(1e3)
+
 // |U| up to which the small determinant-lemma matrix lives in shared memory.
 constexpr int kLemmaSmem = 64;
 
@@ -535,7 +541,8 @@ __global__ void mcmc_accept_kernel(int Wn, int n, int n_up, int D, int k, int Um
                                    const double* __restrict__ lrat, const double* __restrict__ srat,
                                    double* __restrict__ lp, int32_t* __restrict__ acc,
                                    int32_t* __restrict__ acc_count, unsigned long long* __restrict__ nacc,
-                                   const double* __restrict__ lref, int32_t* __restrict__ flag) {
+                                   const double* __restrict__ lref, int32_t* __restrict__ flag,
+                                   const int32_t* __restrict__ xflag) {
   const int w = blockIdx.x;
   const int lane = threadIdx.x;
   double* rw = r + (int64_t)w * n * 3;
@@ -612,7 +619,8 @@ __global__ void mcmc_accept_kernel(int Wn, int n, int n_up, int D, int k, int Um
         lsign[md] = 0.0;
       }
       // refactorise a determinant that shrank too far since its last LU
-      flag[md] = (ldabs[md] >= lref[md] + kRepairLogShrink) ? 0 : 1;
+      // (and one whose ratio needed the exact path: its A is not trusted)
+      flag[md] = (ldabs[md] >= lref[md] + kRepairLogShrink && !xflag[md]) ? 0 : 1;
     }
     lp[w] += logr;
     if (acc_count) acc_count[w] += 1;
@@ -892,6 +900,49 @@ __device__ void lu_block(int n, LT* __restrict__ A, int32_t* __restrict__ pv, do
     *s_sg = zero ? 0.0 : (neg ? -1.0 : 1.0);
   }
   __syncthreads();
+}
+
+// Exact ratios for the (walker, det) pairs whose determinant-lemma ratio is
+// beyond e^{+-kExactLogRatio} or not finite: Phi' = Phi with the rows U
+// replaced (Phi_U + Delta), its float64 LU, lrat = log|det Phi'| - ldabs and
+// srat = sign(det Phi') * lsign.  xflag[pair] = 1 marks them for a
+// refactorisation if the move is accepted.  A persistent grid; CTA b uses
+// slot b of the float64 scratch; dynamic shared memory n ints.
+template <typename T, typename LT>
+__global__ void __launch_bounds__(256) mcmc_exact_ratio_kernel(
+    int Wn, int n, int D, int Umax, const int32_t* __restrict__ Ul, const int32_t* __restrict__ Uc,
+    const T* __restrict__ Phi, const T* __restrict__ Dl, const double* __restrict__ ldabs,
+    const double* __restrict__ lsign, double* __restrict__ lrat, double* __restrict__ srat,
+    int32_t* __restrict__ xflag, LT* __restrict__ scratch, int32_t* __restrict__ spiv) {
+  extern __shared__ int xr_slot[];   // [n]: slot of row i in U, or -1
+  __shared__ double s_la, s_sg;
+  LT* L = scratch + (int64_t)blockIdx.x * n * n;
+  int32_t* pv = spiv + (int64_t)blockIdx.x * n;
+  for (int64_t md = blockIdx.x; md < (int64_t)Wn * D; md += gridDim.x) {
+    const double lr = lrat[md];
+    const bool need = !(fabs(lr) <= kExactLogRatio) && lsign[md] != 0.0;
+    if (threadIdx.x == 0) xflag[md] = need ? 1 : 0;
+    if (!need) continue;
+    const int w = (int)(md / D);
+    const int u = Uc[w];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) xr_slot[i] = -1;
+    __syncthreads();
+    for (int a = threadIdx.x; a < u; a += blockDim.x) xr_slot[Ul[(int64_t)w * Umax + a]] = a;
+    __syncthreads();
+    const T* P = Phi + md * n * n;
+    const T* Dw = Dl + md * Umax * n;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      const int i = e / n, a = xr_slot[i];
+      L[e] = (LT)P[e] + (a >= 0 ? (LT)Dw[(int64_t)a * n + e % n] : LT(0));
+    }
+    __syncthreads();
+    lu_block<LT>(n, L, pv, &s_la, &s_sg);
+    if (threadIdx.x == 0) {
+      lrat[md] = s_la - ldabs[md];
+      srat[md] = s_sg * lsign[md];
+    }
+    __syncthreads();
+  }
 }
 
 // Refactorisation of the flagged (walker, det) pairs of accepted walkers

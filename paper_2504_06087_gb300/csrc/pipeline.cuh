@@ -893,6 +893,7 @@ struct Runner {
     T* H1n = at<T>(pl.mc_H1n);
     double* lref = at<double>(pl.mc_lref);
     int32_t* flag = at<int32_t>(pl.mc_flag);
+    int32_t* xflag = at<int32_t>(pl.mc_xflag);
     // the state, in the value-forward buffers
     T* H0 = at<T>(pl.H0);
     T* PQ = at<T>(pl.PQ);
@@ -1009,11 +1010,19 @@ struct Runner {
         mark("mc_ratio", 1);
         mcmc_ratio_kernel<T><<<(unsigned)(Wn * D), 256, 0, s>>>(Wn, n, n_up, D, k, Umax, Ul, Uc, Urow, On, Fenv, Fk,
                                                                PhiS, AT, Dl, Mt, Mlu, Mpiv, lrat, srat);
+        {
+          const int64_t npair = (int64_t)Wn * D;
+          mcmc_exact_ratio_kernel<T, LT><<<(unsigned)(npair < kWoodburySlots ? npair : kWoodburySlots), 256,
+                                           (size_t)n * sizeof(int), s>>>(
+              Wn, n, D, Umax, Ul, Uc, PhiS, Dl, ldabs, lsign, lrat, srat, xflag, at<LT>(pl.mc_rep),
+              at<int32_t>(pl.mc_rpiv));
+          launches += 1;
+        }
         check("mc ratio");
         mark("mc_accept", 2);
         mcmc_accept_kernel<T><<<Wn, 32, 0, s>>>(Wn, n, n_up, D, k, Umax, dm.flags, r, rk, uacc, Ul, Uc, Urow, jp, F1,
                                                 F2, F1n, F2n, G1, G2, G1n, G2n, ldabs, lsign, lrat, srat, lp, acc,
-                                                mc.acc_count, &ms->n_accepted, lref, flag);
+                                                mc.acc_count, &ms->n_accepted, lref, flag, xflag);
         mcmc_rows_kernel<T><<<(unsigned)capU, 128, 0, s>>>(
             Wn, n, n_up, d, (int)Dn, RD, k, Umax, pl.ld_big, RD1, (dm.flags & FIRE_J_MLP) ? 1 : 0,
             (dm.flags & FIRE_J_ATT) ? 1 : 0, acc, Ul, Uc, Urow, F1n, F2n, F1, F2, SUn, SU, h0k, H0, PQk, PQ, Fk,

@@ -43,7 +43,7 @@ struct Plan {
   size_t PhiS, mc_rk, mc_u, mc_Ul, mc_Uc, mc_Ucu, mc_Urow, mc_rng, mc_h0k, mc_PQk, mc_Qk, mc_Fk;
   size_t mc_X, mc_Z, mc_Y, mc_F1n, mc_F2n, mc_SUn, mc_On, mc_Vn, mc_VZ, mc_VY, mc_G1n, mc_G2n;
   size_t mc_Dl, mc_Mt, mc_Mlu, mc_piv, mc_lrat, mc_srat, mc_acc, mc_Tu, mc_Bw, mc_lp, mc_lpf, mc_sgf, mc_stat;
-  size_t mc_H1, mc_H1n, mc_wdrift, mc_lref, mc_flag, mc_rep, mc_rpiv;
+  size_t mc_H1, mc_H1n, mc_wdrift, mc_lref, mc_flag, mc_xflag, mc_rep, mc_rpiv;
   int64_t nparams;
   size_t total;
   // column layout of `big`
