@@ -164,8 +164,12 @@ def main():
         import torch.distributed as tdist
         tdist.init_process_group("nccl", device_id=dev)
 
+    from paper_2504_06087_gb300 import replicas
     w = synth.workload("c26h24", args.walkers)
-    r_np, p = synth.make_inputs(w, args.walkers)
+    # every rank evaluates its own block of a global seeded walker set
+    r_all, p = synth.make_inputs(w, args.walkers * world)
+    w0, _ = replicas.walker_block(args.walkers * world, rank, world)
+    r_np = np.ascontiguousarray(r_all[w0:w0 + args.walkers])
     k_cap = 64
     f = fire.Fire(w.system, w.arch, p, args.precision, k_cap=k_cap, device=str(dev))
     r = torch.as_tensor(r_np, device=dev)
@@ -232,6 +236,8 @@ def main():
     e2e = {"value": world * args.walkers / (e2e_ms / 1e3), "unit": UNIT,
            "h2d_bytes_per_step": int(r_host.numel() * 8), "d2h_bytes_per_step": int(e_host.numel() * 8)}
 
+    # the one cross-rank reduction of a VMC step: E_L moments (float64)
+    moments = replicas.energy_moments(out["e_loc"])
     if rank != 0:
         if dist:
             tdist.barrier()
@@ -314,10 +320,11 @@ def main():
                                "width 256, 4 MLP layers, 16 determinants, c=5 bohr, c_n=20 bohr, k_cap=64",
                    "precision": {"bf16": "bf16_fp64", "fp32": "fp32", "fp64": "fp64"}[args.precision],
                    "walkers_per_gpu": args.walkers, "l2": "flushed before every step (256 MB write)",
-                   "parallelism": f"replicas x{world} (walkers sharded, no collective)"},
+                   "parallelism": f"replicas x{world} (walker blocks, no data-path collective; one float64 "
+                                  f"all-reduce of E_L moments after the timed calls)"},
         "e2e": e2e, "gpu_launches": int(info["n_launches"]) * args.steps,
         "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "comparison": comparison,
-        "diag": {"rows_total": info["rows_total"], "mean_neighbors": info["mean_neighbors"],
+        "diag": {"e_loc_moments_all_ranks": moments, "rows_total": info["rows_total"], "mean_neighbors": info["mean_neighbors"],
                  "k_required": info["k_required"], "n_chunks": info["n_chunks"], "n_nodes": info["n_nodes"],
                  "launches_per_step": info["n_launches"], "step_ms": times},
     }
