@@ -362,7 +362,8 @@ __global__ void __launch_bounds__(576, 1) gj_inverse_kernel(int n, const IT* __r
   }
 }
 
-// Tiles per thread of contract_kernel for neighbourhoods of up to mcap members.
+// Tiles per thread of contract_kernel for neighbourhoods of up to mcap
+// members (3 x 4 tiles, one pass).
 inline int contract_maxt(int mcap) {
   const int tiles = mcap * ((mcap + 3) / 4);
   for (int t : {1, 2, 3, 5, 9})
@@ -370,12 +371,41 @@ inline int contract_maxt(int mcap) {
   return 0;
 }
 
+// Shared-memory layout of contract_kernel for a chunk of 32 orbitals l:
+// T[l][4 mq] (member k's tangent rows x = 0, 1, 2 at 4k + x) and the inverse
+// columns A[l][mq], mq = members rounded up to 4, each row padded by 4
+// elements to spread the orbitals over the banks; M [3 mcap][mcap] reuses the
+// area at the end.
+constexpr int kContractChunk = 32;
+__host__ __device__ inline int contract_mq(int mcap) { return 4 * ((mcap + 3) / 4); }
+__host__ __device__ inline int contract_stage(int mcap) {
+  const int mq = contract_mq(mcap);
+  return kContractChunk * ((4 * mq + 4) + (mq + 4));
+}
+
 inline size_t contract_smem_bytes(int mcap, size_t tsz) {
-  const size_t region = (size_t)(4 * mcap * 33 > 3 * mcap * mcap ? 4 * mcap * 33 : 3 * mcap * mcap) + 2;
-  return region * tsz + 2 * (size_t)mcap * sizeof(int) + 2 * (size_t)mcap * sizeof(int64_t) + 16;
+  const size_t st = (size_t)contract_stage(mcap), mm = (size_t)3 * mcap * mcap;
+  const size_t region = st > mm ? st : mm;
+  return region * tsz + 2 * (size_t)mcap * sizeof(int) + 2 * (size_t)mcap * sizeof(int64_t) + 32;
 }
 
 inline size_t gj_smem_bytes(int n) { return (size_t)n * n * 4 + 512 * 4 + 768 * 4 + 64 * 4; }
+
+// Four consecutive shared-memory elements (16-byte aligned for float).
+template <typename T>
+struct Quad { T v[4]; };
+template <typename T>
+__device__ __forceinline__ Quad<T> lds4(const T* p) {
+  Quad<T> q;
+  if constexpr (sizeof(T) == 4) {
+    const float4 f = *reinterpret_cast<const float4*>(p);
+    q.v[0] = f.x; q.v[1] = f.y; q.v[2] = f.z; q.v[3] = f.w;
+  } else {
+    const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+    q.v[0] = a.x; q.v[1] = a.y; q.v[2] = b.x; q.v[3] = b.y;
+  }
+  return q;
+}
 
 // Gradient and Laplacian of log det Phi_d restricted to the neighbourhoods.
 // One CTA per (walker, tangent electron n').  O holds h W_d for every row of
@@ -386,30 +416,34 @@ inline size_t gj_smem_bytes(int n) { return (size_t)n * n * 4 + 512 * 4 + 768 * 
 // With Nbar = {i_0 = n', i_1, ...} (m members) the CTA forms
 //   T[(k,x)][l] = d Phi_{i_k l} / d r_{n' x}      (3m rows)
 //   M[(k,x)][k'] = sum_l T[(k,x)][l] A[l][i_k']   (3m x m)
-// as a register-blocked product (3 x 4 outputs per thread, MAXT tiles per
-// thread, all tiles in one pass) over chunks of LC = 32 orbitals staged in
-// shared memory, then
+// and from it
 //   d log det / d r_{n'x} = sum_k M[(k,x)][k]
 //   trace_{n'} = sum_x sum_{k,k'} M[(k,x)][k'] M[(k',x)][k].
+// Orbitals go in chunks of 32: the staging thread (orbital lane, member
+// group) forms T from the member's three O rows and its envelope value, then
+// every thread multiplies member k's 3 rows by 4 columns (MAXT such tiles,
+// all in one pass; two 128-bit shared loads per orbital).  Small shared and
+// register footprints keep many CTAs resident to hide the gathers' latency.
 template <typename T, int MAXT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, (MAXT <= 3 && sizeof(T) == 4) ? 4 : 1)
 contract_kernel(int Wc, int n, int n_up, int K, int mcap, int dd, int D, const int32_t* __restrict__ idx,
                 const int32_t* __restrict__ cnt, const int32_t* __restrict__ rev,
                 const int64_t* __restrict__ blk_off, const T* __restrict__ O, const T* __restrict__ Fenv,
                 const T* __restrict__ AT, T* __restrict__ gdet, T* __restrict__ ldet, DevStatus* st) {
-  // one batch of 3 x 4 tiles: NT * MAXT >= mcap * ceil(mcap / 4) (host-checked)
-  constexpr int LC = 32, LDC = LC + 1, NT = 256;
-  extern __shared__ unsigned char ct_smem[];
-  T* Tc = reinterpret_cast<T*>(ct_smem);              // [3*mcap][LDC]
-  T* Ac = Tc + (int64_t)3 * mcap * LDC;               // [mcap][LDC]
-  // the staging area [Tc | Ac] also holds M [3m][m] at the end
-  const int64_t region = max((int64_t)4 * mcap * LDC, (int64_t)3 * mcap * mcap);
-  int64_t* ro = reinterpret_cast<int64_t*>(Tc + ((region + 1) & ~(int64_t)1));   // O row of (k, x = 0)
-  int64_t* fo = ro + mcap;                                              // Fenv value row of member k
+  constexpr int LC = kContractChunk, NT = 256, NG = NT / LC;
+  extern __shared__ __align__(16) unsigned char ct_smem[];
+  const int mq = contract_mq(mcap);
+  const int ST = 4 * mq + 4, SA = mq + 4;            // row strides of T and A
+  T* Ts = reinterpret_cast<T*>(ct_smem);
+  T* As = Ts + LC * ST;
+  const int64_t region = max((int64_t)contract_stage(mcap), (int64_t)3 * mcap * mcap);
+  int64_t* ro = reinterpret_cast<int64_t*>(Ts + ((region + 1) & ~(int64_t)1));   // O row of (k, x = 0)
+  int64_t* fo = ro + mcap;                                                    // Fenv value row of member k
   int* mi = reinterpret_cast<int*>(fo + mcap);
   int* ms = mi + mcap;
-  __shared__ T red[32];
+  __shared__ T red[NT / 32][5];
   const int tid = threadIdx.x;
+  const int ol = tid & (LC - 1), og = tid / LC;
   const int w = blockIdx.x / n, np = blockIdx.x % n;
   const int64_t Dn = (int64_t)D * n;
   const int64_t base = (int64_t)w * n + np;
@@ -433,115 +467,124 @@ contract_kernel(int Wc, int n, int n_up, int K, int mcap, int dd, int D, const i
   const T* Aw = AT + ((int64_t)w * D + dd) * n * n;
   const int bnp = block_index(w, np, Wc, n, n_up);
   const int64_t onp = blk_off[bnp];
-  const int nq = (m + 3) / 4;
+  const int nq = mq / 4;
   const int ntile = m * nq;
-  T g0 = T(0), g1 = T(0), g2 = T(0), tr = T(0), lt = T(0);
-  T* Ms = Tc;                                         // [3m][m], reuses the staging area
-  for (int tb = 0; tb < ntile; tb += NT * MAXT) {    // a single pass (see above)
-    T acc[MAXT][12];
+
+  // sum_l LapPhi_{n' l} A_{l n'}: the Laplacian row of n' against A's column n'
+  T lt = T(0);
+  {
+    const int64_t fb = (int64_t)bnp * 5 * Dn + (int64_t)dd * n;
+    for (int l = tid; l < n; l += NT) {
+      const T ov = O[onp * n + l], olp = O[(onp + 1) * n + l];
+      T cross = T(0);
+      for (int x = 0; x < 3; ++x) cross += O[(onp + 2 + x) * n + l] * Fenv[fb + (2 + x) * Dn + l];
+      const T lap = olp * Fenv[fb + l] + T(2) * cross + ov * Fenv[fb + Dn + l];
+      lt += lap * Aw[(int64_t)np * n + l];
+    }
+  }
+
+  T acc[MAXT][12];
 #pragma unroll
-    for (int t = 0; t < MAXT; ++t)
+  for (int t = 0; t < MAXT; ++t)
 #pragma unroll
-      for (int q = 0; q < 12; ++q) acc[t][q] = T(0);
-    for (int l0 = 0; l0 < n; l0 += LC) {
-      const int lc = min(LC, n - l0);
-      __syncthreads();
-#pragma unroll 4
-      for (int e = tid; e < m * lc; e += NT) {
-        const int k = e / lc, l = e % lc;
-        Ac[k * LDC + l] = Aw[(int64_t)mi[k] * n + l0 + l];
-      }
-#pragma unroll 4
-      for (int e = tid; e < 3 * m * lc; e += NT) {
-        const int row = e / lc, l = e % lc;
-        const int k = row / 3, x = row - 3 * k;
+    for (int q = 0; q < 12; ++q) acc[t][q] = T(0);
+  for (int l0 = 0; l0 < n; l0 += LC) {
+    const int l = l0 + ol;
+    const bool lin = l < n;
+    __syncthreads();
+#pragma unroll 2
+    for (int k = og; k < mq; k += NG) {
+      T v0 = T(0), v1 = T(0), v2 = T(0), a = T(0);
+      if (lin && k < m) {
         const int64_t r0 = ro[k];
-        const T phi = Fenv[fo[k] + l0 + l];
-        T v = r0 >= 0 ? O[r0 + (int64_t)x * n + l0 + l] * phi : T(0);
-        if (k == 0) v += O[onp * n + l0 + l] * Fenv[fo[0] + (2 + x) * Dn + l0 + l];
-        Tc[row * LDC + l] = v;
-      }
-      // sum_l LapPhi_{n' l} A_{l n'} for this chunk (first pass only)
-      if (tb == 0)
-        for (int l = tid; l < lc; l += NT) {
-          const int64_t fc = dd * n + l0 + l;
-          const int64_t fb = (int64_t)bnp * 5 * Dn;
-          const T ov = O[onp * n + l0 + l], ol = O[(onp + 1) * n + l0 + l];
-          T cross = T(0);
-          for (int x = 0; x < 3; ++x) cross += O[(onp + 2 + x) * n + l0 + l] * Fenv[fb + (2 + x) * Dn + fc];
-          const T lap = ol * Fenv[fb + fc] + T(2) * cross + ov * Fenv[fb + Dn + fc];
-          lt += lap * Aw[(int64_t)np * n + l0 + l];
+        if (r0 >= 0) {
+          const T phi = Fenv[fo[k] + l];
+          v0 = O[r0 + l] * phi;
+          v1 = O[r0 + n + l] * phi;
+          v2 = O[r0 + 2 * (int64_t)n + l] * phi;
         }
-      __syncthreads();
+        if (k == 0) {   // n' itself: its envelope moves too
+          const T ov = O[onp * n + l];
+          v0 += ov * Fenv[fo[0] + 2 * Dn + l];
+          v1 += ov * Fenv[fo[0] + 3 * Dn + l];
+          v2 += ov * Fenv[fo[0] + 4 * Dn + l];
+        }
+        a = Aw[(int64_t)mi[k] * n + l];
+      }
+      T* t = Ts + ol * ST + 4 * k;
+      t[0] = v0;
+      t[1] = v1;
+      t[2] = v2;
+      As[ol * SA + k] = a;
+    }
+    __syncthreads();
 #pragma unroll
-      for (int t = 0; t < MAXT; ++t) {
-        const int tile = tb + tid + t * NT;
-        if (tile < ntile) {
-          const int k = tile / nq, kq = tile % nq;
-          const T* t0 = Tc + (3 * k) * LDC;
-          const T* b0 = Ac + (4 * kq) * LDC;
-          const bool full = (4 * kq + 3) < m;
-          for (int l = 0; l < lc; ++l) {
-            const T a0 = t0[l], a1 = t0[LDC + l], a2 = t0[2 * LDC + l];
-            T bb[4];
+    for (int t = 0; t < MAXT; ++t) {
+      const int tile = tid + t * NT;
+      if (tile < ntile) {
+        const int k = tile / nq, kq = tile - k * nq;
+        const T* tp = Ts + 4 * k;
+        const T* ap = As + 4 * kq;
+#pragma unroll 8
+        for (int q = 0; q < LC; ++q) {
+          const Quad<T> av = lds4<T>(tp + q * ST);
+          const Quad<T> bv = lds4<T>(ap + q * SA);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) bb[j] = (full || 4 * kq + j < m) ? b0[j * LDC + l] : T(0);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              acc[t][j] += a0 * bb[j];
-              acc[t][4 + j] += a1 * bb[j];
-              acc[t][8 + j] += a2 * bb[j];
-            }
+          for (int j = 0; j < 4; ++j) {
+            acc[t][j] += av.v[0] * bv.v[j];
+            acc[t][4 + j] += av.v[1] * bv.v[j];
+            acc[t][8 + j] += av.v[2] * bv.v[j];
           }
         }
       }
     }
-    __syncthreads();
-    // M of this tile batch into shared memory
+  }
+  __syncthreads();
+  // M into shared memory (the staging area is free now)
+  T* Ms = Ts;
 #pragma unroll
-    for (int t = 0; t < MAXT; ++t) {
-      const int tile = tb + tid + t * NT;
-      if (tile < ntile) {
-        const int k = tile / nq, kq = tile % nq;
+  for (int t = 0; t < MAXT; ++t) {
+    const int tile = tid + t * NT;
+    if (tile < ntile) {
+      const int k = tile / nq, kq = tile - k * nq;
 #pragma unroll
-        for (int x = 0; x < 3; ++x)
+      for (int x = 0; x < 3; ++x)
 #pragma unroll
-          for (int j = 0; j < 4; ++j)
-            if (4 * kq + j < m) Ms[(3 * k + x) * m + 4 * kq + j] = acc[t][4 * x + j];
-      }
+        for (int j = 0; j < 4; ++j)
+          if (4 * kq + j < m) Ms[(3 * k + x) * m + 4 * kq + j] = acc[t][4 * x + j];
     }
   }
   __syncthreads();
-  for (int e = tid; e < 3 * m; e += NT) {
-    const int k = e / 3, x = e % 3;
-    const T v = Ms[(3 * k + x) * m + k];
-    if (x == 0) g0 += v; else if (x == 1) g1 += v; else g2 += v;
+  T g0 = T(0), g1 = T(0), g2 = T(0), tr = T(0);
+  for (int k = tid; k < m; k += NT) {
+    g0 += Ms[(3 * k) * m + k];
+    g1 += Ms[(3 * k + 1) * m + k];
+    g2 += Ms[(3 * k + 2) * m + k];
   }
-  for (int e = tid; e < 3 * m * m; e += NT) {
-    const int x = e / (m * m), rem = e % (m * m);
-    const int k = rem / m, kp = rem % m;
-    tr += Ms[(3 * k + x) * m + kp] * Ms[(3 * kp + x) * m + k];
+  for (int e = tid; e < m * m; e += NT) {
+    const int k = e / m, kp = e - k * m;
+#pragma unroll
+    for (int x = 0; x < 3; ++x) tr += Ms[(3 * k + x) * m + kp] * Ms[(3 * kp + x) * m + k];
   }
-  auto bsum = [&](T v) -> T {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    __syncthreads();
-    if ((tid & 31) == 0) red[tid >> 5] = v;
-    __syncthreads();
-    T sm = T(0);
-    for (int q = 0; q < NT / 32; ++q) sm += red[q];
-    return sm;
-  };
-  g0 = bsum(g0);
-  g1 = bsum(g1);
-  g2 = bsum(g2);
-  tr = bsum(tr);
-  lt = bsum(lt);
+  // one block reduction of (g0, g1, g2, tr, lt)
+  T v[5] = {g0, g1, g2, tr, lt};
+#pragma unroll
+  for (int q = 0; q < 5; ++q)
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+  if ((tid & 31) == 0)
+#pragma unroll
+    for (int q = 0; q < 5; ++q) red[tid >> 5][q] = v[q];
+  __syncthreads();
   if (tid == 0) {
+    T sum[5] = {T(0), T(0), T(0), T(0), T(0)};
+    for (int g = 0; g < NT / 32; ++g)
+#pragma unroll
+      for (int q = 0; q < 5; ++q) sum[q] += red[g][q];
     T* gp = gdet + (((int64_t)w * D + dd) * n + np) * 3;
-    gp[0] = g0;
-    gp[1] = g1;
-    gp[2] = g2;
-    ldet[((int64_t)w * D + dd) * n + np] = lt - tr;
+    gp[0] = sum[0];
+    gp[1] = sum[1];
+    gp[2] = sum[2];
+    ldet[((int64_t)w * D + dd) * n + np] = sum[4] - sum[3];
   }
 }
 

@@ -793,7 +793,7 @@ struct Runner {
         const int kmax = kreq < K ? kreq : K;
         const int mcap = 1 + (kmax < n - 1 ? kmax : n - 1);
         const int maxt = contract_maxt(mcap);
-        if (maxt == 0) { set_last_error("contract", "neighbourhood larger than 95 members"); return FIRE_ERR_UNSUPPORTED; }
+        if (maxt == 0) { set_last_error("contract", "neighbourhood larger than 96 members"); return FIRE_ERR_UNSUPPORTED; }
         const size_t ctsm = contract_smem_bytes(mcap, sizeof(T));
         for (int dd = 0; dd < D; ++dd) {
           mark("orb_gemm", 2);
