@@ -775,15 +775,16 @@ __global__ void convert_kernel(int64_t count, const S* __restrict__ src, T* __re
     dst[e] = (T)src[e];
 }
 
-// A = Phi^-1 from the LU factors (P Phi = L U, unit L) of one n x n matrix,
-// written transposed (AT[k][l] = A[l][k]) in AT's type, by one CTA of 256
-// threads.  Columns go in panels of 32: column j of A solves
-// L U x = e_{pinv[j]}; the panel X[n][33] sits in shared memory (sm), warp g
-// owns columns 4g .. 4g+3 with 8 lanes per column splitting each dot product.
-template <typename LT, typename AT>
+// A = Phi^-1 from the LU factors (P Phi = L U, unit L, stored in LT) of one
+// n x n matrix, in arithmetic CT, written transposed (AT[k][l] = A[l][k]) in
+// AT's type, by one CTA of 256 threads.  Columns go in panels of 32: column
+// j of A solves L U x = e_{pinv[j]}; the panel X[n][33] sits in shared
+// memory (sm), warp g owns columns 4g .. 4g+3 with 8 lanes per column
+// splitting each dot product, so no block barrier is needed inside a panel.
+template <typename LT, typename CT, typename AT>
 __device__ void inverse_panel_block(int n, const LT* __restrict__ A, const int32_t* __restrict__ pv,
                                     AT* __restrict__ out, unsigned char* sm) {
-  LT* X = reinterpret_cast<LT*>(sm);                         // [n][33]
+  CT* X = reinterpret_cast<CT*>(sm);                         // [n][33]
   int* pinv = reinterpret_cast<int*>(X + (int64_t)n * 33);   // [n]
   int* perm = pinv + n;                                      // [n]
   __syncthreads();
@@ -804,21 +805,21 @@ __device__ void inverse_panel_block(int n, const LT* __restrict__ A, const int32
     const int j = j0 + cl;
     const int p = j < n ? pinv[j] : -1;
     for (int i = 0; i < n; ++i) {   // forward: unit lower
-      LT s = LT(0);
-      for (int q = sub; q < i; q += 8) s += A[(int64_t)i * n + q] * X[q * 33 + cl];
+      CT s = CT(0);
+      for (int q = sub; q < i; q += 8) s += (CT)A[(int64_t)i * n + q] * X[q * 33 + cl];
       s += __shfl_xor_sync(0xffffffffu, s, 1);
       s += __shfl_xor_sync(0xffffffffu, s, 2);
       s += __shfl_xor_sync(0xffffffffu, s, 4);
-      if (sub == 0) X[i * 33 + cl] = ((i == p) ? LT(1) : LT(0)) - s;
+      if (sub == 0) X[i * 33 + cl] = ((i == p) ? CT(1) : CT(0)) - s;
       __syncwarp();
     }
     for (int i = n - 1; i >= 0; --i) {   // backward: upper
-      LT s = LT(0);
-      for (int q = i + 1 + sub; q < n; q += 8) s += A[(int64_t)i * n + q] * X[q * 33 + cl];
+      CT s = CT(0);
+      for (int q = i + 1 + sub; q < n; q += 8) s += (CT)A[(int64_t)i * n + q] * X[q * 33 + cl];
       s += __shfl_xor_sync(0xffffffffu, s, 1);
       s += __shfl_xor_sync(0xffffffffu, s, 2);
       s += __shfl_xor_sync(0xffffffffu, s, 4);
-      if (sub == 0) X[i * 33 + cl] = (X[i * 33 + cl] - s) / A[(int64_t)i * n + i];
+      if (sub == 0) X[i * 33 + cl] = (X[i * 33 + cl] - s) / (CT)A[(int64_t)i * n + i];
       __syncwarp();
     }
     __syncthreads();
@@ -832,13 +833,13 @@ __device__ void inverse_panel_block(int n, const LT* __restrict__ A, const int32
 }
 
 // The inverse of matrices [m0, m0 + gridDim.x) of a batch, one CTA each.
-template <typename LT, typename AT>
+template <typename LT, typename CT, typename AT>
 __global__ void __launch_bounds__(256) inverse_panel_kernel(int n, int64_t m0, const LT* __restrict__ LU,
                                                             const int32_t* __restrict__ piv,
                                                             AT* __restrict__ Ainv) {
   extern __shared__ unsigned char ip_smem[];
   const int64_t mat = m0 + blockIdx.x;
-  inverse_panel_block<LT, AT>(n, LU + mat * n * n, piv + mat * n, Ainv + mat * n * n, ip_smem);
+  inverse_panel_block<LT, CT, AT>(n, LU + mat * n * n, piv + mat * n, Ainv + mat * n * n, ip_smem);
 }
 
 inline size_t inverse_panel_smem(int n, size_t lsz) { return (size_t)n * 33 * lsz + 2 * (size_t)n * sizeof(int); }
@@ -978,7 +979,7 @@ __global__ void __launch_bounds__(256) mcmc_repair_kernel(int Wn, int n, int D, 
       __syncthreads();
       continue;
     }
-    inverse_panel_block<LT, T>(n, L, pv, A, rp_smem);
+    inverse_panel_block<LT, LT, T>(n, L, pv, A, rp_smem);
   }
 }
 

@@ -119,6 +119,10 @@ struct Runner {
     // 2 attention, 3 orbitals -- which products may use the tensor cores.
     if (const char* m = getenv("FIRE_TC_MASK")) tc_mask = atoi(m);
     if (const char* m = getenv("FIRE_TC_FIX_VALUES")) fix_values = atoi(m);
+    // FIRE_INVERSE (diagnostic): 1 = float32 Gauss-Jordan from a float copy of
+    // Phi (n <= 192, the default of the float32 forms), 0 = triangular solves
+    // on the LU factors (always for float64 and for n > 192)
+    if (const char* m = getenv("FIRE_INVERSE")) use_gj = atoi(m) == 1;
     auto nc_env = [](const char* k, int dflt) {
       const char* v = getenv(k);
       int x = v ? atoi(v) : dflt;
@@ -185,6 +189,16 @@ struct Runner {
   // split-bf16 components of each tensor-core product (1: 1 product, 2: 3, 3: 6)
   // (6 component products everywhere: the E_L error then matches plain fp32)
   int nc_mlp = 3, nc_jas = 3, nc_att = 3, nc_orb = 3;
+  bool use_gj = true;
+  // A^T from the LU factors, matrices in batches of the grid limit
+  void inverse_from_lu(int n, int64_t nmat, const LT* LUb, const int32_t* piv, T* Ainv) {
+    const size_t ism = inverse_panel_smem(n, sizeof(T));
+    for (int64_t m0 = 0; m0 < nmat; m0 += 65535) {
+      const int64_t cnt = nmat - m0 < 65535 ? nmat - m0 : 65535;
+      inverse_panel_kernel<LT, T, T><<<(unsigned)cnt, 256, ism, s>>>(n, m0, LUb, piv, Ainv);
+      launches += 1;
+    }
+  }
   int64_t capA = 0;           // allocated rows of X / Y: the component stride of Xb / Yb
   // value-row fix-up context of the current chunk
   const int64_t* vr_off = nullptr;
@@ -375,14 +389,14 @@ struct Runner {
       int32_t* piv = at<int32_t>(pl.piv);
       double* ldabs = at<double>(pl.ldabs);
       double* lsign = at<double>(pl.lsign);
-      const bool gj = sizeof(T) == 4 && n <= 192;
+      const bool gj = use_gj && sizeof(T) == 4 && n <= 192;
       phi_assemble_kernel<T, LT><<<wc * D, 256, 0, s>>>(wc, n, n_up, D, Ov, Fenv, 1, LUb, gj ? B.Phif : nullptr);
       lu_kernel<LT, 16><<<wc * D, 256, (size_t)2 * n * 16 * sizeof(LT), s>>>(n, LUb, piv, ldabs, lsign);
       if (gj) {
         const int Gq = (n + 7) / 8;
         gj_inverse_kernel<float, T><<<wc * D, ((Gq * Gq + 31) / 32) * 32, gj_smem_bytes(n), s>>>(n, B.Phif, B.AT);
       } else {
-        lu_inverse_kernel<LT, T><<<wc * D, 256, (size_t)n * n * sizeof(T) + 2 * n * sizeof(int), s>>>(n, LUb, piv, B.AT);
+        inverse_from_lu(n, (int64_t)wc * D, LUb, piv, B.AT);
       }
       FinalIn<T, RT> fi{ldabs, lsign, nullptr, nullptr, cval, nullptr, nullptr, jval, jsign, nullptr, nullptr,
                         aval, asign, nullptr, nullptr, vpot};
@@ -747,8 +761,9 @@ struct Runner {
       int32_t* piv = at<int32_t>(pl.piv);
       double* ldabs = at<double>(pl.ldabs);
       double* lsign = at<double>(pl.lsign);
-      // float32 inverse by Gauss-Jordan from a float copy of Phi (n <= 192)
-      const bool gj = deriv && sizeof(T) == 4 && n <= 192;
+      // A^T: float32 Gauss-Jordan from a float copy of Phi (float32 forms,
+      // n <= 192), else triangular solves on the LU factors
+      const bool gj = use_gj && deriv && sizeof(T) == 4 && n <= 192;
       float* Phif = gj ? at<float>(pl.Phif) : nullptr;
       phi_assemble_kernel<T, LT><<<wc * D, 256, 0, s>>>(wc, n, n_up, D, Ov, Fenv, R5, LUb, Phif);
       const bool mc = dm.op == FIRE_OP_MCMC;
@@ -768,7 +783,7 @@ struct Runner {
         const size_t ism = inverse_panel_smem(n, sizeof(LT));
         for (int64_t m0 = 0; m0 < nmat; m0 += 65535) {
           const int64_t cnt = nmat - m0 < 65535 ? nmat - m0 : 65535;
-          inverse_panel_kernel<LT, T><<<(unsigned)cnt, 256, ism, s>>>(n, m0, LUb, piv, at<T>(pl.Ainv));
+          inverse_panel_kernel<LT, LT, T><<<(unsigned)cnt, 256, ism, s>>>(n, m0, LUb, piv, at<T>(pl.Ainv));
           launches += 1;
         }
         check("inverse");
@@ -783,8 +798,7 @@ struct Runner {
           const int thr = ((G * G + 31) / 32) * 32;
           gj_inverse_kernel<float, T><<<wc * D, thr, gj_smem_bytes(n), s>>>(n, Phif, Ainv);
         } else {
-          const size_t invsm = (size_t)n * n * sizeof(T) + 2 * n * sizeof(int);
-          lu_inverse_kernel<LT, T><<<wc * D, 256, invsm, s>>>(n, LUb, piv, Ainv);
+          inverse_from_lu(n, (int64_t)wc * D, LUb, piv, Ainv);
         }
       check("inverse");
         // 8. log-det gradient and Laplacian, determinant by determinant
@@ -1090,7 +1104,8 @@ inline int set_smem_limits() {
   raise((const void*)att_pool_kernel<T>);
   raise((const void*)gj_inverse_kernel<float, T>);
   raise((const void*)mcmc_att_kernel<T>);
-  raise((const void*)inverse_panel_kernel<LT, T>);
+  raise((const void*)inverse_panel_kernel<LT, LT, T>);
+  raise((const void*)inverse_panel_kernel<LT, T, T>);
   raise((const void*)mcmc_repair_kernel<T, LT>);
   cudaError_t e = cudaGetLastError();
   if (rc != FIRE_OK || e != cudaSuccess) set_last_error("smem limits", cudaGetErrorString(e));
