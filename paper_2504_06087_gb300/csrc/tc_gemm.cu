@@ -48,31 +48,52 @@ static bool make_map(CUtensorMap* m, const void* base, uint64_t rows, uint64_t c
 template <int STAGES, int NC>
 static int launch(cudaStream_t s, const CUtensorMap& ma, const CUtensorMap& mb, const TcArgs& g, int64_t m_cap,
                   int nt) {
-  const size_t sm = (size_t)STAGES * NC * (BM * BK * 2 + (size_t)g.BN * BK * 2) + 1024;
+  const size_t sm = tc_smem_bytes(STAGES, NC, g.BN);
   if (cudaFuncSetAttribute(tc_gemm_kernel<STAGES, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
       cudaSuccess)
     return FIRE_ERR_CUDA;
-  const int64_t mt = (m_cap + BM - 1) / BM;
-  if (mt > 65535) return FIRE_ERR_UNSUPPORTED;
-  dim3 grid((unsigned)nt, (unsigned)mt);
-  tc_gemm_kernel<STAGES, NC><<<grid, 128, sm, s>>>(ma, mb, g);
+  static int n_sm = 0;
+  if (n_sm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (n_sm <= 0) n_sm = 1;
+  }
+  const int64_t tiles = ((m_cap + BM - 1) / BM) * nt;
+  const int grid = (int)(tiles < n_sm ? tiles : n_sm);
+  tc_gemm_kernel<STAGES, NC><<<grid, 192, sm, s>>>(ma, mb, g);
   return cudaGetLastError() == cudaSuccess ? FIRE_OK : FIRE_ERR_CUDA;
+}
+
+// Output tile width: among the multiples of 16 (at least 64, or N rounded up
+// to 16 when smaller) whose pipeline stages fit in shared memory, the one that
+// computes the fewest columns in total; ties prefer the wider tile.
+static int choose_bn(int N, int nc, int stages) {
+  const int lo = N < 64 ? (N + 15) / 16 * 16 : 64;
+  int best = 0;
+  int64_t best_cols = -1;
+  for (int bn = lo; bn <= 256; bn += 16) {
+    if (tc_smem_bytes(stages, nc, bn) > 227 * 1024) break;
+    const int64_t cols = (int64_t)((N + bn - 1) / bn) * bn;
+    if (best_cols < 0 || cols < best_cols || (cols == best_cols && bn > best)) { best = bn; best_cols = cols; }
+  }
+  return best;
 }
 
 int gemm_bf16(cudaStream_t s, const void* A, int64_t lda, int64_t a_rows, const void* Bt, int N, int K,
               float* C, int64_t ldc, int64_t m_begin, int64_t m_end, const int64_t* m_range, int64_t m_cap,
               int* err, int nc) {
   if (N < 1 || K < BK || K % BK || m_cap <= 0 || nc < 1 || nc > 3) return FIRE_ERR_UNSUPPORTED;
-  const int bn_max = nc == 3 ? 128 : 256;       // keeps two pipeline stages in shared memory
-  const int nt = (N + bn_max - 1) / bn_max;
-  int BN = (N + nt - 1) / nt;
-  BN = (BN + 15) / 16 * 16;
+  const int stages = nc == 1 ? 4 : (nc == 2 ? 3 : 2);
+  const int BN = choose_bn(N, nc, stages);
+  if (BN == 0) return FIRE_ERR_UNSUPPORTED;
+  const int nt = (N + BN - 1) / BN;
   CUtensorMap ma, mb;
   if (!make_map(&ma, A, (uint64_t)a_rows * nc, (uint64_t)K, (uint64_t)lda, BM)) return FIRE_ERR_CUDA;
   if (!make_map(&mb, Bt, (uint64_t)N * nc, (uint64_t)K, (uint64_t)K, (uint32_t)BN)) return FIRE_ERR_CUDA;
   TcArgs g{C, ldc, m_begin, m_end, m_range, N, K, BN, a_rows, N, err};
   if (nc == 1) return launch<4, 1>(s, ma, mb, g, m_cap, nt);
-  if (nc == 2) return launch<2, 2>(s, ma, mb, g, m_cap, nt);
+  if (nc == 2) return launch<3, 2>(s, ma, mb, g, m_cap, nt);
   return launch<2, 3>(s, ma, mb, g, m_cap, nt);
 }
 

@@ -3,10 +3,15 @@
 // accumulator in tensor memory) fed by TMA (cp.async.bulk.tensor, 128-byte
 // swizzle) through an mbarrier pipeline.
 //
-// One CTA computes one 128 x BN tile.  Warp 0 lane 0 issues the TMA copies,
-// warp 1 lane 0 issues the MMAs, and all four warps drain the accumulator
-// (tcgen05.ld 32x32b) into C.  The row range of A may live on the device
-// ({begin, end}); tiles past the end exit before touching any barrier.
+// A persistent grid of 192-thread CTAs walks the 128 x BN output tiles
+// (N tiles fastest, so CTAs that share an A tile run together and the
+// second reads it from L2).  Warp 0 lane 0 streams A and B k-blocks through
+// a ring of STAGES shared-memory stages (TMA), warp 1 lane 0 issues the MMAs
+// into one of two tensor-memory accumulators, and warps 2-5 drain the other
+// accumulator (tcgen05.ld 32x32b, each warp its 32-lane quarter) through a
+// per-warp transpose buffer into coalesced rows of C, so a tile's epilogue
+// overlaps the next tile's main loop.  The row range of A may live on the
+// device ({begin, end}).
 //
 // Every mbarrier wait is bounded: after kSpinLimit polls the kernel records
 // an error in *err, stops issuing work, waits (bounded) for its own copies
@@ -155,33 +160,38 @@ __host__ __device__ constexpr int split_q(int nc, int k) {
 }
 
 // Dynamic shared memory: STAGES x NC x (A tile 16 KB + B tile BN*128 B),
-// 1024-aligned.
+// 1024-aligned, then 4 x [32][33] fp32 epilogue transpose buffers.
+constexpr int kEpiWarps = 4;
+__host__ __device__ inline size_t tc_smem_bytes(int stages, int nc, int bn) {
+  return (size_t)stages * nc * ((size_t)BM * BK * 2 + (size_t)bn * BK * 2) + (size_t)kEpiWarps * 32 * 33 * 4 + 1024;
+}
+
 template <int STAGES, int NC>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(192, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcArgs g) {
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
-  __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
+  __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], tfull_bar[2], tempty_bar[2], done_bar;
   __shared__ uint32_t tmem_slot;
-  __shared__ int abort_flag;
+  __shared__ volatile int abort_flag;
 
   int64_t mb = g.m_begin, me = g.m_end;
   if (g.m_range) { mb = g.m_range[0]; me = g.m_range[1]; }
-  // N tiles vary fastest, so the CTAs that share an A tile run together and
-  // the second reads it from L2
-  const int64_t m0 = mb + (int64_t)blockIdx.y * BM;
-  if (m0 >= me) return;                       // uniform across the CTA
-  const int n0 = blockIdx.x * g.BN;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int BN = g.BN;
+  const int64_t n_mt = me > mb ? (me - mb + BM - 1) / BM : 0;
+  const int n_nt = (g.N + BN - 1) / BN;
+  const int64_t ntiles = n_mt * n_nt;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t a_bytes = BM * BK * 2, b_bytes = (uint32_t)BN * BK * 2;
   const uint32_t stage_bytes = NC * (a_bytes + b_bytes);
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
+  float* epi = reinterpret_cast<float*>(base + (size_t)STAGES * stage_bytes);
   uint32_t ncols = 32;
-  while ((int)ncols < BN) ncols <<= 1;
+  while ((int)ncols < 2 * BN) ncols <<= 1;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&tfull_bar[b], 1); mbar_init(&tempty_bar[b], kEpiWarps); }
     mbar_init(&done_bar, 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -194,72 +204,113 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   const int nk = g.K / BK;
 
   if (warp == 0 && lane == 0) {
-    // TMA producer
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      if (kb >= STAGES) {
-        if (!mbar_wait(&empty_bar[s], ((kb / STAGES) - 1) & 1)) { atomicExch(g.err, 1); abort_flag = 1; break; }
-      }
-      if (abort_flag) break;
-      unsigned char* sa = base + (size_t)s * stage_bytes;
-      mbar_expect_tx(&full_bar[s], stage_bytes);
+    // TMA producer: runs ahead across tiles through the stage ring
+    int64_t it = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const int64_t m0 = mb + (t / n_nt) * BM;
+      const int n0 = (int)(t % n_nt) * BN;
+      for (int kb = 0; kb < nk; ++kb, ++it) {
+        const int s = (int)(it % STAGES);
+        if (it >= STAGES && !mbar_wait(&empty_bar[s], (uint32_t)((it / STAGES) - 1) & 1)) {
+          atomicExch(g.err, 1); abort_flag = 1; ok = false; break;
+        }
+        if (abort_flag) { ok = false; break; }
+        unsigned char* sa = base + (size_t)s * stage_bytes;
+        mbar_expect_tx(&full_bar[s], stage_bytes);
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        tma_load_2d(sa + c * a_bytes, &mapA, &full_bar[s], kb * BK, (int)(c * g.a_comp_rows + m0));
-        tma_load_2d(sa + NC * a_bytes + c * b_bytes, &mapB, &full_bar[s], kb * BK, (int)(c * g.b_comp_rows + n0));
+        for (int c = 0; c < NC; ++c) {
+          tma_load_2d(sa + c * a_bytes, &mapA, &full_bar[s], kb * BK, (int)(c * g.a_comp_rows + m0));
+          tma_load_2d(sa + NC * a_bytes + c * b_bytes, &mapB, &full_bar[s], kb * BK, (int)(c * g.b_comp_rows + n0));
+        }
       }
+    }
+    if (!ok) {
+      // let the copies already issued land before the CTA can exit
+      for (int64_t j = (it > STAGES ? it - STAGES : 0); j < it; ++j)
+        mbar_wait(&full_bar[j % STAGES], (uint32_t)(j / STAGES) & 1);
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
     const uint32_t idesc = idesc_bf16(BM, BN);
+    int64_t it = 0, tl = 0;
     bool ok = true;
-    for (int kb = 0; kb < nk && ok; ++kb) {
-      const int s = kb % STAGES;
-      if (!mbar_wait(&full_bar[s], (kb / STAGES) & 1)) { atomicExch(g.err, 2); abort_flag = 1; ok = false; break; }
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tl) {
+      const int buf = (int)(tl & 1);
+      if (tl >= 2 && !mbar_wait(&tempty_bar[buf], (uint32_t)((tl / 2) - 1) & 1)) {
+        atomicExch(g.err, 4); abort_flag = 1; ok = false; break;
+      }
       fence_after_sync();
-      const uint32_t sa = smem_u32(base + (size_t)s * stage_bytes);
-      const uint32_t sb = sa + NC * a_bytes;
-#pragma unroll
-      for (int pr = 0; pr < split_count(NC); ++pr) {
-        const uint32_t ap = sa + split_p(NC, pr) * a_bytes;
-        const uint32_t bq = sb + split_q(NC, pr) * b_bytes;
-#pragma unroll
-        for (int k = 0; k < BK / UMMA_K; ++k) {
-          const uint64_t ad = smem_desc_sw128(ap + k * UMMA_K * 2);
-          const uint64_t bd = smem_desc_sw128(bq + k * UMMA_K * 2);
-          mma_bf16(tmem, ad, bd, idesc, (kb > 0 || pr > 0 || k > 0) ? 1u : 0u);
+      const uint32_t d = tmem + (uint32_t)(buf * BN);
+      for (int kb = 0; kb < nk; ++kb, ++it) {
+        const int s = (int)(it % STAGES);
+        if (abort_flag || !mbar_wait(&full_bar[s], (uint32_t)(it / STAGES) & 1)) {
+          atomicExch(g.err, 2); abort_flag = 1; ok = false; break;
         }
+        fence_after_sync();
+        const uint32_t sa = smem_u32(base + (size_t)s * stage_bytes);
+        const uint32_t sb = sa + NC * a_bytes;
+#pragma unroll
+        for (int pr = 0; pr < split_count(NC); ++pr) {
+          const uint32_t ap = sa + split_p(NC, pr) * a_bytes;
+          const uint32_t bq = sb + split_q(NC, pr) * b_bytes;
+#pragma unroll
+          for (int k = 0; k < BK / UMMA_K; ++k) {
+            const uint64_t ad = smem_desc_sw128(ap + k * UMMA_K * 2);
+            const uint64_t bd = smem_desc_sw128(bq + k * UMMA_K * 2);
+            mma_bf16(d, ad, bd, idesc, (kb > 0 || pr > 0 || k > 0) ? 1u : 0u);
+          }
+        }
+        mma_commit(&empty_bar[s]);
       }
-      mma_commit(&empty_bar[s]);
+      if (ok) mma_commit(&tfull_bar[buf]);
     }
-    mma_commit(&done_bar);   // arrives once all MMAs issued above are complete
-  }
-  __syncwarp();
-  // epilogue: all four warps
-  const bool done_ok = mbar_wait(&done_bar, 0);
-  if (!done_ok && lane == 0) atomicExch(g.err, 3);
-  fence_after_sync();
-  if (done_ok && !abort_flag) {
-    const int64_t row = m0 + warp * 32 + lane;
-    const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-      float v[32];
-      tmem_ld32(tbase + (uint32_t)c0, v);
-      if (row < me) {
-        float* out = g.C + row * g.ldc + n0 + c0;
-        const int nvalid = min(32, min(BN, g.N - n0) - c0);
-        if (nvalid == 32 && ((reinterpret_cast<uintptr_t>(out) & 15) == 0)) {
-#pragma unroll
-          for (int q = 0; q < 32; q += 4)
-            *reinterpret_cast<float4*>(out + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
-        } else {
-          for (int q = 0; q < nvalid; ++q) out[q] = v[q];
-        }
+    mma_commit(&done_bar);   // arrives once every MMA issued above is complete
+    if (!mbar_wait(&done_bar, 0)) atomicExch(g.err, 5);
+  } else if (warp >= 2) {
+    // epilogue: warp w drains tensor-memory lanes 32 (w % 4) .. + 31
+    const int q = warp & 3;
+    float* tb = epi + (warp - 2) * 32 * 33;
+    int64_t tl = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
+      const int buf = (int)(tl & 1);
+      bool ok = true;
+      if (abort_flag) ok = false;
+      else if (!mbar_wait(&tfull_bar[buf], (uint32_t)(tl / 2) & 1)) {
+        if (lane == 0) atomicExch(g.err, 3);
+        abort_flag = 1;
+        ok = false;
       }
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) break;
+      fence_after_sync();
+      const int64_t m0 = mb + (t / n_nt) * BM;
+      const int n0 = (int)(t % n_nt) * BN;
+      const int ncol = min(BN, g.N - n0);
+      const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * BN);
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        float v[32];
+        tmem_ld32(tbase + (uint32_t)c0, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) tb[lane * 33 + j] = v[j];
+        __syncwarp();
+        const int col = c0 + lane;
+        if (col < ncol) {
+          for (int r = 0; r < 32; ++r) {
+            const int64_t row = m0 + 32 * q + r;
+            if (row < me) g.C[row * g.ldc + n0 + col] = tb[r * 33 + lane];
+          }
+        }
+        __syncwarp();
+      }
+      fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_expect_tx(&tempty_bar[buf], 0);   // one arrival per epilogue warp
     }
   }
   fence_before_sync();
   __syncthreads();
+  fence_after_sync();
   if (warp == 0) tmem_dealloc(tmem, ncols);
 }
 
