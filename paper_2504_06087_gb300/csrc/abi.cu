@@ -65,6 +65,7 @@ static int64_t numel(const PDesc& p) {
 static int check_system(const fire_system_t* sys, const fire_arch_t* ar) {
   if (!sys || !ar) return FIRE_ERR_INVALID_ARG;
   if (sys->n_el < 1 || sys->n_up < 0 || sys->n_up > sys->n_el || sys->n_nuc < 1) return FIRE_ERR_INVALID_ARG;
+  if (sys->n_nuc > kMaxNuc) return FIRE_ERR_UNSUPPORTED;   // nucleus list of the batched e-n filter
   if (!(sys->cutoff >= 0.0) || !(sys->cutoff_nuc > 0.0)) return FIRE_ERR_INVALID_ARG;
   if (ar->width < 32 || ar->width > 1024 || ar->width % 32) return FIRE_ERR_INVALID_ARG;
   if (ar->n_layers < 0 || ar->n_det < 1 || ar->n_det > 64 || ar->n_env < 1) return FIRE_ERR_INVALID_ARG;

@@ -43,6 +43,24 @@ __device__ __forceinline__ void pair_features_to_smem(const T dv[3], T r, const 
   }
 }
 
+// Feature k of one pair (the layout of pair_features_to_smem).
+template <typename T, typename W>
+__device__ __forceinline__ FL3<T> pair_feature(int k, const T dv[3], T r, const W* w1, const W* b1,
+                                               const W* sigma, T cut) {
+  const int H = kEdgeHidden, G = kGauss;
+  FL3<T> o;
+  if (k < H) pair_hidden<T, W>(dv, r, w1, b1, k, H, o);
+  else if (k < H + G) pair_chi<T>(dv, r, T(sigma[k - H]), cut, o);
+  else pair_ebar<T>(dv, r, k - H - G, o);
+  return o;
+}
+
+// Pairs whose filter features are computed together (one barrier pair per
+// batch instead of per pair).
+constexpr int kPairBatch = 8;
+// Largest nucleus count of the batched electron-nucleus filter.
+constexpr int kMaxNuc = 512;
+
 // One CTA per electron (w, i), blockDim == d.  Writes the filter sum
 // s_i = sum_m Gamma_m * (h^nuc_m + e-bar W) as R5 rows of S.
 template <typename T, typename W>
@@ -50,7 +68,6 @@ __global__ void en_filter_kernel(int Wc, int n, int n_up, int N, int d, const do
                                  const double* __restrict__ R, double cnuc, Params<W> p,
                                  T* __restrict__ S, int R5) {
   constexpr int H = kEdgeHidden, G = kGauss;
-  __shared__ FL3<T> feat[H + G + 4];
   const int blk = blockIdx.x;
   const int w = blk / n, i = blk % n;
   const int c = threadIdx.x;
@@ -65,15 +82,52 @@ __global__ void en_filter_kernel(int Wc, int n, int n_up, int N, int d, const do
   acc.v = acc.l = T(0);
   acc.t[0] = acc.t[1] = acc.t[2] = T(0);
   const double* ri = r + ((int64_t)w * n + i) * 3;
-  for (int m = 0; m < N; ++m) {
-    double dd[3] = {ri[0] - R[3 * m], ri[1] - R[3 * m + 1], ri[2] - R[3 * m + 2]};
-    double rr = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
-    if (!(rr < cnuc)) continue;   // Gamma_m vanishes identically for |x| >= c_n
-    T dv[3] = {T(dd[0]), T(dd[1]), T(dd[2])};
+  // nuclei within c_n (Gamma_m vanishes identically beyond), ascending
+  __shared__ FL3<T> featb[kPairBatch][H + G + 4];
+  __shared__ T s_dv[kPairBatch][3], s_r[kPairBatch];
+  __shared__ int s_m[kPairBatch];
+  __shared__ int s_list[kMaxNuc];
+  __shared__ int s_cnt;
+  if (threadIdx.x < 32) {
+    int cntm = 0;
+    for (int m0 = 0; m0 < N; m0 += 32) {
+      const int m = m0 + threadIdx.x;
+      bool in = false;
+      if (m < N) {
+        const double d0 = ri[0] - R[3 * m], d1 = ri[1] - R[3 * m + 1], d2 = ri[2] - R[3 * m + 2];
+        in = sqrt(d0 * d0 + d1 * d1 + d2 * d2) < cnuc;
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, in);
+      if (in) s_list[cntm + __popc(bal & ((1u << threadIdx.x) - 1u))] = m;
+      cntm += __popc(bal);
+    }
+    if (threadIdx.x == 0) s_cnt = cntm;
+  }
+  __syncthreads();
+  const int nlist = s_cnt;
+  for (int b0 = 0; b0 < nlist; b0 += kPairBatch) {
+    const int nbat = min(kPairBatch, nlist - b0);
+    __syncthreads();   // the previous batch is consumed
+    if (threadIdx.x < nbat) {
+      const int m = s_list[b0 + threadIdx.x];
+      const double dd[3] = {ri[0] - R[3 * m], ri[1] - R[3 * m + 1], ri[2] - R[3 * m + 2]};
+      s_dv[threadIdx.x][0] = T(dd[0]);
+      s_dv[threadIdx.x][1] = T(dd[1]);
+      s_dv[threadIdx.x][2] = T(dd[2]);
+      s_r[threadIdx.x] = T(sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]));
+      s_m[threadIdx.x] = m;
+    }
     __syncthreads();
-    pair_features_to_smem<T, W>(dv, T(rr), p.en_w1 + (int64_t)m * 4 * H, p.en_b1 + (int64_t)m * H,
-                                p.en_sigma, T(cnuc), feat);
+    for (int e = threadIdx.x; e < nbat * (H + G + 4); e += blockDim.x) {
+      const int q = e / (H + G + 4), k = e - q * (H + G + 4);
+      const int m = s_m[q];
+      featb[q][k] = pair_feature<T, W>(k, s_dv[q], s_r[q], p.en_w1 + (int64_t)m * 4 * H, p.en_b1 + (int64_t)m * H,
+                                       p.en_sigma, T(cnuc));
+    }
     __syncthreads();
+    for (int q = 0; q < nbat; ++q) {
+      const int m = s_m[q];
+      const FL3<T>* feat = featb[q];
     FL3<T> gv, ev, fv;
     gv.v = gv.l = ev.v = ev.l = T(0);
     fv.v = T(p.nuc_emb[(int64_t)m * d + c]);
@@ -111,6 +165,7 @@ __global__ void en_filter_kernel(int Wc, int n, int n_up, int N, int d, const do
     acc.l += term.l;
 #pragma unroll
     for (int t = 0; t < 3; ++t) acc.t[t] += term.t[t];
+    }
   }
   const int64_t row = (int64_t)block_index(w, i, Wc, n, n_up) * R5;
   S[row * d + c] = acc.v;
@@ -223,7 +278,6 @@ __global__ void msg_kernel(int Wc, int n, int n_up, int d, int K, const double* 
                            const T* __restrict__ H0, const T* __restrict__ PQ, T* __restrict__ X,
                            __nv_bfloat16* __restrict__ Xb, int xnc, int64_t xcs, int deriv) {
   constexpr int H = kEdgeHidden, G = kGauss;
-  __shared__ FL3<T> feat[H + G + 4];
   const int blk = blockIdx.x;
   const int w = blk / n, i = blk % n;
   const int c = threadIdx.x;
@@ -252,15 +306,29 @@ __global__ void msg_kernel(int Wc, int n, int n_up, int d, int K, const double* 
   const int cpar = cnt[((int64_t)w * n + i) * 2], ctot = cpar + cnt[((int64_t)w * n + i) * 2 + 1];
   const double* rw = r + (int64_t)w * n * 3;
   const int32_t* li = idx + ((int64_t)w * n + i) * K;
-  for (int s = 0; s < ctot; ++s) {
+  __shared__ FL3<T> featb[kPairBatch][H + G + 4];
+  __shared__ T s_dv[kPairBatch][3], s_r[kPairBatch];
+  for (int b0 = 0; b0 < ctot; b0 += kPairBatch) {
+    const int nbat = min(kPairBatch, ctot - b0);
+    __syncthreads();   // the previous batch is consumed
+    if (threadIdx.x < nbat) {
+      const int j = li[b0 + threadIdx.x];
+      const double dd[3] = {rw[3 * i] - rw[3 * j], rw[3 * i + 1] - rw[3 * j + 1], rw[3 * i + 2] - rw[3 * j + 2]};
+      s_dv[threadIdx.x][0] = T(dd[0]);
+      s_dv[threadIdx.x][1] = T(dd[1]);
+      s_dv[threadIdx.x][2] = T(dd[2]);
+      s_r[threadIdx.x] = T(sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]));
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nbat * (H + G + 4); e += blockDim.x) {
+      const int q = e / (H + G + 4), k = e - q * (H + G + 4);
+      featb[q][k] = pair_feature<T, W>(k, s_dv[q], s_r[q], p.ee_w1, p.ee_b1, p.ee_sigma, T(cut));
+    }
+    __syncthreads();
+  for (int s = b0; s < b0 + nbat; ++s) {
     const int j = li[s];
     const int a = (s < cpar) ? 0 : 1;
-    double dd[3] = {rw[3 * i] - rw[3 * j], rw[3 * i + 1] - rw[3 * j + 1], rw[3 * i + 2] - rw[3 * j + 2]};
-    double rr = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
-    T dv[3] = {T(dd[0]), T(dd[1]), T(dd[2])};
-    __syncthreads();
-    pair_features_to_smem<T, W>(dv, T(rr), p.ee_w1, p.ee_b1, p.ee_sigma, T(cut), feat);
-    __syncthreads();
+    const FL3<T>* feat = featb[s - b0];
     // Gamma(e_ij) in delta-space (delta = r_i - r_j)
     FL3<T> gv, ev, gam;
     gv.v = gv.l = ev.v = ev.l = T(0);
@@ -323,6 +391,7 @@ __global__ void msg_kernel(int Wc, int n, int n_up, int d, int K, const double* 
       }
       acc.l += T(2) * gam.l * f + T(2) * cross + gam.v * sl;
     }
+  }
   }
   X[xoff * d + c] = acc.v;
   if (Xb) store_split_bf16(Xb + xoff * d + c, xcs, xnc, (float)acc.v);
