@@ -5,6 +5,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "grad_bufs.h"
 #include "nbr.cuh"
 #include "pipeline.cuh"
@@ -123,6 +125,8 @@ static size_t layout(Plan& pl, int64_t Wc) {
   TAKE(F1, cap * ts);
   TAKE(F2, cap * ts);
   TAKE(Qf, nb * R5 * NE * ts);
+  const int64_t NEp = (NE + 63) / 64 * 64;
+  if (dm.prec == FIRE_PREC_BF16_FP64) TAKE(Qfb, kMaxSplit * nb * R5 * NEp * 2); else pl.Qfb = 0;
   TAKE(Fenv, nb * R5 * D * n * ts);
   // Hv / Ov also serve as value-row scratch of the tensor-core products
   const int64_t wmax = (d > J ? d : J) > dm.R + RD ? (d > J ? d : J) : dm.R + RD;
@@ -145,6 +149,7 @@ static size_t layout(Plan& pl, int64_t Wc) {
   TAKE(VY, Wc * vstride * J * ts);
   TAKE(G1, Wc * vstride * ts);
   TAKE(G2, Wc * vstride * ts);
+  if (dm.deriv && (dm.flags & FIRE_J_ATT)) TAKE(AP, (Wc * dm.R + nb * 12 * RD) * ts); else pl.AP = 0;
   if (bf) {
     // every weight block [N][K] is stored as kMaxSplit components [c][N][K]
     const int64_t S = kMaxSplit;
@@ -154,6 +159,7 @@ static size_t layout(Plan& pl, int64_t Wc) {
     pl.wb_jm2 = e; e += S * (d * J + J * J);
     pl.wb_att = e; e += S * (dm.R + RD) * d;
     pl.wb_orb = e; e += S * 2 * D * n * d;
+    pl.wb_env = e; e += S * 2 * D * n * NEp;
     TAKE(wbf16, e * 2);
   } else {
     pl.wbf16 = 0;
@@ -261,7 +267,9 @@ int make_plan(const fire_system_t* sys, const fire_arch_t* ar, int64_t W, int pr
   // shared-memory limits of the determinant kernels
   const int n = dm.n, mcap = 1 + (k_cap < dm.n - 1 ? k_cap : dm.n - 1);
   const size_t ctsm = contract_smem_bytes(mcap, pl->tsz);
-  const size_t invsm = (size_t)n * n * pl->tsz + 2 * n * sizeof(int);
+  // the float forms invert by Gauss-Jordan in shared memory (n <= 192), the
+  // rest by column panels on the LU factors
+  const size_t invsm = (pl->tsz == 4 && n <= 192) ? gj_smem_bytes(n) : inverse_panel_smem(n, pl->lsz);
   const size_t lim = 227 * 1024;
   if (dm.deriv && (ctsm > lim || invsm > lim)) return FIRE_ERR_UNSUPPORTED;
   pl->Wc = wc;
@@ -291,6 +299,19 @@ void prof_add(const char* name, int launches, float ms) {
   }
   g_prof[k].launches += launches;
   g_prof[k].ms += ms;
+}
+
+// One extra non-blocking stream per device for work that runs beside the
+// caller's stream inside a call (created on first use, kept until exit).
+cudaStream_t side_stream() {
+  static std::mutex mu;
+  static cudaStream_t streams[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess)
+    streams[dev] = nullptr;
+  return streams[dev];
 }
 
 void set_last_error(const char* stage, const char* msg) {

@@ -16,10 +16,14 @@
 namespace fire {
 
 // q_ime = exp(-sigma_me |r_i - R_m|) with gradient and Laplacian (rows:
-// value, Laplacian, d/dx, d/dy, d/dz).  One CTA per electron.
+// value, Laplacian, d/dx, d/dy, d/dz).  One CTA per electron.  With Qb the
+// rows are also written as nc bf16 components (row stride ldb >= N*E, zero
+// beyond N*E; components cs elements apart) for the tensor-core product.
 template <typename T, typename W>
 __global__ void env_feat_kernel(int Wc, int n, int n_up, int N, int E, const double* __restrict__ r,
-                                const double* __restrict__ R, const W* sig, T* __restrict__ Q, int R5) {
+                                const double* __restrict__ R, const W* sig, T* __restrict__ Q, int R5,
+                                __nv_bfloat16* __restrict__ Qb = nullptr, int ldb = 0, int nc = 0,
+                                int64_t cs = 0) {
   const int blk = blockIdx.x;
   const int w = blk / n, i = blk % n;
   const int NE = N * E;
@@ -32,12 +36,23 @@ __global__ void env_feat_kernel(int Wc, int n, int n_up, int N, int E, const dou
     T s = T(sig[q]);
     T rt = T(rr);
     T v = dexp<T>(-s * rt);
+    T o[5];
+    o[0] = v;
     Q[row * NE + q] = v;
     if (R5 > 1) {
-      Q[(row + 1) * NE + q] = (s * s - T(2) * s / rt) * v;
-      for (int t = 0; t < 3; ++t) Q[(row + 2 + t) * NE + q] = -s * v * T(dd[t]) / rt;
+      o[1] = (s * s - T(2) * s / rt) * v;
+      Q[(row + 1) * NE + q] = o[1];
+      for (int t = 0; t < 3; ++t) {
+        o[2 + t] = -s * v * T(dd[t]) / rt;
+        Q[(row + 2 + t) * NE + q] = o[2 + t];
+      }
     }
+    if (Qb)
+      for (int k = 0; k < R5; ++k) store_split_bf16(Qb + (row + k) * ldb + q, cs, nc, (float)o[k]);
   }
+  if (Qb)
+    for (int q = NE + threadIdx.x; q < ldb; q += blockDim.x)
+      for (int k = 0; k < R5; ++k) store_split_bf16(Qb + (row + k) * ldb + q, cs, nc, 0.f);
 }
 
 // Phi[w][d][i][l] = O_v[b(i)][d*n + l] * Fenv[b(i)*R5][d*n + l].
@@ -236,121 +251,145 @@ __global__ void lu_inverse_kernel(int n, const LT* __restrict__ M, const int32_t
 }
 
 // A = Phi^-1 by in-place Gauss-Jordan elimination with partial pivoting, in
-// float32, register-tiled: thread (tr, tc) of a G x G grid (G = ceil(n/8))
-// keeps the 8 x 8 block of rows 8tr.., columns 8tc.. in registers.  Step k
-// picks the unused row p with the largest |a_pk|, broadcasts row p and
-// column k through shared memory and updates every block:
+// float32, register-tiled: thread (tr, tc) of a Gr x Gc grid (Gr = ceil(n/12),
+// Gc = ceil(n/8)) keeps the 12 x 8 block of rows 12tr.., columns 8tc.. in
+// registers.  Step k picks the unused row p with the largest |a_pk|,
+// broadcasts row p and column k through shared memory and updates every
+// block:
 //   a_pj /= v (j != k), a_pk = 1/v;  a_ij -= a_ik a_pj / v, a_ik = -a_ik / v.
 // Rows are never moved: with piv[s] the row used at step s and step[r] its
 // inverse, the stored matrix S satisfies A^-1[r][piv[c]] = S[piv[r]][c].
 // The result is written transposed (AT[k][l] = A^-1[l][k]).  n <= 192.
+//
+// The column k = 8 kt + kj is unrolled over kj, so every register of the
+// pivot column is addressed statically; every element takes the same fused
+// update a_ij -= f_i s_j (f_p = 0), and only the owners of column k and of
+// row p rewrite their entries afterwards.  The broadcast buffers alternate
+// between steps, so three barriers separate the steps.
+constexpr int kGjTR = 12, kGjTC = 8;
+inline int gj_threads(int n) {
+  const int t = ((n + kGjTR - 1) / kGjTR) * ((n + kGjTC - 1) / kGjTC);
+  return ((t + 31) / 32) * 32;
+}
 template <typename IT, typename OT>
-__global__ void __launch_bounds__(576, 1) gj_inverse_kernel(int n, const IT* __restrict__ Phi, OT* __restrict__ AT) {
+__global__ void __launch_bounds__(384, 1) gj_inverse_kernel(int n, const IT* __restrict__ Phi, OT* __restrict__ AT) {
+  constexpr int TR = kGjTR, TC = kGjTC;
   extern __shared__ unsigned char gj_smem[];
   float* S = reinterpret_cast<float*>(gj_smem);          // [n][n] final matrix
-  float* prow = S + (int64_t)n * n;                      // [Gp] pivot row
-  float* pcol = prow + 256;                              // [Gp] pivot column
-  int* piv = reinterpret_cast<int*>(pcol + 256);         // [n]
+  float* prow = S + (int64_t)n * n;                      // [2][256] pivot row
+  float* pcol = prow + 512;                              // [2][256] pivot column
+  int* piv = reinterpret_cast<int*>(pcol + 512);         // [n]
   int* stp = piv + 256;                                  // [n]
   int* used = stp + 256;                                 // [n]
-  float* cv = reinterpret_cast<float*>(used + 256);      // [32] candidate |a|
-  int* ci = reinterpret_cast<int*>(cv + 32);             // [32] candidate row
-  const int G = (n + 7) / 8;
+  float* cv = reinterpret_cast<float*>(used + 256);      // [2][32] candidate |a|
+  int* ci = reinterpret_cast<int*>(cv + 64);             // [2][32] candidate row
+  const int Gr = (n + TR - 1) / TR, Gc = (n + TC - 1) / TC;
   const int tid = threadIdx.x;
-  const int tr = tid / G, tc = tid % G;
-  const bool live = tr < G;
+  const int tr = tid / Gc, tc = tid % Gc;
+  const bool live = tr < Gr;
   const IT* P = Phi + (int64_t)blockIdx.x * n * n;
-  float a[8][8];
+  float a[TR][TC];
 #pragma unroll
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < TR; ++i)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int r = 8 * tr + i, c = 8 * tc + j;
+    for (int j = 0; j < TC; ++j) {
+      const int r = TR * tr + i, c = TC * tc + j;
       a[i][j] = (live && r < n && c < n) ? (float)P[(int64_t)r * n + c] : 0.f;
     }
-  for (int r = tid; r < n; r += blockDim.x) used[r] = 0;
+  for (int r = tid; r < 256; r += blockDim.x) used[r] = 0;
   __syncthreads();
-  for (int k = 0; k < n; ++k) {
-    const int kt = k / 8, kj = k % 8;
-    // candidates: the threads of column block kt, one per row block
-    if (live && tc == kt) {
-      float best = -1.f;
-      int bi = n;
+  for (int kt = 0; kt < Gc; ++kt) {
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int r = 8 * tr + i;
-        float v = -1.f;
+    for (int kj = 0; kj < TC; ++kj) {
+      const int k = TC * kt + kj;
+      if (k < n) {
+        const int bsel = k & 1;
+        float* pr = prow + 256 * bsel;
+        float* pc = pcol + 256 * bsel;
+        float* cvb = cv + 32 * bsel;
+        int* cib = ci + 32 * bsel;
+        // candidates: the threads of column block kt, one per row block
+        if (live && tc == kt) {
+          float best = -1.f;
+          int bi = n;
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-          if (j == kj) v = fabsf(a[i][j]);
-        if (r < n && !used[r] && v > best) { best = v; bi = r; }
-      }
-      cv[tr] = best;
-      ci[tr] = bi;
-    }
-    __syncthreads();
-    if (tid < 32) {
-      float best = -1.f;
-      int bi = n;
-      for (int q = tid; q < G; q += 32)
-        if (cv[q] > best || (cv[q] == best && ci[q] < bi)) { best = cv[q]; bi = ci[q]; }
-      for (int o = 16; o > 0; o >>= 1) {
-        const float ov = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-      }
-      if (tid == 0) {
-        if (bi >= n) bi = 0;   // singular: any row, the result is not finite
-        piv[k] = bi;
-        stp[bi] = k;
-        used[bi] = 1;
-      }
-    }
-    __syncthreads();
-    const int p = piv[k];
-    const int pt = p / 8, pi = p % 8;
-    if (live && tr == pt)
+          for (int i = 0; i < TR; ++i) {
+            const int r = TR * tr + i;
+            const float v = fabsf(a[i][kj]);
+            if (r < n && !used[r] && v > best) { best = v; bi = r; }
+          }
+          cvb[tr] = best;
+          cib[tr] = bi;
+        }
+        __syncthreads();
+        if (tid < 32) {
+          float best = -1.f;
+          int bi = n;
+          for (int q = tid; q < Gr; q += 32)
+            if (cvb[q] > best || (cvb[q] == best && cib[q] < bi)) { best = cvb[q]; bi = cib[q]; }
+          for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+          }
+          if (tid == 0) {
+            if (bi >= n) bi = 0;   // singular: any row, the result is not finite
+            piv[k] = bi;
+            stp[bi] = k;
+            used[bi] = 1;
+          }
+        }
+        __syncthreads();
+        const int p = piv[k];
+        const int pt = p / TR, pi = p % TR;
+        if (live && tr == pt)
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
-        if (i == pi)
+          for (int i = 0; i < TR; ++i)
+            if (i == pi)
 #pragma unroll
-          for (int j = 0; j < 8; ++j) prow[8 * tc + j] = a[i][j];
-    if (live && tc == kt)
+              for (int j = 0; j < TC; ++j) pr[TC * tc + j] = a[i][j];
+        if (live && tc == kt)
 #pragma unroll
-      for (int j = 0; j < 8; ++j)
-        if (j == kj)
+          for (int i = 0; i < TR; ++i) pc[TR * tr + i] = a[i][kj];
+        __syncthreads();
+        const float v = pc[p];
+        const float iv = 1.f / v;
+        if (live) {
+          float f[TR];
 #pragma unroll
-          for (int i = 0; i < 8; ++i) pcol[8 * tr + i] = a[i][j];
-    __syncthreads();
-    const float v = pcol[p];
-    const float iv = 1.f / v;
-    if (live) {
-      float sp[8], f[8];
+          for (int i = 0; i < TR; ++i) f[i] = pc[TR * tr + i];
+          if (tr == pt) {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) sp[j] = prow[8 * tc + j] * iv;
+            for (int i = 0; i < TR; ++i)
+              if (i == pi) f[i] = 0.f;
+          }
 #pragma unroll
-      for (int i = 0; i < 8; ++i) f[i] = pcol[8 * tr + i];
+          for (int j = 0; j < TC; ++j) {
+            const float spj = pr[TC * tc + j] * iv;
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const bool isp = (tr == pt) && (i == pi);
+            for (int i = 0; i < TR; ++i) a[i][j] = fmaf(-f[i], spj, a[i][j]);
+          }
+          if (tc == kt) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const bool isk = (tc == kt) && (j == kj);
-          float x;
-          if (isp) x = isk ? iv : sp[j];
-          else x = isk ? -f[i] * iv : fmaf(-f[i], sp[j], a[i][j]);
-          a[i][j] = x;
+            for (int i = 0; i < TR; ++i) a[i][kj] = -f[i] * iv;
+          }
+          if (tr == pt) {
+#pragma unroll
+            for (int i = 0; i < TR; ++i)
+              if (i == pi)
+#pragma unroll
+                for (int j = 0; j < TC; ++j) a[i][j] = (tc == kt && j == kj) ? iv : pr[TC * tc + j] * iv;
+          }
         }
       }
     }
-    __syncthreads();
   }
   if (live)
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < TR; ++i)
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int r = 8 * tr + i, c = 8 * tc + j;
+      for (int j = 0; j < TC; ++j) {
+        const int r = TR * tr + i, c = TC * tc + j;
         if (r < n && c < n) S[r * n + c] = a[i][j];
       }
   __syncthreads();
@@ -389,7 +428,7 @@ inline size_t contract_smem_bytes(int mcap, size_t tsz) {
   return region * tsz + 2 * (size_t)mcap * sizeof(int) + 2 * (size_t)mcap * sizeof(int64_t) + 32;
 }
 
-inline size_t gj_smem_bytes(int n) { return (size_t)n * n * 4 + 512 * 4 + 768 * 4 + 64 * 4; }
+inline size_t gj_smem_bytes(int n) { return (size_t)n * n * 4 + 1024 * 4 + 768 * 4 + 128 * 4; }
 
 // Four consecutive shared-memory elements (16-byte aligned for float).
 template <typename T>

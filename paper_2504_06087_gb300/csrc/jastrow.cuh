@@ -170,6 +170,135 @@ __global__ void att_pool_kernel(int Wc, int n, int n_up, int K, int R, int dr,
   Vw[RD + col] = NL / Z - T(2) * A1 / (Z * Z) - Nv * ZL / (Z * Z) + T(2) * Nv * A2 / (Z * Z * Z);
 }
 
+// The same registers V with tangents and Laplacian, spread over electrons
+// (the single-CTA form above walks every forward-Laplacian row of a walker
+// serially).  Three launches:
+//   att_max_kernel   per walker, the largest score of each register r (the
+//                    softmax shift);
+//   att_part_kernel  one CTA per electron i (blockDim == R*dr), writing a
+//                    record of 12 rows of R*dr columns:
+//                      0 e_i, 1 e_i u_i, 2 e_i (Lap s_i + |grad s_i|^2),
+//                      3 e_i ((Lap s_i + |grad s_i|^2) u_i + 2 grad s_i.grad u_i + Lap u_i),
+//                      4 sum_x dN_x dZ_x, 5 sum_x dZ_x^2,
+//                      6..8 dZ_x, 9..11 dN_x   (x = the three coordinates of r_i),
+//                    where e_i = exp(s_ir - max_r), Z = sum_i e_i, N = sum_i e_i u_i
+//                    and dZ_x, dN_x their derivatives with respect to r_ix
+//                    (only electrons of Nbar_i contribute);
+//   att_fin_kernel   grid (walker, electron slice): the sums over electrons
+//                    in ascending order, then V = N / Z, its Laplacian
+//                      Lap N / Z - 2 grad N . grad Z / Z^2 - N Lap Z / Z^2 + 2 N |grad Z|^2 / Z^3
+//                    and the tangent rows dN/Z - N dZ / Z^2 of the slice.
+// AP holds Wc*R shifts followed by the Wc*n records (electron order).
+template <typename T>
+__global__ void att_max_kernel(int Wc, int n, int n_up, int R, const int64_t* __restrict__ blk_off,
+                               const T* __restrict__ SU, int64_t ld, T* __restrict__ AP) {
+  const int w = blockIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int q = wid; q < R; q += nw) {
+    T m = -INFINITY;
+    for (int i = lane; i < n; i += 32) m = fmax(m, SU[blk_off[block_index(w, i, Wc, n, n_up)] * ld + q]);
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) AP[(int64_t)w * R + q] = m;
+  }
+}
+
+template <typename T>
+__global__ void att_part_kernel(int Wc, int n, int n_up, int K, int R, int dr, const int32_t* __restrict__ idx,
+                                const int32_t* __restrict__ cnt, const int32_t* __restrict__ rev,
+                                const int64_t* __restrict__ blk_off, const T* __restrict__ SU, int64_t ld,
+                                T* __restrict__ AP) {
+  const int RD = R * dr;
+  const int col = threadIdx.x;
+  if (col >= RD) return;
+  const int w = blockIdx.x / n, i = blockIdx.x % n;
+  const int rg = col / dr;
+  const T mx = AP[(int64_t)w * R + rg];
+  T* rec = AP + (int64_t)Wc * R + (int64_t)blockIdx.x * 12 * RD;
+  const int bi = block_index(w, i, Wc, n, n_up);
+  const int64_t o = blk_off[bi], o1 = blk_off[bi + 1];
+  const T e = dexp<T>(SU[o * ld + rg] - mx);
+  const T u = SU[o * ld + R + col];
+  T ss = T(0), su = T(0);
+  for (int64_t q = o + 2; q < o1; ++q) {
+    const T st = SU[q * ld + rg];
+    ss += st * st;
+    su += st * SU[q * ld + R + col];
+  }
+  const T sl = SU[(o + 1) * ld + rg], ul = SU[(o + 1) * ld + R + col];
+  rec[0 * RD + col] = e;
+  rec[1 * RD + col] = e * u;
+  rec[2 * RD + col] = e * (sl + ss);
+  rec[3 * RD + col] = e * ((sl + ss) * u + T(2) * su + ul);
+  // tangents with respect to r_i: electron i itself (slot 0) and every j
+  // that has i in its list (slot rev + 1)
+  T dZ[3], dN[3];
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    const T st = SU[(o + 2 + x) * ld + rg];
+    dZ[x] = e * st;
+    dN[x] = e * (st * u + SU[(o + 2 + x) * ld + R + col]);
+  }
+  const int64_t base = (int64_t)w * n + i;
+  const int ct = cnt[base * 2] + cnt[base * 2 + 1];
+  for (int k = 0; k < ct; ++k) {
+    const int j = idx[base * K + k];
+    const int rv = rev[base * K + k];
+    if (rv < 0) continue;
+    const int bj = block_index(w, j, Wc, n, n_up);
+    const int64_t oj = blk_off[bj];
+    const T ej = dexp<T>(SU[oj * ld + rg] - mx);
+    const T uj = SU[oj * ld + R + col];
+    const int64_t rr = oj + 2 + 3 * (int64_t)(rv + 1);
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      const T st = SU[(rr + x) * ld + rg];
+      dZ[x] += ej * st;
+      dN[x] += ej * (st * uj + SU[(rr + x) * ld + R + col]);
+    }
+  }
+  T a1 = T(0), a2 = T(0);
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    a1 += dN[x] * dZ[x];
+    a2 += dZ[x] * dZ[x];
+    rec[(6 + x) * RD + col] = dZ[x];
+    rec[(9 + x) * RD + col] = dN[x];
+  }
+  rec[4 * RD + col] = a1;
+  rec[5 * RD + col] = a2;
+}
+
+template <typename T>
+__global__ void att_fin_kernel(int Wc, int n, int R, int dr, const T* __restrict__ AP, T* __restrict__ V) {
+  const int RD = R * dr;
+  const int col = threadIdx.x;
+  if (col >= RD) return;
+  const int w = blockIdx.x;
+  const T* recw = AP + (int64_t)Wc * R + (int64_t)w * n * 12 * RD;
+  T sm[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+  for (int i = 0; i < n; ++i) {
+    const T* rec = recw + (int64_t)i * 12 * RD;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) sm[q] += rec[q * RD + col];
+  }
+  const T Z = sm[0], Nv = sm[1], ZL = sm[2], NL = sm[3], A1 = sm[4], A2 = sm[5];
+  T* Vw = V + (int64_t)w * (2 + 3 * (int64_t)n) * RD;
+  if (blockIdx.y == 0) {
+    Vw[col] = Nv / Z;
+    Vw[RD + col] = NL / Z - T(2) * A1 / (Z * Z) - Nv * ZL / (Z * Z) + T(2) * Nv * A2 / (Z * Z * Z);
+  }
+  const int per = (n + gridDim.y - 1) / gridDim.y;
+  const int i0 = blockIdx.y * per, i1 = min(n, i0 + per);
+  for (int i = i0; i < i1; ++i) {
+    const T* rec = recw + (int64_t)i * 12 * RD;
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      const T dZ = rec[(6 + x) * RD + col], dN = rec[(9 + x) * RD + col];
+      Vw[(2 + 3 * (int64_t)i + x) * RD + col] = dN / Z - Nv * dZ / (Z * Z);
+    }
+  }
+}
+
 // log|J_att| from the two readouts of V.  One CTA per walker.
 template <typename T, typename W>
 __global__ void att_reduce_kernel(int n, const T* __restrict__ G1, const T* __restrict__ G2,

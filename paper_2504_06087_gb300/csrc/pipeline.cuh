@@ -67,6 +67,7 @@ struct CallArgs {
 };
 
 void set_last_error(const char* stage, const char* msg);
+cudaStream_t side_stream();
 bool prof_enabled();
 void prof_add(const char* name, int launches, float ms);
 int run_fp64(const Plan& pl, const CallArgs& a);
@@ -116,28 +117,51 @@ struct Runner {
     p = make_params<T>(a.theta, a.poff);
     dbg = getenv("FIRE_DEBUG_SYNC") != nullptr;
     // FIRE_TC_MASK (diagnostic): bit 0 embedding MLP, 1 Jastrow MLPs,
-    // 2 attention, 3 orbitals -- which products may use the tensor cores.
+    // 2 attention, 3 orbitals, 4 envelopes -- which products may use the
+    // tensor cores.
     if (const char* m = getenv("FIRE_TC_MASK")) tc_mask = atoi(m);
     if (const char* m = getenv("FIRE_TC_FIX_VALUES")) fix_values = atoi(m);
     // FIRE_INVERSE (diagnostic): 1 = float32 Gauss-Jordan from a float copy of
     // Phi (n <= 192, the default of the float32 forms), 0 = triangular solves
     // on the LU factors (always for float64 and for n > 192)
     if (const char* m = getenv("FIRE_INVERSE")) use_gj = atoi(m) == 1;
-    auto nc_env = [](const char* k, int dflt) {
+    auto split_env = [](const char* k, int dflt) {
       const char* v = getenv(k);
       int x = v ? atoi(v) : dflt;
       return x < 1 ? 1 : (x > kMaxSplit ? kMaxSplit : x);
     };
-    nc_mlp = nc_env("FIRE_TC_SPLIT_MLP", nc_mlp);
-    nc_jas = nc_env("FIRE_TC_SPLIT_JASTROW", nc_jas);
-    nc_att = nc_env("FIRE_TC_SPLIT_ATT", nc_att);
-    nc_orb = nc_env("FIRE_TC_SPLIT_ORB", nc_orb);
+    nc_mlp = split_env("FIRE_TC_SPLIT_MLP", nc_mlp);
+    nc_jas = split_env("FIRE_TC_SPLIT_JASTROW", nc_jas);
+    nc_att = split_env("FIRE_TC_SPLIT_ATT", nc_att);
+    nc_orb = split_env("FIRE_TC_SPLIT_ORB", nc_orb);
+    nc_env = split_env("FIRE_TC_SPLIT_ENV", nc_env);
+    ncw = nc_mlp > nc_jas ? nc_mlp : nc_jas;
+    if (nc_att > ncw) ncw = nc_att;
+    if (nc_orb > ncw) ncw = nc_orb;
     capA = pl.Wc * dm.n * pl.rows_per_el;
     prof = prof_enabled();
     ws = reinterpret_cast<unsigned char*>(a.ws);
     s = a.stream;
   }
   template <typename X> X* at(size_t off) { return reinterpret_cast<X*>(ws + off); }
+
+  // Second stream of this device (created once, non-blocking) and the fork /
+  // join events of the current call.
+  bool lu_side = false;
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool side_ready() {
+    if (getenv("FIRE_SERIAL")) return false;   // diagnostic: one stream only
+    if (!s2) s2 = side_stream();
+    if (!s2) return false;
+    if (!ev_fork && cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) != cudaSuccess) return false;
+    if (!ev_join && cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming) != cudaSuccess) return false;
+    return true;
+  }
+  ~Runner() {
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+  }
 
   // With FIRE_DEBUG_SYNC set, every stage is synchronised and checked, and the
   // name of the first failing stage is kept for fire_last_error().
@@ -184,11 +208,18 @@ struct Runner {
   // stride lda, a_rows rows allocated) and packed bf16 weights Bt [N][K] it
   // runs on the tensor cores (BF16_FP64 form); otherwise SIMT in T.
   int tc_rc = FIRE_OK;
-  int tc_mask = 0xF;
+  int tc_mask = 0x1F;
   int fix_values = 1;         // value rows recomputed in fp32 after a tensor-core product
-  // split-bf16 components of each tensor-core product (1: 1 product, 2: 3, 3: 6)
-  // (6 component products everywhere: the E_L error then matches plain fp32)
-  int nc_mlp = 3, nc_jas = 3, nc_att = 3, nc_orb = 3;
+  // split-bf16 components of each tensor-core product (1: 1 product, 2: 3, 3: 6).
+  // Two components (hi + lo, three products) for the products whose value
+  // rows are recomputed in fp32 afterwards: measured against the float64 path
+  // on 128 C26H24 walkers, the E_L error distribution then equals that of
+  // plain fp32 (median 2e-5) and of three components; one component raises
+  // the median error to 8e-4.  The attention product has no value-row
+  // recompute (its value rows set log|J_att|) and keeps three components.
+  int nc_mlp = 2, nc_jas = 2, nc_att = 3, nc_orb = 2;
+  int ncw = 3;                // components written for the bf16 copies of X and Y
+  int nc_env = 3;             // envelope product: its value rows enter Phi directly
   bool use_gj = true;
   // A^T from the LU factors, matrices in batches of the grid limit
   void inverse_from_lu(int n, int64_t nmat, const LT* LUb, const int32_t* piv, T* Ainv) {
@@ -237,7 +268,7 @@ struct Runner {
                    __nv_bfloat16* Yb, int64_t ldy, T* F) {
     const int J = dm.J;
     row_gemm(Xin, Xinb, ldx, capA, w1, w1b, J, Z, ldz, range, rb, re, cap, J, din, nc_jas);
-    fl_act_kernel<T, T><<<nblk, 256, 0, s>>>(J, off, stride, Z, ldz, b1, Y, ldy, 0, Yb, kMaxSplit,
+    fl_act_kernel<T, T><<<nblk, 256, 0, s>>>(J, off, stride, Z, ldz, b1, Y, ldy, 0, Yb, nc_jas,
                                              capA * ldy);
     row_gemm(Y, Yb, ldy, capA, w2, w2b, J, Z, ldz, range, rb, re, cap, J, J, nc_jas);
     fl_act_kernel<T, T><<<nblk, 256, 0, s>>>(J, off, stride, Z, ldz, b2, Y, ldy, 0);
@@ -393,8 +424,7 @@ struct Runner {
       phi_assemble_kernel<T, LT><<<wc * D, 256, 0, s>>>(wc, n, n_up, D, Ov, Fenv, 1, LUb, gj ? B.Phif : nullptr);
       lu_kernel<LT, 16><<<wc * D, 256, (size_t)2 * n * 16 * sizeof(LT), s>>>(n, LUb, piv, ldabs, lsign);
       if (gj) {
-        const int Gq = (n + 7) / 8;
-        gj_inverse_kernel<float, T><<<wc * D, ((Gq * Gq + 31) / 32) * 32, gj_smem_bytes(n), s>>>(n, B.Phif, B.AT);
+        gj_inverse_kernel<float, T><<<wc * D, gj_threads(n), gj_smem_bytes(n), s>>>(n, B.Phif, B.AT);
       } else {
         inverse_from_lu(n, (int64_t)wc * D, LUb, piv, B.AT);
       }
@@ -585,6 +615,12 @@ struct Runner {
         for (int rr = 0; rr < R; ++rr, ++np)
           tc::pack_bf16(s, reinterpret_cast<const float*>(p.att_wv) + rr * d * dr, dr, (int)d, (int)dr, 1,
                         dst(pl.wb_att + (R + rr * dr) * d), S, acs);
+        {
+          const int64_t NE = (int64_t)dm.N * dm.E, NEp = ((NE + 63) / 64) * 64, Dn = D * n;
+          for (int sp = 0; sp < 2; ++sp, ++np)
+            tc::pack_bf16(s, reinterpret_cast<const float*>(p.env_pi) + sp * Dn * NE, NE, (int)NE, (int)Dn, 0,
+                          dst(pl.wb_env + S * sp * Dn * NEp), S, Dn * NEp, (int)NEp);
+        }
         for (int sp = 0; sp < 2; ++sp)
           for (int dd = 0; dd < D; ++dd, ++np)
             tc::pack_bf16(s, reinterpret_cast<const float*>(p.orb_w) + (sp * D + dd) * d * n, n, (int)d, (int)n, 1,
@@ -656,7 +692,7 @@ struct Runner {
         return (WB && (tc_mask >> bit & 1)) ? WB + off : nullptr;
       };
       mark("msg", 1);
-      msg_kernel<T, T><<<nb, d, 0, s>>>(wc, n, n_up, d, K, r, c, p, idx, cnt, boff, H0, PQ, X, Xb, kMaxSplit,
+      msg_kernel<T, T><<<nb, d, 0, s>>>(wc, n, n_up, d, K, r, c, p, idx, cnt, boff, H0, PQ, X, Xb, ncw,
                                         capA * d, deriv);
       check("msg");
       if (dm.op == FIRE_OP_MCMC) {   // the Metropolis state keeps h^1 (value rows, block order)
@@ -677,7 +713,90 @@ struct Runner {
                  d, Z, ldb, fullr, 0, 0, cap, d, d, nc_mlp);
         mark("fl_act", 1);
         fl_act_kernel<T, T><<<nb, 256, 0, s>>>(d, boff, 0, Z, ldb, p.mlp_b + (int64_t)l * d, X, d, 1, Xb,
-                                               kMaxSplit, capA * d);
+                                               ncw, capA * d);
+      }
+      // 7. envelopes and orbital values
+      const int E = dm.E, NE = N * E;
+      const int64_t Dn = (int64_t)D * n;
+      T* Qf = at<T>(pl.Qf);
+      T* Fenv = at<T>(pl.Fenv);
+      mark("envelope", 3);
+      // BF16 form: the features also as bf16 components (K padded to a
+      // multiple of 64) for the tensor-core product with the packed pi
+      const int NEp = ((NE + 63) / 64) * 64;
+      const int64_t r5cap = (int64_t)pl.Wc * n * R5;
+      __nv_bfloat16* Qfb = (pl.Qfb && WB && (tc_mask & 16)) ? at<__nv_bfloat16>(pl.Qfb) : nullptr;
+      env_feat_kernel<T, T><<<nb, 128, 0, s>>>(wc, n, n_up, N, E, r, sys->nuc_pos, p.env_sigma, Qf, R5, Qfb, NEp,
+                                               nc_env, r5cap * NEp);
+      const int64_t up5 = (int64_t)wc * n_up * R5;
+      for (int sp = 0; sp < 2; ++sp) {
+        const int64_t rb = sp ? up5 : 0, re = sp ? r5 : up5;
+        if (re <= rb) continue;
+        if constexpr (sizeof(T) == 4) {
+          if (Qfb) {
+            const int rc = tc::gemm_bf16(s, Qfb, NEp, r5cap, WB + pl.wb_env + (int64_t)kMaxSplit * sp * Dn * NEp,
+                                         (int)Dn, NEp, reinterpret_cast<float*>(Fenv), Dn, rb, re, nullptr, re - rb,
+                                         &st->tc_err, nc_env);
+            if (rc == FIRE_OK) continue;
+            tc_rc = rc;
+          }
+        }
+        gemm<T>(s, Qf, NE, p.env_pi + (int64_t)sp * Dn * NE, NE, true, Fenv, Dn, rb, re, nullptr, re - rb,
+                (int)Dn, NE);
+      }
+      T* Hv = at<T>(pl.Hv);
+      T* Ov = at<T>(pl.Ov);
+      mark("orb_values", 4);
+      gather_value_rows_kernel<T><<<nb, 256, 0, s>>>(nb, d, boff, X, Hv);
+      const int64_t upv = (int64_t)wc * n_up;
+      for (int sp = 0; sp < 2; ++sp) {
+        const int64_t rb = sp ? upv : 0, re = sp ? nb : upv;
+        if (re > rb)
+          gemm<T>(s, Hv, d, p.orb_w + (int64_t)sp * D * d * n, n, false, Ov, Dn, rb, re, nullptr, re - rb, n, d,
+                  D, 0, (int64_t)d * n, n);
+      }
+      LT* LUb = at<LT>(pl.LU);
+      int32_t* piv = at<int32_t>(pl.piv);
+      double* ldabs = at<double>(pl.ldabs);
+      double* lsign = at<double>(pl.lsign);
+      // A^T: float32 Gauss-Jordan from a float copy of Phi (float32 forms,
+      // n <= 192), else triangular solves on the LU factors
+      const bool gj = use_gj && deriv && sizeof(T) == 4 && n <= 192;
+      float* Phif = gj ? at<float>(pl.Phif) : nullptr;
+      phi_assemble_kernel<T, LT><<<wc * D, 256, 0, s>>>(wc, n, n_up, D, Ov, Fenv, R5, LUb, Phif);
+      const bool mc = dm.op == FIRE_OP_MCMC;
+      if (mc) {
+        // the Metropolis state keeps Phi itself next to its factors
+        convert_kernel<LT, T><<<1024, 256, 0, s>>>((int64_t)wc * D * n * n, LUb, at<T>(pl.PhiS));
+        launches += 1;
+      }
+      const size_t lusm = (size_t)2 * n * 16 * sizeof(LT);
+      // slogdet: when the inverse does not come from these factors (float
+      // forms: Gauss-Jordan on a float copy of Phi; value-only calls), the
+      // float64 LU runs on a second stream, beside the Jastrow factors and the
+      // log-det derivatives, and joins before the final combination
+      lu_side = !mc && (!deriv || gj) && side_ready();
+      mark("lu", 1);
+      if (lu_side) {
+        cudaEventRecord(ev_fork, s);
+        cudaStreamWaitEvent(s2, ev_fork, 0);
+        lu_kernel<LT, 16><<<wc * D, 256, lusm, s2>>>(n, LUb, piv, ldabs, lsign);
+        cudaEventRecord(ev_join, s2);
+      } else {
+        lu_kernel<LT, 16><<<wc * D, 256, lusm, s>>>(n, LUb, piv, ldabs, lsign);
+      }
+      check("lu");
+      if (mc) {
+        // A^T = (Phi^-1)^T from the float64 factors
+        mark("inverse", 1);
+        const int64_t nmat = (int64_t)wc * D;
+        const size_t ism = inverse_panel_smem(n, sizeof(LT));
+        for (int64_t m0 = 0; m0 < nmat; m0 += 65535) {
+          const int64_t cnt = nmat - m0 < 65535 ? nmat - m0 : 65535;
+          inverse_panel_kernel<LT, LT, T><<<(unsigned)cnt, 256, ism, s>>>(n, m0, LUb, piv, at<T>(pl.Ainv));
+          launches += 1;
+        }
+        check("inverse");
       }
       // 6. Jastrow factors
       T* jval = at<T>(pl.jval); T* jsign = at<T>(pl.jsign); T* jgrad = at<T>(pl.jgrad); T* jlap = at<T>(pl.jlap);
@@ -715,10 +834,19 @@ struct Runner {
         T* VY = at<T>(pl.VY);
         T* G1 = at<T>(pl.G1);
         T* G2 = at<T>(pl.G2);
-        const size_t apsm = (size_t)(R + n * R) * sizeof(T);
         const int bt = ((RD + 31) / 32) * 32;
-        mark("att_pool", 1);
-        att_pool_kernel<T><<<wc, bt, apsm, s>>>(wc, n, n_up, K, R, dr, idx, cnt, rev, boff, SU, ldb, V, deriv);
+        if (deriv) {
+          // per-electron partial records, then ordered sums per walker
+          T* AP = at<T>(pl.AP);
+          mark("att_pool", 3);
+          att_max_kernel<T><<<wc, 256, 0, s>>>(wc, n, n_up, R, boff, SU, ldb, AP);
+          att_part_kernel<T><<<nb, bt, 0, s>>>(wc, n, n_up, K, R, dr, idx, cnt, rev, boff, SU, ldb, AP);
+          att_fin_kernel<T><<<dim3(wc, 8), bt, 0, s>>>(wc, n, R, dr, AP, V);
+        } else {
+          const size_t apsm = (size_t)(R + n * R) * sizeof(T);
+          mark("att_pool", 1);
+          att_pool_kernel<T><<<wc, bt, apsm, s>>>(wc, n, n_up, K, R, dr, idx, cnt, rev, boff, SU, ldb, V, deriv);
+        }
         const int64_t vstride = deriv ? (2 + 3 * (int64_t)n) : 1;
         const int64_t vrows = (int64_t)wc * vstride;
         mark("att_mlp", 11);
@@ -732,70 +860,13 @@ struct Runner {
       mark("coulomb_cusp", 1);
       coulomb_cusp_kernel<T, T><<<wc, 256, 0, s>>>(n, n_up, N, r, sys->nuc_pos, sys->nuc_charge, p.cusp, vpot,
                                                    cval, cgrad, clap, deriv);
-      // 7. envelopes and orbital values
-      const int E = dm.E, NE = N * E;
-      const int64_t Dn = (int64_t)D * n;
-      T* Qf = at<T>(pl.Qf);
-      T* Fenv = at<T>(pl.Fenv);
-      mark("envelope", 3);
-      env_feat_kernel<T, T><<<nb, 128, 0, s>>>(wc, n, n_up, N, E, r, sys->nuc_pos, p.env_sigma, Qf, R5);
-      const int64_t up5 = (int64_t)wc * n_up * R5;
-      for (int sp = 0; sp < 2; ++sp) {
-        const int64_t rb = sp ? up5 : 0, re = sp ? r5 : up5;
-        if (re > rb)
-          gemm<T>(s, Qf, NE, p.env_pi + (int64_t)sp * Dn * NE, NE, true, Fenv, Dn, rb, re, nullptr, re - rb,
-                  (int)Dn, NE);
-      }
-      T* Hv = at<T>(pl.Hv);
-      T* Ov = at<T>(pl.Ov);
-      mark("orb_values", 4);
-      gather_value_rows_kernel<T><<<nb, 256, 0, s>>>(nb, d, boff, X, Hv);
-      const int64_t upv = (int64_t)wc * n_up;
-      for (int sp = 0; sp < 2; ++sp) {
-        const int64_t rb = sp ? upv : 0, re = sp ? nb : upv;
-        if (re > rb)
-          gemm<T>(s, Hv, d, p.orb_w + (int64_t)sp * D * d * n, n, false, Ov, Dn, rb, re, nullptr, re - rb, n, d,
-                  D, 0, (int64_t)d * n, n);
-      }
-      LT* LUb = at<LT>(pl.LU);
-      int32_t* piv = at<int32_t>(pl.piv);
-      double* ldabs = at<double>(pl.ldabs);
-      double* lsign = at<double>(pl.lsign);
-      // A^T: float32 Gauss-Jordan from a float copy of Phi (float32 forms,
-      // n <= 192), else triangular solves on the LU factors
-      const bool gj = use_gj && deriv && sizeof(T) == 4 && n <= 192;
-      float* Phif = gj ? at<float>(pl.Phif) : nullptr;
-      phi_assemble_kernel<T, LT><<<wc * D, 256, 0, s>>>(wc, n, n_up, D, Ov, Fenv, R5, LUb, Phif);
-      const bool mc = dm.op == FIRE_OP_MCMC;
-      if (mc) {
-        // the Metropolis state keeps Phi itself next to its factors
-        convert_kernel<LT, T><<<1024, 256, 0, s>>>((int64_t)wc * D * n * n, LUb, at<T>(pl.PhiS));
-        launches += 1;
-      }
-      const size_t lusm = (size_t)2 * n * 16 * sizeof(LT);
-      mark("lu", 1);
-      lu_kernel<LT, 16><<<wc * D, 256, lusm, s>>>(n, LUb, piv, ldabs, lsign);
-      check("lu");
-      if (mc) {
-        // A^T = (Phi^-1)^T from the float64 factors
-        mark("inverse", 1);
-        const int64_t nmat = (int64_t)wc * D;
-        const size_t ism = inverse_panel_smem(n, sizeof(LT));
-        for (int64_t m0 = 0; m0 < nmat; m0 += 65535) {
-          const int64_t cnt = nmat - m0 < 65535 ? nmat - m0 : 65535;
-          inverse_panel_kernel<LT, LT, T><<<(unsigned)cnt, 256, ism, s>>>(n, m0, LUb, piv, at<T>(pl.Ainv));
-          launches += 1;
-        }
-        check("inverse");
-      }
       T* gdet = at<T>(pl.gdet);
       T* ldet = at<T>(pl.ldet);
       if (deriv) {
         T* Ainv = at<T>(pl.Ainv);
         mark("inverse", 1);
         if (gj) {
-          const int G = (n + 7) / 8;
-          const int thr = ((G * G + 31) / 32) * 32;
+          const int thr = gj_threads(n);
           gj_inverse_kernel<float, T><<<wc * D, thr, gj_smem_bytes(n), s>>>(n, Phif, Ainv);
         } else {
           inverse_from_lu(n, (int64_t)wc * D, LUb, piv, Ainv);
@@ -826,6 +897,7 @@ struct Runner {
         }
       }
       // 9. final combination
+      if (lu_side) cudaStreamWaitEvent(s, ev_join, 0);
       FinalIn<T, RT> fi{ldabs, lsign, gdet, ldet, cval, cgrad, clap, jval, jsign, jgrad, jlap,
                         aval, asign, agrad, alap, vpot};
       mark("final", 1);

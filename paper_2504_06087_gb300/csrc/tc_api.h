@@ -17,9 +17,10 @@ int gemm_bf16(cudaStream_t s, const void* A, int64_t lda, int64_t a_rows, const 
               float* C, int64_t ldc, int64_t m_begin, int64_t m_end, const int64_t* m_range, int64_t m_cap,
               int* err, int nc);
 
-// dst = nc-component bf16 K-major copy of a weight matrix (pack_bf16_kernel).
+// dst = nc-component bf16 K-major copy of a weight matrix (pack_bf16_kernel),
+// rows ldd >= K elements apart with zero padding (ldd = 0: K).
 void pack_bf16(cudaStream_t s, const float* src, int64_t lds, int K, int N, int trans, void* dst, int nc,
-               int64_t comp_stride);
+               int64_t comp_stride, int ldd = 0);
 
 }  // namespace tc
 }  // namespace fire

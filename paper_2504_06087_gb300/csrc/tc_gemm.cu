@@ -99,13 +99,14 @@ int gemm_bf16(cudaStream_t s, const void* A, int64_t lda, int64_t a_rows, const 
 
 // dst[c][n][k] = component c of src[k * lds + n] for a [K][N] source
 // (trans = 1), or of src[n * lds + k] for an [N][K] source (trans = 0);
-// components are comp_stride elements apart.
+// components are comp_stride elements apart, rows ldd >= K elements apart,
+// and the row padding k in [K, ldd) is zero.
 __global__ void pack_bf16_kernel(const float* __restrict__ src, int64_t lds, int K, int N, int trans,
-                                 __nv_bfloat16* __restrict__ dst, int nc, int64_t comp_stride) {
+                                 __nv_bfloat16* __restrict__ dst, int nc, int64_t comp_stride, int ldd) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (int64_t)N * K) return;
-  const int nn = (int)(e / K), kk = (int)(e % K);
-  float v = trans ? src[(int64_t)kk * lds + nn] : src[(int64_t)nn * lds + kk];
+  if (e >= (int64_t)N * ldd) return;
+  const int nn = (int)(e / ldd), kk = (int)(e % ldd);
+  float v = kk >= K ? 0.f : (trans ? src[(int64_t)kk * lds + nn] : src[(int64_t)nn * lds + kk]);
   for (int c = 0; c < nc; ++c) {
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
     dst[c * comp_stride + e] = h;
@@ -114,11 +115,12 @@ __global__ void pack_bf16_kernel(const float* __restrict__ src, int64_t lds, int
 }
 
 void pack_bf16(cudaStream_t s, const float* src, int64_t lds, int K, int N, int trans, void* dst, int nc,
-               int64_t comp_stride) {
-  const int64_t tot = (int64_t)N * K;
+               int64_t comp_stride, int ldd) {
+  if (ldd < K) ldd = K;
+  const int64_t tot = (int64_t)N * ldd;
   pack_bf16_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(src, lds, K, N, trans,
                                                                  reinterpret_cast<__nv_bfloat16*>(dst), nc,
-                                                                 comp_stride);
+                                                                 comp_stride, ldd);
 }
 
 }  // namespace tc
