@@ -127,6 +127,14 @@ static size_t layout(Plan& pl, int64_t Wc) {
   TAKE(Qf, nb * R5 * NE * ts);
   const int64_t NEp = (NE + 63) / 64 * 64;
   if (dm.prec == FIRE_PREC_BF16_FP64) TAKE(Qfb, kMaxSplit * nb * R5 * NEp * 2); else pl.Qfb = 0;
+  if (dm.prec == FIRE_PREC_BF16_FP64) {
+    TAKE(Y5b, kMaxSplit * nb * R5 * d * 2);
+    TAKE(P5b, kMaxSplit * nb * R5 * d * 2);
+    TAKE(H0b, kMaxSplit * nb * R5 * d * 2);
+    TAKE(Hvb, kMaxSplit * nb * d * 2);
+  } else {
+    pl.Y5b = pl.P5b = pl.H0b = pl.Hvb = 0;
+  }
   TAKE(Fenv, nb * R5 * D * n * ts);
   // Hv / Ov also serve as value-row scratch of the tensor-core products
   const int64_t wmax = (d > J ? d : J) > dm.R + RD ? (d > J ? d : J) : dm.R + RD;
@@ -160,6 +168,10 @@ static size_t layout(Plan& pl, int64_t Wc) {
     pl.wb_att = e; e += S * (dm.R + RD) * d;
     pl.wb_orb = e; e += S * 2 * D * n * d;
     pl.wb_env = e; e += S * 2 * D * n * NEp;
+    pl.wb_glu = e; e += S * 2 * d * d;
+    pl.wb_gluo = e; e += S * d * d;
+    pl.wb_msg = e; e += S * 4 * d * d;
+    pl.wb_orbv = e; e += S * 2 * D * n * d;
     TAKE(wbf16, e * 2);
   } else {
     pl.wbf16 = 0;

@@ -627,4 +627,240 @@ contract_kernel(int Wc, int n, int n_up, int K, int mcap, int dd, int D, const i
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same contraction on the tensor cores (mma.sync m16n8k8, TF32 operands,
+// FP32 accumulation).  Each operand v is split into v_hi = tf32(v) and
+// v_lo = tf32(v - v_hi) and every product takes the three passes
+// lo*hi + hi*lo + hi*hi, which keeps the float32 accuracy of the SIMT form.
+//
+// One warp per tangent electron n' (8 per CTA, no CTA barriers).  For each
+// coordinate x the warp forms M_x[k][k'] = sum_l T_x[k][l] A[l][i_k'] over
+// the m members of Nbar_n' in 32 x 32 blocks (2 x 4 tiles of 16 x 8), with
+// T_x[k][l] = O[row(i_k, slot of n', x)][l] * phi[i_k][l] (+ the envelope
+// derivative term of n' itself, k = 0) built in registers straight from the
+// gathered rows.  Within a 16-wide step of l, lane (g, t) holds l0 + 4t ..
+// l0 + 4t + 3 of its rows of T and of its columns of A: the first k8 step
+// takes the pairs (4t, 4t+1), the second (4t+2, 4t+3) -- one consistent
+// permutation of l for both operands, so every load is a 128-bit row slice.
+// M_x goes to a per-warp shared-memory block, from which
+//   d log det / d r_n'x = sum_k M_x[k][k],  trace_x = sum_{k,k'} M_x[k][k'] M_x[k'][k].
+// Neighbourhoods of up to 64 members.
+constexpr int kCtWarps = 8;
+constexpr int kCtMaxMembers = 64;
+__host__ __device__ inline size_t contract_tc_warp_bytes(int mcap) {
+  const size_t msb = ((size_t)mcap * (mcap + 1) * 4 + 15) & ~(size_t)15;
+  return (msb + (size_t)mcap * 20 + 15) & ~(size_t)15;
+}
+inline size_t contract_tc_smem_bytes(int mcap) { return kCtWarps * contract_tc_warp_bytes(mcap); }
+
+__device__ __forceinline__ uint32_t to_tf32(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return r;
+}
+__device__ __forceinline__ void split_tf32(float v, uint32_t& hi, uint32_t& lo) {
+  hi = to_tf32(v);
+  lo = to_tf32(v - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+// Four consecutive elements p[l .. l+3] (zero beyond n; 128-bit load when
+// the row slice is 16-byte aligned, i.e. n % 4 == 0).
+__device__ __forceinline__ float4 ld_row4(const float* __restrict__ p, int l, int n, bool vec) {
+  if (vec) return l < n ? __ldg(reinterpret_cast<const float4*>(p + l)) : make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 v;
+  v.x = l < n ? __ldg(p + l) : 0.f;
+  v.y = l + 1 < n ? __ldg(p + l + 1) : 0.f;
+  v.z = l + 2 < n ? __ldg(p + l + 2) : 0.f;
+  v.w = l + 3 < n ? __ldg(p + l + 3) : 0.f;
+  return v;
+}
+
+template <int kUnused = 0>
+__global__ void __launch_bounds__(256, 2)
+contract_tc_kernel(int Wc, int n, int n_up, int K, int mcap, int dd, int D, const int32_t* __restrict__ idx,
+                   const int32_t* __restrict__ cnt, const int32_t* __restrict__ rev,
+                   const int64_t* __restrict__ blk_off, const float* __restrict__ O, const float* __restrict__ Fenv,
+                   const float* __restrict__ AT, float* __restrict__ gdet, float* __restrict__ ldet,
+                   DevStatus* st) {
+  extern __shared__ __align__(16) unsigned char cm_smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  const int ngrp = (n + kCtWarps - 1) / kCtWarps;
+  const int w = blockIdx.x / ngrp;
+  const int np = (blockIdx.x % ngrp) * kCtWarps + warp;
+  if (np >= n) return;   // warps are independent: no CTA barrier below
+  const size_t msb = ((size_t)mcap * (mcap + 1) * 4 + 15) & ~(size_t)15;
+  unsigned char* wb = cm_smem + (size_t)warp * contract_tc_warp_bytes(mcap);
+  float* Ms = reinterpret_cast<float*>(wb);
+  const int SM = mcap + 1;
+  int64_t* ro = reinterpret_cast<int64_t*>(wb + msb);   // O element offset of (member k, x = 0), -1: none
+  int64_t* fo = ro + mcap;                              // Fenv element offset of member k's value row
+  int* mi = reinterpret_cast<int*>(fo + mcap);          // member k's electron index
+  const int64_t Dn = (int64_t)D * n;
+  const int64_t base = (int64_t)w * n + np;
+  int m = 1 + cnt[base * 2] + cnt[base * 2 + 1];
+  if (m > mcap) m = mcap;
+  for (int k = lane; k < m; k += 32) {
+    int i = np, slot = 0;
+    if (k > 0) {
+      i = idx[base * K + k - 1];
+      const int rv = rev[base * K + k - 1];
+      slot = rv < 0 ? -1 : rv + 1;
+      if (rv < 0) atomicExch(&st->overflow, 1);
+    }
+    const int64_t b = block_index(w, i, Wc, n, n_up);
+    mi[k] = i;
+    ro[k] = slot < 0 ? -1 : (blk_off[b] + 2 + 3 * (int64_t)slot) * n;
+    fo[k] = b * 5 * Dn + (int64_t)dd * n;
+  }
+  __syncwarp();
+  const float* Aw = AT + ((int64_t)w * D + dd) * n * n;
+  const int bnp = block_index(w, np, Wc, n, n_up);
+  const int64_t onp = blk_off[bnp] * n;
+  const bool vec = (n & 3) == 0;
+
+  // sum_l LapPhi_{n' l} A_{l n'}: the Laplacian row of n' against A's column n'
+  float lt = 0.f;
+  {
+    const int64_t fb = (int64_t)bnp * 5 * Dn + (int64_t)dd * n;
+    for (int l = lane; l < n; l += 32) {
+      const float ov = O[onp + l], olp = O[onp + n + l];
+      float cross = 0.f;
+      for (int x = 0; x < 3; ++x) cross += O[onp + (2 + x) * (int64_t)n + l] * Fenv[fb + (2 + x) * Dn + l];
+      const float lap = olp * Fenv[fb + l] + 2.f * cross + ov * Fenv[fb + Dn + l];
+      lt += lap * Aw[(int64_t)np * n + l];
+    }
+  }
+
+  float gx3[3] = {0.f, 0.f, 0.f};
+  float tr = 0.f;
+  for (int x = 0; x < 3; ++x) {
+    for (int r0 = 0; r0 < m; r0 += 32) {
+      // this lane's four rows: tile 0 rows r0+g, r0+g+8; tile 1 rows r0+16+g, r0+24+g
+      int64_t oo[4], ff[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int r = r0 + 8 * q + g;
+        oo[q] = (r < m && ro[r] >= 0) ? ro[r] + (int64_t)x * n : -1;
+        ff[q] = r < m ? fo[r] : -1;
+      }
+      // n' itself (row 0): its envelope moves too
+      const bool self = (r0 == 0 && g == 0);
+      const int64_t gfo = fo[0] + (2 + x) * Dn;
+      const int nrt = (m - r0) > 16 ? 2 : 1;
+      for (int c0 = 0; c0 < m; c0 += 32) {
+        int64_t ao[4];
+#pragma unroll
+        for (int ct = 0; ct < 4; ++ct) {
+          const int c = c0 + 8 * ct + g;
+          ao[ct] = c < m ? (int64_t)mi[c] * n : -1;
+        }
+        const int nct = min(4, (m - c0 + 7) / 8);
+        float acc[2][4][4];
+#pragma unroll
+        for (int rt = 0; rt < 2; ++rt)
+#pragma unroll
+          for (int ct = 0; ct < 4; ++ct)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[rt][ct][e] = 0.f;
+        for (int l0 = 0; l0 < n; l0 += 16) {
+          const int l = l0 + 4 * t;
+          uint32_t bh[4][4], bl[4][4];
+#pragma unroll
+          for (int ct = 0; ct < 4; ++ct) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (ct < nct && ao[ct] >= 0) v = ld_row4(Aw + ao[ct], l, n, vec);
+            split_tf32(v.x, bh[ct][0], bl[ct][0]);
+            split_tf32(v.y, bh[ct][1], bl[ct][1]);
+            split_tf32(v.z, bh[ct][2], bl[ct][2]);
+            split_tf32(v.w, bh[ct][3], bl[ct][3]);
+          }
+#pragma unroll
+          for (int rt = 0; rt < 2; ++rt) {
+            if (rt < nrt) {
+              float tv[2][4];
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const int q = 2 * rt + h;
+                float4 o4 = make_float4(0.f, 0.f, 0.f, 0.f), f4 = o4;
+                if (oo[q] >= 0) o4 = ld_row4(O + oo[q], l, n, vec);
+                if (ff[q] >= 0) f4 = ld_row4(Fenv + ff[q], l, n, vec);
+                tv[h][0] = o4.x * f4.x;
+                tv[h][1] = o4.y * f4.y;
+                tv[h][2] = o4.z * f4.z;
+                tv[h][3] = o4.w * f4.w;
+              }
+              if (rt == 0 && self) {
+                const float4 o4 = ld_row4(O + onp, l, n, vec), f4 = ld_row4(Fenv + gfo, l, n, vec);
+                tv[0][0] += o4.x * f4.x;
+                tv[0][1] += o4.y * f4.y;
+                tv[0][2] += o4.z * f4.z;
+                tv[0][3] += o4.w * f4.w;
+              }
+              uint32_t ah[2][4], al[2][4];
+#pragma unroll
+              for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) split_tf32(tv[h][e], ah[h][e], al[h][e]);
+#pragma unroll
+              for (int j = 0; j < 2; ++j) {
+#pragma unroll
+                for (int ct = 0; ct < 4; ++ct) {
+                  if (ct < nct) {
+                    mma_tf32(acc[rt][ct], al[0][2 * j], al[1][2 * j], al[0][2 * j + 1], al[1][2 * j + 1],
+                             bh[ct][2 * j], bh[ct][2 * j + 1]);
+                    mma_tf32(acc[rt][ct], ah[0][2 * j], ah[1][2 * j], ah[0][2 * j + 1], ah[1][2 * j + 1],
+                             bl[ct][2 * j], bl[ct][2 * j + 1]);
+                    mma_tf32(acc[rt][ct], ah[0][2 * j], ah[1][2 * j], ah[0][2 * j + 1], ah[1][2 * j + 1],
+                             bh[ct][2 * j], bh[ct][2 * j + 1]);
+                  }
+                }
+              }
+            }
+          }
+        }
+        // accumulator (rt, ct): rows r0 + 16 rt + g (+8), columns c0 + 8 ct + 2t (+1)
+#pragma unroll
+        for (int rt = 0; rt < 2; ++rt)
+#pragma unroll
+          for (int ct = 0; ct < 4; ++ct)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int r = r0 + 16 * rt + g + 8 * (e >> 1), c = c0 + 8 * ct + 2 * t + (e & 1);
+              if (r < m && c < m) Ms[r * SM + c] = acc[rt][ct][e];
+            }
+      }
+    }
+    __syncwarp();
+    float gs = 0.f, ts = 0.f;
+    for (int k = lane; k < m; k += 32) gs += Ms[k * SM + k];
+    for (int e = lane; e < m * m; e += 32) {
+      const int k = e / m, kp = e - k * m;
+      ts += Ms[k * SM + kp] * Ms[kp * SM + k];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      gs += __shfl_xor_sync(0xffffffffu, gs, o);
+      ts += __shfl_xor_sync(0xffffffffu, ts, o);
+    }
+    gx3[x] = gs;
+    tr += ts;
+    __syncwarp();
+  }
+  for (int o = 16; o > 0; o >>= 1) lt += __shfl_xor_sync(0xffffffffu, lt, o);
+  if (lane == 0) {
+    float* gp = gdet + (((int64_t)w * D + dd) * n + np) * 3;
+    gp[0] = gx3[0];
+    gp[1] = gx3[1];
+    gp[2] = gx3[2];
+    ldet[((int64_t)w * D + dd) * n + np] = lt - tr;
+  }
+}
+
 }  // namespace fire

@@ -194,7 +194,8 @@ __device__ __forceinline__ T block_sum(T v, T* red) {
 // One CTA per electron, blockDim == d.
 template <typename T, typename W>
 __global__ void ln_fl_kernel(int d, const T* __restrict__ X, T* __restrict__ Y, const W* gamma,
-                             const W* beta, int R5) {
+                             const W* beta, int R5, __nv_bfloat16* __restrict__ Yb = nullptr, int ync = 0,
+                             int64_t ycs = 0) {
   __shared__ T red[32];
   const int64_t row = (int64_t)blockIdx.x * R5;
   const int c = threadIdx.x;
@@ -230,30 +231,39 @@ __global__ void ln_fl_kernel(int d, const T* __restrict__ X, T* __restrict__ Y, 
   }
   const T sl = varl / (T(2) * s) - vt2 / (T(4) * s * s * s);
   const T g = T(gamma[c]);
-  Y[row * d + c] = g * (cc.v / s) + T(beta[c]);
+  auto put = [&](int64_t q, T v) {
+    Y[q * d + c] = v;
+    if (Yb) store_split_bf16(Yb + q * d + c, ycs, ync, (float)v);
+  };
+  put(row, g * (cc.v / s) + T(beta[c]));
   if (R5 > 1) {
     T cross = T(0);
 #pragma unroll
     for (int t = 0; t < 3; ++t) {
       cross += cc.t[t] * st[t];
-      Y[(row + 2 + t) * d + c] = g * (cc.t[t] / s - cc.v * st[t] / (s * s));
+      put(row + 2 + t, g * (cc.t[t] / s - cc.v * st[t] / (s * s)));
     }
     T yl = cc.l / s - T(2) * cross / (s * s) - cc.v * sl / (s * s) + T(2) * cc.v * st2 / (s * s * s);
-    Y[(row + 1) * d + c] = g * yl;
+    put(row + 1, g * yl);
   }
 }
 
 // GLU gate p = SiLU(z_g) * z_v in forward-Laplacian form; Z is [rows][2d]
 // (gate columns first), P [rows][d].  One CTA per electron, blockDim == d.
 template <typename T>
-__global__ void glu_gate_kernel(int d, const T* __restrict__ Z, T* __restrict__ P, int R5) {
+__global__ void glu_gate_kernel(int d, const T* __restrict__ Z, T* __restrict__ P, int R5,
+                                __nv_bfloat16* __restrict__ Pb = nullptr, int pnc = 0, int64_t pcs = 0) {
   const int64_t row = (int64_t)blockIdx.x * R5;
   const int c = threadIdx.x;
   const int64_t ld = 2 * d;
+  auto put = [&](int64_t q, T v) {
+    P[q * d + c] = v;
+    if (Pb) store_split_bf16(Pb + q * d + c, pcs, pnc, (float)v);
+  };
   T zg = Z[row * ld + c], zv = Z[row * ld + d + c];
   T f, f1, f2;
   silu3<T>(zg, f, f1, f2);
-  P[row * d + c] = f * zv;
+  put(row, f * zv);
   if (R5 > 1) {
     T gl = Z[(row + 1) * ld + c], vl = Z[(row + 1) * ld + d + c];
     T sq = T(0), cross = T(0);
@@ -262,10 +272,22 @@ __global__ void glu_gate_kernel(int d, const T* __restrict__ Z, T* __restrict__ 
       T gt = Z[(row + 2 + t) * ld + c], vt = Z[(row + 2 + t) * ld + d + c];
       sq += gt * gt;
       cross += f1 * gt * vt;
-      P[(row + 2 + t) * d + c] = f1 * gt * zv + f * vt;
+      put(row + 2 + t, f1 * gt * zv + f * vt);
     }
-    P[(row + 1) * d + c] = (f1 * gl + f2 * sq) * zv + T(2) * cross + f * vl;
+    put(row + 1, (f1 * gl + f2 * sq) * zv + T(2) * cross + f * vl);
   }
+}
+
+// Xb = nc bf16 components of the float rows X[0 .. rows) x [0 .. ncol)
+// (row strides ldx and ldb, components cs elements apart).
+template <typename T>
+__global__ void split_rows_kernel(int64_t rows, int ncol, const T* __restrict__ X, int64_t ldx,
+                                  __nv_bfloat16* __restrict__ Xb, int64_t ldb, int nc, int64_t cs) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= rows * ncol) return;
+  const int64_t r = e / ncol;
+  const int c = (int)(e - r * ncol);
+  store_split_bf16(Xb + r * ldb + c, cs, nc, (float)X[r * ldx + c]);
 }
 
 // Message passing step.  One CTA per electron (w, i), blockDim == d.
@@ -432,7 +454,26 @@ __global__ void fl_act_kernel(int ncol, const int64_t* __restrict__ off, int64_t
       Y[q * ldy + c] = o;
       if (Yb) store_split_bf16(Yb + q * ldy + c, ycs, ync, (float)o);
     };
-    for (int64_t q = r0 + 2; q < r1; ++q) {
+    // tangent rows, eight at a time: the loads of a group are issued before
+    // its stores
+    int64_t q = r0 + 2;
+    for (; q + 8 <= r1; q += 8) {
+      T zt[8], yo[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) zt[u] = Z[(q + u) * ldz + c];
+      if (residual) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) yo[u] = Y[(q + u) * ldy + c];
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        sq += zt[u] * zt[u];
+        const T o = residual ? yo[u] + f1 * zt[u] : f1 * zt[u];
+        Y[(q + u) * ldy + c] = o;
+        if (Yb) store_split_bf16(Yb + (q + u) * ldy + c, ycs, ync, (float)o);
+      }
+    }
+    for (; q < r1; ++q) {
       T zt = Z[q * ldz + c];
       sq += zt * zt;
       put(q, f1 * zt);
@@ -462,11 +503,16 @@ __global__ void rowdot_kernel(const T* __restrict__ Y, int64_t ldy, int ncol, co
 // (block order).
 template <typename T>
 __global__ void gather_value_rows_kernel(int nb, int d, const int64_t* __restrict__ off,
-                                         const T* __restrict__ X, T* __restrict__ Hv, int64_t ldx = -1) {
+                                         const T* __restrict__ X, T* __restrict__ Hv, int64_t ldx = -1,
+                                         __nv_bfloat16* __restrict__ Hb = nullptr, int hnc = 0, int64_t hcs = 0) {
   const int b = blockIdx.x;
   const int64_t r0 = off[b];
   const int64_t ld = ldx < 0 ? d : ldx;
-  for (int c = threadIdx.x; c < d; c += blockDim.x) Hv[(int64_t)b * d + c] = X[r0 * ld + c];
+  for (int c = threadIdx.x; c < d; c += blockDim.x) {
+    const T v = X[r0 * ld + c];
+    Hv[(int64_t)b * d + c] = v;
+    if (Hb) store_split_bf16(Hb + (int64_t)b * d + c, hcs, hnc, (float)v);
+  }
 }
 
 // Writes dense rows back into the value row of every block: Z[off[b]] = Zv[b].

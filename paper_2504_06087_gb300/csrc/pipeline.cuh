@@ -117,7 +117,8 @@ struct Runner {
     p = make_params<T>(a.theta, a.poff);
     dbg = getenv("FIRE_DEBUG_SYNC") != nullptr;
     // FIRE_TC_MASK (diagnostic): bit 0 embedding MLP, 1 Jastrow MLPs,
-    // 2 attention, 3 orbitals, 4 envelopes -- which products may use the
+    // 2 attention, 3 orbitals, 4 envelopes, 5 h^0 products (GLU, message
+    // projections) and orbital value rows -- which products may use the
     // tensor cores.
     if (const char* m = getenv("FIRE_TC_MASK")) tc_mask = atoi(m);
     if (const char* m = getenv("FIRE_TC_FIX_VALUES")) fix_values = atoi(m);
@@ -135,6 +136,7 @@ struct Runner {
     nc_att = split_env("FIRE_TC_SPLIT_ATT", nc_att);
     nc_orb = split_env("FIRE_TC_SPLIT_ORB", nc_orb);
     nc_env = split_env("FIRE_TC_SPLIT_ENV", nc_env);
+    nc_h0 = split_env("FIRE_TC_SPLIT_H0", nc_h0);
     ncw = nc_mlp > nc_jas ? nc_mlp : nc_jas;
     if (nc_att > ncw) ncw = nc_att;
     if (nc_orb > ncw) ncw = nc_orb;
@@ -208,7 +210,7 @@ struct Runner {
   // stride lda, a_rows rows allocated) and packed bf16 weights Bt [N][K] it
   // runs on the tensor cores (BF16_FP64 form); otherwise SIMT in T.
   int tc_rc = FIRE_OK;
-  int tc_mask = 0x1F;
+  int tc_mask = 0x3F;
   int fix_values = 1;         // value rows recomputed in fp32 after a tensor-core product
   // split-bf16 components of each tensor-core product (1: 1 product, 2: 3, 3: 6).
   // Two components (hi + lo, three products) for the products whose value
@@ -220,6 +222,7 @@ struct Runner {
   int nc_mlp = 2, nc_jas = 2, nc_att = 3, nc_orb = 2;
   int ncw = 3;                // components written for the bf16 copies of X and Y
   int nc_env = 3;             // envelope product: its value rows enter Phi directly
+  int nc_h0 = 3;              // h^0 products and orbital value rows (no fp32 recompute)
   bool use_gj = true;
   // A^T from the LU factors, matrices in batches of the grid limit
   void inverse_from_lu(int n, int64_t nmat, const LT* LUb, const int32_t* piv, T* Ainv) {
@@ -621,6 +624,25 @@ struct Runner {
             tc::pack_bf16(s, reinterpret_cast<const float*>(p.env_pi) + sp * Dn * NE, NE, (int)NE, (int)Dn, 0,
                           dst(pl.wb_env + S * sp * Dn * NEp), S, Dn * NEp, (int)NEp);
         }
+        {
+          // h^0 products: [W_g | W_v] (N = 2d), W_o, and the four message
+          // projections [W^par_a | W^anti_a | W^par_b | W^anti_b] (N = 4d)
+          tc::pack_bf16(s, reinterpret_cast<const float*>(p.glu_wg), d, (int)d, (int)d, 1, dst(pl.wb_glu), S, 2 * d * d);
+          tc::pack_bf16(s, reinterpret_cast<const float*>(p.glu_wv), d, (int)d, (int)d, 1, dst(pl.wb_glu + d * d), S,
+                        2 * d * d);
+          tc::pack_bf16(s, reinterpret_cast<const float*>(p.glu_wo), d, (int)d, (int)d, 1, dst(pl.wb_gluo), S, d * d);
+          np += 3;
+          for (int part = 0; part < 2; ++part)
+            for (int a = 0; a < 2; ++a, ++np)
+              tc::pack_bf16(s, reinterpret_cast<const float*>(p.msg_w) + a * (2 * d + 4) * d + part * d * d, d, (int)d,
+                            (int)d, 1, dst(pl.wb_msg + (part * 2 + a) * d * d), S, 4 * d * d);
+          // orbital value rows: all determinants of one spin in one product (N = D n)
+          const int64_t Dn = D * n;
+          for (int sp = 0; sp < 2; ++sp)
+            for (int dd = 0; dd < D; ++dd, ++np)
+              tc::pack_bf16(s, reinterpret_cast<const float*>(p.orb_w) + (sp * D + dd) * d * n, n, (int)d, (int)n, 1,
+                            dst(pl.wb_orbv + S * sp * Dn * d + dd * n * d), S, Dn * d);
+        }
         for (int sp = 0; sp < 2; ++sp)
           for (int dd = 0; dd < D; ++dd, ++np)
             tc::pack_bf16(s, reinterpret_cast<const float*>(p.orb_w) + (sp * D + dd) * d * n, n, (int)d, (int)n, 1,
@@ -670,18 +692,45 @@ struct Runner {
       const int64_t r5 = (int64_t)nb * R5;
       mark("en_filter", 1);
       en_filter_kernel<T, T><<<nb, d, 0, s>>>(wc, n, n_up, N, d, r, sys->nuc_pos, sys->cutoff_nuc, p, S5, R5);
+      // BF16 form: the h^0 products on the tensor cores (nc_h0 components)
+      const __nv_bfloat16* WBh = (pl.wbf16 && (tc_mask & 32) && d % 64 == 0) ? at<__nv_bfloat16>(pl.wbf16) : nullptr;
+      const int64_t r5cap = (int64_t)pl.Wc * n * R5;
+      __nv_bfloat16* Y5b = WBh ? at<__nv_bfloat16>(pl.Y5b) : nullptr;
+      __nv_bfloat16* P5b = WBh ? at<__nv_bfloat16>(pl.P5b) : nullptr;
+      __nv_bfloat16* H0b = WBh ? at<__nv_bfloat16>(pl.H0b) : nullptr;
+      auto tc_rows = [&](const __nv_bfloat16* Ab, int64_t a_rows, int64_t woff, int Nn, T* C, int64_t ldc,
+                         int64_t rb, int64_t re) -> bool {
+        if constexpr (sizeof(T) == 4) {
+          if (!WBh) return false;
+          const int rc = tc::gemm_bf16(s, Ab, d, a_rows, WBh + woff, Nn, d, reinterpret_cast<float*>(C), ldc, rb, re,
+                                       nullptr, re - rb, &st->tc_err, nc_h0);
+          if (rc == FIRE_OK) return true;
+          tc_rc = rc;
+        }
+        return false;
+      };
       mark("glu", 5);
-      ln_fl_kernel<T, T><<<nb, d, 0, s>>>(d, S5, Y5, p.ln_gamma, p.ln_beta, R5);
-      gemm<T>(s, Y5, d, p.glu_wg, d, false, Z5, 2 * d, 0, r5, nullptr, r5, d, d);
-      gemm<T>(s, Y5, d, p.glu_wv, d, false, Z5 + d, 2 * d, 0, r5, nullptr, r5, d, d);
-      glu_gate_kernel<T><<<nb, d, 0, s>>>(d, Z5, P5, R5);
+      ln_fl_kernel<T, T><<<nb, d, 0, s>>>(d, S5, Y5, p.ln_gamma, p.ln_beta, R5, Y5b, nc_h0, r5cap * d);
+      if (!tc_rows(Y5b, r5cap, pl.wb_glu, 2 * d, Z5, 2 * d, 0, r5)) {
+        gemm<T>(s, Y5, d, p.glu_wg, d, false, Z5, 2 * d, 0, r5, nullptr, r5, d, d);
+        gemm<T>(s, Y5, d, p.glu_wv, d, false, Z5 + d, 2 * d, 0, r5, nullptr, r5, d, d);
+      }
+      glu_gate_kernel<T><<<nb, d, 0, s>>>(d, Z5, P5, R5, P5b, nc_h0, r5cap * d);
       check("h0");
-      gemm<T>(s, P5, d, p.glu_wo, d, false, H0, d, 0, r5, nullptr, r5, d, d);
+      if (!tc_rows(P5b, r5cap, pl.wb_gluo, d, H0, d, 0, r5))
+        gemm<T>(s, P5, d, p.glu_wo, d, false, H0, d, 0, r5, nullptr, r5, d, d);
       // 3. h^0 W^alpha_a, h^0 W^alpha_b for both spin channels
       mark("msg_proj_gemm", 2);
-      for (int part = 0; part < 2; ++part)
-        gemm<T>(s, H0, d, p.msg_w + (int64_t)part * d * d, d, false, PQ + (int64_t)part * 2 * d, 4 * d, 0, r5,
-                nullptr, r5, d, d, 2, 0, (int64_t)(2 * d + 4) * d, d);
+      bool pq_tc = false;
+      if (H0b) {
+        split_rows_kernel<T><<<(unsigned)((r5 * d + 255) / 256), 256, 0, s>>>(r5, d, H0, d, H0b, d, nc_h0, r5cap * d);
+        launches += 1;
+        pq_tc = tc_rows(H0b, r5cap, pl.wb_msg, 4 * d, PQ, 4 * d, 0, r5);
+      }
+      if (!pq_tc)
+        for (int part = 0; part < 2; ++part)
+          gemm<T>(s, H0, d, p.msg_w + (int64_t)part * d * d, d, false, PQ + (int64_t)part * 2 * d, 4 * d, 0, r5,
+                  nullptr, r5, d, d, 2, 0, (int64_t)(2 * d + 4) * d, d);
       // 4. message passing -> h^1 blocks
       T* X = at<T>(pl.X);
       T* Y = at<T>(pl.Y);
@@ -724,7 +773,6 @@ struct Runner {
       // BF16 form: the features also as bf16 components (K padded to a
       // multiple of 64) for the tensor-core product with the packed pi
       const int NEp = ((NE + 63) / 64) * 64;
-      const int64_t r5cap = (int64_t)pl.Wc * n * R5;
       __nv_bfloat16* Qfb = (pl.Qfb && WB && (tc_mask & 16)) ? at<__nv_bfloat16>(pl.Qfb) : nullptr;
       env_feat_kernel<T, T><<<nb, 128, 0, s>>>(wc, n, n_up, N, E, r, sys->nuc_pos, p.env_sigma, Qf, R5, Qfb, NEp,
                                                nc_env, r5cap * NEp);
@@ -747,13 +795,17 @@ struct Runner {
       T* Hv = at<T>(pl.Hv);
       T* Ov = at<T>(pl.Ov);
       mark("orb_values", 4);
-      gather_value_rows_kernel<T><<<nb, 256, 0, s>>>(nb, d, boff, X, Hv);
+      __nv_bfloat16* Hvb = WBh ? at<__nv_bfloat16>(pl.Hvb) : nullptr;
+      const int64_t nbcap = (int64_t)pl.Wc * n;
+      gather_value_rows_kernel<T><<<nb, 256, 0, s>>>(nb, d, boff, X, Hv, -1, Hvb, nc_h0, nbcap * d);
       const int64_t upv = (int64_t)wc * n_up;
       for (int sp = 0; sp < 2; ++sp) {
         const int64_t rb = sp ? upv : 0, re = sp ? nb : upv;
-        if (re > rb)
-          gemm<T>(s, Hv, d, p.orb_w + (int64_t)sp * D * d * n, n, false, Ov, Dn, rb, re, nullptr, re - rb, n, d,
-                  D, 0, (int64_t)d * n, n);
+        if (re <= rb) continue;
+        if (Hvb && tc_rows(Hvb, nbcap, pl.wb_orbv + (int64_t)kMaxSplit * sp * Dn * d, (int)Dn, Ov, Dn, rb, re))
+          continue;
+        gemm<T>(s, Hv, d, p.orb_w + (int64_t)sp * D * d * n, n, false, Ov, Dn, rb, re, nullptr, re - rb, n, d,
+                D, 0, (int64_t)d * n, n);
       }
       LT* LUb = at<LT>(pl.LU);
       int32_t* piv = at<int32_t>(pl.piv);
@@ -880,6 +932,11 @@ struct Runner {
         const int maxt = contract_maxt(mcap);
         if (maxt == 0) { set_last_error("contract", "neighbourhood larger than 96 members"); return FIRE_ERR_UNSUPPORTED; }
         const size_t ctsm = contract_smem_bytes(mcap, sizeof(T));
+        // float forms: the tensor-core contraction (TF32, three passes) for
+        // neighbourhoods of up to 64 members; FIRE_CONTRACT=simt keeps the
+        // SIMT kernel (diagnostic)
+        const char* cenv = getenv("FIRE_CONTRACT");
+        const bool tc_contract = sizeof(T) == 4 && mcap <= kCtMaxMembers && !(cenv && strcmp(cenv, "simt") == 0);
         for (int dd = 0; dd < D; ++dd) {
           mark("orb_gemm", 2);
           for (int sp = 0; sp < 2; ++sp)
@@ -887,6 +944,17 @@ struct Runner {
                      wbm(3, pl.wb_orb + kMaxSplit * ((int64_t)sp * D + dd) * n * d), n, O, n, rng + 2 * sp, 0, 0,
                      cap, n, d, nc_orb);
           mark("contract", 1);
+          if constexpr (sizeof(T) == 4) {
+            if (tc_contract) {
+              const int ngrp = (n + kCtWarps - 1) / kCtWarps;
+              contract_tc_kernel<0><<<(unsigned)(wc * ngrp), 32 * kCtWarps, contract_tc_smem_bytes(mcap), s>>>(
+                  wc, n, n_up, K, mcap, dd, D, idx, cnt, rev, boff, reinterpret_cast<const float*>(O),
+                  reinterpret_cast<const float*>(Fenv), reinterpret_cast<const float*>(Ainv),
+                  reinterpret_cast<float*>(gdet), reinterpret_cast<float*>(ldet), st);
+              check("contract");
+              continue;
+            }
+          }
           auto ck = contract_kernel<T, 1>;
           if (maxt == 2) ck = contract_kernel<T, 2>;
           else if (maxt == 3) ck = contract_kernel<T, 3>;
@@ -1171,6 +1239,7 @@ inline int set_smem_limits() {
   raise((const void*)contract_kernel<T, 3>);
   raise((const void*)contract_kernel<T, 5>);
   raise((const void*)contract_kernel<T, 9>);
+  raise((const void*)contract_tc_kernel<0>);
   raise((const void*)lu_inverse_kernel<LT, T>);
   raise((const void*)lu_kernel<LT, 16>);
   raise((const void*)att_pool_kernel<T>);
