@@ -627,49 +627,6 @@ contract_kernel(int Wc, int n, int n_up, int K, int mcap, int dd, int D, const i
   }
 }
 
-// ---------------------------------------------------------------------------
-// The same contraction on the tensor cores (mma.sync m16n8k8, TF32 operands,
-// FP32 accumulation).  Each operand v is split into v_hi = tf32(v) and
-// v_lo = tf32(v - v_hi) and every product takes the three passes
-// lo*hi + hi*lo + hi*hi, which keeps the float32 accuracy of the SIMT form.
-//
-// One warp per tangent electron n' (8 per CTA, no CTA barriers).  For each
-// coordinate x the warp forms M_x[k][k'] = sum_l T_x[k][l] A[l][i_k'] over
-// the m members of Nbar_n' in 32 x 32 blocks (2 x 4 tiles of 16 x 8), with
-// T_x[k][l] = O[row(i_k, slot of n', x)][l] * phi[i_k][l] (+ the envelope
-// derivative term of n' itself, k = 0) built in registers straight from the
-// gathered rows.  Within a 16-wide step of l, lane (g, t) holds l0 + 4t ..
-// l0 + 4t + 3 of its rows of T and of its columns of A: the first k8 step
-// takes the pairs (4t, 4t+1), the second (4t+2, 4t+3) -- one consistent
-// permutation of l for both operands, so every load is a 128-bit row slice.
-// M_x goes to a per-warp shared-memory block, from which
-//   d log det / d r_n'x = sum_k M_x[k][k],  trace_x = sum_{k,k'} M_x[k][k'] M_x[k'][k].
-// Neighbourhoods of up to 64 members.
-constexpr int kCtWarps = 8;
-constexpr int kCtMaxMembers = 64;
-__host__ __device__ inline size_t contract_tc_warp_bytes(int mcap) {
-  const size_t msb = ((size_t)mcap * (mcap + 1) * 4 + 15) & ~(size_t)15;
-  return (msb + (size_t)mcap * 20 + 15) & ~(size_t)15;
-}
-inline size_t contract_tc_smem_bytes(int mcap) { return kCtWarps * contract_tc_warp_bytes(mcap); }
-
-__device__ __forceinline__ uint32_t to_tf32(float v) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
-  return r;
-}
-__device__ __forceinline__ void split_tf32(float v, uint32_t& hi, uint32_t& lo) {
-  hi = to_tf32(v);
-  lo = to_tf32(v - __uint_as_float(hi));
-}
-__device__ __forceinline__ void mma_tf32(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                         uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-      "{%0, %1, %2, %3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
 // Four consecutive elements p[l .. l+3] (zero beyond n; 128-bit load when
 // the row slice is 16-byte aligned, i.e. n % 4 == 0).
 __device__ __forceinline__ float4 ld_row4(const float* __restrict__ p, int l, int n, bool vec) {
@@ -682,32 +639,58 @@ __device__ __forceinline__ float4 ld_row4(const float* __restrict__ p, int l, in
   return v;
 }
 
-template <int kUnused = 0>
-__global__ void __launch_bounds__(256, 2)
-contract_tc_kernel(int Wc, int n, int n_up, int K, int mcap, int dd, int D, const int32_t* __restrict__ idx,
-                   const int32_t* __restrict__ cnt, const int32_t* __restrict__ rev,
-                   const int64_t* __restrict__ blk_off, const float* __restrict__ O, const float* __restrict__ Fenv,
-                   const float* __restrict__ AT, float* __restrict__ gdet, float* __restrict__ ldet,
-                   DevStatus* st) {
-  extern __shared__ __align__(16) unsigned char cm_smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int g = lane >> 2, t = lane & 3;
-  const int ngrp = (n + kCtWarps - 1) / kCtWarps;
-  const int w = blockIdx.x / ngrp;
-  const int np = (blockIdx.x % ngrp) * kCtWarps + warp;
-  if (np >= n) return;   // warps are independent: no CTA barrier below
-  const size_t msb = ((size_t)mcap * (mcap + 1) * 4 + 15) & ~(size_t)15;
-  unsigned char* wb = cm_smem + (size_t)warp * contract_tc_warp_bytes(mcap);
-  float* Ms = reinterpret_cast<float*>(wb);
-  const int SM = mcap + 1;
-  int64_t* ro = reinterpret_cast<int64_t*>(wb + msb);   // O element offset of (member k, x = 0), -1: none
-  int64_t* fo = ro + mcap;                              // Fenv element offset of member k's value row
-  int* mi = reinterpret_cast<int*>(fo + mcap);          // member k's electron index
-  const int64_t Dn = (int64_t)D * n;
+// ---------------------------------------------------------------------------
+// The same contraction with small CTAs and larger register tiles.  One CTA of
+// NT threads per (walker, tangent electron n'); thread tile = 3 members x 3
+// coordinates (9 rows of T) x 4 member columns of A, so every orbital l costs
+// four 128-bit shared loads for 36 FMAs.  Orbitals go in chunks of 32: each
+// staging item (member k, 4 orbitals) reads 128-bit slices of k's three O
+// rows, its envelope row and its row of A^T and writes the T quads
+// (x = 0, 1, 2, pad) member-contiguous, so neither the gathers nor the shared
+// stores conflict.  Neighbourhood sizes are bucketed: a CTA whose member
+// count m lies outside [mlo, mhi] exits at once, so one launch per bucket
+// sizes its tiles and shared memory for that bucket only.
+//   MP = member slots of the bucket (multiple of 12, >= mhi)
+//   Ts [32][4 MP + 4]  T quads     As [32][MP + 4]  A values
+//   (M [3 m][m] reuses the area after the last chunk)
+constexpr int kC2Chunk = 32;
+constexpr int kC2SmallMax = 36;   // members of the 64-thread bucket
+constexpr int kC2BigMax = 60;     // members of the 128-thread bucket
+__host__ __device__ inline int contract2_slots(int mhi) { return 12 * ((mhi + 11) / 12); }
+__host__ __device__ inline size_t contract2_region(int mp) {
+  const size_t st = (size_t)kC2Chunk * (4 * mp + 4) + (size_t)kC2Chunk * (mp + 4);
+  const size_t mm = (size_t)3 * mp * mp;
+  return st > mm ? st : mm;
+}
+inline size_t contract2_smem_bytes(int mhi) {
+  const int mp = contract2_slots(mhi);
+  return contract2_region(mp) * 4 + (size_t)mp * 20 + 64;
+}
+
+template <int NT, int MAXT>
+__global__ void __launch_bounds__(NT, (NT == 64 ? 8 : 3))
+contract2_kernel(int Wc, int n, int n_up, int K, int mlo, int mhi, int dd, int D, const int32_t* __restrict__ idx,
+                 const int32_t* __restrict__ cnt, const int32_t* __restrict__ rev,
+                 const int64_t* __restrict__ blk_off, const float* __restrict__ O, const float* __restrict__ Fenv,
+                 const float* __restrict__ AT, float* __restrict__ gdet, float* __restrict__ ldet, DevStatus* st) {
+  constexpr int LC = kC2Chunk;
+  extern __shared__ __align__(16) unsigned char c2_smem[];
+  __shared__ float red[NT / 32][5];
+  const int tid = threadIdx.x;
+  const int w = blockIdx.x / n, np = blockIdx.x % n;
   const int64_t base = (int64_t)w * n + np;
-  int m = 1 + cnt[base * 2] + cnt[base * 2 + 1];
-  if (m > mcap) m = mcap;
-  for (int k = lane; k < m; k += 32) {
+  const int m = 1 + cnt[base * 2] + cnt[base * 2 + 1];
+  if (m < mlo || m > mhi) return;   // another bucket's launch handles this n'
+  const int MP = contract2_slots(mhi);
+  const int ST = 4 * MP + 4, SA = MP + 4;
+  float* Ts = reinterpret_cast<float*>(c2_smem);
+  float* As = Ts + LC * ST;
+  const size_t region = contract2_region(MP);
+  int64_t* ro = reinterpret_cast<int64_t*>(Ts + ((region + 3) & ~(size_t)3));   // O offset of (k, x = 0), -1: none
+  int64_t* fo = ro + MP;                                                        // Fenv offset of k's value row
+  int* mi = reinterpret_cast<int*>(fo + MP);
+  const int64_t Dn = (int64_t)D * n;
+  for (int k = tid; k < m; k += NT) {
     int i = np, slot = 0;
     if (k > 0) {
       i = idx[base * K + k - 1];
@@ -720,7 +703,7 @@ contract_tc_kernel(int Wc, int n, int n_up, int K, int mcap, int dd, int D, cons
     ro[k] = slot < 0 ? -1 : (blk_off[b] + 2 + 3 * (int64_t)slot) * n;
     fo[k] = b * 5 * Dn + (int64_t)dd * n;
   }
-  __syncwarp();
+  __syncthreads();
   const float* Aw = AT + ((int64_t)w * D + dd) * n * n;
   const int bnp = block_index(w, np, Wc, n, n_up);
   const int64_t onp = blk_off[bnp] * n;
@@ -730,7 +713,7 @@ contract_tc_kernel(int Wc, int n, int n_up, int K, int mcap, int dd, int D, cons
   float lt = 0.f;
   {
     const int64_t fb = (int64_t)bnp * 5 * Dn + (int64_t)dd * n;
-    for (int l = lane; l < n; l += 32) {
+    for (int l = tid; l < n; l += NT) {
       const float ov = O[onp + l], olp = O[onp + n + l];
       float cross = 0.f;
       for (int x = 0; x < 3; ++x) cross += O[onp + (2 + x) * (int64_t)n + l] * Fenv[fb + (2 + x) * Dn + l];
@@ -739,127 +722,126 @@ contract_tc_kernel(int Wc, int n, int n_up, int K, int mcap, int dd, int D, cons
     }
   }
 
-  float gx3[3] = {0.f, 0.f, 0.f};
-  float tr = 0.f;
-  for (int x = 0; x < 3; ++x) {
-    for (int r0 = 0; r0 < m; r0 += 32) {
-      // this lane's four rows: tile 0 rows r0+g, r0+g+8; tile 1 rows r0+16+g, r0+24+g
-      int64_t oo[4], ff[4];
+  const int nkg = (m + 2) / 3, ncg = (m + 3) / 4, ntile = nkg * ncg;
+  const int kfill = max(3 * nkg, 4 * ncg);   // member slots read by the tiles (zero beyond m)
+  float acc[MAXT][36];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int r = r0 + 8 * q + g;
-        oo[q] = (r < m && ro[r] >= 0) ? ro[r] + (int64_t)x * n : -1;
-        ff[q] = r < m ? fo[r] : -1;
+  for (int t = 0; t < MAXT; ++t)
+#pragma unroll
+    for (int q = 0; q < 36; ++q) acc[t][q] = 0.f;
+
+  for (int l0 = 0; l0 < n; l0 += LC) {
+    __syncthreads();   // the previous chunk is consumed
+    // staging items (member k, orbitals l0 + 4 q4 .. + 3), members fastest
+    for (int e = tid; e < kfill * (LC / 4); e += NT) {
+      const int k = e % kfill, q4 = e / kfill;
+      const int l = l0 + 4 * q4;
+      float4 t0 = make_float4(0.f, 0.f, 0.f, 0.f), t1 = t0, t2 = t0, av = t0;
+      if (k < m) {
+        const float4 ph = ld_row4(Fenv + fo[k], l, n, vec);
+        if (ro[k] >= 0) {
+          const float4 o0 = ld_row4(O + ro[k], l, n, vec);
+          const float4 o1 = ld_row4(O + ro[k] + n, l, n, vec);
+          const float4 o2 = ld_row4(O + ro[k] + 2 * (int64_t)n, l, n, vec);
+          t0 = make_float4(o0.x * ph.x, o0.y * ph.y, o0.z * ph.z, o0.w * ph.w);
+          t1 = make_float4(o1.x * ph.x, o1.y * ph.y, o1.z * ph.z, o1.w * ph.w);
+          t2 = make_float4(o2.x * ph.x, o2.y * ph.y, o2.z * ph.z, o2.w * ph.w);
+        }
+        if (k == 0) {   // n' itself: its envelope moves too
+          const float4 ov = ld_row4(O + onp, l, n, vec);
+          const float4 g0 = ld_row4(Fenv + fo[0] + 2 * Dn, l, n, vec);
+          const float4 g1 = ld_row4(Fenv + fo[0] + 3 * Dn, l, n, vec);
+          const float4 g2 = ld_row4(Fenv + fo[0] + 4 * Dn, l, n, vec);
+          t0.x += ov.x * g0.x; t0.y += ov.y * g0.y; t0.z += ov.z * g0.z; t0.w += ov.w * g0.w;
+          t1.x += ov.x * g1.x; t1.y += ov.y * g1.y; t1.z += ov.z * g1.z; t1.w += ov.w * g1.w;
+          t2.x += ov.x * g2.x; t2.y += ov.y * g2.y; t2.z += ov.z * g2.z; t2.w += ov.w * g2.w;
+        }
+        av = ld_row4(Aw + (int64_t)mi[k] * n, l, n, vec);
       }
-      // n' itself (row 0): its envelope moves too
-      const bool self = (r0 == 0 && g == 0);
-      const int64_t gfo = fo[0] + (2 + x) * Dn;
-      const int nrt = (m - r0) > 16 ? 2 : 1;
-      for (int c0 = 0; c0 < m; c0 += 32) {
-        int64_t ao[4];
+      float* tq = Ts + (4 * q4) * ST + 4 * k;
+      *reinterpret_cast<float4*>(tq) = make_float4(t0.x, t1.x, t2.x, 0.f);
+      *reinterpret_cast<float4*>(tq + ST) = make_float4(t0.y, t1.y, t2.y, 0.f);
+      *reinterpret_cast<float4*>(tq + 2 * ST) = make_float4(t0.z, t1.z, t2.z, 0.f);
+      *reinterpret_cast<float4*>(tq + 3 * ST) = make_float4(t0.w, t1.w, t2.w, 0.f);
+      float* aq = As + (4 * q4) * SA + k;
+      aq[0] = av.x;
+      aq[SA] = av.y;
+      aq[2 * SA] = av.z;
+      aq[3 * SA] = av.w;
+    }
+    __syncthreads();
 #pragma unroll
-        for (int ct = 0; ct < 4; ++ct) {
-          const int c = c0 + 8 * ct + g;
-          ao[ct] = c < m ? (int64_t)mi[c] * n : -1;
+    for (int t = 0; t < MAXT; ++t) {
+      const int tile = tid + t * NT;
+      if (tile < ntile) {
+        const int kg = tile / ncg, cg = tile - kg * ncg;
+        const float* tp = Ts + 12 * kg;
+        const float* ap = As + 4 * cg;
+#pragma unroll 4
+        for (int q = 0; q < LC; ++q) {
+          const float4 a0 = *reinterpret_cast<const float4*>(tp + q * ST);
+          const float4 a1 = *reinterpret_cast<const float4*>(tp + q * ST + 4);
+          const float4 a2 = *reinterpret_cast<const float4*>(tp + q * ST + 8);
+          const float4 bv = *reinterpret_cast<const float4*>(ap + q * SA);
+          const float tr9[9] = {a0.x, a0.y, a0.z, a1.x, a1.y, a1.z, a2.x, a2.y, a2.z};
+          const float bc[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+          for (int r = 0; r < 9; ++r)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[t][4 * r + j] = fmaf(tr9[r], bc[j], acc[t][4 * r + j]);
         }
-        const int nct = min(4, (m - c0 + 7) / 8);
-        float acc[2][4][4];
-#pragma unroll
-        for (int rt = 0; rt < 2; ++rt)
-#pragma unroll
-          for (int ct = 0; ct < 4; ++ct)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[rt][ct][e] = 0.f;
-        for (int l0 = 0; l0 < n; l0 += 16) {
-          const int l = l0 + 4 * t;
-          uint32_t bh[4][4], bl[4][4];
-#pragma unroll
-          for (int ct = 0; ct < 4; ++ct) {
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (ct < nct && ao[ct] >= 0) v = ld_row4(Aw + ao[ct], l, n, vec);
-            split_tf32(v.x, bh[ct][0], bl[ct][0]);
-            split_tf32(v.y, bh[ct][1], bl[ct][1]);
-            split_tf32(v.z, bh[ct][2], bl[ct][2]);
-            split_tf32(v.w, bh[ct][3], bl[ct][3]);
-          }
-#pragma unroll
-          for (int rt = 0; rt < 2; ++rt) {
-            if (rt < nrt) {
-              float tv[2][4];
-#pragma unroll
-              for (int h = 0; h < 2; ++h) {
-                const int q = 2 * rt + h;
-                float4 o4 = make_float4(0.f, 0.f, 0.f, 0.f), f4 = o4;
-                if (oo[q] >= 0) o4 = ld_row4(O + oo[q], l, n, vec);
-                if (ff[q] >= 0) f4 = ld_row4(Fenv + ff[q], l, n, vec);
-                tv[h][0] = o4.x * f4.x;
-                tv[h][1] = o4.y * f4.y;
-                tv[h][2] = o4.z * f4.z;
-                tv[h][3] = o4.w * f4.w;
-              }
-              if (rt == 0 && self) {
-                const float4 o4 = ld_row4(O + onp, l, n, vec), f4 = ld_row4(Fenv + gfo, l, n, vec);
-                tv[0][0] += o4.x * f4.x;
-                tv[0][1] += o4.y * f4.y;
-                tv[0][2] += o4.z * f4.z;
-                tv[0][3] += o4.w * f4.w;
-              }
-              uint32_t ah[2][4], al[2][4];
-#pragma unroll
-              for (int h = 0; h < 2; ++h)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) split_tf32(tv[h][e], ah[h][e], al[h][e]);
-#pragma unroll
-              for (int j = 0; j < 2; ++j) {
-#pragma unroll
-                for (int ct = 0; ct < 4; ++ct) {
-                  if (ct < nct) {
-                    mma_tf32(acc[rt][ct], al[0][2 * j], al[1][2 * j], al[0][2 * j + 1], al[1][2 * j + 1],
-                             bh[ct][2 * j], bh[ct][2 * j + 1]);
-                    mma_tf32(acc[rt][ct], ah[0][2 * j], ah[1][2 * j], ah[0][2 * j + 1], ah[1][2 * j + 1],
-                             bl[ct][2 * j], bl[ct][2 * j + 1]);
-                    mma_tf32(acc[rt][ct], ah[0][2 * j], ah[1][2 * j], ah[0][2 * j + 1], ah[1][2 * j + 1],
-                             bh[ct][2 * j], bh[ct][2 * j + 1]);
-                  }
-                }
-              }
-            }
-          }
-        }
-        // accumulator (rt, ct): rows r0 + 16 rt + g (+8), columns c0 + 8 ct + 2t (+1)
-#pragma unroll
-        for (int rt = 0; rt < 2; ++rt)
-#pragma unroll
-          for (int ct = 0; ct < 4; ++ct)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const int r = r0 + 16 * rt + g + 8 * (e >> 1), c = c0 + 8 * ct + 2 * t + (e & 1);
-              if (r < m && c < m) Ms[r * SM + c] = acc[rt][ct][e];
-            }
       }
     }
-    __syncwarp();
-    float gs = 0.f, ts = 0.f;
-    for (int k = lane; k < m; k += 32) gs += Ms[k * SM + k];
-    for (int e = lane; e < m * m; e += 32) {
-      const int k = e / m, kp = e - k * m;
-      ts += Ms[k * SM + kp] * Ms[kp * SM + k];
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      gs += __shfl_xor_sync(0xffffffffu, gs, o);
-      ts += __shfl_xor_sync(0xffffffffu, ts, o);
-    }
-    gx3[x] = gs;
-    tr += ts;
-    __syncwarp();
   }
-  for (int o = 16; o > 0; o >>= 1) lt += __shfl_xor_sync(0xffffffffu, lt, o);
-  if (lane == 0) {
+  __syncthreads();
+  // M[(k, x)][k'] into shared memory (the staging area is free now)
+  float* Ms = Ts;
+#pragma unroll
+  for (int t = 0; t < MAXT; ++t) {
+    const int tile = tid + t * NT;
+    if (tile < ntile) {
+      const int kg = tile / ncg, cg = tile - kg * ncg;
+#pragma unroll
+      for (int u = 0; u < 3; ++u)
+#pragma unroll
+        for (int x = 0; x < 3; ++x)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int k = 3 * kg + u, kp = 4 * cg + j;
+            if (k < m && kp < m) Ms[(3 * k + x) * m + kp] = acc[t][4 * (3 * u + x) + j];
+          }
+    }
+  }
+  __syncthreads();
+  float g0 = 0.f, g1 = 0.f, g2 = 0.f, tr = 0.f;
+  for (int k = tid; k < m; k += NT) {
+    g0 += Ms[(3 * k) * m + k];
+    g1 += Ms[(3 * k + 1) * m + k];
+    g2 += Ms[(3 * k + 2) * m + k];
+  }
+  for (int e = tid; e < m * m; e += NT) {
+    const int k = e / m, kp = e - k * m;
+#pragma unroll
+    for (int x = 0; x < 3; ++x) tr += Ms[(3 * k + x) * m + kp] * Ms[(3 * kp + x) * m + k];
+  }
+  float v[5] = {g0, g1, g2, tr, lt};
+#pragma unroll
+  for (int q = 0; q < 5; ++q)
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+  if ((tid & 31) == 0)
+#pragma unroll
+    for (int q = 0; q < 5; ++q) red[tid >> 5][q] = v[q];
+  __syncthreads();
+  if (tid == 0) {
+    float sum[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int g = 0; g < NT / 32; ++g)
+#pragma unroll
+      for (int q = 0; q < 5; ++q) sum[q] += red[g][q];
     float* gp = gdet + (((int64_t)w * D + dd) * n + np) * 3;
-    gp[0] = gx3[0];
-    gp[1] = gx3[1];
-    gp[2] = gx3[2];
-    ldet[((int64_t)w * D + dd) * n + np] = lt - tr;
+    gp[0] = sum[0];
+    gp[1] = sum[1];
+    gp[2] = sum[2];
+    ldet[((int64_t)w * D + dd) * n + np] = sum[4] - sum[3];
   }
 }
 

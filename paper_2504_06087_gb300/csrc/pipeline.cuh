@@ -932,11 +932,11 @@ struct Runner {
         const int maxt = contract_maxt(mcap);
         if (maxt == 0) { set_last_error("contract", "neighbourhood larger than 96 members"); return FIRE_ERR_UNSUPPORTED; }
         const size_t ctsm = contract_smem_bytes(mcap, sizeof(T));
-        // float forms: the tensor-core contraction (TF32, three passes) for
-        // neighbourhoods of up to 64 members; FIRE_CONTRACT=simt keeps the
-        // SIMT kernel (diagnostic)
+        // float forms: the bucketed small-CTA contraction for neighbourhoods
+        // of up to 60 members; FIRE_CONTRACT=v1 keeps the 256-thread kernel
+        // (diagnostic)
         const char* cenv = getenv("FIRE_CONTRACT");
-        const bool tc_contract = sizeof(T) == 4 && mcap <= kCtMaxMembers && !(cenv && strcmp(cenv, "simt") == 0);
+        const bool c2 = sizeof(T) == 4 && mcap <= kC2BigMax && !(cenv && strcmp(cenv, "v1") == 0);
         for (int dd = 0; dd < D; ++dd) {
           mark("orb_gemm", 2);
           for (int sp = 0; sp < 2; ++sp)
@@ -945,12 +945,21 @@ struct Runner {
                      cap, n, d, nc_orb);
           mark("contract", 1);
           if constexpr (sizeof(T) == 4) {
-            if (tc_contract) {
-              const int ngrp = (n + kCtWarps - 1) / kCtWarps;
-              contract_tc_kernel<0><<<(unsigned)(wc * ngrp), 32 * kCtWarps, contract_tc_smem_bytes(mcap), s>>>(
-                  wc, n, n_up, K, mcap, dd, D, idx, cnt, rev, boff, reinterpret_cast<const float*>(O),
+            if (c2) {
+              // bucket A: up to 36 members (64 threads); bucket B: the rest
+              const int ma = mcap < kC2SmallMax ? mcap : kC2SmallMax;
+              contract2_kernel<64, 2><<<nb, 64, contract2_smem_bytes(ma), s>>>(
+                  wc, n, n_up, K, 1, ma, dd, D, idx, cnt, rev, boff, reinterpret_cast<const float*>(O),
                   reinterpret_cast<const float*>(Fenv), reinterpret_cast<const float*>(Ainv),
                   reinterpret_cast<float*>(gdet), reinterpret_cast<float*>(ldet), st);
+              if (mcap > kC2SmallMax) {
+                contract2_kernel<128, 3><<<nb, 128, contract2_smem_bytes(mcap), s>>>(
+                    wc, n, n_up, K, kC2SmallMax + 1, mcap, dd, D, idx, cnt, rev, boff,
+                    reinterpret_cast<const float*>(O), reinterpret_cast<const float*>(Fenv),
+                    reinterpret_cast<const float*>(Ainv), reinterpret_cast<float*>(gdet),
+                    reinterpret_cast<float*>(ldet), st);
+                launches += 1;
+              }
               check("contract");
               continue;
             }
@@ -1239,7 +1248,8 @@ inline int set_smem_limits() {
   raise((const void*)contract_kernel<T, 3>);
   raise((const void*)contract_kernel<T, 5>);
   raise((const void*)contract_kernel<T, 9>);
-  raise((const void*)contract_tc_kernel<0>);
+  raise((const void*)contract2_kernel<64, 2>);
+  raise((const void*)contract2_kernel<128, 3>);
   raise((const void*)lu_inverse_kernel<LT, T>);
   raise((const void*)lu_kernel<LT, 16>);
   raise((const void*)att_pool_kernel<T>);
