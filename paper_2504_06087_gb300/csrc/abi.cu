@@ -313,6 +313,12 @@ void prof_add(const char* name, int launches, float ms) {
   g_prof[k].ms += ms;
 }
 
+// Calls on this host thread that must create nothing (no stream, no event):
+// the static-workspace entry point runs every kernel on the caller's stream.
+static thread_local bool g_single_stream = false;
+void set_single_stream(bool on) { g_single_stream = on; }
+bool single_stream() { return g_single_stream; }
+
 // One extra non-blocking stream per device for work that runs beside the
 // caller's stream inside a call (created on first use, kept until exit).
 cudaStream_t side_stream() {

@@ -17,6 +17,7 @@
 
 namespace fire {
 void set_last_error(const char* stage, const char* msg);
+void set_single_stream(bool on);
 }
 
 // The static workspace.  In host code this name is only a stand-in for the
@@ -70,7 +71,11 @@ extern "C" int fire_local_energy_static(const fire_system_t* sys, const fire_arc
   int rc = static_ws(&ws);
   if (rc) return rc;
   // The pipeline clears its status word at the start of every call; every
-  // other buffer is written before it is read.
-  return fire_local_energy(sys, arch, params, n_walkers, r, k_cap, precision, e_loc, logabs, sign, e_kin, e_pot,
-                           info, ws, (size_t)FIRE_STATIC_WORKSPACE_BYTES, stream);
+  // other buffer is written before it is read.  Every kernel runs on the
+  // caller's stream (no second stream or event is created for this call).
+  fire::set_single_stream(true);
+  rc = fire_local_energy(sys, arch, params, n_walkers, r, k_cap, precision, e_loc, logabs, sign, e_kin, e_pot, info,
+                         ws, (size_t)FIRE_STATIC_WORKSPACE_BYTES, stream);
+  fire::set_single_stream(false);
+  return rc;
 }

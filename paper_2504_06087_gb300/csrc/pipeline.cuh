@@ -68,6 +68,7 @@ struct CallArgs {
 
 void set_last_error(const char* stage, const char* msg);
 cudaStream_t side_stream();
+bool single_stream();
 bool prof_enabled();
 void prof_add(const char* name, int launches, float ms);
 int run_fp64(const Plan& pl, const CallArgs& a);
@@ -153,7 +154,7 @@ struct Runner {
   cudaStream_t s2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool side_ready() {
-    if (getenv("FIRE_SERIAL")) return false;   // diagnostic: one stream only
+    if (getenv("FIRE_SERIAL") || single_stream()) return false;   // one stream only
     if (!s2) s2 = side_stream();
     if (!s2) return false;
     if (!ev_fork && cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) != cudaSuccess) return false;
