@@ -117,6 +117,11 @@ static size_t layout(Plan& pl, int64_t Wc) {
   pl.sucol = zw;
   int64_t ldb = zw + dm.R + RD;
   if (ldb < n) ldb = n;
+  // BF16 form: the orbital rows of kOrbGroup determinants share one product
+  if (dm.prec == FIRE_PREC_BF16_FP64 && dm.deriv) {
+    const int64_t og = D < kOrbGroup ? D : kOrbGroup;
+    if (ldb < og * n) ldb = og * n;
+  }
   pl.ld_big = ldb;
   TAKE(big, cap * ldb * ts);
   TAKE(Y, cap * J * ts);
@@ -166,7 +171,6 @@ static size_t layout(Plan& pl, int64_t Wc) {
     pl.wb_jm1 = e; e += S * (d * J + J * J);
     pl.wb_jm2 = e; e += S * (d * J + J * J);
     pl.wb_att = e; e += S * (dm.R + RD) * d;
-    pl.wb_orb = e; e += S * 2 * D * n * d;
     pl.wb_env = e; e += S * 2 * D * n * NEp;
     pl.wb_glu = e; e += S * 2 * d * d;
     pl.wb_gluo = e; e += S * d * d;

@@ -448,7 +448,7 @@ __device__ __forceinline__ Quad<T> lds4(const T* p) {
 
 // Gradient and Laplacian of log det Phi_d restricted to the neighbourhoods.
 // One CTA per (walker, tangent electron n').  O holds h W_d for every row of
-// the forward-Laplacian blocks ([rows][n]); Fenv the envelope rows
+// the forward-Laplacian blocks ([rows][n], row stride ldo); Fenv the envelope rows
 // ([Wc*n*5][D*n]); AT the transposed inverses (AT[k][l] = A[l][k],
 // [Wc][D][n][n]).
 //
@@ -467,8 +467,9 @@ template <typename T, int MAXT>
 __global__ void __launch_bounds__(256, (MAXT <= 3 && sizeof(T) == 4) ? 4 : 1)
 contract_kernel(int Wc, int n, int n_up, int K, int mcap, int dd, int D, const int32_t* __restrict__ idx,
                 const int32_t* __restrict__ cnt, const int32_t* __restrict__ rev,
-                const int64_t* __restrict__ blk_off, const T* __restrict__ O, const T* __restrict__ Fenv,
-                const T* __restrict__ AT, T* __restrict__ gdet, T* __restrict__ ldet, DevStatus* st) {
+                const int64_t* __restrict__ blk_off, const T* __restrict__ O, int64_t ldo,
+                const T* __restrict__ Fenv, const T* __restrict__ AT, T* __restrict__ gdet, T* __restrict__ ldet,
+                DevStatus* st) {
   constexpr int LC = kContractChunk, NT = 256, NG = NT / LC;
   extern __shared__ __align__(16) unsigned char ct_smem[];
   const int mq = contract_mq(mcap);
@@ -499,7 +500,7 @@ contract_kernel(int Wc, int n, int n_up, int K, int mcap, int dd, int D, const i
     const int i = k == 0 ? np : idx[base * K + k - 1];
     const int64_t b = block_index(w, i, Wc, n, n_up);
     const int slot = k == 0 ? 0 : (ms[k] < 0 ? 0 : ms[k]);
-    ro[k] = (k > 0 && ms[k] < 0) ? -1 : (blk_off[b] + 2 + 3 * slot) * n;
+    ro[k] = (k > 0 && ms[k] < 0) ? -1 : (blk_off[b] + 2 + 3 * slot) * ldo;
     fo[k] = b * 5 * Dn + (int64_t)dd * n;
   }
   __syncthreads();
@@ -514,9 +515,9 @@ contract_kernel(int Wc, int n, int n_up, int K, int mcap, int dd, int D, const i
   {
     const int64_t fb = (int64_t)bnp * 5 * Dn + (int64_t)dd * n;
     for (int l = tid; l < n; l += NT) {
-      const T ov = O[onp * n + l], olp = O[(onp + 1) * n + l];
+      const T ov = O[onp * ldo + l], olp = O[(onp + 1) * ldo + l];
       T cross = T(0);
-      for (int x = 0; x < 3; ++x) cross += O[(onp + 2 + x) * n + l] * Fenv[fb + (2 + x) * Dn + l];
+      for (int x = 0; x < 3; ++x) cross += O[(onp + 2 + x) * ldo + l] * Fenv[fb + (2 + x) * Dn + l];
       const T lap = olp * Fenv[fb + l] + T(2) * cross + ov * Fenv[fb + Dn + l];
       lt += lap * Aw[(int64_t)np * n + l];
     }
@@ -539,11 +540,11 @@ contract_kernel(int Wc, int n, int n_up, int K, int mcap, int dd, int D, const i
         if (r0 >= 0) {
           const T phi = Fenv[fo[k] + l];
           v0 = O[r0 + l] * phi;
-          v1 = O[r0 + n + l] * phi;
-          v2 = O[r0 + 2 * (int64_t)n + l] * phi;
+          v1 = O[r0 + ldo + l] * phi;
+          v2 = O[r0 + 2 * ldo + l] * phi;
         }
         if (k == 0) {   // n' itself: its envelope moves too
-          const T ov = O[onp * n + l];
+          const T ov = O[onp * ldo + l];
           v0 += ov * Fenv[fo[0] + 2 * Dn + l];
           v1 += ov * Fenv[fo[0] + 3 * Dn + l];
           v2 += ov * Fenv[fo[0] + 4 * Dn + l];
@@ -671,8 +672,9 @@ template <int NT, int MAXT>
 __global__ void __launch_bounds__(NT, (NT == 64 ? 8 : 3))
 contract2_kernel(int Wc, int n, int n_up, int K, int mlo, int mhi, int dd, int D, const int32_t* __restrict__ idx,
                  const int32_t* __restrict__ cnt, const int32_t* __restrict__ rev,
-                 const int64_t* __restrict__ blk_off, const float* __restrict__ O, const float* __restrict__ Fenv,
-                 const float* __restrict__ AT, float* __restrict__ gdet, float* __restrict__ ldet, DevStatus* st) {
+                 const int64_t* __restrict__ blk_off, const float* __restrict__ O, int64_t ldo,
+                 const float* __restrict__ Fenv, const float* __restrict__ AT, float* __restrict__ gdet,
+                 float* __restrict__ ldet, DevStatus* st) {
   constexpr int LC = kC2Chunk;
   extern __shared__ __align__(16) unsigned char c2_smem[];
   __shared__ float red[NT / 32][5];
@@ -700,23 +702,23 @@ contract2_kernel(int Wc, int n, int n_up, int K, int mlo, int mhi, int dd, int D
     }
     const int64_t b = block_index(w, i, Wc, n, n_up);
     mi[k] = i;
-    ro[k] = slot < 0 ? -1 : (blk_off[b] + 2 + 3 * (int64_t)slot) * n;
+    ro[k] = slot < 0 ? -1 : (blk_off[b] + 2 + 3 * (int64_t)slot) * ldo;
     fo[k] = b * 5 * Dn + (int64_t)dd * n;
   }
   __syncthreads();
   const float* Aw = AT + ((int64_t)w * D + dd) * n * n;
   const int bnp = block_index(w, np, Wc, n, n_up);
-  const int64_t onp = blk_off[bnp] * n;
-  const bool vec = (n & 3) == 0;
+  const int64_t onp = blk_off[bnp] * ldo;
+  const bool vec = (n & 3) == 0 && (ldo & 3) == 0;
 
   // sum_l LapPhi_{n' l} A_{l n'}: the Laplacian row of n' against A's column n'
   float lt = 0.f;
   {
     const int64_t fb = (int64_t)bnp * 5 * Dn + (int64_t)dd * n;
     for (int l = tid; l < n; l += NT) {
-      const float ov = O[onp + l], olp = O[onp + n + l];
+      const float ov = O[onp + l], olp = O[onp + ldo + l];
       float cross = 0.f;
-      for (int x = 0; x < 3; ++x) cross += O[onp + (2 + x) * (int64_t)n + l] * Fenv[fb + (2 + x) * Dn + l];
+      for (int x = 0; x < 3; ++x) cross += O[onp + (2 + x) * ldo + l] * Fenv[fb + (2 + x) * Dn + l];
       const float lap = olp * Fenv[fb + l] + 2.f * cross + ov * Fenv[fb + Dn + l];
       lt += lap * Aw[(int64_t)np * n + l];
     }
@@ -741,8 +743,8 @@ contract2_kernel(int Wc, int n, int n_up, int K, int mlo, int mhi, int dd, int D
         const float4 ph = ld_row4(Fenv + fo[k], l, n, vec);
         if (ro[k] >= 0) {
           const float4 o0 = ld_row4(O + ro[k], l, n, vec);
-          const float4 o1 = ld_row4(O + ro[k] + n, l, n, vec);
-          const float4 o2 = ld_row4(O + ro[k] + 2 * (int64_t)n, l, n, vec);
+          const float4 o1 = ld_row4(O + ro[k] + ldo, l, n, vec);
+          const float4 o2 = ld_row4(O + ro[k] + 2 * ldo, l, n, vec);
           t0 = make_float4(o0.x * ph.x, o0.y * ph.y, o0.z * ph.z, o0.w * ph.w);
           t1 = make_float4(o1.x * ph.x, o1.y * ph.y, o1.z * ph.z, o1.w * ph.w);
           t2 = make_float4(o2.x * ph.x, o2.y * ph.y, o2.z * ph.z, o2.w * ph.w);

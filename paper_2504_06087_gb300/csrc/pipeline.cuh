@@ -644,10 +644,6 @@ struct Runner {
               tc::pack_bf16(s, reinterpret_cast<const float*>(p.orb_w) + (sp * D + dd) * d * n, n, (int)d, (int)n, 1,
                             dst(pl.wb_orbv + S * sp * Dn * d + dd * n * d), S, Dn * d);
         }
-        for (int sp = 0; sp < 2; ++sp)
-          for (int dd = 0; dd < D; ++dd, ++np)
-            tc::pack_bf16(s, reinterpret_cast<const float*>(p.orb_w) + (sp * D + dd) * d * n, n, (int)d, (int)n, 1,
-                          dst(pl.wb_orb + S * (sp * D + dd) * n * d), S, n * d);
         launches += np + 1;
       }
     }
@@ -938,40 +934,65 @@ struct Runner {
         // (diagnostic)
         const char* cenv = getenv("FIRE_CONTRACT");
         const bool c2 = sizeof(T) == 4 && mcap <= kC2BigMax && !(cenv && strcmp(cenv, "v1") == 0);
-        for (int dd = 0; dd < D; ++dd) {
+        // orbital rows of G determinants per product (BF16 form: one slice of
+        // the packed [D n][d] weights of a spin, so X is read D / G times)
+        int G = 1;
+        const __nv_bfloat16* WBo = wbm(3, pl.wb_orbv);
+        if (WBo && d % 64 == 0) G = (int)(pl.ld_big / n) < kOrbGroup ? (int)(pl.ld_big / n) : kOrbGroup;
+        if (G < 1) G = 1;
+        for (int dd0 = 0; dd0 < D; dd0 += G) {
+          const int g = D - dd0 < G ? D - dd0 : G;
+          const int64_t ldo = (int64_t)g * n;
           mark("orb_gemm", 2);
-          for (int sp = 0; sp < 2; ++sp)
-            row_gemm(X, Xb, d, capA, p.orb_w + ((int64_t)sp * D + dd) * d * n,
-                     wbm(3, pl.wb_orb + kMaxSplit * ((int64_t)sp * D + dd) * n * d), n, O, n, rng + 2 * sp, 0, 0,
-                     cap, n, d, nc_orb);
-          mark("contract", 1);
-          if constexpr (sizeof(T) == 4) {
-            if (c2) {
-              // bucket A: up to 36 members (64 threads); bucket B: the rest
-              const int ma = mcap < kC2SmallMax ? mcap : kC2SmallMax;
-              contract2_kernel<64, 2><<<nb, 64, contract2_smem_bytes(ma), s>>>(
-                  wc, n, n_up, K, 1, ma, dd, D, idx, cnt, rev, boff, reinterpret_cast<const float*>(O),
-                  reinterpret_cast<const float*>(Fenv), reinterpret_cast<const float*>(Ainv),
-                  reinterpret_cast<float*>(gdet), reinterpret_cast<float*>(ldet), st);
-              if (mcap > kC2SmallMax) {
-                contract2_kernel<128, 3><<<nb, 128, contract2_smem_bytes(mcap), s>>>(
-                    wc, n, n_up, K, kC2SmallMax + 1, mcap, dd, D, idx, cnt, rev, boff,
-                    reinterpret_cast<const float*>(O), reinterpret_cast<const float*>(Fenv),
-                    reinterpret_cast<const float*>(Ainv), reinterpret_cast<float*>(gdet),
-                    reinterpret_cast<float*>(ldet), st);
-                launches += 1;
+          for (int sp = 0; sp < 2; ++sp) {
+            bool done = false;
+            if constexpr (sizeof(T) == 4) {
+              if (WBo && d % 64 == 0) {
+                const int rc = tc::gemm_bf16_rows(s, Xb, d, capA, WBo + (int64_t)kMaxSplit * sp * Dn * d, (int)Dn,
+                                                  dd0 * n, g * n, d, reinterpret_cast<float*>(O), ldo, 0, 0,
+                                                  rng + 2 * sp, cap, &st->tc_err, nc_orb);
+                if (rc == FIRE_OK) done = true;
+                else tc_rc = rc;
               }
-              check("contract");
-              continue;
             }
+            if (!done)
+              for (int j = 0; j < g; ++j)
+                gemm<T>(s, X, d, p.orb_w + ((int64_t)sp * D + dd0 + j) * d * n, n, false, O + (int64_t)j * n, ldo,
+                        0, 0, rng + 2 * sp, cap, n, d);
           }
-          auto ck = contract_kernel<T, 1>;
-          if (maxt == 2) ck = contract_kernel<T, 2>;
-          else if (maxt == 3) ck = contract_kernel<T, 3>;
-          else if (maxt == 5) ck = contract_kernel<T, 5>;
-          else if (maxt == 9) ck = contract_kernel<T, 9>;
-          ck<<<nb, 256, ctsm, s>>>(wc, n, n_up, K, mcap, dd, D, idx, cnt, rev, boff, O, Fenv, Ainv, gdet, ldet, st);
-      check("contract");
+          for (int j = 0; j < g; ++j) {
+            const int dd = dd0 + j;
+            const T* Oj = O + (int64_t)j * n;
+            mark("contract", 1);
+            if constexpr (sizeof(T) == 4) {
+              if (c2) {
+                // bucket A: up to 36 members (64 threads); bucket B: the rest
+                const int ma = mcap < kC2SmallMax ? mcap : kC2SmallMax;
+                contract2_kernel<64, 2><<<nb, 64, contract2_smem_bytes(ma), s>>>(
+                    wc, n, n_up, K, 1, ma, dd, D, idx, cnt, rev, boff, reinterpret_cast<const float*>(Oj), ldo,
+                    reinterpret_cast<const float*>(Fenv), reinterpret_cast<const float*>(Ainv),
+                    reinterpret_cast<float*>(gdet), reinterpret_cast<float*>(ldet), st);
+                if (mcap > kC2SmallMax) {
+                  contract2_kernel<128, 3><<<nb, 128, contract2_smem_bytes(mcap), s>>>(
+                      wc, n, n_up, K, kC2SmallMax + 1, mcap, dd, D, idx, cnt, rev, boff,
+                      reinterpret_cast<const float*>(Oj), ldo, reinterpret_cast<const float*>(Fenv),
+                      reinterpret_cast<const float*>(Ainv), reinterpret_cast<float*>(gdet),
+                      reinterpret_cast<float*>(ldet), st);
+                  launches += 1;
+                }
+                check("contract");
+                continue;
+              }
+            }
+            auto ck = contract_kernel<T, 1>;
+            if (maxt == 2) ck = contract_kernel<T, 2>;
+            else if (maxt == 3) ck = contract_kernel<T, 3>;
+            else if (maxt == 5) ck = contract_kernel<T, 5>;
+            else if (maxt == 9) ck = contract_kernel<T, 9>;
+            ck<<<nb, 256, ctsm, s>>>(wc, n, n_up, K, mcap, dd, D, idx, cnt, rev, boff, Oj, ldo, Fenv, Ainv, gdet, ldet,
+                                     st);
+            check("contract");
+          }
         }
       }
       // 9. final combination

@@ -28,7 +28,7 @@ struct Plan {
   size_t S5, Y5, Z5, P5, H0, PQ;
   size_t X, big, F1, F2;   // big holds Z | SU, and O (aliased) in the det phase
   size_t Y, Xb, Yb;        // Jastrow hidden rows; bf16 copies of X and Y (BF16 form)
-  int64_t wb_mlp, wb_jm1, wb_jm2, wb_att, wb_orb, wb_env, wb_glu, wb_gluo, wb_msg, wb_orbv;   // element offsets inside wbf16
+  int64_t wb_mlp, wb_jm1, wb_jm2, wb_att, wb_env, wb_glu, wb_gluo, wb_msg, wb_orbv;   // element offsets inside wbf16
   size_t Qf, Qfb, Fenv, Hv, Ov;   // Qfb: bf16 components of Qf (BF16 form)
   size_t Y5b, P5b, H0b, Hvb;      // bf16 components of Y5, P5, H0, Hv (BF16 form)
   size_t LU, piv, ldabs, lsign, Ainv, gdet, ldet, Phif;
@@ -54,6 +54,9 @@ struct Plan {
   struct Ent { const char* name; size_t off, bytes; } ent[160];
   int nent;
 };
+
+// Determinants whose orbital rows share one tensor-core product (BF16 form).
+constexpr int kOrbGroup = 4;
 
 // CTAs (and scratch slots) of the Woodbury update: a persistent grid over
 // the (walker, determinant) pairs, 4 per SM.

@@ -17,6 +17,12 @@ int gemm_bf16(cudaStream_t s, const void* A, int64_t lda, int64_t a_rows, const 
               float* C, int64_t ldc, int64_t m_begin, int64_t m_end, const int64_t* m_range, int64_t m_cap,
               int* err, int nc);
 
+// The same product with Bt rows [b_row0, b_row0 + N) of a weight block whose
+// components hold b_rows rows each (a slice of a larger packed matrix).
+int gemm_bf16_rows(cudaStream_t s, const void* A, int64_t lda, int64_t a_rows, const void* Bt, int b_rows,
+                   int b_row0, int N, int K, float* C, int64_t ldc, int64_t m_begin, int64_t m_end,
+                   const int64_t* m_range, int64_t m_cap, int* err, int nc);
+
 // dst = nc-component bf16 K-major copy of a weight matrix (pack_bf16_kernel),
 // rows ldd >= K elements apart with zero padding (ldd = 0: K).
 void pack_bf16(cudaStream_t s, const float* src, int64_t lds, int K, int N, int trans, void* dst, int nc,

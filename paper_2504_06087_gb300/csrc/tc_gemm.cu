@@ -83,6 +83,13 @@ static int choose_bn(int N, int nc, int stages) {
 int gemm_bf16(cudaStream_t s, const void* A, int64_t lda, int64_t a_rows, const void* Bt, int N, int K,
               float* C, int64_t ldc, int64_t m_begin, int64_t m_end, const int64_t* m_range, int64_t m_cap,
               int* err, int nc) {
+  return gemm_bf16_rows(s, A, lda, a_rows, Bt, N, 0, N, K, C, ldc, m_begin, m_end, m_range, m_cap, err, nc);
+}
+
+int gemm_bf16_rows(cudaStream_t s, const void* A, int64_t lda, int64_t a_rows, const void* Bt, int b_rows,
+                   int b_row0, int N, int K, float* C, int64_t ldc, int64_t m_begin, int64_t m_end,
+                   const int64_t* m_range, int64_t m_cap, int* err, int nc) {
+  if (b_row0 < 0 || b_row0 + N > b_rows) return FIRE_ERR_UNSUPPORTED;
   if (N < 1 || K < BK || K % BK || m_cap <= 0 || nc < 1 || nc > 3) return FIRE_ERR_UNSUPPORTED;
   const int stages = nc == 1 ? 4 : (nc == 2 ? 3 : 2);
   const int BN = choose_bn(N, nc, stages);
@@ -90,8 +97,8 @@ int gemm_bf16(cudaStream_t s, const void* A, int64_t lda, int64_t a_rows, const 
   const int nt = (N + BN - 1) / BN;
   CUtensorMap ma, mb;
   if (!make_map(&ma, A, (uint64_t)a_rows * nc, (uint64_t)K, (uint64_t)lda, BM)) return FIRE_ERR_CUDA;
-  if (!make_map(&mb, Bt, (uint64_t)N * nc, (uint64_t)K, (uint64_t)K, (uint32_t)BN)) return FIRE_ERR_CUDA;
-  TcArgs g{C, ldc, m_begin, m_end, m_range, N, K, BN, a_rows, N, err};
+  if (!make_map(&mb, Bt, (uint64_t)b_rows * nc, (uint64_t)K, (uint64_t)K, (uint32_t)BN)) return FIRE_ERR_CUDA;
+  TcArgs g{C, ldc, m_begin, m_end, m_range, N, K, BN, a_rows, b_rows, b_row0, err};
   if (nc == 1) return launch<4, 1>(s, ma, mb, g, m_cap, nt);
   if (nc == 2) return launch<3, 2>(s, ma, mb, g, m_cap, nt);
   return launch<2, 3>(s, ma, mb, g, m_cap, nt);

@@ -144,6 +144,7 @@ struct TcArgs {
   int N, K, BN;                  // BN multiple of 16, <= 256
   int64_t a_comp_rows;           // rows between the bf16 components of A
   int64_t b_comp_rows;           // rows between the bf16 components of Bt
+  int64_t b_row0;                // first row of Bt inside each component
   int* err;                      // device error word (timeouts)
 };
 
@@ -221,7 +222,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           tma_load_2d(sa + c * a_bytes, &mapA, &full_bar[s], kb * BK, (int)(c * g.a_comp_rows + m0));
-          tma_load_2d(sa + NC * a_bytes + c * b_bytes, &mapB, &full_bar[s], kb * BK, (int)(c * g.b_comp_rows + n0));
+          tma_load_2d(sa + NC * a_bytes + c * b_bytes, &mapB, &full_bar[s], kb * BK, (int)(c * g.b_comp_rows + g.b_row0 + n0));
         }
       }
     }
