@@ -655,8 +655,12 @@ __device__ __forceinline__ float4 ld_row4(const float* __restrict__ p, int l, in
 //   Ts [32][4 MP + 4]  T quads     As [32][MP + 4]  A values
 //   (M [3 m][m] reuses the area after the last chunk)
 constexpr int kC2Chunk = 32;
-constexpr int kC2SmallMax = 36;   // members of the 64-thread bucket
-constexpr int kC2BigMax = 60;     // members of the 128-thread bucket
+// Buckets: up to 24 members on 64 threads, 36 on 128, 60 on 320 (one tile per
+// thread: ceil(m/3) * ceil(m/4) <= threads).
+constexpr int kC2Buckets = 3;
+constexpr int kC2BucketMax[kC2Buckets] = {24, 36, 60};
+constexpr int kC2BucketThreads[kC2Buckets] = {64, 128, 320};
+constexpr int kC2BigMax = 60;
 __host__ __device__ inline int contract2_slots(int mhi) { return 12 * ((mhi + 11) / 12); }
 __host__ __device__ inline size_t contract2_region(int mp) {
   const size_t st = (size_t)kC2Chunk * (4 * mp + 4) + (size_t)kC2Chunk * (mp + 4);
@@ -669,7 +673,7 @@ inline size_t contract2_smem_bytes(int mhi) {
 }
 
 template <int NT, int MAXT>
-__global__ void __launch_bounds__(NT, (NT == 64 ? 8 : 3))
+__global__ void __launch_bounds__(NT, 819 / NT)   // at most 80 registers
 contract2_kernel(int Wc, int n, int n_up, int K, int mlo, int mhi, int dd, int D, const int32_t* __restrict__ idx,
                  const int32_t* __restrict__ cnt, const int32_t* __restrict__ rev,
                  const int64_t* __restrict__ blk_off, const float* __restrict__ O, int64_t ldo,

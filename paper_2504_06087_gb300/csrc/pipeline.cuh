@@ -966,19 +966,17 @@ struct Runner {
             mark("contract", 1);
             if constexpr (sizeof(T) == 4) {
               if (c2) {
-                // bucket A: up to 36 members (64 threads); bucket B: the rest
-                const int ma = mcap < kC2SmallMax ? mcap : kC2SmallMax;
-                contract2_kernel<64, 2><<<nb, 64, contract2_smem_bytes(ma), s>>>(
-                    wc, n, n_up, K, 1, ma, dd, D, idx, cnt, rev, boff, reinterpret_cast<const float*>(Oj), ldo,
-                    reinterpret_cast<const float*>(Fenv), reinterpret_cast<const float*>(Ainv),
-                    reinterpret_cast<float*>(gdet), reinterpret_cast<float*>(ldet), st);
-                if (mcap > kC2SmallMax) {
-                  contract2_kernel<128, 3><<<nb, 128, contract2_smem_bytes(mcap), s>>>(
-                      wc, n, n_up, K, kC2SmallMax + 1, mcap, dd, D, idx, cnt, rev, boff,
-                      reinterpret_cast<const float*>(Oj), ldo, reinterpret_cast<const float*>(Fenv),
-                      reinterpret_cast<const float*>(Ainv), reinterpret_cast<float*>(gdet),
-                      reinterpret_cast<float*>(ldet), st);
-                  launches += 1;
+                // one launch per neighbourhood-size bucket that the chunk reaches
+                int lo = 1;
+                for (int q = 0; q < kC2Buckets && lo <= mcap; ++q) {
+                  const int hi = mcap < kC2BucketMax[q] ? mcap : kC2BucketMax[q];
+                  auto kern = q == 0 ? contract2_kernel<64, 1> : (q == 1 ? contract2_kernel<128, 1> : contract2_kernel<320, 1>);
+                  kern<<<nb, kC2BucketThreads[q], contract2_smem_bytes(hi), s>>>(
+                      wc, n, n_up, K, lo, hi, dd, D, idx, cnt, rev, boff, reinterpret_cast<const float*>(Oj), ldo,
+                      reinterpret_cast<const float*>(Fenv), reinterpret_cast<const float*>(Ainv),
+                      reinterpret_cast<float*>(gdet), reinterpret_cast<float*>(ldet), st);
+                  if (q > 0) launches += 1;
+                  lo = hi + 1;
                 }
                 check("contract");
                 continue;
@@ -1270,8 +1268,9 @@ inline int set_smem_limits() {
   raise((const void*)contract_kernel<T, 3>);
   raise((const void*)contract_kernel<T, 5>);
   raise((const void*)contract_kernel<T, 9>);
-  raise((const void*)contract2_kernel<64, 2>);
-  raise((const void*)contract2_kernel<128, 3>);
+  raise((const void*)contract2_kernel<64, 1>);
+  raise((const void*)contract2_kernel<128, 1>);
+  raise((const void*)contract2_kernel<320, 1>);
   raise((const void*)lu_inverse_kernel<LT, T>);
   raise((const void*)lu_kernel<LT, 16>);
   raise((const void*)att_pool_kernel<T>);
