@@ -331,8 +331,14 @@ cudaStream_t side_stream() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
   std::lock_guard<std::mutex> lk(mu);
-  if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess)
-    streams[dev] = nullptr;
+  if (!streams[dev]) {
+    // highest priority: its few long CTAs (the float64 LU) are scheduled as
+    // soon as an SM has room, the caller's stream fills the rest
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (cudaStreamCreateWithPriority(&streams[dev], cudaStreamNonBlocking, greatest) != cudaSuccess)
+      streams[dev] = nullptr;
+  }
   return streams[dev];
 }
 

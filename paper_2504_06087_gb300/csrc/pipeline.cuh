@@ -847,68 +847,6 @@ struct Runner {
         }
         check("inverse");
       }
-      // 6. Jastrow factors
-      T* jval = at<T>(pl.jval); T* jsign = at<T>(pl.jsign); T* jgrad = at<T>(pl.jgrad); T* jlap = at<T>(pl.jlap);
-      T* aval = at<T>(pl.aval); T* asign = at<T>(pl.asign); T* agrad = at<T>(pl.agrad); T* alap = at<T>(pl.alap);
-      T* cval = at<T>(pl.cval); T* cgrad = at<T>(pl.cgrad); T* clap = at<T>(pl.clap); T* vpot = at<T>(pl.vpot);
-      if (dm.flags & FIRE_J_MLP) {
-        mark("jastrow_mlp", 10);
-        T* F1 = at<T>(pl.F1);
-        T* F2 = at<T>(pl.F2);
-        const int64_t JJ = (int64_t)dm.J;
-        mlp_readout(X, Xb, d, d, fullr, 0, 0, cap, boff, 0, nb, p.jm1_w1, wbm(1, pl.wb_jm1), p.jm1_b1, p.jm1_w2,
-                    wbm(1, pl.wb_jm1 + kMaxSplit * d * JJ), p.jm1_b2, p.jm1_w3, Z, ldb, Y, Yb, JJ, F1);
-        mlp_readout(X, Xb, d, d, fullr, 0, 0, cap, boff, 0, nb, p.jm2_w1, wbm(1, pl.wb_jm2), p.jm2_b1, p.jm2_w2,
-                    wbm(1, pl.wb_jm2 + kMaxSplit * d * JJ), p.jm2_b2, p.jm2_w3, Z, ldb, Y, Yb, JJ, F2);
-        mark("jastrow_reduce", 1);
-        jmlp_reduce_kernel<T, T><<<wc, 256, 0, s>>>(wc, n, n_up, K, idx, cnt, rev, boff, F1, F2, p.jm1_b3,
-                                                    p.jm2_b3, jval, jsign, jgrad, jlap, deriv);
-      check("jmlp");
-      }
-      if (dm.flags & FIRE_J_ATT) {
-        const int R = dm.R, dr = dm.dr, RD = R * dr;
-        mark("att_gemm", 2);
-        bool att_tc = false;
-        if constexpr (sizeof(T) == 4) {
-          if (Xb && WB && d % 64 == 0 && (tc_mask & 4))
-            att_tc = tc::gemm_bf16(s, Xb, d, capA, WB + pl.wb_att, R + RD, d, reinterpret_cast<float*>(SU), ldb, 0,
-                                   0, fullr, cap, &st->tc_err, nc_att) == FIRE_OK;
-        }
-        if (!att_tc) {
-          gemm<T>(s, X, d, p.att_q, d, true, SU, ldb, 0, 0, fullr, cap, R, d);
-          gemm<T>(s, X, d, p.att_wv, dr, false, SU + R, ldb, 0, 0, fullr, cap, dr, d, R, 0, (int64_t)d * dr, dr);
-        }
-        T* V = at<T>(pl.V);
-        T* VZ = at<T>(pl.VZ);
-        T* VY = at<T>(pl.VY);
-        T* G1 = at<T>(pl.G1);
-        T* G2 = at<T>(pl.G2);
-        const int bt = ((RD + 31) / 32) * 32;
-        if (deriv) {
-          // per-electron partial records, then ordered sums per walker
-          T* AP = at<T>(pl.AP);
-          mark("att_pool", 3);
-          att_max_kernel<T><<<wc, 256, 0, s>>>(wc, n, n_up, R, boff, SU, ldb, AP);
-          att_part_kernel<T><<<nb, bt, 0, s>>>(wc, n, n_up, K, R, dr, idx, cnt, rev, boff, SU, ldb, AP);
-          att_fin_kernel<T><<<dim3(wc, 8), bt, 0, s>>>(wc, n, R, dr, AP, V);
-        } else {
-          const size_t apsm = (size_t)(R + n * R) * sizeof(T);
-          mark("att_pool", 1);
-          att_pool_kernel<T><<<wc, bt, apsm, s>>>(wc, n, n_up, K, R, dr, idx, cnt, rev, boff, SU, ldb, V, deriv);
-        }
-        const int64_t vstride = deriv ? (2 + 3 * (int64_t)n) : 1;
-        const int64_t vrows = (int64_t)wc * vstride;
-        mark("att_mlp", 11);
-        mlp_readout(V, nullptr, RD, RD, nullptr, 0, vrows, vrows, nullptr, vstride, wc, p.ja1_w1, nullptr,
-                    p.ja1_b1, p.ja1_w2, nullptr, p.ja1_b2, p.ja1_w3, VZ, dm.J, VY, nullptr, dm.J, G1);
-        mlp_readout(V, nullptr, RD, RD, nullptr, 0, vrows, vrows, nullptr, vstride, wc, p.ja2_w1, nullptr,
-                    p.ja2_b1, p.ja2_w2, nullptr, p.ja2_b2, p.ja2_w3, VZ, dm.J, VY, nullptr, dm.J, G2);
-        att_reduce_kernel<T, T><<<wc, 256, 0, s>>>(n, G1, G2, p.ja1_b3, p.ja2_b3, aval, asign, agrad, alap, deriv);
-      check("att");
-      }
-      mark("coulomb_cusp", 1);
-      coulomb_cusp_kernel<T, T><<<wc, 256, 0, s>>>(n, n_up, N, r, sys->nuc_pos, sys->nuc_charge, p.cusp, vpot,
-                                                   cval, cgrad, clap, deriv);
       T* gdet = at<T>(pl.gdet);
       T* ldet = at<T>(pl.ldet);
       if (deriv) {
@@ -993,6 +931,71 @@ struct Runner {
           }
         }
       }
+      // 6. Jastrow factors (after the log-det derivatives, so the float64 LU
+      // on the second stream runs beside the contraction kernels, whose small
+      // CTAs leave room for it)
+      vr_off = boff;   // value rows of the Jastrow products recomputed in fp32
+      T* jval = at<T>(pl.jval); T* jsign = at<T>(pl.jsign); T* jgrad = at<T>(pl.jgrad); T* jlap = at<T>(pl.jlap);
+      T* aval = at<T>(pl.aval); T* asign = at<T>(pl.asign); T* agrad = at<T>(pl.agrad); T* alap = at<T>(pl.alap);
+      T* cval = at<T>(pl.cval); T* cgrad = at<T>(pl.cgrad); T* clap = at<T>(pl.clap); T* vpot = at<T>(pl.vpot);
+      if (dm.flags & FIRE_J_MLP) {
+        mark("jastrow_mlp", 10);
+        T* F1 = at<T>(pl.F1);
+        T* F2 = at<T>(pl.F2);
+        const int64_t JJ = (int64_t)dm.J;
+        mlp_readout(X, Xb, d, d, fullr, 0, 0, cap, boff, 0, nb, p.jm1_w1, wbm(1, pl.wb_jm1), p.jm1_b1, p.jm1_w2,
+                    wbm(1, pl.wb_jm1 + kMaxSplit * d * JJ), p.jm1_b2, p.jm1_w3, Z, ldb, Y, Yb, JJ, F1);
+        mlp_readout(X, Xb, d, d, fullr, 0, 0, cap, boff, 0, nb, p.jm2_w1, wbm(1, pl.wb_jm2), p.jm2_b1, p.jm2_w2,
+                    wbm(1, pl.wb_jm2 + kMaxSplit * d * JJ), p.jm2_b2, p.jm2_w3, Z, ldb, Y, Yb, JJ, F2);
+        mark("jastrow_reduce", 1);
+        jmlp_reduce_kernel<T, T><<<wc, 256, 0, s>>>(wc, n, n_up, K, idx, cnt, rev, boff, F1, F2, p.jm1_b3,
+                                                    p.jm2_b3, jval, jsign, jgrad, jlap, deriv);
+      check("jmlp");
+      }
+      if (dm.flags & FIRE_J_ATT) {
+        const int R = dm.R, dr = dm.dr, RD = R * dr;
+        mark("att_gemm", 2);
+        bool att_tc = false;
+        if constexpr (sizeof(T) == 4) {
+          if (Xb && WB && d % 64 == 0 && (tc_mask & 4))
+            att_tc = tc::gemm_bf16(s, Xb, d, capA, WB + pl.wb_att, R + RD, d, reinterpret_cast<float*>(SU), ldb, 0,
+                                   0, fullr, cap, &st->tc_err, nc_att) == FIRE_OK;
+        }
+        if (!att_tc) {
+          gemm<T>(s, X, d, p.att_q, d, true, SU, ldb, 0, 0, fullr, cap, R, d);
+          gemm<T>(s, X, d, p.att_wv, dr, false, SU + R, ldb, 0, 0, fullr, cap, dr, d, R, 0, (int64_t)d * dr, dr);
+        }
+        T* V = at<T>(pl.V);
+        T* VZ = at<T>(pl.VZ);
+        T* VY = at<T>(pl.VY);
+        T* G1 = at<T>(pl.G1);
+        T* G2 = at<T>(pl.G2);
+        const int bt = ((RD + 31) / 32) * 32;
+        if (deriv) {
+          // per-electron partial records, then ordered sums per walker
+          T* AP = at<T>(pl.AP);
+          mark("att_pool", 3);
+          att_max_kernel<T><<<wc, 256, 0, s>>>(wc, n, n_up, R, boff, SU, ldb, AP);
+          att_part_kernel<T><<<nb, bt, 0, s>>>(wc, n, n_up, K, R, dr, idx, cnt, rev, boff, SU, ldb, AP);
+          att_fin_kernel<T><<<dim3(wc, 8), bt, 0, s>>>(wc, n, R, dr, AP, V);
+        } else {
+          const size_t apsm = (size_t)(R + n * R) * sizeof(T);
+          mark("att_pool", 1);
+          att_pool_kernel<T><<<wc, bt, apsm, s>>>(wc, n, n_up, K, R, dr, idx, cnt, rev, boff, SU, ldb, V, deriv);
+        }
+        const int64_t vstride = deriv ? (2 + 3 * (int64_t)n) : 1;
+        const int64_t vrows = (int64_t)wc * vstride;
+        mark("att_mlp", 11);
+        mlp_readout(V, nullptr, RD, RD, nullptr, 0, vrows, vrows, nullptr, vstride, wc, p.ja1_w1, nullptr,
+                    p.ja1_b1, p.ja1_w2, nullptr, p.ja1_b2, p.ja1_w3, VZ, dm.J, VY, nullptr, dm.J, G1);
+        mlp_readout(V, nullptr, RD, RD, nullptr, 0, vrows, vrows, nullptr, vstride, wc, p.ja2_w1, nullptr,
+                    p.ja2_b1, p.ja2_w2, nullptr, p.ja2_b2, p.ja2_w3, VZ, dm.J, VY, nullptr, dm.J, G2);
+        att_reduce_kernel<T, T><<<wc, 256, 0, s>>>(n, G1, G2, p.ja1_b3, p.ja2_b3, aval, asign, agrad, alap, deriv);
+      check("att");
+      }
+      mark("coulomb_cusp", 1);
+      coulomb_cusp_kernel<T, T><<<wc, 256, 0, s>>>(n, n_up, N, r, sys->nuc_pos, sys->nuc_charge, p.cusp, vpot,
+                                                   cval, cgrad, clap, deriv);
       // 9. final combination
       if (lu_side) cudaStreamWaitEvent(s, ev_join, 0);
       FinalIn<T, RT> fi{ldabs, lsign, gdet, ldet, cval, cgrad, clap, jval, jsign, jgrad, jlap,
