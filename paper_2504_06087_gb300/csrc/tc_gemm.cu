@@ -4,6 +4,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include "../../include/fire.h"
@@ -91,17 +92,31 @@ int gemm_bf16_rows(cudaStream_t s, const void* A, int64_t lda, int64_t a_rows, c
                    const int64_t* m_range, int64_t m_cap, int* err, int nc) {
   if (b_row0 < 0 || b_row0 + N > b_rows) return FIRE_ERR_UNSUPPORTED;
   if (N < 1 || K < BK || K % BK || m_cap <= 0 || nc < 1 || nc > 3) return FIRE_ERR_UNSUPPORTED;
-  const int stages = nc == 1 ? 4 : (nc == 2 ? 3 : 2);
-  const int BN = choose_bn(N, nc, stages);
+  int stages = nc == 1 ? 4 : (nc == 2 ? 3 : 2);
+  // FIRE_TC_STAGES / FIRE_TC_BN (diagnostic): pipeline depth and tile width
+  if (const char* e = getenv("FIRE_TC_STAGES")) {
+    const int v = atoi(e);
+    if (v >= 2 && v <= 4) stages = v;
+  }
+  int BN = choose_bn(N, nc, stages);
+  if (const char* e = getenv("FIRE_TC_BN")) {
+    const int v = atoi(e);
+    if (v >= 16 && v <= 256 && v % 16 == 0 && tc_smem_bytes(stages, nc, v) <= 227 * 1024) BN = v;
+  }
   if (BN == 0) return FIRE_ERR_UNSUPPORTED;
   const int nt = (N + BN - 1) / BN;
   CUtensorMap ma, mb;
   if (!make_map(&ma, A, (uint64_t)a_rows * nc, (uint64_t)K, (uint64_t)lda, BM)) return FIRE_ERR_CUDA;
   if (!make_map(&mb, Bt, (uint64_t)b_rows * nc, (uint64_t)K, (uint64_t)K, (uint32_t)BN)) return FIRE_ERR_CUDA;
   TcArgs g{C, ldc, m_begin, m_end, m_range, N, K, BN, a_rows, b_rows, b_row0, err};
-  if (nc == 1) return launch<4, 1>(s, ma, mb, g, m_cap, nt);
-  if (nc == 2) return launch<3, 2>(s, ma, mb, g, m_cap, nt);
-  return launch<2, 3>(s, ma, mb, g, m_cap, nt);
+  if (nc == 1) return stages == 2 ? launch<2, 1>(s, ma, mb, g, m_cap, nt)
+                                   : (stages == 3 ? launch<3, 1>(s, ma, mb, g, m_cap, nt)
+                                                  : launch<4, 1>(s, ma, mb, g, m_cap, nt));
+  if (nc == 2) return stages == 2 ? launch<2, 2>(s, ma, mb, g, m_cap, nt)
+                                   : (stages == 3 ? launch<3, 2>(s, ma, mb, g, m_cap, nt)
+                                                  : launch<4, 2>(s, ma, mb, g, m_cap, nt));
+  return stages == 2 ? launch<2, 3>(s, ma, mb, g, m_cap, nt)
+                     : (stages == 3 ? launch<3, 3>(s, ma, mb, g, m_cap, nt) : launch<4, 3>(s, ma, mb, g, m_cap, nt));
 }
 
 // dst[c][n][k] = component c of src[k * lds + n] for a [K][N] source
