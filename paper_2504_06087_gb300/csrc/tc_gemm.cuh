@@ -8,9 +8,9 @@
 // second reads it from L2).  Warp 0 lane 0 streams A and B k-blocks through
 // a ring of STAGES shared-memory stages (TMA), warp 1 lane 0 issues the MMAs
 // into one of two tensor-memory accumulators, and warps 2-5 drain the other
-// accumulator (tcgen05.ld 32x32b, each warp its 32-lane quarter) through a
-// per-warp transpose buffer into coalesced rows of C, so a tile's epilogue
-// overlaps the next tile's main loop.  The row range of A may live on the
+// accumulator (tcgen05.ld 32x32b, each warp its 32-lane quarter; every lane
+// stores its row's 32-column slices straight from registers with 128-bit
+// stores), so a tile's epilogue overlaps the next tile's main loop.  The row range of A may live on the
 // device ({begin, end}).
 //
 // Every mbarrier wait is bounded: after kSpinLimit polls the kernel records
@@ -161,10 +161,10 @@ __host__ __device__ constexpr int split_q(int nc, int k) {
 }
 
 // Dynamic shared memory: STAGES x NC x (A tile 16 KB + B tile BN*128 B),
-// 1024-aligned, then 4 x [32][33] fp32 epilogue transpose buffers.
+// 1024-aligned.
 constexpr int kEpiWarps = 4;
 __host__ __device__ inline size_t tc_smem_bytes(int stages, int nc, int bn) {
-  return (size_t)stages * nc * ((size_t)BM * BK * 2 + (size_t)bn * BK * 2) + (size_t)kEpiWarps * 32 * 33 * 4 + 1024;
+  return (size_t)stages * nc * ((size_t)BM * BK * 2 + (size_t)bn * BK * 2) + 1024;
 }
 
 template <int STAGES, int NC>
@@ -186,7 +186,6 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   const uint32_t stage_bytes = NC * (a_bytes + b_bytes);
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
-  float* epi = reinterpret_cast<float*>(base + (size_t)STAGES * stage_bytes);
   uint32_t ncols = 32;
   while ((int)ncols < 2 * BN) ncols <<= 1;
 
@@ -271,7 +270,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   } else if (warp >= 2) {
     // epilogue: warp w drains tensor-memory lanes 32 (w % 4) .. + 31
     const int q = warp & 3;
-    float* tb = epi + (warp - 2) * 32 * 33;
+    const bool vec = (g.ldc % 4 == 0) && ((reinterpret_cast<uintptr_t>(g.C) & 15) == 0);
     int64_t tl = 0;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
       const int buf = (int)(tl & 1);
@@ -289,20 +288,25 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       const int n0 = (int)(t % n_nt) * BN;
       const int ncol = min(BN, g.N - n0);
       const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * BN);
+      // lane = row m0 + 32 q + lane: its 32 accumulator columns of a chunk go
+      // straight from registers to its row of C (eight 128-bit stores)
+      const int64_t row = m0 + 32 * q + lane;
+      float* crow = g.C + row * g.ldc + n0;
       for (int c0 = 0; c0 < BN; c0 += 32) {
         float v[32];
         tmem_ld32(tbase + (uint32_t)c0, v);
+        const int nval = ncol - c0;
+        if (row < me && nval > 0) {
+          if (vec && nval >= 32) {
+            float4* d4 = reinterpret_cast<float4*>(crow + c0);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) tb[lane * 33 + j] = v[j];
-        __syncwarp();
-        const int col = c0 + lane;
-        if (col < ncol) {
-          for (int r = 0; r < 32; ++r) {
-            const int64_t row = m0 + 32 * q + r;
-            if (row < me) g.C[row * g.ldc + n0 + col] = tb[r * 33 + lane];
+            for (int j = 0; j < 8; ++j) d4[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (j < nval) crow[c0 + j] = v[j];
           }
         }
-        __syncwarp();
       }
       fence_before_sync();
       __syncwarp();
