@@ -162,6 +162,12 @@ static size_t layout(Plan& pl, int64_t Wc) {
   TAKE(VY, Wc * vstride * J * ts);
   TAKE(G1, Wc * vstride * ts);
   TAKE(G2, Wc * vstride * ts);
+  if (dm.prec == FIRE_PREC_BF16_FP64 && dm.deriv) {
+    TAKE(Vb, kMaxSplit * Wc * vstride * RD * 2);
+    TAKE(VYb, kMaxSplit * Wc * vstride * J * 2);
+  } else {
+    pl.Vb = pl.VYb = 0;
+  }
   if (dm.deriv && (dm.flags & FIRE_J_ATT)) TAKE(AP, (Wc * dm.R + nb * 12 * RD) * ts); else pl.AP = 0;
   if (bf) {
     // every weight block [N][K] is stored as kMaxSplit components [c][N][K]
@@ -176,6 +182,8 @@ static size_t layout(Plan& pl, int64_t Wc) {
     pl.wb_gluo = e; e += S * d * d;
     pl.wb_msg = e; e += S * 4 * d * d;
     pl.wb_orbv = e; e += S * 2 * D * n * d;
+    pl.wb_ja1 = e; e += S * (RD * J + J * J);
+    pl.wb_ja2 = e; e += S * (RD * J + J * J);
     TAKE(wbf16, e * 2);
   } else {
     pl.wbf16 = 0;

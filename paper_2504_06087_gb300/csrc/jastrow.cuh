@@ -269,7 +269,8 @@ __global__ void att_part_kernel(int Wc, int n, int n_up, int K, int R, int dr, c
 }
 
 template <typename T>
-__global__ void att_fin_kernel(int Wc, int n, int R, int dr, const T* __restrict__ AP, T* __restrict__ V) {
+__global__ void att_fin_kernel(int Wc, int n, int R, int dr, const T* __restrict__ AP, T* __restrict__ V,
+                               __nv_bfloat16* __restrict__ Vb = nullptr, int vnc = 0, int64_t vcs = 0) {
   const int RD = R * dr;
   const int col = threadIdx.x;
   if (col >= RD) return;
@@ -282,10 +283,15 @@ __global__ void att_fin_kernel(int Wc, int n, int R, int dr, const T* __restrict
     for (int q = 0; q < 6; ++q) sm[q] += rec[q * RD + col];
   }
   const T Z = sm[0], Nv = sm[1], ZL = sm[2], NL = sm[3], A1 = sm[4], A2 = sm[5];
-  T* Vw = V + (int64_t)w * (2 + 3 * (int64_t)n) * RD;
+  const int64_t vo = (int64_t)w * (2 + 3 * (int64_t)n) * RD;
+  T* Vw = V + vo;
+  auto put = [&](int64_t e, T v) {
+    Vw[e] = v;
+    if (Vb) store_split_bf16(Vb + vo + e, vcs, vnc, (float)v);
+  };
   if (blockIdx.y == 0) {
-    Vw[col] = Nv / Z;
-    Vw[RD + col] = NL / Z - T(2) * A1 / (Z * Z) - Nv * ZL / (Z * Z) + T(2) * Nv * A2 / (Z * Z * Z);
+    put(col, Nv / Z);
+    put(RD + col, NL / Z - T(2) * A1 / (Z * Z) - Nv * ZL / (Z * Z) + T(2) * Nv * A2 / (Z * Z * Z));
   }
   const int per = (n + gridDim.y - 1) / gridDim.y;
   const int i0 = blockIdx.y * per, i1 = min(n, i0 + per);
@@ -294,7 +300,7 @@ __global__ void att_fin_kernel(int Wc, int n, int R, int dr, const T* __restrict
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
       const T dZ = rec[(6 + x) * RD + col], dN = rec[(9 + x) * RD + col];
-      Vw[(2 + 3 * (int64_t)i + x) * RD + col] = dN / Z - Nv * dZ / (Z * Z);
+      put((2 + 3 * (int64_t)i + x) * RD + col, dN / Z - Nv * dZ / (Z * Z));
     }
   }
 }

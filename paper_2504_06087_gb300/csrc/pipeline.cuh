@@ -119,8 +119,8 @@ struct Runner {
     dbg = getenv("FIRE_DEBUG_SYNC") != nullptr;
     // FIRE_TC_MASK (diagnostic): bit 0 embedding MLP, 1 Jastrow MLPs,
     // 2 attention, 3 orbitals, 4 envelopes, 5 h^0 products (GLU, message
-    // projections) and orbital value rows -- which products may use the
-    // tensor cores.
+    // projections) and orbital value rows, 6 attention register MLPs --
+    // which products may use the tensor cores.
     if (const char* m = getenv("FIRE_TC_MASK")) tc_mask = atoi(m);
     if (const char* m = getenv("FIRE_TC_FIX_VALUES")) fix_values = atoi(m);
     // FIRE_INVERSE (diagnostic): 1 = float32 Gauss-Jordan from a float copy of
@@ -211,7 +211,7 @@ struct Runner {
   // stride lda, a_rows rows allocated) and packed bf16 weights Bt [N][K] it
   // runs on the tensor cores (BF16_FP64 form); otherwise SIMT in T.
   int tc_rc = FIRE_OK;
-  int tc_mask = 0x3F;
+  int tc_mask = 0x7F;
   int fix_values = 1;         // value rows recomputed in fp32 after a tensor-core product
   // split-bf16 components of each tensor-core product (1: 1 product, 2: 3, 3: 6).
   // Two components (hi + lo, three products) for the products whose value
@@ -269,12 +269,13 @@ struct Runner {
                    int64_t rb, int64_t re, int64_t cap, const int64_t* off, int64_t stride, int nblk,
                    const T* w1, const __nv_bfloat16* w1b, const T* b1, const T* w2,
                    const __nv_bfloat16* w2b, const T* b2, const T* w3, T* Z, int64_t ldz, T* Y,
-                   __nv_bfloat16* Yb, int64_t ldy, T* F) {
+                   __nv_bfloat16* Yb, int64_t ldy, T* F, int64_t a_rows = -1, int nc = -1) {
     const int J = dm.J;
-    row_gemm(Xin, Xinb, ldx, capA, w1, w1b, J, Z, ldz, range, rb, re, cap, J, din, nc_jas);
-    fl_act_kernel<T, T><<<nblk, 256, 0, s>>>(J, off, stride, Z, ldz, b1, Y, ldy, 0, Yb, nc_jas,
-                                             capA * ldy);
-    row_gemm(Y, Yb, ldy, capA, w2, w2b, J, Z, ldz, range, rb, re, cap, J, J, nc_jas);
+    if (a_rows < 0) a_rows = capA;   // rows between the bf16 components of Xinb and Yb
+    if (nc < 0) nc = nc_jas;
+    row_gemm(Xin, Xinb, ldx, a_rows, w1, w1b, J, Z, ldz, range, rb, re, cap, J, din, nc);
+    fl_act_kernel<T, T><<<nblk, 256, 0, s>>>(J, off, stride, Z, ldz, b1, Y, ldy, 0, Yb, nc, a_rows * ldy);
+    row_gemm(Y, Yb, ldy, a_rows, w2, w2b, J, Z, ldz, range, rb, re, cap, J, J, nc);
     fl_act_kernel<T, T><<<nblk, 256, 0, s>>>(J, off, stride, Z, ldz, b2, Y, ldy, 0);
     const int64_t nrows_grid = cap;
     rowdot_kernel<T, T><<<(unsigned)((nrows_grid + 7) / 8), 256, 0, s>>>(Y, ldy, J, w3, F, range, rb, re);
@@ -637,6 +638,16 @@ struct Runner {
             for (int a = 0; a < 2; ++a, ++np)
               tc::pack_bf16(s, reinterpret_cast<const float*>(p.msg_w) + a * (2 * d + 4) * d + part * d * d, d, (int)d,
                             (int)d, 1, dst(pl.wb_msg + (part * 2 + a) * d * d), S, 4 * d * d);
+          // attention register MLPs
+          const int64_t RDa = R * dr;
+          const T* aw[2][2] = {{p.ja1_w1, p.ja1_w2}, {p.ja2_w1, p.ja2_w2}};
+          const int64_t ao[2] = {pl.wb_ja1, pl.wb_ja2};
+          for (int q = 0; q < 2; ++q) {
+            tc::pack_bf16(s, reinterpret_cast<const float*>(aw[q][0]), J, (int)RDa, (int)J, 1, dst(ao[q]), S, RDa * J);
+            tc::pack_bf16(s, reinterpret_cast<const float*>(aw[q][1]), J, (int)J, (int)J, 1, dst(ao[q] + S * RDa * J),
+                          S, J * J);
+            np += 2;
+          }
           // orbital value rows: all determinants of one spin in one product (N = D n)
           const int64_t Dn = D * n;
           for (int sp = 0; sp < 2; ++sp)
@@ -971,13 +982,15 @@ struct Runner {
         T* G1 = at<T>(pl.G1);
         T* G2 = at<T>(pl.G2);
         const int bt = ((RD + 31) / 32) * 32;
+        __nv_bfloat16* Vb = pl.Vb ? at<__nv_bfloat16>(pl.Vb) : nullptr;
         if (deriv) {
           // per-electron partial records, then ordered sums per walker
           T* AP = at<T>(pl.AP);
           mark("att_pool", 3);
           att_max_kernel<T><<<wc, 256, 0, s>>>(wc, n, n_up, R, boff, SU, ldb, AP);
           att_part_kernel<T><<<nb, bt, 0, s>>>(wc, n, n_up, K, R, dr, idx, cnt, rev, boff, SU, ldb, AP);
-          att_fin_kernel<T><<<dim3(wc, 8), bt, 0, s>>>(wc, n, R, dr, AP, V);
+          att_fin_kernel<T><<<dim3(wc, 8), bt, 0, s>>>(wc, n, R, dr, AP, V, Vb, 3,
+                                                        (int64_t)pl.Wc * (2 + 3 * (int64_t)n) * RD);
         } else {
           const size_t apsm = (size_t)(R + n * R) * sizeof(T);
           mark("att_pool", 1);
@@ -986,10 +999,19 @@ struct Runner {
         const int64_t vstride = deriv ? (2 + 3 * (int64_t)n) : 1;
         const int64_t vrows = (int64_t)wc * vstride;
         mark("att_mlp", 11);
-        mlp_readout(V, nullptr, RD, RD, nullptr, 0, vrows, vrows, nullptr, vstride, wc, p.ja1_w1, nullptr,
-                    p.ja1_b1, p.ja1_w2, nullptr, p.ja1_b2, p.ja1_w3, VZ, dm.J, VY, nullptr, dm.J, G1);
-        mlp_readout(V, nullptr, RD, RD, nullptr, 0, vrows, vrows, nullptr, vstride, wc, p.ja2_w1, nullptr,
-                    p.ja2_b1, p.ja2_w2, nullptr, p.ja2_b2, p.ja2_w3, VZ, dm.J, VY, nullptr, dm.J, G2);
+        // BF16 form: the register MLPs on the tensor cores, three components
+        // (their value rows set log|J_att| and get no fp32 recompute)
+        const int64_t JJ = dm.J;
+        const __nv_bfloat16* WBa = (Vb && WB && (tc_mask & 64) && RD % 64 == 0 && JJ % 64 == 0) ? WB : nullptr;
+        __nv_bfloat16* VYb = WBa ? at<__nv_bfloat16>(pl.VYb) : nullptr;
+        const int64_t vcap = (int64_t)pl.Wc * vstride;
+        auto wa = [&](int64_t off) -> const __nv_bfloat16* { return WBa ? WBa + off : nullptr; };
+        mlp_readout(V, WBa ? Vb : nullptr, RD, RD, nullptr, 0, vrows, vrows, nullptr, vstride, wc, p.ja1_w1,
+                    wa(pl.wb_ja1), p.ja1_b1, p.ja1_w2, wa(pl.wb_ja1 + kMaxSplit * (int64_t)RD * JJ), p.ja1_b2, p.ja1_w3,
+                    VZ, JJ, VY, VYb, JJ, G1, vcap, 3);
+        mlp_readout(V, WBa ? Vb : nullptr, RD, RD, nullptr, 0, vrows, vrows, nullptr, vstride, wc, p.ja2_w1,
+                    wa(pl.wb_ja2), p.ja2_b1, p.ja2_w2, wa(pl.wb_ja2 + kMaxSplit * (int64_t)RD * JJ), p.ja2_b2, p.ja2_w3,
+                    VZ, JJ, VY, VYb, JJ, G2, vcap, 3);
         att_reduce_kernel<T, T><<<wc, 256, 0, s>>>(n, G1, G2, p.ja1_b3, p.ja2_b3, aval, asign, agrad, alap, deriv);
       check("att");
       }

@@ -28,13 +28,14 @@ struct Plan {
   size_t S5, Y5, Z5, P5, H0, PQ;
   size_t X, big, F1, F2;   // big holds Z | SU, and O (aliased) in the det phase
   size_t Y, Xb, Yb;        // Jastrow hidden rows; bf16 copies of X and Y (BF16 form)
-  int64_t wb_mlp, wb_jm1, wb_jm2, wb_att, wb_env, wb_glu, wb_gluo, wb_msg, wb_orbv;   // element offsets inside wbf16
+  int64_t wb_mlp, wb_jm1, wb_jm2, wb_att, wb_env, wb_glu, wb_gluo, wb_msg, wb_orbv, wb_ja1, wb_ja2;   // element offsets inside wbf16
   size_t Qf, Qfb, Fenv, Hv, Ov;   // Qfb: bf16 components of Qf (BF16 form)
   size_t Y5b, P5b, H0b, Hvb;      // bf16 components of Y5, P5, H0, Hv (BF16 form)
   size_t LU, piv, ldabs, lsign, Ainv, gdet, ldet, Phif;
   size_t jval, jsign, jgrad, jlap, aval, asign, agrad, alap, cval, cgrad, clap, vpot;
   size_t V, VZ, VY, G1, G2;
   size_t AP;               // attention-pool shifts and per-electron records (local energy)
+  size_t Vb, VYb;          // bf16 components of V and of the register-MLP hidden rows (BF16 form)
   size_t wbf16;            // packed BF16 weights (tensor-core form)
   size_t poff_dev;         // device copy of the parameter offsets (gradient call)
   size_t gradws;           // gradient scratch region (GradBufs)
