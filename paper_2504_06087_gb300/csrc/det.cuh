@@ -851,4 +851,228 @@ contract2_kernel(int Wc, int n, int n_up, int K, int mlo, int mhi, int dd, int D
   }
 }
 
+// ---------------------------------------------------------------------------
+// contract2_kernel with asynchronous staging (n and the O row stride multiples
+// of 4): the raw 128-byte row slices of a chunk -- member k's three O rows,
+// its envelope row and its row of A^T, plus n''s value row and envelope
+// gradient rows -- are copied with cp.async into a raw buffer (rows of 36
+// floats, so the transform's member-strided 128-bit reads do not conflict)
+// while the previous chunk is being multiplied; a transform pass then forms
+// the T quads and the A columns of the compute layout.
+//   raw rows: O (k, x) at 3k + x; envelope k at 3 MP + k; A^T k at 4 MP + k;
+//             n' value row at 5 MP; envelope gradient x at 5 MP + 1 + x
+constexpr int kC3RawStride = 36;
+__host__ __device__ inline size_t contract3_raw_floats(int mp) { return (size_t)(5 * mp + 4) * kC3RawStride; }
+inline size_t contract3_smem_bytes(int mhi) {
+  const int mp = contract2_slots(mhi);
+  return (contract2_region(mp) + contract3_raw_floats(mp)) * 4 + (size_t)mp * 20 + 64;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 819 / NT)   // at most 80 registers
+contract3_kernel(int Wc, int n, int n_up, int K, int mlo, int mhi, int dd, int D, const int32_t* __restrict__ idx,
+                 const int32_t* __restrict__ cnt, const int32_t* __restrict__ rev,
+                 const int64_t* __restrict__ blk_off, const float* __restrict__ O, int64_t ldo,
+                 const float* __restrict__ Fenv, const float* __restrict__ AT, float* __restrict__ gdet,
+                 float* __restrict__ ldet, DevStatus* st) {
+  constexpr int LC = kC2Chunk, RS = kC3RawStride;
+  extern __shared__ __align__(16) unsigned char c3_smem[];
+  __shared__ float red[NT / 32][5];
+  const int tid = threadIdx.x;
+  const int w = blockIdx.x / n, np = blockIdx.x % n;
+  const int64_t base = (int64_t)w * n + np;
+  const int m = 1 + cnt[base * 2] + cnt[base * 2 + 1];
+  if (m < mlo || m > mhi) return;   // another bucket's launch handles this n'
+  const int MP = contract2_slots(mhi);
+  const int ST = 4 * MP + 4, SA = MP + 4;
+  float* Ts = reinterpret_cast<float*>(c3_smem);
+  float* As = Ts + LC * ST;
+  const size_t region = contract2_region(MP);
+  float* raw = Ts + region;
+  int64_t* ro = reinterpret_cast<int64_t*>(raw + ((contract3_raw_floats(MP) + 3) & ~(size_t)3));
+  int64_t* fo = ro + MP;
+  int* mi = reinterpret_cast<int*>(fo + MP);
+  const int64_t Dn = (int64_t)D * n;
+  for (int k = tid; k < m; k += NT) {
+    int i = np, slot = 0;
+    if (k > 0) {
+      i = idx[base * K + k - 1];
+      const int rv = rev[base * K + k - 1];
+      slot = rv < 0 ? -1 : rv + 1;
+      if (rv < 0) atomicExch(&st->overflow, 1);
+    }
+    const int64_t b = block_index(w, i, Wc, n, n_up);
+    mi[k] = i;
+    ro[k] = slot < 0 ? -1 : (blk_off[b] + 2 + 3 * (int64_t)slot) * ldo;
+    fo[k] = b * 5 * Dn + (int64_t)dd * n;
+  }
+  __syncthreads();
+  const float* Aw = AT + ((int64_t)w * D + dd) * n * n;
+  const int bnp = block_index(w, np, Wc, n, n_up);
+  const int64_t onp = blk_off[bnp] * ldo;
+  const int nkg = (m + 2) / 3, ncg = (m + 3) / 4, ntile = nkg * ncg;
+  const int kfill = max(3 * nkg, 4 * ncg);
+
+  // raw copies of the chunk starting at orbital c0 (zero beyond n and m)
+  const int nraw = 5 * kfill + 4;
+  auto issue = [&](int c0) {
+    for (int e = tid; e < nraw * 8; e += NT) {
+      const int q = e >> 3, j = e & 7;
+      const int l = c0 + 4 * j;
+      const float* src = O;
+      int rrow;
+      bool ok = l < n;
+      if (q < 3 * kfill) {
+        const int k = q / 3, x = q - 3 * k;
+        rrow = q;
+        ok = ok && k < m && ro[k] >= 0;
+        if (ok) src = O + ro[k] + x * ldo + l;
+      } else if (q < 4 * kfill) {
+        const int k = q - 3 * kfill;
+        rrow = 3 * MP + k;
+        ok = ok && k < m;
+        if (ok) src = Fenv + fo[k] + l;
+      } else if (q < 5 * kfill) {
+        const int k = q - 4 * kfill;
+        rrow = 4 * MP + k;
+        ok = ok && k < m;
+        if (ok) src = Aw + (int64_t)mi[k] * n + l;
+      } else {
+        const int u = q - 5 * kfill;
+        rrow = 5 * MP + u;
+        if (ok) src = u == 0 ? O + onp + l : Fenv + fo[0] + (1 + u) * Dn + l;
+      }
+      cp_async16(raw + rrow * RS + 4 * j, src, ok ? 16 : 0);
+    }
+    cp_async_commit();
+  };
+  issue(0);
+
+  // sum_l LapPhi_{n' l} A_{l n'}: the Laplacian row of n' against A's column n'
+  float lt = 0.f;
+  {
+    const int64_t fb = (int64_t)bnp * 5 * Dn + (int64_t)dd * n;
+    for (int l = tid; l < n; l += NT) {
+      const float ov = O[onp + l], olp = O[onp + ldo + l];
+      float cross = 0.f;
+      for (int x = 0; x < 3; ++x) cross += O[onp + (2 + x) * ldo + l] * Fenv[fb + (2 + x) * Dn + l];
+      const float lap = olp * Fenv[fb + l] + 2.f * cross + ov * Fenv[fb + Dn + l];
+      lt += lap * Aw[(int64_t)np * n + l];
+    }
+  }
+
+  float acc[36];
+#pragma unroll
+  for (int q = 0; q < 36; ++q) acc[q] = 0.f;
+  const bool act = tid < ntile;
+  const int kg = act ? tid / ncg : 0, cg = act ? tid - kg * ncg : 0;
+
+  for (int l0 = 0; l0 < n; l0 += LC) {
+    cp_async_wait_all();
+    __syncthreads();   // the raw chunk has landed; the previous chunk is consumed
+    for (int e = tid; e < kfill * (LC / 4); e += NT) {
+      const int k = e % kfill, q4 = e / kfill;
+      const float4 o0 = *reinterpret_cast<const float4*>(raw + (3 * k) * RS + 4 * q4);
+      const float4 o1 = *reinterpret_cast<const float4*>(raw + (3 * k + 1) * RS + 4 * q4);
+      const float4 o2 = *reinterpret_cast<const float4*>(raw + (3 * k + 2) * RS + 4 * q4);
+      const float4 ph = *reinterpret_cast<const float4*>(raw + (3 * MP + k) * RS + 4 * q4);
+      const float4 av = *reinterpret_cast<const float4*>(raw + (4 * MP + k) * RS + 4 * q4);
+      float4 t0 = make_float4(o0.x * ph.x, o0.y * ph.y, o0.z * ph.z, o0.w * ph.w);
+      float4 t1 = make_float4(o1.x * ph.x, o1.y * ph.y, o1.z * ph.z, o1.w * ph.w);
+      float4 t2 = make_float4(o2.x * ph.x, o2.y * ph.y, o2.z * ph.z, o2.w * ph.w);
+      if (k == 0) {   // n' itself: its envelope moves too
+        const float4 ov = *reinterpret_cast<const float4*>(raw + (5 * MP) * RS + 4 * q4);
+        const float4 g0 = *reinterpret_cast<const float4*>(raw + (5 * MP + 1) * RS + 4 * q4);
+        const float4 g1 = *reinterpret_cast<const float4*>(raw + (5 * MP + 2) * RS + 4 * q4);
+        const float4 g2 = *reinterpret_cast<const float4*>(raw + (5 * MP + 3) * RS + 4 * q4);
+        t0.x += ov.x * g0.x; t0.y += ov.y * g0.y; t0.z += ov.z * g0.z; t0.w += ov.w * g0.w;
+        t1.x += ov.x * g1.x; t1.y += ov.y * g1.y; t1.z += ov.z * g1.z; t1.w += ov.w * g1.w;
+        t2.x += ov.x * g2.x; t2.y += ov.y * g2.y; t2.z += ov.z * g2.z; t2.w += ov.w * g2.w;
+      }
+      float* tq = Ts + (4 * q4) * ST + 4 * k;
+      *reinterpret_cast<float4*>(tq) = make_float4(t0.x, t1.x, t2.x, 0.f);
+      *reinterpret_cast<float4*>(tq + ST) = make_float4(t0.y, t1.y, t2.y, 0.f);
+      *reinterpret_cast<float4*>(tq + 2 * ST) = make_float4(t0.z, t1.z, t2.z, 0.f);
+      *reinterpret_cast<float4*>(tq + 3 * ST) = make_float4(t0.w, t1.w, t2.w, 0.f);
+      float* aq = As + (4 * q4) * SA + k;
+      aq[0] = av.x;
+      aq[SA] = av.y;
+      aq[2 * SA] = av.z;
+      aq[3 * SA] = av.w;
+    }
+    __syncthreads();   // compute layout ready; the raw buffer is free
+    if (l0 + LC < n) issue(l0 + LC);
+    if (act) {
+      const float* tp = Ts + 12 * kg;
+      const float* ap = As + 4 * cg;
+#pragma unroll 4
+      for (int q = 0; q < LC; ++q) {
+        const float4 a0 = *reinterpret_cast<const float4*>(tp + q * ST);
+        const float4 a1 = *reinterpret_cast<const float4*>(tp + q * ST + 4);
+        const float4 a2 = *reinterpret_cast<const float4*>(tp + q * ST + 8);
+        const float4 bv = *reinterpret_cast<const float4*>(ap + q * SA);
+        const float tr9[9] = {a0.x, a0.y, a0.z, a1.x, a1.y, a1.z, a2.x, a2.y, a2.z};
+        const float bc[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+        for (int r = 0; r < 9; ++r)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[4 * r + j] = fmaf(tr9[r], bc[j], acc[4 * r + j]);
+      }
+    }
+  }
+  __syncthreads();
+  // M[(k, x)][k'] into shared memory (the staging area is free now)
+  float* Ms = Ts;
+  if (act) {
+#pragma unroll
+    for (int u = 0; u < 3; ++u)
+#pragma unroll
+      for (int x = 0; x < 3; ++x)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int k = 3 * kg + u, kp = 4 * cg + j;
+          if (k < m && kp < m) Ms[(3 * k + x) * m + kp] = acc[4 * (3 * u + x) + j];
+        }
+  }
+  __syncthreads();
+  float g0 = 0.f, g1 = 0.f, g2 = 0.f, tr = 0.f;
+  for (int k = tid; k < m; k += NT) {
+    g0 += Ms[(3 * k) * m + k];
+    g1 += Ms[(3 * k + 1) * m + k];
+    g2 += Ms[(3 * k + 2) * m + k];
+  }
+  for (int e = tid; e < m * m; e += NT) {
+    const int k = e / m, kp = e - k * m;
+#pragma unroll
+    for (int x = 0; x < 3; ++x) tr += Ms[(3 * k + x) * m + kp] * Ms[(3 * kp + x) * m + k];
+  }
+  float v[5] = {g0, g1, g2, tr, lt};
+#pragma unroll
+  for (int q = 0; q < 5; ++q)
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+  if ((tid & 31) == 0)
+#pragma unroll
+    for (int q = 0; q < 5; ++q) red[tid >> 5][q] = v[q];
+  __syncthreads();
+  if (tid == 0) {
+    float sum[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int g = 0; g < NT / 32; ++g)
+#pragma unroll
+      for (int q = 0; q < 5; ++q) sum[q] += red[g][q];
+    float* gp = gdet + (((int64_t)w * D + dd) * n + np) * 3;
+    gp[0] = sum[0];
+    gp[1] = sum[1];
+    gp[2] = sum[2];
+    ldet[((int64_t)w * D + dd) * n + np] = sum[4] - sum[3];
+  }
+}
+
 }  // namespace fire

@@ -919,8 +919,12 @@ struct Runner {
                 int lo = 1;
                 for (int q = 0; q < kC2Buckets && lo <= mcap; ++q) {
                   const int hi = mcap < kC2BucketMax[q] ? mcap : kC2BucketMax[q];
-                  auto kern = q == 0 ? contract2_kernel<64, 1> : (q == 1 ? contract2_kernel<128, 1> : contract2_kernel<320, 1>);
-                  kern<<<nb, kC2BucketThreads[q], contract2_smem_bytes(hi), s>>>(
+                  // asynchronous staging when every 128-bit row slice is aligned
+                  const bool c3 = (n % 4 == 0) && (ldo % 4 == 0) && !(cenv && strcmp(cenv, "v2") == 0);
+                  auto kern = c3 ? (q == 0 ? contract3_kernel<64> : (q == 1 ? contract3_kernel<128> : contract3_kernel<320>))
+                                 : (q == 0 ? contract2_kernel<64, 1>
+                                           : (q == 1 ? contract2_kernel<128, 1> : contract2_kernel<320, 1>));
+                  kern<<<nb, kC2BucketThreads[q], c3 ? contract3_smem_bytes(hi) : contract2_smem_bytes(hi), s>>>(
                       wc, n, n_up, K, lo, hi, dd, D, idx, cnt, rev, boff, reinterpret_cast<const float*>(Oj), ldo,
                       reinterpret_cast<const float*>(Fenv), reinterpret_cast<const float*>(Ainv),
                       reinterpret_cast<float*>(gdet), reinterpret_cast<float*>(ldet), st);
@@ -1296,6 +1300,9 @@ inline int set_smem_limits() {
   raise((const void*)contract2_kernel<64, 1>);
   raise((const void*)contract2_kernel<128, 1>);
   raise((const void*)contract2_kernel<320, 1>);
+  raise((const void*)contract3_kernel<64>);
+  raise((const void*)contract3_kernel<128>);
+  raise((const void*)contract3_kernel<320>);
   raise((const void*)lu_inverse_kernel<LT, T>);
   raise((const void*)lu_kernel<LT, 16>);
   raise((const void*)att_pool_kernel<T>);
