@@ -104,6 +104,7 @@ static size_t layout(Plan& pl, int64_t Wc) {
   TAKE(blk_rows, nb * 8);
   TAKE(blk_off, (nb + 1) * 8);
   TAKE(ranges, 8 * 8);
+  if (dm.deriv) TAKE(clist, (16 + kC3Buckets * nb) * 4); else pl.clist = 0;
   TAKE(S5, nb * R5 * d * ts);
   TAKE(Y5, nb * R5 * d * ts);
   TAKE(Z5, nb * R5 * 2 * d * ts);

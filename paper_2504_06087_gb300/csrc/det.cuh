@@ -651,7 +651,7 @@ __device__ __forceinline__ float4 ld_row4(const float* __restrict__ p, int l, in
 // stores conflict.  Neighbourhood sizes are bucketed: a CTA whose member
 // count m lies outside [mlo, mhi] exits at once, so one launch per bucket
 // sizes its tiles and shared memory for that bucket only.
-//   MP = member slots of the bucket (multiple of 12, >= mhi)
+//   MP = member slots of the bucket (>= every tile's member and column, multiple of 4)
 //   Ts [32][4 MP + 4]  T quads     As [32][MP + 4]  A values
 //   (M [3 m][m] reuses the area after the last chunk)
 constexpr int kC2Chunk = 32;
@@ -661,7 +661,13 @@ constexpr int kC2Buckets = 3;
 constexpr int kC2BucketMax[kC2Buckets] = {24, 36, 60};
 constexpr int kC2BucketThreads[kC2Buckets] = {64, 128, 320};
 constexpr int kC2BigMax = 60;
-__host__ __device__ inline int contract2_slots(int mhi) { return 12 * ((mhi + 11) / 12); }
+// member slots of a bucket: every tile's members (3 per group) and columns
+// (4 per group) of the largest m, rounded to 4 (128-bit rows)
+__host__ __device__ inline int contract2_slots(int mhi) {
+  const int a = 3 * ((mhi + 2) / 3), b = 4 * ((mhi + 3) / 4);
+  const int k = a > b ? a : b;
+  return 4 * ((k + 3) / 4);
+}
 __host__ __device__ inline size_t contract2_region(int mp) {
   const size_t st = (size_t)kC2Chunk * (4 * mp + 4) + (size_t)kC2Chunk * (mp + 4);
   const size_t mm = (size_t)3 * mp * mp;
@@ -862,6 +868,37 @@ contract2_kernel(int Wc, int n, int n_up, int K, int mlo, int mhi, int dd, int D
 //   raw rows: O (k, x) at 3k + x; envelope k at 3 MP + k; A^T k at 4 MP + k;
 //             n' value row at 5 MP; envelope gradient x at 5 MP + 1 + x
 constexpr int kC3RawStride = 36;
+// Buckets of the asynchronous form: the thread count of each is the smallest
+// multiple of 32 that gives every (3-member, 4-column) tile its own thread.
+constexpr int kC3Buckets = 5;
+constexpr int kC3BucketMax[kC3Buckets] = {27, 32, 36, 48, 60};
+constexpr int kC3BucketThreads[kC3Buckets] = {64, 96, 128, 192, 320};
+struct C3Buckets { int v[kC3Buckets]; };
+
+// Sorts the tangent electrons e = w n + n' of a chunk into the buckets by
+// their neighbourhood size m = 1 + |N_n'| (warp-aggregated atomics; the
+// order inside a bucket does not matter).
+template <int kUnused = 0>
+__global__ void contract_bucket_kernel(int nb, const int32_t* __restrict__ cnt, C3Buckets bm,
+                                       int* __restrict__ counts, int* __restrict__ lists) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool in = e < nb;
+  int b = kC3Buckets - 1;
+  if (in) {
+    const int m = 1 + cnt[2 * (int64_t)e] + cnt[2 * (int64_t)e + 1];
+    for (int q = kC3Buckets - 1; q >= 0; --q)
+      if (m <= bm.v[q]) b = q;
+  }
+  const unsigned act = __ballot_sync(0xffffffffu, in);
+  if (!in) return;
+  const unsigned same = __match_any_sync(act, b);
+  const int leader = __ffs(same) - 1;
+  const int lane = threadIdx.x & 31;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(&counts[b], __popc(same));
+  base = __shfl_sync(same, base, leader);
+  lists[(int64_t)b * nb + base + __popc(same & ((1u << lane) - 1u))] = e;
+}
 __host__ __device__ inline size_t contract3_raw_floats(int mp) { return (size_t)(5 * mp + 4) * kC3RawStride; }
 inline size_t contract3_smem_bytes(int mhi) {
   const int mp = contract2_slots(mhi);
@@ -882,12 +919,14 @@ contract3_kernel(int Wc, int n, int n_up, int K, int mlo, int mhi, int dd, int D
                  const int32_t* __restrict__ cnt, const int32_t* __restrict__ rev,
                  const int64_t* __restrict__ blk_off, const float* __restrict__ O, int64_t ldo,
                  const float* __restrict__ Fenv, const float* __restrict__ AT, float* __restrict__ gdet,
-                 float* __restrict__ ldet, DevStatus* st) {
+                 float* __restrict__ ldet, DevStatus* st, const int* __restrict__ list) {
   constexpr int LC = kC2Chunk, RS = kC3RawStride;
   extern __shared__ __align__(16) unsigned char c3_smem[];
   __shared__ float red[NT / 32][5];
   const int tid = threadIdx.x;
-  const int w = blockIdx.x / n, np = blockIdx.x % n;
+  // CTA -> tangent electron: from the bucket list, else blockIdx = w n + n'
+  const int e0 = list ? list[blockIdx.x] : (int)blockIdx.x;
+  const int w = e0 / n, np = e0 % n;
   const int64_t base = (int64_t)w * n + np;
   const int m = 1 + cnt[base * 2] + cnt[base * 2 + 1];
   if (m < mlo || m > mhi) return;   // another bucket's launch handles this n'

@@ -676,6 +676,22 @@ struct Runner {
                                                                         brow, st, deriv);
       nbr_reverse_kernel<<<wc, 256, 0, s>>>(n, n_up, K, idx, cnt, rev);
       blk_scan_kernel<<<1, 1024, 0, s>>>(nb, wc * n_up, brow, boff, rng, st);
+      // float forms with aligned rows: the tangent electrons sorted into the
+      // contraction buckets by neighbourhood size
+      const char* cenv = getenv("FIRE_CONTRACT");
+      const bool c3 = sizeof(T) == 4 && deriv && pl.clist && n % 4 == 0 &&
+                      !(cenv && (strcmp(cenv, "v1") == 0 || strcmp(cenv, "v2") == 0));
+      int* ccount = pl.clist ? at<int>(pl.clist) : nullptr;
+      int* clists = pl.clist ? ccount + 16 : nullptr;
+      int hcount[kC3Buckets] = {0};
+      if (c3) {
+        cudaMemsetAsync(ccount, 0, 16 * sizeof(int), s);
+        C3Buckets bm;
+        for (int q = 0; q < kC3Buckets; ++q) bm.v[q] = kC3BucketMax[q];
+        contract_bucket_kernel<0><<<(nb + 255) / 256, 256, 0, s>>>(nb, cnt, bm, ccount, clists);
+        cudaMemcpyAsync(hcount, ccount, sizeof(hcount), cudaMemcpyDeviceToHost, s);
+        launches += 1;
+      }
       check("nbr");
       // the chunk's row total and largest neighbour count, read back once:
       // they size the grids and the contraction tiles exactly
@@ -881,7 +897,6 @@ struct Runner {
         // float forms: the bucketed small-CTA contraction for neighbourhoods
         // of up to 60 members; FIRE_CONTRACT=v1 keeps the 256-thread kernel
         // (diagnostic)
-        const char* cenv = getenv("FIRE_CONTRACT");
         const bool c2 = sizeof(T) == 4 && mcap <= kC2BigMax && !(cenv && strcmp(cenv, "v1") == 0);
         // orbital rows of G determinants per product (BF16 form: one slice of
         // the packed [D n][d] weights of a spin, so X is read D / G times)
@@ -914,17 +929,32 @@ struct Runner {
             const T* Oj = O + (int64_t)j * n;
             mark("contract", 1);
             if constexpr (sizeof(T) == 4) {
+              if (c3 && c2) {
+                // one launch per non-empty bucket, over exactly its electrons
+                for (int q = 0; q < kC3Buckets; ++q) {
+                  if (hcount[q] <= 0) continue;
+                  auto kern = q == 0 ? contract3_kernel<64>
+                                     : (q == 1 ? contract3_kernel<96>
+                                               : (q == 2 ? contract3_kernel<128>
+                                                         : (q == 3 ? contract3_kernel<192> : contract3_kernel<320>)));
+                  kern<<<hcount[q], kC3BucketThreads[q], contract3_smem_bytes(kC3BucketMax[q]), s>>>(
+                      wc, n, n_up, K, 1, kC3BucketMax[q], dd, D, idx, cnt, rev, boff,
+                      reinterpret_cast<const float*>(Oj), ldo, reinterpret_cast<const float*>(Fenv),
+                      reinterpret_cast<const float*>(Ainv), reinterpret_cast<float*>(gdet),
+                      reinterpret_cast<float*>(ldet), st, clists + (int64_t)q * nb);
+                  launches += 1;
+                }
+                check("contract");
+                continue;
+              }
               if (c2) {
                 // one launch per neighbourhood-size bucket that the chunk reaches
                 int lo = 1;
                 for (int q = 0; q < kC2Buckets && lo <= mcap; ++q) {
                   const int hi = mcap < kC2BucketMax[q] ? mcap : kC2BucketMax[q];
-                  // asynchronous staging when every 128-bit row slice is aligned
-                  const bool c3 = (n % 4 == 0) && (ldo % 4 == 0) && !(cenv && strcmp(cenv, "v2") == 0);
-                  auto kern = c3 ? (q == 0 ? contract3_kernel<64> : (q == 1 ? contract3_kernel<128> : contract3_kernel<320>))
-                                 : (q == 0 ? contract2_kernel<64, 1>
-                                           : (q == 1 ? contract2_kernel<128, 1> : contract2_kernel<320, 1>));
-                  kern<<<nb, kC2BucketThreads[q], c3 ? contract3_smem_bytes(hi) : contract2_smem_bytes(hi), s>>>(
+                  auto kern = q == 0 ? contract2_kernel<64, 1>
+                                     : (q == 1 ? contract2_kernel<128, 1> : contract2_kernel<320, 1>);
+                  kern<<<nb, kC2BucketThreads[q], contract2_smem_bytes(hi), s>>>(
                       wc, n, n_up, K, lo, hi, dd, D, idx, cnt, rev, boff, reinterpret_cast<const float*>(Oj), ldo,
                       reinterpret_cast<const float*>(Fenv), reinterpret_cast<const float*>(Ainv),
                       reinterpret_cast<float*>(gdet), reinterpret_cast<float*>(ldet), st);
@@ -1301,7 +1331,9 @@ inline int set_smem_limits() {
   raise((const void*)contract2_kernel<128, 1>);
   raise((const void*)contract2_kernel<320, 1>);
   raise((const void*)contract3_kernel<64>);
+  raise((const void*)contract3_kernel<96>);
   raise((const void*)contract3_kernel<128>);
+  raise((const void*)contract3_kernel<192>);
   raise((const void*)contract3_kernel<320>);
   raise((const void*)lu_inverse_kernel<LT, T>);
   raise((const void*)lu_kernel<LT, 16>);

@@ -25,6 +25,7 @@ struct Plan {
   int64_t rows_per_el;     // upper bound of rows per electron block
   size_t tsz, lsz;         // element sizes of the compute and LU types
   size_t status, idx, cnt, rev, blk_rows, blk_off, ranges;
+  size_t clist;            // contraction bucket counters and lists (local energy)
   size_t S5, Y5, Z5, P5, H0, PQ;
   size_t X, big, F1, F2;   // big holds Z | SU, and O (aliased) in the det phase
   size_t Y, Xb, Yb;        // Jastrow hidden rows; bf16 copies of X and Y (BF16 form)
