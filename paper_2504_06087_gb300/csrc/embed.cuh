@@ -483,6 +483,65 @@ __global__ void fl_act_kernel(int ncol, const int64_t* __restrict__ off, int64_t
   }
 }
 
+// The last activation of a readout MLP fused with its readout vector:
+// F[q] = sum_c SiLU-layer(Z + b)[q][c] * wv[c] for every row q of every block
+// (same forward-Laplacian rules as fl_act_kernel), without storing the
+// activated rows.  One CTA per block, threads over the columns; the per-row
+// sums go through warp shuffles and a [warps][rows] shared array, summed in
+// warp order.  Dynamic shared memory: (blockDim / 32) * max_rows floats.
+template <typename T, typename W>
+__global__ void fl_act_dot_kernel(int ncol, const int64_t* __restrict__ off, int64_t stride,
+                                  const T* __restrict__ Z, int64_t ldz, const W* bias, const W* wv,
+                                  T* __restrict__ F, int max_rows) {
+  extern __shared__ unsigned char fd_smem[];
+  T* red = reinterpret_cast<T*>(fd_smem);
+  const int b = blockIdx.x;
+  int64_t r0, r1;
+  if (off) { r0 = off[b]; r1 = off[b + 1]; }
+  else { r0 = (int64_t)b * stride; r1 = r0 + stride; }
+  const int nr = (int)(r1 - r0);
+  if (nr <= 0) return;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // per-thread column partials of every row, reduced per warp as we go
+  auto emit = [&](int rl, T part) {
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane == 0) red[wid * max_rows + rl] = part;
+  };
+  // columns in passes of blockDim (one column per thread per pass)
+  for (int c0 = 0; c0 < ncol; c0 += blockDim.x) {
+    const int c = c0 + threadIdx.x;
+    const bool in = c < ncol;
+    T f = T(0), f1 = T(0), f2 = T(0), w = T(0);
+    if (in) {
+      const T z = Z[r0 * ldz + c] + (bias ? T(bias[c]) : T(0));
+      silu3<T>(z, f, f1, f2);
+      w = T(wv[c]);
+    }
+    T sq = T(0);
+    for (int q = 2; q < nr; ++q) {
+      const T zt = in ? Z[(r0 + q) * ldz + c] : T(0);
+      sq += zt * zt;
+      T part = f1 * zt * w;
+      if (c0 > 0) part += red[wid * max_rows + q] * (lane == 0 ? T(1) : T(0));
+      emit(q, part);
+    }
+    if (nr > 1) {
+      T part = (in ? (f1 * Z[(r0 + 1) * ldz + c] + f2 * sq) : T(0)) * w;
+      if (c0 > 0) part += red[wid * max_rows + 1] * (lane == 0 ? T(1) : T(0));
+      emit(1, part);
+    }
+    T part = f * w;
+    if (c0 > 0) part += red[wid * max_rows] * (lane == 0 ? T(1) : T(0));
+    emit(0, part);
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < nr; q += blockDim.x) {
+    T sum = T(0);
+    for (int g = 0; g < nw; ++g) sum += red[g * max_rows + q];
+    F[r0 + q] = sum;
+  }
+}
+
 // out[row] = Y[row] . w for rows [r_begin, r_end) (device range or host).
 template <typename T, typename W>
 __global__ void rowdot_kernel(const T* __restrict__ Y, int64_t ldy, int ncol, const W* wv,

@@ -276,9 +276,10 @@ struct Runner {
     row_gemm(Xin, Xinb, ldx, a_rows, w1, w1b, J, Z, ldz, range, rb, re, cap, J, din, nc);
     fl_act_kernel<T, T><<<nblk, 256, 0, s>>>(J, off, stride, Z, ldz, b1, Y, ldy, 0, Yb, nc, a_rows * ldy);
     row_gemm(Y, Yb, ldy, a_rows, w2, w2b, J, Z, ldz, range, rb, re, cap, J, J, nc);
-    fl_act_kernel<T, T><<<nblk, 256, 0, s>>>(J, off, stride, Z, ldz, b2, Y, ldy, 0);
-    const int64_t nrows_grid = cap;
-    rowdot_kernel<T, T><<<(unsigned)((nrows_grid + 7) / 8), 256, 0, s>>>(Y, ldy, J, w3, F, range, rb, re);
+    // last activation fused with the readout vector: F = act(Z + b2) . w3
+    const int max_rows = off ? (int)pl.rows_per_el : (int)stride;
+    fl_act_dot_kernel<T, T><<<nblk, 256, (size_t)8 * max_rows * sizeof(T), s>>>(J, off, stride, Z, ldz, b2, w3, F,
+                                                                               max_rows);
   }
 
 
