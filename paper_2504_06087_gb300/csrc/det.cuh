@@ -843,15 +843,16 @@ contract2_kernel(int Wc, int n, int n_up, int K, int mlo, int mhi, int dd, int D
 
 // ---------------------------------------------------------------------------
 // contract2_kernel with asynchronous staging (n and the O row stride multiples
-// of 4): the raw 128-byte row slices of a chunk -- member k's three O rows,
+// of 4) and 16-orbital chunks: the raw 64-byte row slices of a chunk -- member k's three O rows,
 // its envelope row and its row of A^T, plus n''s value row and envelope
-// gradient rows -- are copied with cp.async into a raw buffer (rows of 36
+// gradient rows -- are copied with cp.async into a raw buffer (rows of 20
 // floats, so the transform's member-strided 128-bit reads do not conflict)
 // while the previous chunk is being multiplied; a transform pass then forms
 // the T quads and the A columns of the compute layout.
 //   raw rows: O (k, x) at 3k + x; envelope k at 3 MP + k; A^T k at 4 MP + k;
 //             n' value row at 5 MP; envelope gradient x at 5 MP + 1 + x
-constexpr int kC3RawStride = 36;
+constexpr int kC3Chunk = 16;       // orbitals per chunk (small buffers: more CTAs per SM)
+constexpr int kC3RawStride = 20;   // raw row: 16 floats + 4 pad (member-strided reads do not conflict)
 // Buckets of the asynchronous form: the thread count of each is the smallest
 // multiple of 32 that gives every (3-member, 4-column) tile its own thread.
 constexpr int kC3Buckets = 5;
@@ -884,9 +885,14 @@ __global__ void contract_bucket_kernel(int nb, const int32_t* __restrict__ cnt, 
   lists[(int64_t)b * nb + base + __popc(same & ((1u << lane) - 1u))] = e;
 }
 __host__ __device__ inline size_t contract3_raw_floats(int mp) { return (size_t)(5 * mp + 4) * kC3RawStride; }
+__host__ __device__ inline size_t contract3_region(int mp) {
+  const size_t st = (size_t)kC3Chunk * (4 * mp + 4) + (size_t)kC3Chunk * (mp + 4);
+  const size_t mm = (size_t)3 * mp * mp;
+  return st > mm ? st : mm;
+}
 inline size_t contract3_smem_bytes(int mhi) {
   const int mp = contract2_slots(mhi);
-  return (contract2_region(mp) + contract3_raw_floats(mp)) * 4 + (size_t)mp * 20 + 64;
+  return (contract3_region(mp) + contract3_raw_floats(mp)) * 4 + (size_t)mp * 20 + 64;
 }
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
@@ -904,7 +910,7 @@ contract3_kernel(int Wc, int n, int n_up, int K, int mlo, int mhi, int dd, int D
                  const int64_t* __restrict__ blk_off, const float* __restrict__ O, int64_t ldo,
                  const float* __restrict__ Fenv, const float* __restrict__ AT, float* __restrict__ gdet,
                  float* __restrict__ ldet, DevStatus* st, const int* __restrict__ list) {
-  constexpr int LC = kC2Chunk, RS = kC3RawStride;
+  constexpr int LC = kC3Chunk, RS = kC3RawStride, NJ = LC / 4;
   extern __shared__ __align__(16) unsigned char c3_smem[];
   __shared__ float red[NT / 32][5];
   const int tid = threadIdx.x;
@@ -918,7 +924,7 @@ contract3_kernel(int Wc, int n, int n_up, int K, int mlo, int mhi, int dd, int D
   const int ST = 4 * MP + 4, SA = MP + 4;
   float* Ts = reinterpret_cast<float*>(c3_smem);
   float* As = Ts + LC * ST;
-  const size_t region = contract2_region(MP);
+  const size_t region = contract3_region(MP);
   float* raw = Ts + region;
   int64_t* ro = reinterpret_cast<int64_t*>(raw + ((contract3_raw_floats(MP) + 3) & ~(size_t)3));
   int64_t* fo = ro + MP;
@@ -947,8 +953,8 @@ contract3_kernel(int Wc, int n, int n_up, int K, int mlo, int mhi, int dd, int D
   // raw copies of the chunk starting at orbital c0 (zero beyond n and m)
   const int nraw = 5 * kfill + 4;
   auto issue = [&](int c0) {
-    for (int e = tid; e < nraw * 8; e += NT) {
-      const int q = e >> 3, j = e & 7;
+    for (int e = tid; e < nraw * NJ; e += NT) {
+      const int q = e / NJ, j = e - q * NJ;
       const int l = c0 + 4 * j;
       const float* src = O;
       int rrow;
