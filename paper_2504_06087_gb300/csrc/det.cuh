@@ -81,8 +81,9 @@ template <typename LT, int NB>
 __global__ void lu_kernel(int n, LT* __restrict__ M, int32_t* __restrict__ piv,
                           double* __restrict__ logabs, double* __restrict__ sgn) {
   extern __shared__ unsigned char lu_smem[];
-  LT* P = reinterpret_cast<LT*>(lu_smem);      // [n][NB]
-  LT* U = P + (int64_t)n * NB;                 // [NB][n]
+  constexpr int PS = NB + 1;                   // panel row stride: rows fall in different banks
+  LT* P = reinterpret_cast<LT*>(lu_smem);      // [n][NB + 1]
+  LT* U = P + (int64_t)n * PS;                 // [NB][n]
   __shared__ double red_v[32];
   __shared__ int red_i[32];
   __shared__ int s_piv;
@@ -96,7 +97,7 @@ __global__ void lu_kernel(int n, LT* __restrict__ M, int32_t* __restrict__ piv,
     const int pr = n - k0;  // panel rows
     for (int e = tid; e < pr * nb; e += bd) {
       const int r = e / nb, c = e % nb;
-      P[r * NB + c] = A[(int64_t)(k0 + r) * n + k0 + c];
+      P[r * PS + c] = A[(int64_t)(k0 + r) * n + k0 + c];
     }
     __syncthreads();
     for (int kk = 0; kk < nb; ++kk) {
@@ -104,7 +105,7 @@ __global__ void lu_kernel(int n, LT* __restrict__ M, int32_t* __restrict__ piv,
       double best = -1.0;
       int bi = kk;
       for (int r = kk + tid; r < pr; r += bd) {
-        double v = fabs((double)P[r * NB + kk]);
+        double v = fabs((double)P[r * PS + kk]);
         if (v > best) { best = v; bi = r; }
       }
       for (int o = 16; o > 0; o >>= 1) {
@@ -127,18 +128,18 @@ __global__ void lu_kernel(int n, LT* __restrict__ M, int32_t* __restrict__ piv,
       const int p = s_piv;
       if (p != kk) {
         for (int c = tid; c < nb; c += bd) {
-          LT t = P[kk * NB + c];
-          P[kk * NB + c] = P[p * NB + c];
-          P[p * NB + c] = t;
+          LT t = P[kk * PS + c];
+          P[kk * PS + c] = P[p * PS + c];
+          P[p * PS + c] = t;
         }
       }
       __syncthreads();
-      const LT pivot = P[kk * NB + kk];
+      const LT pivot = P[kk * PS + kk];
       if (pivot != LT(0)) {
         for (int r = kk + 1 + tid; r < pr; r += bd) {
-          LT l = P[r * NB + kk] / pivot;
-          P[r * NB + kk] = l;
-          for (int c = kk + 1; c < nb; ++c) P[r * NB + c] -= l * P[kk * NB + c];
+          LT l = P[r * PS + kk] / pivot;
+          P[r * PS + kk] = l;
+          for (int c = kk + 1; c < nb; ++c) P[r * PS + c] -= l * P[kk * PS + c];
         }
       }
       __syncthreads();
@@ -146,7 +147,7 @@ __global__ void lu_kernel(int n, LT* __restrict__ M, int32_t* __restrict__ piv,
     // panel back to global
     for (int e = tid; e < pr * nb; e += bd) {
       const int r = e / nb, c = e % nb;
-      A[(int64_t)(k0 + r) * n + k0 + c] = P[r * NB + c];
+      A[(int64_t)(k0 + r) * n + k0 + c] = P[r * PS + c];
     }
     // row swaps of this panel on the columns outside it
     for (int kk = 0; kk < nb; ++kk) {
@@ -169,7 +170,7 @@ __global__ void lu_kernel(int n, LT* __restrict__ M, int32_t* __restrict__ piv,
       for (int kk = 0; kk < NB; ++kk) {
         if (kk < nb) {
           LT s = A[(int64_t)(k0 + kk) * n + j];
-          for (int q = 0; q < kk; ++q) s -= P[kk * NB + q] * u[q];
+          for (int q = 0; q < kk; ++q) s -= P[kk * PS + q] * u[q];
           u[kk] = s;
           A[(int64_t)(k0 + kk) * n + j] = s;
           U[kk * n + j] = s;
@@ -182,7 +183,7 @@ __global__ void lu_kernel(int n, LT* __restrict__ M, int32_t* __restrict__ piv,
     for (int e = tid; e < rows2 * cols2; e += bd) {
       const int r = c0 + e / cols2, j = c0 + e % cols2;
       LT s = A[(int64_t)r * n + j];
-      const LT* lrow = P + (int64_t)(r - k0) * NB;
+      const LT* lrow = P + (int64_t)(r - k0) * PS;
       for (int kk = 0; kk < nb; ++kk) s -= lrow[kk] * U[kk * n + j];
       A[(int64_t)r * n + j] = s;
     }
@@ -208,6 +209,9 @@ __global__ void lu_kernel(int n, LT* __restrict__ M, int32_t* __restrict__ piv,
     }
   }
 }
+
+// Dynamic shared memory of lu_kernel<LT, 16>: the panel [n][17] and U12 [16][n].
+inline size_t lu_smem_bytes(int n, size_t lsz) { return (size_t)(2 * 16 + 1) * n * lsz; }
 
 // A = Phi^-1 from the LU factors: column j of A solves L U x = e_{pinv[j]}.
 // One CTA per matrix, one thread per column, x kept in shared memory; the

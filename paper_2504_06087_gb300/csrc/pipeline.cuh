@@ -428,7 +428,7 @@ struct Runner {
       double* lsign = at<double>(pl.lsign);
       const bool gj = use_gj && sizeof(T) == 4 && n <= 192;
       phi_assemble_kernel<T, LT><<<wc * D, 256, 0, s>>>(wc, n, n_up, D, Ov, Fenv, 1, LUb, gj ? B.Phif : nullptr);
-      lu_kernel<LT, 16><<<wc * D, 256, (size_t)2 * n * 16 * sizeof(LT), s>>>(n, LUb, piv, ldabs, lsign);
+      lu_kernel<LT, 16><<<wc * D, 256, lu_smem_bytes(n, sizeof(LT)), s>>>(n, LUb, piv, ldabs, lsign);
       if (gj) {
         gj_inverse_kernel<float, T><<<wc * D, gj_threads(n), gj_smem_bytes(n), s>>>(n, B.Phif, B.AT);
       } else {
@@ -847,7 +847,7 @@ struct Runner {
         convert_kernel<LT, T><<<1024, 256, 0, s>>>((int64_t)wc * D * n * n, LUb, at<T>(pl.PhiS));
         launches += 1;
       }
-      const size_t lusm = (size_t)2 * n * 16 * sizeof(LT);
+      const size_t lusm = lu_smem_bytes(n, sizeof(LT));
       // slogdet: when the inverse does not come from these factors (float
       // forms: Gauss-Jordan on a float copy of Phi; value-only calls), the
       // float64 LU runs on a second stream, beside the Jastrow factors and the
