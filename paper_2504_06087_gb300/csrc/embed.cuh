@@ -438,7 +438,7 @@ __global__ void msg_kernel(int Wc, int n, int n_up, int d, int K, const double* 
 // Block b spans rows off[b] .. off[b+1]-1 (or b*stride .. if off == nullptr).
 // One CTA per block; threads stride over the ncol columns.
 template <typename T, typename W>
-__global__ void fl_act_kernel(int ncol, const int64_t* __restrict__ off, int64_t stride,
+__global__ void __launch_bounds__(256, 4) fl_act_kernel(int ncol, const int64_t* __restrict__ off, int64_t stride,
                               const T* __restrict__ Z, int64_t ldz, const W* bias,
                               T* __restrict__ Y, int64_t ldy, int residual,
                               __nv_bfloat16* __restrict__ Yb = nullptr, int ync = 1, int64_t ycs = 0) {
