@@ -213,22 +213,6 @@ __device__ __forceinline__ void store_split_bf16(__nv_bfloat16* p, int64_t cstri
   }
 }
 
-// Four consecutive shared-memory elements (16-byte aligned for float).
-template <typename T>
-struct Quad { T v[4]; };
-template <typename T>
-__device__ __forceinline__ Quad<T> lds4(const T* p) {
-  Quad<T> q;
-  if constexpr (sizeof(T) == 4) {
-    const float4 f = *reinterpret_cast<const float4*>(p);
-    q.v[0] = f.x; q.v[1] = f.y; q.v[2] = f.z; q.v[3] = f.w;
-  } else {
-    const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
-    q.v[0] = a.x; q.v[1] = a.y; q.v[2] = b.x; q.v[3] = b.y;
-  }
-  return q;
-}
-
 constexpr int kMaxSplit = 3;
 
 __device__ __forceinline__ int block_index(int w, int i, int Wc, int n, int n_up) {

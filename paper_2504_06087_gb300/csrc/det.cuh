@@ -434,6 +434,22 @@ inline size_t contract_smem_bytes(int mcap, size_t tsz) {
 
 inline size_t gj_smem_bytes(int n) { return (size_t)n * n * 4 + 1024 * 4 + 768 * 4 + 128 * 4; }
 
+// Four consecutive shared-memory elements (16-byte aligned for float).
+template <typename T>
+struct Quad { T v[4]; };
+template <typename T>
+__device__ __forceinline__ Quad<T> lds4(const T* p) {
+  Quad<T> q;
+  if constexpr (sizeof(T) == 4) {
+    const float4 f = *reinterpret_cast<const float4*>(p);
+    q.v[0] = f.x; q.v[1] = f.y; q.v[2] = f.z; q.v[3] = f.w;
+  } else {
+    const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+    q.v[0] = a.x; q.v[1] = a.y; q.v[2] = b.x; q.v[3] = b.y;
+  }
+  return q;
+}
+
 // Gradient and Laplacian of log det Phi_d restricted to the neighbourhoods.
 // One CTA per (walker, tangent electron n').  O holds h W_d for every row of
 // the forward-Laplacian blocks ([rows][n], row stride ldo); Fenv the envelope rows

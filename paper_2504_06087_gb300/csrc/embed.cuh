@@ -58,44 +58,6 @@ __device__ __forceinline__ FL3<T> pair_feature(int k, const T dv[3], T r, const 
 // Pairs whose filter features are computed together (one barrier pair per
 // batch instead of per pair).
 constexpr int kPairBatch = 8;
-constexpr int kFeat = kEdgeHidden + kGauss + 4;   // features of one pair
-
-// The filter features of a batch of pairs, component-major (0 value,
-// 1 Laplacian, 2..4 tangents), so four consecutive features of one component
-// load as one 128-bit word.
-template <typename T>
-struct FeatBatch {
-  T c[kPairBatch][5][kFeat];
-};
-template <typename T>
-__device__ __forceinline__ void feat_store(FeatBatch<T>& fb, int q, int k, const FL3<T>& o) {
-  fb.c[q][0][k] = o.v;
-  fb.c[q][1][k] = o.l;
-  fb.c[q][2][k] = o.t[0];
-  fb.c[q][3][k] = o.t[1];
-  fb.c[q][4][k] = o.t[2];
-}
-// out += sum_{j < NK} feature (k0 + j) of pair q * wgt[j]   (k0, NK multiples of 4)
-template <typename T, int NK>
-__device__ __forceinline__ void feat_dot(const FeatBatch<T>& fb, int q, int k0, const T (&wgt)[NK], FL3<T>& out) {
-#pragma unroll
-  for (int k = 0; k < NK; k += 4) {
-    const Quad<T> av = lds4<T>(&fb.c[q][0][k0 + k]);
-    const Quad<T> al = lds4<T>(&fb.c[q][1][k0 + k]);
-    const Quad<T> a0 = lds4<T>(&fb.c[q][2][k0 + k]);
-    const Quad<T> a1 = lds4<T>(&fb.c[q][3][k0 + k]);
-    const Quad<T> a2 = lds4<T>(&fb.c[q][4][k0 + k]);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const T wv = wgt[k + u];
-      out.v += av.v[u] * wv;
-      out.l += al.v[u] * wv;
-      out.t[0] += a0.v[u] * wv;
-      out.t[1] += a1.v[u] * wv;
-      out.t[2] += a2.v[u] * wv;
-    }
-  }
-}
 // Largest nucleus count of the batched electron-nucleus filter.
 constexpr int kMaxNuc = 512;
 
@@ -121,7 +83,7 @@ __global__ void en_filter_kernel(int Wc, int n, int n_up, int N, int d, const do
   acc.t[0] = acc.t[1] = acc.t[2] = T(0);
   const double* ri = r + ((int64_t)w * n + i) * 3;
   // nuclei within c_n (Gamma_m vanishes identically beyond), ascending
-  __shared__ __align__(16) FeatBatch<T> featb;
+  __shared__ FL3<T> featb[kPairBatch][H + G + 4];
   __shared__ T s_dv[kPairBatch][3], s_r[kPairBatch];
   __shared__ int s_m[kPairBatch];
   __shared__ int s_list[kMaxNuc];
@@ -159,22 +121,43 @@ __global__ void en_filter_kernel(int Wc, int n, int n_up, int N, int d, const do
     for (int e = threadIdx.x; e < nbat * (H + G + 4); e += blockDim.x) {
       const int q = e / (H + G + 4), k = e - q * (H + G + 4);
       const int m = s_m[q];
-      feat_store(featb, q, k,
-                 pair_feature<T, W>(k, s_dv[q], s_r[q], p.en_w1 + (int64_t)m * 4 * H, p.en_b1 + (int64_t)m * H,
-                                    p.en_sigma, T(cnuc)));
+      featb[q][k] = pair_feature<T, W>(k, s_dv[q], s_r[q], p.en_w1 + (int64_t)m * 4 * H, p.en_b1 + (int64_t)m * H,
+                                       p.en_sigma, T(cnuc));
     }
     __syncthreads();
     for (int q = 0; q < nbat; ++q) {
       const int m = s_m[q];
+      const FL3<T>* feat = featb[q];
     FL3<T> gv, ev, fv;
     gv.v = gv.l = ev.v = ev.l = T(0);
     fv.v = T(p.nuc_emb[(int64_t)m * d + c]);
     fv.l = T(0);
 #pragma unroll
     for (int t = 0; t < 3; ++t) gv.t[t] = ev.t[t] = fv.t[t] = T(0);
-    feat_dot<T, H>(featb, q, 0, w2, gv);
-    feat_dot<T, G>(featb, q, H, we, ev);
-    feat_dot<T, 4>(featb, q, H + G, wf, fv);
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+      const FL3<T> a = feat[h];
+      gv.v += a.v * w2[h];
+      gv.l += a.l * w2[h];
+#pragma unroll
+      for (int t = 0; t < 3; ++t) gv.t[t] += a.t[t] * w2[h];
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const FL3<T> a = feat[H + g];
+      ev.v += a.v * we[g];
+      ev.l += a.l * we[g];
+#pragma unroll
+      for (int t = 0; t < 3; ++t) ev.t[t] += a.t[t] * we[g];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const FL3<T> a = feat[H + G + k];
+      fv.v += a.v * wf[k];
+      fv.l += a.l * wf[k];
+#pragma unroll
+      for (int t = 0; t < 3; ++t) fv.t[t] += a.t[t] * wf[k];
+    }
     FL3<T> gam, term;
     fl3_mul(gv, ev, gam);
     fl3_mul(gam, fv, term);
@@ -345,7 +328,7 @@ __global__ void msg_kernel(int Wc, int n, int n_up, int d, int K, const double* 
   const int cpar = cnt[((int64_t)w * n + i) * 2], ctot = cpar + cnt[((int64_t)w * n + i) * 2 + 1];
   const double* rw = r + (int64_t)w * n * 3;
   const int32_t* li = idx + ((int64_t)w * n + i) * K;
-  __shared__ __align__(16) FeatBatch<T> featb;
+  __shared__ FL3<T> featb[kPairBatch][H + G + 4];
   __shared__ T s_dv[kPairBatch][3], s_r[kPairBatch];
   for (int b0 = 0; b0 < ctot; b0 += kPairBatch) {
     const int nbat = min(kPairBatch, ctot - b0);
@@ -361,35 +344,48 @@ __global__ void msg_kernel(int Wc, int n, int n_up, int d, int K, const double* 
     __syncthreads();
     for (int e = threadIdx.x; e < nbat * (H + G + 4); e += blockDim.x) {
       const int q = e / (H + G + 4), k = e - q * (H + G + 4);
-      feat_store(featb, q, k, pair_feature<T, W>(k, s_dv[q], s_r[q], p.ee_w1, p.ee_b1, p.ee_sigma, T(cut)));
+      featb[q][k] = pair_feature<T, W>(k, s_dv[q], s_r[q], p.ee_w1, p.ee_b1, p.ee_sigma, T(cut));
     }
     __syncthreads();
   for (int s = b0; s < b0 + nbat; ++s) {
     const int j = li[s];
     const int a = (s < cpar) ? 0 : 1;
-    const int qb = s - b0;
+    const FL3<T>* feat = featb[s - b0];
     // Gamma(e_ij) in delta-space (delta = r_i - r_j)
     FL3<T> gv, ev, gam;
     gv.v = gv.l = ev.v = ev.l = T(0);
 #pragma unroll
     for (int t = 0; t < 3; ++t) gv.t[t] = ev.t[t] = T(0);
-    feat_dot<T, H>(featb, qb, 0, w2, gv);
-    feat_dot<T, G>(featb, qb, H, we, ev);
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+      const FL3<T> q = feat[h];
+      gv.v += q.v * w2[h];
+      gv.l += q.l * w2[h];
+#pragma unroll
+      for (int t = 0; t < 3; ++t) gv.t[t] += q.t[t] * w2[h];
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const FL3<T> q = feat[H + g];
+      ev.v += q.v * we[g];
+      ev.l += q.l * we[g];
+#pragma unroll
+      for (int t = 0; t < 3; ++t) ev.t[t] += q.t[t] * we[g];
+    }
     fl3_mul(gv, ev, gam);
     // z = P_i + Q_j + e-bar_ij W_c + b ; tangents in r_i and r_j
     const int bj = block_index(w, j, Wc, n, n_up);
     const int64_t prow = hrow, qrow = (int64_t)bj * R5;
     const int64_t pcol = (int64_t)a * d + c, qcol = 2 * (int64_t)d + (int64_t)a * d + c;
-    FL3<T> eb;
-    eb.v = eb.l = eb.t[0] = eb.t[1] = eb.t[2] = T(0);
-    {
-      T wca[4];
+    T ebv = T(0), ebt[3] = {T(0), T(0), T(0)}, ebl = T(0);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) wca[k] = a ? wc[1][k] : wc[0][k];
-      feat_dot<T, 4>(featb, qb, H + G, wca, eb);
+    for (int k = 0; k < 4; ++k) {
+      const FL3<T> q = feat[H + G + k];
+      ebv += q.v * wc[a][k];
+      ebl += q.l * wc[a][k];
+#pragma unroll
+      for (int t = 0; t < 3; ++t) ebt[t] += q.t[t] * wc[a][k];
     }
-    const T ebv = eb.v, ebl = eb.l;
-    const T ebt[3] = {eb.t[0], eb.t[1], eb.t[2]};
     T zv = PQ[prow * ld4 + pcol] + PQ[qrow * ld4 + qcol] + ebv + bb[a];
     T f, f1, f2;
     silu3<T>(zv, f, f1, f2);
