@@ -341,11 +341,13 @@ cudaStream_t side_stream() {
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
   std::lock_guard<std::mutex> lk(mu);
   if (!streams[dev]) {
-    // highest priority: its few long CTAs (the float64 LU) are scheduled as
-    // soon as an SM has room, the caller's stream fills the rest
+    // FIRE_SIDE_PRIORITY=high (diagnostic): the greatest stream priority;
+    // default: the same priority as an ordinary stream
     int least = 0, greatest = 0;
     cudaDeviceGetStreamPriorityRange(&least, &greatest);
-    if (cudaStreamCreateWithPriority(&streams[dev], cudaStreamNonBlocking, greatest) != cudaSuccess)
+    const char* e = getenv("FIRE_SIDE_PRIORITY");
+    const int prio = (e && strcmp(e, "high") == 0) ? greatest : least;
+    if (cudaStreamCreateWithPriority(&streams[dev], cudaStreamNonBlocking, prio) != cudaSuccess)
       streams[dev] = nullptr;
   }
   return streams[dev];

@@ -853,12 +853,18 @@ struct Runner {
       // float64 LU runs on a second stream, beside the Jastrow factors and the
       // log-det derivatives, and joins before the final combination
       lu_side = !mc && (!deriv || gj) && side_ready();
-      mark("lu", 1);
-      if (lu_side) {
+      // with the derivatives, the fork waits until the Gauss-Jordan inverse is
+      // enqueued: the LU then shares the SMs with the orbital products and
+      // the contraction, whose CTAs leave room for it
+      auto launch_lu_side = [&]() {
         cudaEventRecord(ev_fork, s);
         cudaStreamWaitEvent(s2, ev_fork, 0);
         lu_kernel<LT, 16><<<wc * D, 256, lusm, s2>>>(n, LUb, piv, ldabs, lsign);
         cudaEventRecord(ev_join, s2);
+      };
+      mark("lu", 1);
+      if (lu_side) {
+        if (!deriv) launch_lu_side();
       } else {
         lu_kernel<LT, 16><<<wc * D, 256, lusm, s>>>(n, LUb, piv, ldabs, lsign);
       }
@@ -886,6 +892,7 @@ struct Runner {
         } else {
           inverse_from_lu(n, (int64_t)wc * D, LUb, piv, Ainv);
         }
+        if (lu_side) launch_lu_side();
       check("inverse");
         // 8. log-det gradient and Laplacian, determinant by determinant
         T* O = big;  // aliases Z | Y | SU, which are dead by now
