@@ -859,7 +859,9 @@ struct Runner {
       auto launch_lu_side = [&]() {
         cudaEventRecord(ev_fork, s);
         cudaStreamWaitEvent(s2, ev_fork, 0);
-        lu_kernel<LT, 16><<<wc * D, 256, lusm, s2>>>(n, LUb, piv, ldabs, lsign);
+        const int64_t nmat = (int64_t)wc * D;
+        lu2_kernel<LT, 8><<<(unsigned)((nmat + 1) / 2), 512, lu2_smem_bytes(n, sizeof(LT)), s2>>>(n, nmat, LUb, piv,
+                                                                                             ldabs, lsign);
         cudaEventRecord(ev_join, s2);
       };
       mark("lu", 1);
@@ -1345,6 +1347,7 @@ inline int set_smem_limits() {
   raise((const void*)contract3_kernel<320>);
   raise((const void*)lu_inverse_kernel<LT, T>);
   raise((const void*)lu_kernel<LT, 16>);
+  raise((const void*)lu2_kernel<LT, 8>);
   raise((const void*)att_pool_kernel<T>);
   raise((const void*)gj_inverse_kernel<float, T>);
   raise((const void*)mcmc_att_kernel<T>);
