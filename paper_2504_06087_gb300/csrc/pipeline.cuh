@@ -1331,6 +1331,10 @@ inline int set_smem_limits() {
     if (cudaFuncGetAttributes(&at, fn) != cudaSuccess) { rc = FIRE_ERR_CUDA; return; }
     const int dyn = maxopt - (int)at.sharedSizeBytes;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) != cudaSuccess) rc = FIRE_ERR_CUDA;
+    // the largest shared-memory carveout: an SM running these kernels keeps
+    // room for a CTA of the tensor-core product (the L1 / shared split only
+    // changes once an SM has drained)
+    cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
   };
   raise((const void*)contract_kernel<T, 1>);
   raise((const void*)contract_kernel<T, 2>);
