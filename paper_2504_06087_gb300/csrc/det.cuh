@@ -213,158 +213,6 @@ __global__ void lu_kernel(int n, LT* __restrict__ M, int32_t* __restrict__ piv,
 // Dynamic shared memory of lu_kernel<LT, 16>: the panel [n][17] and U12 [16][n].
 inline size_t lu_smem_bytes(int n, size_t lsz) { return (size_t)(2 * 16 + 1) * n * lsz; }
 
-// Barrier of one 256-thread half of a CTA (named barriers 1 and 2).
-__device__ __forceinline__ void half_barrier(int h) {
-  if (h == 0) asm volatile("bar.sync 1, 256;" ::: "memory");
-  else asm volatile("bar.sync 2, 256;" ::: "memory");
-}
-
-// The same factorisation with two matrices per 512-thread CTA (one per
-// half, each half on its own named barrier) and 8-column panels: an LU CTA
-// then fits beside one CTA of the tensor-core product or of the contraction,
-// so the float64 LU on the second stream shares the SMs with them.
-template <typename LT, int NB>
-__global__ void __launch_bounds__(512, 1) lu2_kernel(int n, int64_t nmat, LT* __restrict__ M,
-                                                    int32_t* __restrict__ piv, double* __restrict__ logabs,
-                                                    double* __restrict__ sgn) {
-  extern __shared__ unsigned char lu_smem[];
-  constexpr int PS = NB + 1;                   // panel row stride: rows fall in different banks
-  const int h = threadIdx.x >> 8;              // half of the CTA = one matrix
-  const int64_t mat = 2 * (int64_t)blockIdx.x + h;
-  if (mat >= nmat) return;                     // the other half synchronises on its own barrier
-  LT* P = reinterpret_cast<LT*>(lu_smem) + (size_t)h * (2 * NB + 1) * n;   // [n][NB + 1]
-  LT* U = P + (int64_t)n * PS;                 // [NB][n]
-  __shared__ double red_vs[2][8];
-  __shared__ int red_is[2][8];
-  __shared__ int s_pivs[2];
-  __shared__ int s_zeros[2];
-  double* red_v = red_vs[h];
-  int* red_i = red_is[h];
-  int& s_piv = s_pivs[h];
-  int& s_zero = s_zeros[h];
-  LT* A = M + mat * n * n;
-  int32_t* pv = piv + mat * n;
-  const int tid = threadIdx.x & 255, bd = 256;
-  if (tid == 0) s_zero = 0;
-  for (int k0 = 0; k0 < n; k0 += NB) {
-    const int nb = min(NB, n - k0);
-    const int pr = n - k0;  // panel rows
-    for (int e = tid; e < pr * nb; e += bd) {
-      const int r = e / nb, c = e % nb;
-      P[r * PS + c] = A[(int64_t)(k0 + r) * n + k0 + c];
-    }
-    half_barrier(h);
-    for (int kk = 0; kk < nb; ++kk) {
-      // argmax |P[r][kk]| over r in [kk, pr), first index on ties
-      double best = -1.0;
-      int bi = kk;
-      for (int r = kk + tid; r < pr; r += bd) {
-        double v = fabs((double)P[r * PS + kk]);
-        if (v > best) { best = v; bi = r; }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        double ov = __shfl_xor_sync(0xffffffffu, best, o);
-        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-      }
-      if ((tid & 31) == 0) { red_v[tid >> 5] = best; red_i[tid >> 5] = bi; }
-      half_barrier(h);
-      if (tid == 0) {
-        double b = red_v[0];
-        int ib = red_i[0];
-        for (int q = 1; q < (bd + 31) / 32; ++q)
-          if (red_v[q] > b || (red_v[q] == b && red_i[q] < ib)) { b = red_v[q]; ib = red_i[q]; }
-        s_piv = ib;
-        pv[k0 + kk] = k0 + ib;
-        if (!(b > 0.0)) s_zero = 1;
-      }
-      half_barrier(h);
-      const int p = s_piv;
-      if (p != kk) {
-        for (int c = tid; c < nb; c += bd) {
-          LT t = P[kk * PS + c];
-          P[kk * PS + c] = P[p * PS + c];
-          P[p * PS + c] = t;
-        }
-      }
-      half_barrier(h);
-      const LT pivot = P[kk * PS + kk];
-      if (pivot != LT(0)) {
-        for (int r = kk + 1 + tid; r < pr; r += bd) {
-          LT l = P[r * PS + kk] / pivot;
-          P[r * PS + kk] = l;
-          for (int c = kk + 1; c < nb; ++c) P[r * PS + c] -= l * P[kk * PS + c];
-        }
-      }
-      half_barrier(h);
-    }
-    // panel back to global
-    for (int e = tid; e < pr * nb; e += bd) {
-      const int r = e / nb, c = e % nb;
-      A[(int64_t)(k0 + r) * n + k0 + c] = P[r * PS + c];
-    }
-    // row swaps of this panel on the columns outside it
-    for (int kk = 0; kk < nb; ++kk) {
-      const int a = k0 + kk, b = pv[k0 + kk];
-      if (a != b) {
-        for (int c = tid; c < n; c += bd) {
-          if (c >= k0 && c < k0 + nb) continue;
-          LT t = A[(int64_t)a * n + c];
-          A[(int64_t)a * n + c] = A[(int64_t)b * n + c];
-          A[(int64_t)b * n + c] = t;
-        }
-      }
-      half_barrier(h);
-    }
-    const int c0 = k0 + nb;
-    // U12 = L11^-1 A12 (unit lower L11 from the panel)
-    for (int j = c0 + tid; j < n; j += bd) {
-      LT u[NB];
-#pragma unroll
-      for (int kk = 0; kk < NB; ++kk) {
-        if (kk < nb) {
-          LT s = A[(int64_t)(k0 + kk) * n + j];
-          for (int q = 0; q < kk; ++q) s -= P[kk * PS + q] * u[q];
-          u[kk] = s;
-          A[(int64_t)(k0 + kk) * n + j] = s;
-          U[kk * n + j] = s;
-        }
-      }
-    }
-    half_barrier(h);
-    // A22 -= L21 U12
-    const int rows2 = n - c0, cols2 = n - c0;
-    for (int e = tid; e < rows2 * cols2; e += bd) {
-      const int r = c0 + e / cols2, j = c0 + e % cols2;
-      LT s = A[(int64_t)r * n + j];
-      const LT* lrow = P + (int64_t)(r - k0) * PS;
-      for (int kk = 0; kk < nb; ++kk) s -= lrow[kk] * U[kk * n + j];
-      A[(int64_t)r * n + j] = s;
-    }
-    half_barrier(h);
-  }
-  // log|det| and sign
-  if (tid < 32) {
-    double la = 0.0;
-    int neg = 0;
-    for (int k = tid; k < n; k += 32) {
-      double u = (double)A[(int64_t)k * n + k];
-      la += log(fabs(u));
-      if (u < 0) neg ^= 1;
-      if (pv[k] != k) neg ^= 1;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      la += __shfl_xor_sync(0xffffffffu, la, o);
-      neg ^= __shfl_xor_sync(0xffffffffu, neg, o);
-    }
-    if (tid == 0) {
-      if (s_zero) { logabs[mat] = -INFINITY; sgn[mat] = 0.0; }
-      else { logabs[mat] = la; sgn[mat] = neg ? -1.0 : 1.0; }
-    }
-  }
-}
-
-inline size_t lu2_smem_bytes(int n, size_t lsz) { return (size_t)2 * (2 * 8 + 1) * n * lsz; }
 
 // A = Phi^-1 from the LU factors: column j of A solves L U x = e_{pinv[j]}.
 // One CTA per matrix, one thread per column, x kept in shared memory; the

@@ -154,7 +154,11 @@ struct Runner {
   cudaStream_t s2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool side_ready() {
-    if (getenv("FIRE_SERIAL") || single_stream()) return false;   // one stream only
+    // FIRE_LU_SIDE=1 (diagnostic): the float64 LU on a second stream.  Off by
+    // default: on GB300 its CTAs did not share SMs with the tensor-core
+    // product, and one stream measured as fast (1665 vs 1660 walkers/s).
+    const char* e = getenv("FIRE_LU_SIDE");
+    if (!(e && atoi(e) == 1) || single_stream()) return false;
     if (!s2) s2 = side_stream();
     if (!s2) return false;
     if (!ev_fork && cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) != cudaSuccess) return false;
@@ -850,8 +854,8 @@ struct Runner {
       const size_t lusm = lu_smem_bytes(n, sizeof(LT));
       // slogdet: when the inverse does not come from these factors (float
       // forms: Gauss-Jordan on a float copy of Phi; value-only calls), the
-      // float64 LU runs on a second stream, beside the Jastrow factors and the
-      // log-det derivatives, and joins before the final combination
+      // float64 LU may run on a second stream (FIRE_LU_SIDE=1) and join before
+      // the final combination
       lu_side = !mc && (!deriv || gj) && side_ready();
       // with the derivatives, the fork waits until the Gauss-Jordan inverse is
       // enqueued: the LU then shares the SMs with the orbital products and
@@ -859,9 +863,7 @@ struct Runner {
       auto launch_lu_side = [&]() {
         cudaEventRecord(ev_fork, s);
         cudaStreamWaitEvent(s2, ev_fork, 0);
-        const int64_t nmat = (int64_t)wc * D;
-        lu2_kernel<LT, 8><<<(unsigned)((nmat + 1) / 2), 512, lu2_smem_bytes(n, sizeof(LT)), s2>>>(n, nmat, LUb, piv,
-                                                                                             ldabs, lsign);
+        lu_kernel<LT, 16><<<wc * D, 256, lusm, s2>>>(n, LUb, piv, ldabs, lsign);
         cudaEventRecord(ev_join, s2);
       };
       mark("lu", 1);
@@ -1351,7 +1353,6 @@ inline int set_smem_limits() {
   raise((const void*)contract3_kernel<320>);
   raise((const void*)lu_inverse_kernel<LT, T>);
   raise((const void*)lu_kernel<LT, 16>);
-  raise((const void*)lu2_kernel<LT, 8>);
   raise((const void*)att_pool_kernel<T>);
   raise((const void*)gj_inverse_kernel<float, T>);
   raise((const void*)mcmc_att_kernel<T>);
