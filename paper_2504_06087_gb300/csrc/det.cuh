@@ -277,7 +277,8 @@ inline int gj_threads(int n) {
   return ((t + 31) / 32) * 32;
 }
 template <typename IT, typename OT>
-__global__ void __launch_bounds__(384, 1) gj_inverse_kernel(int n, const IT* __restrict__ Phi, OT* __restrict__ AT) {
+__global__ void __launch_bounds__(384, 1) gj_inverse_kernel(int n, const IT* __restrict__ Phi, OT* __restrict__ AT,
+                                                            const int32_t* __restrict__ lu_piv = nullptr) {
   constexpr int TR = kGjTR, TC = kGjTC;
   extern __shared__ unsigned char gj_smem[];
   float* S = reinterpret_cast<float*>(gj_smem);          // [n][n] final matrix
@@ -302,6 +303,23 @@ __global__ void __launch_bounds__(384, 1) gj_inverse_kernel(int n, const IT* __r
       a[i][j] = (live && r < n && c < n) ? (float)P[(int64_t)r * n + c] : 0.f;
     }
   for (int r = tid; r < 256; r += blockDim.x) used[r] = 0;
+  // With the row interchanges of a partial-pivoting LU of the same matrix
+  // (lu_piv, LAPACK order: step k swapped rows k and lu_piv[k]) the pivot
+  // rows are known up front: piv[k] is the original row at position k after
+  // the first k + 1 interchanges.  Each step then needs one barrier.
+  const bool pre = lu_piv != nullptr;
+  if (pre && tid == 0) {
+    const int32_t* lp = lu_piv + (int64_t)blockIdx.x * n;
+    for (int k = 0; k < n; ++k) stp[k] = k;   // stp: position -> original row
+    for (int k = 0; k < n; ++k) {
+      const int q = lp[k];
+      const int t = stp[k];
+      stp[k] = stp[q];
+      stp[q] = t;
+    }
+    for (int k = 0; k < n; ++k) piv[k] = stp[k];
+    for (int k = 0; k < n; ++k) stp[piv[k]] = k;
+  }
   __syncthreads();
   for (int kt = 0; kt < Gc; ++kt) {
 #pragma unroll
@@ -313,6 +331,7 @@ __global__ void __launch_bounds__(384, 1) gj_inverse_kernel(int n, const IT* __r
         float* pc = pcol + 256 * bsel;
         float* cvb = cv + 32 * bsel;
         int* cib = ci + 32 * bsel;
+        if (!pre) {
         // candidates: the threads of column block kt, one per row block
         if (live && tc == kt) {
           float best = -1.f;
@@ -345,6 +364,7 @@ __global__ void __launch_bounds__(384, 1) gj_inverse_kernel(int n, const IT* __r
           }
         }
         __syncthreads();
+        }
         const int p = piv[k];
         const int pt = p / TR, pi = p % TR;
         if (live && tr == pt)

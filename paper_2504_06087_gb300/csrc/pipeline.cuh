@@ -892,7 +892,8 @@ struct Runner {
         mark("inverse", 1);
         if (gj) {
           const int thr = gj_threads(n);
-          gj_inverse_kernel<float, T><<<wc * D, thr, gj_smem_bytes(n), s>>>(n, Phif, Ainv);
+          // pivot rows from the float64 LU when it has already run on this stream
+          gj_inverse_kernel<float, T><<<wc * D, thr, gj_smem_bytes(n), s>>>(n, Phif, Ainv, lu_side ? nullptr : piv);
         } else {
           inverse_from_lu(n, (int64_t)wc * D, LUb, piv, Ainv);
         }
