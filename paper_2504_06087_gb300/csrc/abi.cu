@@ -254,9 +254,11 @@ static size_t layout(Plan& pl, int64_t Wc) {
 
 static size_t budget_bytes() {
   const char* e = getenv("FIRE_WORKSPACE_BUDGET_MB");
-  // default: 64 GiB of the 280 GB of HBM3e; FIRE_WORKSPACE_BUDGET_MB overrides
-  double mb = e ? atof(e) : 65536.0;
-  if (!(mb > 0)) mb = 65536.0;
+  // default: 128 GiB of the 280 GB of HBM3e (C26H24 at 4096 walkers: 10
+  // chunks; measured 1.7 % faster than 64 GiB, no gain beyond);
+  // FIRE_WORKSPACE_BUDGET_MB overrides
+  double mb = e ? atof(e) : 131072.0;
+  if (!(mb > 0)) mb = 131072.0;
   return (size_t)(mb * 1024.0 * 1024.0);
 }
 
