@@ -66,7 +66,7 @@ def test_workspace_size_and_chunking(monkeypatch):
     b = L.fire_workspace_size(ctypes.byref(sys_c), ctypes.byref(arch_c), 4, 2, 64, fire.OP_LOCAL_ENERGY)
     c = L.fire_workspace_size(ctypes.byref(sys_c), ctypes.byref(arch_c), 4, 2, 64, fire.OP_LOGPSI)
     assert a > b > c > 0
-    assert a <= 66 * 2 ** 30          # the default budget bounds a chunk
+    assert a <= 130 * 2 ** 30         # the default budget (128 GiB) bounds a chunk
     # invalid arguments -> 0
     assert L.fire_workspace_size(ctypes.byref(sys_c), ctypes.byref(arch_c), 0, 2, 64, 2) == 0
     assert L.fire_workspace_size(ctypes.byref(sys_c), ctypes.byref(arch_c), 4, 7, 64, 2) == 0
