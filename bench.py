@@ -102,6 +102,21 @@ class ClockSampler:
 # algorithmic work per stage (for the roofline of the dominant kernel)
 # ---------------------------------------------------------------------------
 
+def stage_traffic(stage, walker_dets, launches):
+    """DRAM bytes (read + write) per stage launch, from the ncu capture summarised
+    in profiles/<stage>_c26h24.md (a line 'dram_bytes_per_walker_det: X'); the
+    stage launches once per determinant and chunk, so one launch covers
+    walker_dets / launches walker-determinants.  None without a capture."""
+    path = os.path.join(ROOT, "profiles", f"{stage}_c26h24.md")
+    if not os.path.exists(path):
+        return None
+    for ln in open(path):
+        if ln.strip().startswith("dram_bytes_per_walker_det:"):
+            per = float(ln.split(":", 1)[1].split()[0])
+            return per * walker_dets / launches
+    return None
+
+
 def stage_work(stage, w, info, n_walkers, nbr_sq_sum):
     """(flops_total, bytes_total, bound) of one call's stage, from the shapes.
 
@@ -258,7 +273,7 @@ def main():
     dname, (dl, dms) = dom
     flops, _, bound = stage_work(dname, w, info, args.walkers, nbr_sq_sum)
     roof = {"kernel": dname, "share_of_step": dms / sum(v[1] for v in stages.values()), "launches": dl,
-            "traffic": None}
+            "traffic": stage_traffic(dname, args.walkers * w.arch.n_det, dl)}
     if flops is not None:
         per_launch = flops / dl
         achieved = per_launch / (dms / dl / 1e3) / 1e12
