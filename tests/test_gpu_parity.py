@@ -202,3 +202,23 @@ def test_dense_limit_large_neighbourhoods(prec):
     assert out["info"]["k_required"] == 57
     assert rel(out["logabs"].cpu().numpy(), la).max() < 1e-5
     assert np.median(rel(out["e_loc"].cpu().numpy(), e)) < 1e-4
+
+
+@pytest.mark.parametrize("variant", [{"FIRE_CONTRACT": "v1"}, {"FIRE_CONTRACT": "v2"}, {"FIRE_LU_SIDE": "1"}])
+def test_c26h24_kernel_variants_agree(variant, monkeypatch):
+    """The log-det contraction and inverse exist in several kernel forms: the
+    bucket-listed asynchronous contraction (default), its synchronous form
+    (v2) and the 256-thread form (v1); the inverse with pivot rows from the
+    float64 LU (default) or with its own pivot search (LU on a second stream).
+    Each neighbourhood-size bucket up to 52 members occurs at C26H24 with
+    c = 5; every form must give the same local energies up to float32
+    rounding of the contraction."""
+    w = synth.workload("c26h24")
+    r, p = synth.make_inputs(w, 8)
+    ref = fire.Fire(w.system, w.arch, p, "bf16").local_energy(r)
+    for k, v in variant.items():
+        monkeypatch.setenv(k, v)
+    out = fire.Fire(w.system, w.arch, p, "bf16").local_energy(r)
+    np.testing.assert_array_equal(out["sign"].cpu().numpy(), ref["sign"].cpu().numpy())
+    assert rel(out["logabs"].cpu().numpy(), ref["logabs"].cpu().numpy()).max() < 1e-6
+    assert np.median(rel(out["e_loc"].cpu().numpy(), ref["e_loc"].cpu().numpy())) < 1e-4
