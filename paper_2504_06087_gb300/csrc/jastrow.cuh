@@ -218,12 +218,29 @@ __global__ void att_part_kernel(int Wc, int n, int n_up, int K, int R, int dr, c
   const int64_t o = blk_off[bi], o1 = blk_off[bi + 1];
   const T e = dexp<T>(SU[o * ld + rg] - mx);
   const T u = SU[o * ld + R + col];
-  T ss = T(0), su = T(0);
-  for (int64_t q = o + 2; q < o1; ++q) {
-    const T st = SU[q * ld + rg];
-    ss += st * st;
-    su += st * SU[q * ld + R + col];
+  // tangent rows four at a time (independent partial sums keep four loads
+  // in flight), summed in a fixed order
+  T ss4[4] = {T(0), T(0), T(0), T(0)}, su4[4] = {T(0), T(0), T(0), T(0)};
+  int64_t q = o + 2;
+  for (; q + 4 <= o1; q += 4) {
+    T st[4], ut[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      st[u] = SU[(q + u) * ld + rg];
+      ut[u] = SU[(q + u) * ld + R + col];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      ss4[u] += st[u] * st[u];
+      su4[u] += st[u] * ut[u];
+    }
   }
+  for (int u = 0; q < o1; ++q, ++u) {
+    const T st = SU[q * ld + rg];
+    ss4[u] += st * st;
+    su4[u] += st * SU[q * ld + R + col];
+  }
+  const T ss = (ss4[0] + ss4[1]) + (ss4[2] + ss4[3]), su = (su4[0] + su4[1]) + (su4[2] + su4[3]);
   const T sl = SU[(o + 1) * ld + rg], ul = SU[(o + 1) * ld + R + col];
   rec[0 * RD + col] = e;
   rec[1 * RD + col] = e * u;
