@@ -57,7 +57,7 @@ __device__ __forceinline__ FL3<T> pair_feature(int k, const T dv[3], T r, const 
 
 // Pairs whose filter features are computed together (one barrier pair per
 // batch instead of per pair).
-constexpr int kPairBatch = 8;
+constexpr int kPairBatch = 16;
 // Largest nucleus count of the batched electron-nucleus filter.
 constexpr int kMaxNuc = 512;
 
