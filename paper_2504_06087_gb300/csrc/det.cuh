@@ -214,47 +214,6 @@ __global__ void lu_kernel(int n, LT* __restrict__ M, int32_t* __restrict__ piv,
 inline size_t lu_smem_bytes(int n, size_t lsz) { return (size_t)(2 * 16 + 1) * n * lsz; }
 
 
-// A = Phi^-1 from the LU factors: column j of A solves L U x = e_{pinv[j]}.
-// One CTA per matrix, one thread per column, x kept in shared memory; the
-// result is written transposed (Ainv[k][l] = A[l][k]).
-template <typename LT, typename AT>
-__global__ void lu_inverse_kernel(int n, const LT* __restrict__ M, const int32_t* __restrict__ piv,
-                                  AT* __restrict__ Ainv) {
-  extern __shared__ unsigned char inv_smem[];
-  AT* X = reinterpret_cast<AT*>(inv_smem);        // [n][n]
-  int* perm = reinterpret_cast<int*>(X + (int64_t)n * n);
-  int* pinv = perm + n;
-  const LT* A = M + (int64_t)blockIdx.x * n * n;
-  const int32_t* pv = piv + (int64_t)blockIdx.x * n;
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < n; ++i) perm[i] = i;
-    for (int k = 0; k < n; ++k) {
-      int t = perm[k];
-      perm[k] = perm[pv[k]];
-      perm[pv[k]] = t;
-    }
-    for (int i = 0; i < n; ++i) pinv[perm[i]] = i;
-  }
-  __syncthreads();
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    const int p = pinv[j];
-    for (int i = 0; i < n; ++i) {
-      AT s = (i == p) ? AT(1) : AT(0);
-      for (int k = 0; k < i; ++k) s -= AT(A[(int64_t)i * n + k]) * X[(int64_t)k * n + j];
-      X[(int64_t)i * n + j] = s;
-    }
-    for (int i = n - 1; i >= 0; --i) {
-      AT s = X[(int64_t)i * n + j];
-      for (int k = i + 1; k < n; ++k) s -= AT(A[(int64_t)i * n + k]) * X[(int64_t)k * n + j];
-      X[(int64_t)i * n + j] = s / AT(A[(int64_t)i * n + i]);
-    }
-  }
-  __syncthreads();
-  // stored transposed: out[k][l] = A[l][k], so a column of A is one row
-  AT* out = Ainv + (int64_t)blockIdx.x * n * n;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) out[e] = X[(int64_t)(e % n) * n + e / n];
-}
-
 // A = Phi^-1 by in-place Gauss-Jordan elimination with partial pivoting, in
 // float32, register-tiled: thread (tr, tc) of a Gr x Gc grid (Gr = ceil(n/12),
 // Gc = ceil(n/8)) keeps the 12 x 8 block of rows 12tr.., columns 8tc.. in
@@ -270,7 +229,8 @@ __global__ void lu_inverse_kernel(int n, const LT* __restrict__ M, const int32_t
 // pivot column is addressed statically; every element takes the same fused
 // update a_ij -= f_i s_j (f_p = 0), and only the owners of column k and of
 // row p rewrite their entries afterwards.  The broadcast buffers alternate
-// between steps, so three barriers separate the steps.
+// between steps, so three barriers separate the steps (one when the pivot
+// rows come from the LU's interchanges).
 constexpr int kGjTR = 12, kGjTC = 8;
 inline int gj_threads(int n) {
   const int t = ((n + kGjTR - 1) / kGjTR) * ((n + kGjTC - 1) / kGjTC);

@@ -1352,7 +1352,6 @@ inline int set_smem_limits() {
   raise((const void*)contract3_kernel<128>);
   raise((const void*)contract3_kernel<192>);
   raise((const void*)contract3_kernel<320>);
-  raise((const void*)lu_inverse_kernel<LT, T>);
   raise((const void*)lu_kernel<LT, 16>);
   raise((const void*)att_pool_kernel<T>);
   raise((const void*)gj_inverse_kernel<float, T>);
