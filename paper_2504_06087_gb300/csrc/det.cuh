@@ -210,8 +210,8 @@ __global__ void lu_kernel(int n, LT* __restrict__ M, int32_t* __restrict__ piv,
   }
 }
 
-// Dynamic shared memory of lu_kernel<LT, 16>: the panel [n][17] and U12 [16][n].
-inline size_t lu_smem_bytes(int n, size_t lsz) { return (size_t)(2 * 16 + 1) * n * lsz; }
+// Dynamic shared memory of lu_kernel<LT, NB>: the panel [n][NB + 1] and U12 [NB][n].
+inline size_t lu_smem_bytes(int n, size_t lsz, int nb = 16) { return (size_t)(2 * nb + 1) * n * lsz; }
 
 
 // A = Phi^-1 by in-place Gauss-Jordan elimination with partial pivoting, in

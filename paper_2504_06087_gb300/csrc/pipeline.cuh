@@ -127,6 +127,7 @@ struct Runner {
     // Phi (n <= 192, the default of the float32 forms), 0 = triangular solves
     // on the LU factors (always for float64 and for n > 192)
     if (const char* m = getenv("FIRE_INVERSE")) use_gj = atoi(m) == 1;
+    if (const char* m = getenv("FIRE_LU_NB")) lu_nb = atoi(m) == 32 ? 32 : 16;
     auto split_env = [](const char* k, int dflt) {
       const char* v = getenv(k);
       int x = v ? atoi(v) : dflt;
@@ -229,6 +230,7 @@ struct Runner {
   int nc_env = 3;             // envelope product: its value rows enter Phi directly
   int nc_h0 = 3;              // h^0 products and orbital value rows (no fp32 recompute)
   bool use_gj = true;
+  int lu_nb = 16;             // FIRE_LU_NB (diagnostic): 16 or 32-column LU panels
   // A^T from the LU factors, matrices in batches of the grid limit
   void inverse_from_lu(int n, int64_t nmat, const LT* LUb, const int32_t* piv, T* Ainv) {
     const size_t ism = inverse_panel_smem(n, sizeof(T));
@@ -870,7 +872,8 @@ struct Runner {
       if (lu_side) {
         if (!deriv) launch_lu_side();
       } else {
-        lu_kernel<LT, 16><<<wc * D, 256, lusm, s>>>(n, LUb, piv, ldabs, lsign);
+        if (lu_nb == 32) lu_kernel<LT, 32><<<wc * D, 256, lu_smem_bytes(n, sizeof(LT), 32), s>>>(n, LUb, piv, ldabs, lsign);
+        else lu_kernel<LT, 16><<<wc * D, 256, lusm, s>>>(n, LUb, piv, ldabs, lsign);
       }
       check("lu");
       if (mc) {
@@ -1353,6 +1356,7 @@ inline int set_smem_limits() {
   raise((const void*)contract3_kernel<192>);
   raise((const void*)contract3_kernel<320>);
   raise((const void*)lu_kernel<LT, 16>);
+  raise((const void*)lu_kernel<LT, 32>);
   raise((const void*)att_pool_kernel<T>);
   raise((const void*)gj_inverse_kernel<float, T>);
   raise((const void*)mcmc_att_kernel<T>);
