@@ -893,7 +893,7 @@ __host__ __device__ inline size_t contract3_region(int mp) {
 }
 inline size_t contract3_smem_bytes(int mhi) {
   const int mp = contract2_slots(mhi);
-  return (contract3_region(mp) + contract3_raw_floats(mp)) * 4 + (size_t)mp * 20 + 64;
+  return (contract3_region(mp) + contract3_raw_floats(mp)) * 4 + (size_t)mp * 20 + (size_t)(5 * mp + 4) * 12 + 80;
 }
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
@@ -930,6 +930,9 @@ contract3_kernel(int Wc, int n, int n_up, int K, int mlo, int mhi, int dd, int D
   int64_t* ro = reinterpret_cast<int64_t*>(raw + ((contract3_raw_floats(MP) + 3) & ~(size_t)3));
   int64_t* fo = ro + MP;
   int* mi = reinterpret_cast<int*>(fo + MP);
+  // source row (nullptr: zero fill) and raw row of every copy row, set once
+  const float** rsrc = reinterpret_cast<const float**>(mi + ((MP + 1) & ~1));
+  int* rrow = reinterpret_cast<int*>(rsrc + 5 * MP + 4);
   const int64_t Dn = (int64_t)D * n;
   for (int k = tid; k < m; k += NT) {
     int i = np, slot = 0;
@@ -953,34 +956,37 @@ contract3_kernel(int Wc, int n, int n_up, int K, int mlo, int mhi, int dd, int D
 
   // raw copies of the chunk starting at orbital c0 (zero beyond n and m)
   const int nraw = 5 * kfill + 4;
+  for (int q = tid; q < nraw; q += NT) {
+    const float* src = nullptr;
+    int rr;
+    if (q < 3 * kfill) {
+      const int k = q / 3, x = q - 3 * k;
+      rr = q;
+      if (k < m && ro[k] >= 0) src = O + ro[k] + x * ldo;
+    } else if (q < 4 * kfill) {
+      const int k = q - 3 * kfill;
+      rr = 3 * MP + k;
+      if (k < m) src = Fenv + fo[k];
+    } else if (q < 5 * kfill) {
+      const int k = q - 4 * kfill;
+      rr = 4 * MP + k;
+      if (k < m) src = Aw + (int64_t)mi[k] * n;
+    } else {
+      const int u = q - 5 * kfill;
+      rr = 5 * MP + u;
+      src = u == 0 ? O + onp : Fenv + fo[0] + (1 + u) * Dn;
+    }
+    rsrc[q] = src;
+    rrow[q] = rr;
+  }
+  __syncthreads();
   auto issue = [&](int c0) {
     for (int e = tid; e < nraw * NJ; e += NT) {
       const int q = e / NJ, j = e - q * NJ;
       const int l = c0 + 4 * j;
-      const float* src = O;
-      int rrow;
-      bool ok = l < n;
-      if (q < 3 * kfill) {
-        const int k = q / 3, x = q - 3 * k;
-        rrow = q;
-        ok = ok && k < m && ro[k] >= 0;
-        if (ok) src = O + ro[k] + x * ldo + l;
-      } else if (q < 4 * kfill) {
-        const int k = q - 3 * kfill;
-        rrow = 3 * MP + k;
-        ok = ok && k < m;
-        if (ok) src = Fenv + fo[k] + l;
-      } else if (q < 5 * kfill) {
-        const int k = q - 4 * kfill;
-        rrow = 4 * MP + k;
-        ok = ok && k < m;
-        if (ok) src = Aw + (int64_t)mi[k] * n + l;
-      } else {
-        const int u = q - 5 * kfill;
-        rrow = 5 * MP + u;
-        if (ok) src = u == 0 ? O + onp + l : Fenv + fo[0] + (1 + u) * Dn + l;
-      }
-      cp_async16(raw + rrow * RS + 4 * j, src, ok ? 16 : 0);
+      const float* src = rsrc[q];
+      const bool ok = src != nullptr && l < n;
+      cp_async16(raw + rrow[q] * RS + 4 * j, ok ? src + l : O, ok ? 16 : 0);
     }
     cp_async_commit();
   };
