@@ -161,12 +161,39 @@ __global__ void att_bwd_kernel(int Wc, int n, int n_up, int R, int dr, const T* 
 template <typename T>
 __device__ __forceinline__ void block_reduce48(T v[48], T* part, T* out) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // warp transpose-reduction (recursive halving): at each step a lane keeps
+  // half of its values and adds its partner's copy of them, so lane L ends
+  // with the warp sums of values L and (L < 16) 32 + L -- 62 shuffles
+  // instead of 5 per value
+  T a[32], b[16];
 #pragma unroll
-  for (int k = 0; k < 48; ++k) {
-    T x = v[k];
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if (lane == 0) part[wid * 48 + k] = x;
+  for (int k = 0; k < 32; ++k) a[k] = v[k];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) b[k] = v[32 + k];
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const bool up = (lane & s) != 0;
+#pragma unroll
+    for (int k = 0; k < s; ++k) {
+      const T send = up ? a[k] : a[k + s];
+      const T keep = up ? a[k + s] : a[k];
+      a[k] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
   }
+#pragma unroll
+  for (int k = 0; k < 16; ++k) b[k] += __shfl_xor_sync(0xffffffffu, b[k], 16);
+#pragma unroll
+  for (int s = 8; s >= 1; s >>= 1) {
+    const bool up = (lane & s) != 0;
+#pragma unroll
+    for (int k = 0; k < s; ++k) {
+      const T send = up ? b[k] : b[k + s];
+      const T keep = up ? b[k + s] : b[k];
+      b[k] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
+  }
+  part[wid * 48 + lane] = a[0];
+  if (lane < 16) part[wid * 48 + 32 + lane] = b[0];
   __syncthreads();
   if (threadIdx.x < 48) {
     T s = T(0);
