@@ -195,10 +195,10 @@ __device__ __forceinline__ void block_reduce48(T v[48], T* part, T* out) {
   part[wid * 48 + lane] = a[0];
   if (lane < 16) part[wid * 48 + 32 + lane] = b[0];
   __syncthreads();
-  if (threadIdx.x < 48) {
+  for (int t = threadIdx.x; t < 48; t += blockDim.x) {
     T s = T(0);
-    for (int q = 0; q < nw; ++q) s += part[q * 48 + threadIdx.x];
-    out[threadIdx.x] = s;
+    for (int q = 0; q < nw; ++q) s += part[q * 48 + t];
+    out[t] = s;
   }
   __syncthreads();
 }
@@ -206,12 +206,17 @@ __device__ __forceinline__ void block_reduce48(T v[48], T* part, T* out) {
 // Filter backward shared by the message and electron-nucleus passes: given
 // dGamma_c for the pair vector delta (features in feat, see
 // pair_features_to_smem), accumulates the gradient of W2 (16 x d), W_env
-// (32 x d) in registers and of W1 (4 x H), b1, sigma via atomics.
-template <typename T, typename W>
+// (32 x d) in registers and of W1 (4 x H), b1, sigma either into the CTA's
+// shared accumulator acc[5H + G] (ACC: the weights are the same for every
+// pair of the CTA; layout W1 rows 0..3, b1, sigma) or by atomics into
+// gW1/gb1/gsig (per-nucleus weights).  Entry t of the 48 reduced values is
+// handled by thread t mod blockDim, the same thread for every pair, so the
+// shared accumulator needs no atomics.
+template <bool ACC, typename T, typename W>
 __device__ __forceinline__ void filter_bwd(const FL3<T>* feat, const T dv[3], T r, T cut, const W* w1,
                                            const W* b1, const W* sigma, const T w2c[kEdgeHidden],
                                            const T wec[kGauss], T gv, T ev, T dgam, T gW2[kEdgeHidden],
-                                           T gWe[kGauss], T* part, T* red48, T* gW1, T* gb1, T* gsig) {
+                                           T gWe[kGauss], T* part, T* red48, T* acc, T* gW1, T* gb1, T* gsig) {
   constexpr int H = kEdgeHidden, G = kGauss;
   T v[48];
 #pragma unroll
@@ -225,22 +230,31 @@ __device__ __forceinline__ void filter_bwd(const FL3<T>* feat, const T dv[3], T 
     v[H + g] = dgam * gv * wec[g];
   }
   block_reduce48<T>(v, part, red48);
-  const int t = threadIdx.x;
-  if (t < H) {
-    // du_h = da_h * SiLU'(u_h), u_h = x . W1[:, h] + b1[h], x = [r, delta]
-    T u = T(b1[t]) + T(w1[t]) * r;
-    for (int k = 0; k < 3; ++k) u += T(w1[(1 + k) * H + t]) * dv[k];
-    T f, f1, f2;
-    silu3<T>(u, f, f1, f2);
-    const T du = red48[t] * f1;
-    atomicAdd(&gW1[0 * H + t], du * r);
-    for (int k = 0; k < 3; ++k) atomicAdd(&gW1[(1 + k) * H + t], du * dv[k]);
-    atomicAdd(&gb1[t], du);
-  } else if (t < H + G) {
-    // chi_g = f_cut exp(-sigma_g^2 r^2): d chi_g / d sigma_g = -2 sigma_g r^2 chi_g
-    const int g = t - H;
-    const T sg = T(sigma[g]);
-    atomicAdd(&gsig[g], red48[t] * (-T(2) * sg * r * r) * feat[H + g].v);
+  for (int t = threadIdx.x; t < H + G; t += blockDim.x) {
+    if (t < H) {
+      // du_h = da_h * SiLU'(u_h), u_h = x . W1[:, h] + b1[h], x = [r, delta]
+      T u = T(b1[t]) + T(w1[t]) * r;
+      for (int k = 0; k < 3; ++k) u += T(w1[(1 + k) * H + t]) * dv[k];
+      T f, f1, f2;
+      silu3<T>(u, f, f1, f2);
+      const T du = red48[t] * f1;
+      if (ACC) {
+        acc[t] += du * r;
+        for (int k = 0; k < 3; ++k) acc[(1 + k) * H + t] += du * dv[k];
+        acc[4 * H + t] += du;
+      } else {
+        atomicAdd(&gW1[0 * H + t], du * r);
+        for (int k = 0; k < 3; ++k) atomicAdd(&gW1[(1 + k) * H + t], du * dv[k]);
+        atomicAdd(&gb1[t], du);
+      }
+    } else {
+      // chi_g = f_cut exp(-sigma_g^2 r^2): d chi_g / d sigma_g = -2 sigma_g r^2 chi_g
+      const int g = t - H;
+      const T sg = T(sigma[g]);
+      const T ds = red48[t] * (-T(2) * sg * r * r) * feat[H + g].v;
+      if (ACC) acc[5 * H + g] += ds;
+      else atomicAdd(&gsig[g], ds);
+    }
   }
 }
 
@@ -258,10 +272,12 @@ __global__ void msg_bwd_kernel(int Wc, int n, int n_up, int d, int K, const doub
   __shared__ FL3<T> feat[H + G + 4];
   __shared__ T part[32 * 48];
   __shared__ T red48[48];
+  __shared__ T acc[5 * H + G];
   const int blk = blockIdx.x;
   const int w = blk / n, i = blk % n;
   const int c = threadIdx.x;
   const int bi = block_index(w, i, Wc, n, n_up);
+  for (int t = c; t < 5 * H + G; t += blockDim.x) acc[t] = T(0);
   const int64_t ld4 = 4 * (int64_t)d;
   T* gw = grad + (int64_t)w * P;
   T w2[H], we[G], wc[2][4], bb[2];
@@ -319,12 +335,18 @@ __global__ void msg_bwd_kernel(int Wc, int n, int n_up, int d, int K, const doub
     gB[a] += dz;
 #pragma unroll
     for (int k = 0; k < 4; ++k) gWc[a][k] += feat[H + G + k].v * dz;
-    filter_bwd<T, W>(feat, dv, T(rr), T(cut), p.ee_w1, p.ee_b1, p.ee_sigma, w2, we, gv, ev, dgam, gW2, gWe,
-                     part, red48, gw + po[P_EE_W1], gw + po[P_EE_B1], gw + po[P_EE_SIGMA]);
+    filter_bwd<true, T, W>(feat, dv, T(rr), T(cut), p.ee_w1, p.ee_b1, p.ee_sigma, w2, we, gv, ev, dgam, gW2,
+                           gWe, part, red48, acc, nullptr, nullptr, nullptr);
   }
   dP[(int64_t)bi * 2 * d + c] = dPa[0];
   dP[(int64_t)bi * 2 * d + d + c] = dPa[1];
+  __syncthreads();
   if (ctot > 0) {
+    for (int t = c; t < 5 * H + G; t += blockDim.x) {
+      if (t < 4 * H) atomicAdd(&gw[po[P_EE_W1] + t], acc[t]);
+      else if (t < 5 * H) atomicAdd(&gw[po[P_EE_B1] + t - 4 * H], acc[t]);
+      else atomicAdd(&gw[po[P_EE_SIGMA] + t - 5 * H], acc[t]);
+    }
 #pragma unroll
     for (int h = 0; h < H; ++h) atomicAdd(&gw[po[P_EE_W2] + h * d + c], gW2[h]);
 #pragma unroll
@@ -393,8 +415,8 @@ __global__ void en_bwd_kernel(int Wc, int n, int n_up, int N, int d, const doubl
     atomicAdd(&gw[po[P_NUC_EMB] + (int64_t)m * d + c], dfv);
 #pragma unroll
     for (int k = 0; k < 4; ++k) gWf[k] += feat[H + G + k].v * dfv;
-    filter_bwd<T, W>(feat, dv, T(rr), T(cnuc), p.en_w1 + (int64_t)m * 4 * H, p.en_b1 + (int64_t)m * H,
-                     p.en_sigma, w2, we, gv, ev, dgam, gW2, gWe, part, red48,
+    filter_bwd<false, T, W>(feat, dv, T(rr), T(cnuc), p.en_w1 + (int64_t)m * 4 * H, p.en_b1 + (int64_t)m * H,
+                     p.en_sigma, w2, we, gv, ev, dgam, gW2, gWe, part, red48, nullptr,
                      gw + po[P_EN_W1] + (int64_t)m * 4 * H, gw + po[P_EN_B1] + (int64_t)m * H,
                      gw + po[P_EN_SIGMA]);
   }

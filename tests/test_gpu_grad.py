@@ -38,6 +38,25 @@ def test_water_fp64_gradient_matches_oracle():
     assert not bad, bad
 
 
+def test_width32_fp64_gradient_matches_oracle():
+    """The narrowest width the library takes (d = 32): the filter backward
+    runs CTAs of 32 threads, which handle the 48 reduced filter values
+    (16 hidden units, 32 Gaussian widths) two per thread."""
+    s = synth.water()
+    arch = synth.Arch(width=32, n_layers=2, n_det=2)
+    p = synth.init_params(s, arch, 5)
+    r = synth.walkers(s, 3, 55)
+    ref = O.grad_logpsi(s, arch, p, r)
+    f = fire.Fire(s, arch, p, "fp64")
+    g = f.unflatten(f.grad_logpsi(r)["grad"].cpu().numpy())
+    for name in ("ee_sigma", "en_sigma"):
+        assert np.abs(ref[name][..., 16:]).max() > 0, name
+    worst = {name: float((np.abs(g[name] - ref[name]) / np.maximum(np.abs(ref[name]), 1.0)).max())
+             for name in ref}
+    bad = {k: v for k, v in worst.items() if v > 1e-9}
+    assert not bad, bad
+
+
 def test_water_fp64_gradient_matches_finite_differences():
     w = synth.workload("water")
     r, p = synth.make_inputs(w, 2)
