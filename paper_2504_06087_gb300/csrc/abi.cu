@@ -298,6 +298,7 @@ int make_plan(const fire_system_t* sys, const fire_arch_t* ar, int64_t W, int pr
   // rest by column panels on the LU factors
   const size_t invsm = (pl->tsz == 4 && n <= 192) ? gj_smem_bytes(n) : inverse_panel_smem(n, pl->lsz);
   const size_t lim = 227 * 1024;
+  if (lu_smem_bytes(n, pl->lsz) > lim) return FIRE_ERR_UNSUPPORTED;   // the LU panel and U12 block
   if (dm.deriv && (ctsm > lim || invsm > lim)) return FIRE_ERR_UNSUPPORTED;
   pl->Wc = wc;
   pl->nchunks = (W + wc - 1) / wc;

@@ -73,10 +73,22 @@ __global__ void phi_assemble_kernel(int Wc, int n, int n_up, int D, const T* __r
   }
 }
 
+// |v| as an unsigned key that orders like |v| for every non-NaN value (the
+// IEEE bit pattern without the sign bit), so the pivot search compares
+// integers and keeps the float64 pipe for the elimination.
+__device__ __forceinline__ unsigned long long mag_key(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ unsigned long long mag_key(float v) {
+  return (unsigned long long)((unsigned)__float_as_int(v) & 0x7fffffffu);
+}
+
 // Blocked right-looking LU with partial pivoting, one CTA per matrix, the
 // matrix in global memory (L2-resident), the current panel and U12 block in
 // shared memory.  Writes the pivots, log|det| and sign (0 and -inf for an
-// exactly zero pivot).
+// exactly zero pivot).  The float64 pipe is the bottleneck, so the pivot
+// search compares magnitude keys (mag_key) and the multipliers of a column
+// use one reciprocal of the pivot, formed by one thread.
 template <typename LT, int NB>
 __global__ void lu_kernel(int n, LT* __restrict__ M, int32_t* __restrict__ piv,
                           double* __restrict__ logabs, double* __restrict__ sgn) {
@@ -84,10 +96,11 @@ __global__ void lu_kernel(int n, LT* __restrict__ M, int32_t* __restrict__ piv,
   constexpr int PS = NB + 1;                   // panel row stride: rows fall in different banks
   LT* P = reinterpret_cast<LT*>(lu_smem);      // [n][NB + 1]
   LT* U = P + (int64_t)n * PS;                 // [NB][n]
-  __shared__ double red_v[32];
+  __shared__ unsigned long long red_v[32];
   __shared__ int red_i[32];
   __shared__ int s_piv;
   __shared__ int s_zero;
+  __shared__ LT s_rinv;
   LT* A = M + (int64_t)blockIdx.x * n * n;
   int32_t* pv = piv + (int64_t)blockIdx.x * n;
   const int tid = threadIdx.x, bd = blockDim.x;
@@ -102,27 +115,28 @@ __global__ void lu_kernel(int n, LT* __restrict__ M, int32_t* __restrict__ piv,
     __syncthreads();
     for (int kk = 0; kk < nb; ++kk) {
       // argmax |P[r][kk]| over r in [kk, pr), first index on ties
-      double best = -1.0;
+      unsigned long long best = 0;
       int bi = kk;
       for (int r = kk + tid; r < pr; r += bd) {
-        double v = fabs((double)P[r * PS + kk]);
+        const unsigned long long v = mag_key(P[r * PS + kk]);
         if (v > best) { best = v; bi = r; }
       }
       for (int o = 16; o > 0; o >>= 1) {
-        double ov = __shfl_xor_sync(0xffffffffu, best, o);
-        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        const unsigned long long ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
       }
       if ((tid & 31) == 0) { red_v[tid >> 5] = best; red_i[tid >> 5] = bi; }
       __syncthreads();
       if (tid == 0) {
-        double b = red_v[0];
+        unsigned long long b = red_v[0];
         int ib = red_i[0];
         for (int q = 1; q < (bd + 31) / 32; ++q)
           if (red_v[q] > b || (red_v[q] == b && red_i[q] < ib)) { b = red_v[q]; ib = red_i[q]; }
         s_piv = ib;
         pv[k0 + kk] = k0 + ib;
-        if (!(b > 0.0)) s_zero = 1;
+        if (b == 0) s_zero = 1;
+        s_rinv = b == 0 ? LT(0) : LT(1) / P[ib * PS + kk];
       }
       __syncthreads();
       const int p = s_piv;
@@ -134,10 +148,10 @@ __global__ void lu_kernel(int n, LT* __restrict__ M, int32_t* __restrict__ piv,
         }
       }
       __syncthreads();
-      const LT pivot = P[kk * PS + kk];
+      const LT pivot = P[kk * PS + kk], rinv = s_rinv;
       if (pivot != LT(0)) {
         for (int r = kk + 1 + tid; r < pr; r += bd) {
-          LT l = P[r * PS + kk] / pivot;
+          LT l = P[r * PS + kk] * rinv;
           P[r * PS + kk] = l;
           for (int c = kk + 1; c < nb; ++c) P[r * PS + c] -= l * P[kk * PS + c];
         }

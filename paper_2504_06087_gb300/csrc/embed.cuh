@@ -432,12 +432,15 @@ __global__ void msg_kernel(int Wc, int n, int n_up, int d, int K, const double* 
 //   y = SiLU(z + b)  (residual: x += y), tangents y_t = SiLU'(z) z_t,
 //   Laplacian y_l = SiLU'(z) z_l + SiLU''(z) sum_t z_t^2.
 // Block b spans rows off[b] .. off[b+1]-1 (or b*stride .. if off == nullptr).
-// One CTA per block; threads stride over the ncol columns.
+// One CTA per block; threads stride over the ncol columns.  With yall == 0
+// (no residual, split output Yb given) only the value row goes to Y: the
+// other rows are consumed through Yb alone.
 template <typename T, typename W>
 __global__ void __launch_bounds__(256, 4) fl_act_kernel(int ncol, const int64_t* __restrict__ off, int64_t stride,
                               const T* __restrict__ Z, int64_t ldz, const W* bias,
                               T* __restrict__ Y, int64_t ldy, int residual,
-                              __nv_bfloat16* __restrict__ Yb = nullptr, int ync = 1, int64_t ycs = 0) {
+                              __nv_bfloat16* __restrict__ Yb = nullptr, int ync = 1, int64_t ycs = 0,
+                              int yall = 1) {
   const int b = blockIdx.x;
   int64_t r0, r1;
   if (off) { r0 = off[b]; r1 = off[b + 1]; }
@@ -451,7 +454,7 @@ __global__ void __launch_bounds__(256, 4) fl_act_kernel(int ncol, const int64_t*
     T sq = T(0);
     auto put = [&](int64_t q, T v) {
       T o = residual ? Y[q * ldy + c] + v : v;
-      Y[q * ldy + c] = o;
+      if (yall || q == r0) Y[q * ldy + c] = o;
       if (Yb) store_split_bf16(Yb + q * ldy + c, ycs, ync, (float)o);
     };
     // tangent rows, eight at a time: the loads of a group are issued before
@@ -469,7 +472,7 @@ __global__ void __launch_bounds__(256, 4) fl_act_kernel(int ncol, const int64_t*
       for (int u = 0; u < 8; ++u) {
         sq += zt[u] * zt[u];
         const T o = residual ? yo[u] + f1 * zt[u] : f1 * zt[u];
-        Y[(q + u) * ldy + c] = o;
+        if (yall) Y[(q + u) * ldy + c] = o;
         if (Yb) store_split_bf16(Yb + (q + u) * ldy + c, ycs, ync, (float)o);
       }
     }

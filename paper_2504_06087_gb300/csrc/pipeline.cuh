@@ -249,6 +249,13 @@ struct Runner {
   void row_gemm(const T* A, const __nv_bfloat16* Ab, int64_t lda, int64_t a_rows, const T* B,
                 const __nv_bfloat16* Bt, int64_t ldb, T* C, int64_t ldc, const int64_t* m_range,
                 int64_t m_begin, int64_t m_end, int64_t m_cap, int N, int K, int nc = 1) {
+    if (!row_gemm_tc(A, Ab, lda, a_rows, B, Bt, ldb, C, ldc, m_range, m_begin, m_end, m_cap, N, K, nc))
+      gemm<T>(s, A, lda, B, ldb, false, C, ldc, m_begin, m_end, m_range, m_cap, N, K);
+  }
+  // The tensor-core form of row_gemm; false (nothing launched) where it does not apply.
+  bool row_gemm_tc(const T* A, const __nv_bfloat16* Ab, int64_t lda, int64_t a_rows, const T* B,
+                   const __nv_bfloat16* Bt, int64_t ldb, T* C, int64_t ldc, const int64_t* m_range,
+                   int64_t m_begin, int64_t m_end, int64_t m_cap, int N, int K, int nc) {
     if constexpr (sizeof(T) == 4) {
       if (Ab && Bt && K % 64 == 0) {
         int rc = tc::gemm_bf16(s, Ab, lda, a_rows, Bt, N, K, reinterpret_cast<float*>(C), ldc, m_begin, m_end,
@@ -261,12 +268,12 @@ struct Runner {
             scatter_value_rows_kernel<T><<<vr_nb, 256, 0, s>>>(N, vr_off, vr_C, C, ldc);
             launches += 3;
           }
-          return;
+          return true;
         }
         tc_rc = rc;
       }
     }
-    gemm<T>(s, A, lda, B, ldb, false, C, ldc, m_begin, m_end, m_range, m_cap, N, K);
+    return false;
   }
 
   // SiLU-MLP readout with two hidden layers over ragged blocks (rows of X
@@ -280,8 +287,16 @@ struct Runner {
     if (a_rows < 0) a_rows = capA;   // rows between the bf16 components of Xinb and Yb
     if (nc < 0) nc = nc_jas;
     row_gemm(Xin, Xinb, ldx, a_rows, w1, w1b, J, Z, ldz, range, rb, re, cap, J, din, nc);
-    fl_act_kernel<T, T><<<nblk, 256, 0, s>>>(J, off, stride, Z, ldz, b1, Y, ldy, 0, Yb, nc, a_rows * ldy);
-    row_gemm(Y, Yb, ldy, a_rows, w2, w2b, J, Z, ldz, range, rb, re, cap, J, J, nc);
+    // the hidden layer feeds a tensor-core product through Yb: of the float
+    // rows only the value rows (read again in fp32) are stored; should the
+    // product not apply, the layer is recomputed in full for the fallback
+    const bool via_b = sizeof(T) == 4 && Yb && w2b && J % 64 == 0;
+    fl_act_kernel<T, T><<<nblk, 256, 0, s>>>(J, off, stride, Z, ldz, b1, Y, ldy, 0, Yb, nc, a_rows * ldy,
+                                             via_b ? 0 : 1);
+    if (!row_gemm_tc(Y, Yb, ldy, a_rows, w2, w2b, J, Z, ldz, range, rb, re, cap, J, J, nc)) {
+      if (via_b) fl_act_kernel<T, T><<<nblk, 256, 0, s>>>(J, off, stride, Z, ldz, b1, Y, ldy, 0);
+      gemm<T>(s, Y, ldy, w2, J, false, Z, ldz, rb, re, range, cap, J, J);
+    }
     // last activation fused with the readout vector: F = act(Z + b2) . w3
     const int max_rows = off ? (int)pl.rows_per_el : (int)stride;
     fl_act_dot_kernel<T, T><<<nblk, 256, (size_t)8 * max_rows * sizeof(T), s>>>(J, off, stride, Z, ldz, b2, w3, F,
