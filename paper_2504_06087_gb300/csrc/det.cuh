@@ -874,6 +874,17 @@ constexpr int kC3Buckets = 5;
 constexpr int kC3BucketMax[kC3Buckets] = {27, 32, 36, 48, 60};
 constexpr int kC3BucketThreads[kC3Buckets] = {64, 96, 128, 192, 320};
 struct C3Buckets { int v[kC3Buckets]; };
+// Every bucket's transform pass has at most two (member, quad) items per
+// thread: 4 kfill <= 2 NT at the bucket maximum (kfill grows with m).
+constexpr bool c3_transform_fits() {
+  for (int q = 0; q < kC3Buckets; ++q) {
+    const int m = kC3BucketMax[q];
+    const int a = 3 * ((m + 2) / 3), b = 4 * ((m + 3) / 4);
+    if ((a > b ? a : b) * (kC3Chunk / 4) > 2 * kC3BucketThreads[q]) return false;
+  }
+  return true;
+}
+static_assert(c3_transform_fits(), "contract3 transform items exceed two per thread");
 
 // Sorts the tangent electrons e = w n + n' of a chunk into the buckets by
 // their neighbourhood size m = 1 + |N_n'| (warp-aggregated atomics; the
@@ -994,13 +1005,17 @@ contract3_kernel(int Wc, int n, int n_up, int K, int mlo, int mhi, int dd, int D
     rrow[q] = rr;
   }
   __syncthreads();
+  // a thread always copies quad j = tid % NJ of its rows (NT is a multiple
+  // of NJ), rows tid / NJ, tid / NJ + NT / NJ, ...
+  static_assert(NT % NJ == 0, "thread count must be a multiple of the quads per row");
+  const int jq = tid % NJ;
   auto issue = [&](int c0) {
-    for (int e = tid; e < nraw * NJ; e += NT) {
-      const int q = e / NJ, j = e - q * NJ;
-      const int l = c0 + 4 * j;
+    const int l = c0 + 4 * jq;
+    const bool lin = l < n;
+    for (int q = tid / NJ; q < nraw; q += NT / NJ) {
       const float* src = rsrc[q];
-      const bool ok = src != nullptr && l < n;
-      cp_async16(raw + rrow[q] * RS + 4 * j, ok ? src + l : O, ok ? 16 : 0);
+      const bool ok = lin && src != nullptr;
+      cp_async16(raw + rrow[q] * RS + 4 * jq, ok ? src + l : O, ok ? 16 : 0);
     }
     cp_async_commit();
   };
@@ -1028,8 +1043,14 @@ contract3_kernel(int Wc, int n, int n_up, int K, int mlo, int mhi, int dd, int D
   for (int l0 = 0; l0 < n; l0 += LC) {
     cp_async_wait_all();
     __syncthreads();   // the raw chunk has landed; the previous chunk is consumed
-    for (int e = tid; e < kfill * (LC / 4); e += NT) {
-      const int k = e % kfill, q4 = e / kfill;
+    // transform items e = (quad q4, member k), k fastest: at most two per
+    // thread (4 kfill <= 2 NT in every bucket); q4 = e / kfill by compares
+#pragma unroll 1
+    for (int it = 0; it < 2; ++it) {
+      const int e = tid + it * NT;
+      if (e >= kfill * (LC / 4)) continue;
+      const int q4 = (e >= kfill) + (e >= 2 * kfill) + (e >= 3 * kfill);
+      const int k = e - q4 * kfill;
       const float4 o0 = *reinterpret_cast<const float4*>(raw + (3 * k) * RS + 4 * q4);
       const float4 o1 = *reinterpret_cast<const float4*>(raw + (3 * k + 1) * RS + 4 * q4);
       const float4 o2 = *reinterpret_cast<const float4*>(raw + (3 * k + 2) * RS + 4 * q4);
