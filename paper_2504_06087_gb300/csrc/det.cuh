@@ -400,6 +400,127 @@ __global__ void __launch_bounds__(384, 1) gj_inverse_kernel(int n, const IT* __r
   }
 }
 
+// gj_inverse_kernel with the pivot rows known up front (the interchanges of a
+// partial-pivoting LU of the same matrix, LAPACK order).  The rows are loaded
+// in pivot order -- position k holds original row piv[k] -- so step k
+// pivots on position k and column k, and S ends as the inverse of the
+// row-permuted matrix: (Phi^-1)[l][c] = S[l][stp[c]] with stp[piv[k]] = k.
+// Steps run in unrolled groups of 24 = lcm(12, 8), so the pivot row's place
+// in its register tile (k mod 12) and the pivot column's (k mod 8) are
+// static: the owners store them with 128-bit stores and every thread reads
+// its slices with 128-bit loads.  Every element takes the arithmetic of
+// gj_inverse_kernel, in the same order.
+template <typename IT, typename OT>
+__global__ void __launch_bounds__(384, 1) gj_inverse_pre_kernel(int n, const IT* __restrict__ Phi,
+                                                                OT* __restrict__ AT,
+                                                                const int32_t* __restrict__ lu_piv) {
+  constexpr int TR = kGjTR, TC = kGjTC, U = 24;
+  static_assert(U % TR == 0 && U % TC == 0 && TR % 4 == 0 && TC % 4 == 0, "step group and vector slices");
+  extern __shared__ __align__(16) unsigned char gj_smem[];
+  float* S = reinterpret_cast<float*>(gj_smem);                      // [n][n] final matrix
+  float* prow = S + (((int64_t)n * n + 3) & ~(int64_t)3);            // [2][256] pivot row, 16-byte aligned
+  float* pcol = prow + 512;                                          // [2][256] pivot column
+  int* piv = reinterpret_cast<int*>(pcol + 512);                     // [n] position -> original row
+  int* stp = piv + 256;                                              // [n] original row -> position
+  const int Gr = (n + TR - 1) / TR, Gc = (n + TC - 1) / TC;
+  const int tid = threadIdx.x;
+  const int tr = tid / Gc, tc = tid % Gc;
+  const bool live = tr < Gr;
+  if (tid == 0) {
+    const int32_t* lp = lu_piv + (int64_t)blockIdx.x * n;
+    for (int k = 0; k < n; ++k) stp[k] = k;
+    for (int k = 0; k < n; ++k) {
+      const int q = lp[k];
+      const int t = stp[k];
+      stp[k] = stp[q];
+      stp[q] = t;
+    }
+    for (int k = 0; k < n; ++k) piv[k] = stp[k];
+    for (int k = 0; k < n; ++k) stp[piv[k]] = k;
+  }
+  __syncthreads();
+  const IT* P = Phi + (int64_t)blockIdx.x * n * n;
+  float a[TR][TC];
+#pragma unroll
+  for (int i = 0; i < TR; ++i) {
+    const int r = TR * tr + i;
+    const bool rin = live && r < n;
+    const int64_t src = rin ? (int64_t)piv[r] * n : 0;
+#pragma unroll
+    for (int j = 0; j < TC; ++j) {
+      const int c = TC * tc + j;
+      a[i][j] = (rin && c < n) ? (float)P[src + c] : 0.f;
+    }
+  }
+  for (int k0 = 0; k0 < n; k0 += U) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int k = k0 + u;
+      if (k >= n) break;
+      const int pt = k0 / TR + u / TR, kt = k0 / TC + u / TC;
+      const int pi = u % TR, kj = u % TC;
+      float* pr = prow + 256 * (u & 1);
+      float* pc = pcol + 256 * (u & 1);
+      if (live && tr == pt) {
+        float4* q = reinterpret_cast<float4*>(pr + TC * tc);
+#pragma unroll
+        for (int j4 = 0; j4 < TC / 4; ++j4)
+          q[j4] = make_float4(a[pi][4 * j4], a[pi][4 * j4 + 1], a[pi][4 * j4 + 2], a[pi][4 * j4 + 3]);
+      }
+      if (live && tc == kt) {
+        float4* q = reinterpret_cast<float4*>(pc + TR * tr);
+#pragma unroll
+        for (int i4 = 0; i4 < TR / 4; ++i4)
+          q[i4] = make_float4(a[4 * i4][kj], a[4 * i4 + 1][kj], a[4 * i4 + 2][kj], a[4 * i4 + 3][kj]);
+      }
+      __syncthreads();
+      const float v = pc[k];
+      const float iv = 1.f / v;
+      if (live) {
+        float f[TR], sp[TC];
+#pragma unroll
+        for (int i4 = 0; i4 < TR / 4; ++i4) {
+          const float4 q = reinterpret_cast<const float4*>(pc + TR * tr)[i4];
+          f[4 * i4] = q.x; f[4 * i4 + 1] = q.y; f[4 * i4 + 2] = q.z; f[4 * i4 + 3] = q.w;
+        }
+        if (tr == pt) f[pi] = 0.f;
+#pragma unroll
+        for (int j4 = 0; j4 < TC / 4; ++j4) {
+          const float4 q = reinterpret_cast<const float4*>(pr + TC * tc)[j4];
+          sp[4 * j4] = q.x * iv; sp[4 * j4 + 1] = q.y * iv; sp[4 * j4 + 2] = q.z * iv; sp[4 * j4 + 3] = q.w * iv;
+        }
+#pragma unroll
+        for (int j = 0; j < TC; ++j)
+#pragma unroll
+          for (int i = 0; i < TR; ++i) a[i][j] = fmaf(-f[i], sp[j], a[i][j]);
+        if (tc == kt) {
+#pragma unroll
+          for (int i = 0; i < TR; ++i) a[i][kj] = -f[i] * iv;
+        }
+        if (tr == pt) {
+#pragma unroll
+          for (int j = 0; j < TC; ++j) a[pi][j] = (tc == kt && j == kj) ? iv : sp[j];
+        }
+      }
+    }
+  }
+  if (live)
+#pragma unroll
+    for (int i = 0; i < TR; ++i)
+#pragma unroll
+      for (int j = 0; j < TC; ++j) {
+        const int r = TR * tr + i, c = TC * tc + j;
+        if (r < n && c < n) S[r * n + c] = a[i][j];
+      }
+  __syncthreads();
+  // AT[k][l] = (Phi^-1)[l][k] = S[l][stp[k]]
+  OT* out = AT + (int64_t)blockIdx.x * n * n;
+  for (int e = tid; e < n * n; e += blockDim.x) {
+    const int kk = e / n, l = e % n;
+    out[e] = (OT)S[l * n + stp[kk]];
+  }
+}
+
 // Tiles per thread of contract_kernel for neighbourhoods of up to mcap
 // members (3 x 4 tiles, one pass).
 inline int contract_maxt(int mcap) {

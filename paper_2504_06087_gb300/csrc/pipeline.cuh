@@ -911,7 +911,8 @@ struct Runner {
         if (gj) {
           const int thr = gj_threads(n);
           // pivot rows from the float64 LU when it has already run on this stream
-          gj_inverse_kernel<float, T><<<wc * D, thr, gj_smem_bytes(n), s>>>(n, Phif, Ainv, lu_side ? nullptr : piv);
+          if (lu_side) gj_inverse_kernel<float, T><<<wc * D, thr, gj_smem_bytes(n), s>>>(n, Phif, Ainv, nullptr);
+          else gj_inverse_pre_kernel<float, T><<<wc * D, thr, gj_smem_bytes(n), s>>>(n, Phif, Ainv, piv);
         } else {
           inverse_from_lu(n, (int64_t)wc * D, LUb, piv, Ainv);
         }
@@ -1374,6 +1375,7 @@ inline int set_smem_limits() {
   raise((const void*)lu_kernel<LT, 32>);
   raise((const void*)att_pool_kernel<T>);
   raise((const void*)gj_inverse_kernel<float, T>);
+  raise((const void*)gj_inverse_pre_kernel<float, T>);
   raise((const void*)mcmc_att_kernel<T>);
   raise((const void*)inverse_panel_kernel<LT, LT, T>);
   raise((const void*)inverse_panel_kernel<LT, T, T>);
