@@ -486,6 +486,97 @@ __global__ void __launch_bounds__(256, 4) fl_act_kernel(int ncol, const int64_t*
   }
 }
 
+// fl_act_kernel for float rows, four columns per thread: 128-bit loads and
+// stores, eight rows of loads in flight per thread (the layer is bound by
+// HBM bandwidth, and one column per thread kept too few bytes in flight).
+// CTAs of 64 threads, one block each.  Requires ncol, ldz, ldy and ycs
+// multiples of 4 and Z, Y 16-byte, Yb 8-byte aligned (fl_act4_ok).
+__device__ __forceinline__ void store_split_bf16x4(__nv_bfloat16* p, int64_t cstride, int nc, float4 v) {
+  for (int c = 0; c < nc; ++c) {
+    const __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y), h23 = __floats2bfloat162_rn(v.z, v.w);
+    uint2 u;
+    u.x = *reinterpret_cast<const uint32_t*>(&h01);
+    u.y = *reinterpret_cast<const uint32_t*>(&h23);
+    *reinterpret_cast<uint2*>(p + c * cstride) = u;
+    v.x -= __low2float(h01);
+    v.y -= __high2float(h01);
+    v.z -= __low2float(h23);
+    v.w -= __high2float(h23);
+  }
+}
+inline bool fl_act4_ok(int ncol, int64_t ldz, int64_t ldy, int64_t ycs, const void* Z, const void* Y,
+                       const void* Yb) {
+  return ncol % 4 == 0 && ldz % 4 == 0 && ldy % 4 == 0 && ycs % 4 == 0 && (reinterpret_cast<uintptr_t>(Z) & 15) == 0 &&
+         (reinterpret_cast<uintptr_t>(Y) & 15) == 0 && (reinterpret_cast<uintptr_t>(Yb) & 7) == 0;
+}
+template <typename W>
+__global__ void __launch_bounds__(64, 6) fl_act4_kernel(int ncol, const int64_t* __restrict__ off, int64_t stride,
+                                                       const float* __restrict__ Z, int64_t ldz, const W* bias,
+                                                       float* __restrict__ Y, int64_t ldy, int residual,
+                                                       __nv_bfloat16* __restrict__ Yb, int ync, int64_t ycs,
+                                                       int yall) {
+  const int b = blockIdx.x;
+  int64_t r0, r1;
+  if (off) { r0 = off[b]; r1 = off[b + 1]; }
+  else { r0 = (int64_t)b * stride; r1 = r0 + stride; }
+  const int64_t nr = r1 - r0;
+  if (nr <= 0) return;
+  auto ld4 = [](const float* p) { return *reinterpret_cast<const float4*>(p); };
+  for (int c = 4 * threadIdx.x; c < ncol; c += 4 * blockDim.x) {
+    float4 z = ld4(Z + r0 * ldz + c);
+    if (bias) { z.x += float(bias[c]); z.y += float(bias[c + 1]); z.z += float(bias[c + 2]); z.w += float(bias[c + 3]); }
+    float f[4], f1[4], f2[4];
+    silu3<float>(z.x, f[0], f1[0], f2[0]);
+    silu3<float>(z.y, f[1], f1[1], f2[1]);
+    silu3<float>(z.z, f[2], f1[2], f2[2]);
+    silu3<float>(z.w, f[3], f1[3], f2[3]);
+    float4 sq = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto put = [&](int64_t q, float4 o) {
+      if (residual) {
+        const float4 y = ld4(Y + q * ldy + c);
+        o.x += y.x; o.y += y.y; o.z += y.z; o.w += y.w;
+      }
+      if (yall || q == r0) *reinterpret_cast<float4*>(Y + q * ldy + c) = o;
+      if (Yb) store_split_bf16x4(Yb + q * ldy + c, ycs, ync, o);
+    };
+    // tangent rows, eight at a time: the loads of a group are issued before
+    // its stores
+    int64_t q = r0 + 2;
+    for (; q + 8 <= r1; q += 8) {
+      float4 zt[8], yo[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) zt[u] = ld4(Z + (q + u) * ldz + c);
+      if (residual) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) yo[u] = ld4(Y + (q + u) * ldy + c);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        sq.x += zt[u].x * zt[u].x; sq.y += zt[u].y * zt[u].y; sq.z += zt[u].z * zt[u].z; sq.w += zt[u].w * zt[u].w;
+        float4 o;
+        if (residual)
+          o = make_float4(yo[u].x + f1[0] * zt[u].x, yo[u].y + f1[1] * zt[u].y, yo[u].z + f1[2] * zt[u].z,
+                          yo[u].w + f1[3] * zt[u].w);
+        else
+          o = make_float4(f1[0] * zt[u].x, f1[1] * zt[u].y, f1[2] * zt[u].z, f1[3] * zt[u].w);
+        if (yall) *reinterpret_cast<float4*>(Y + (q + u) * ldy + c) = o;
+        if (Yb) store_split_bf16x4(Yb + (q + u) * ldy + c, ycs, ync, o);
+      }
+    }
+    for (; q < r1; ++q) {
+      const float4 zt = ld4(Z + q * ldz + c);
+      sq.x += zt.x * zt.x; sq.y += zt.y * zt.y; sq.z += zt.z * zt.z; sq.w += zt.w * zt.w;
+      put(q, make_float4(f1[0] * zt.x, f1[1] * zt.y, f1[2] * zt.z, f1[3] * zt.w));
+    }
+    if (nr > 1) {
+      const float4 zl = ld4(Z + (r0 + 1) * ldz + c);
+      put(r0 + 1, make_float4(f1[0] * zl.x + f2[0] * sq.x, f1[1] * zl.y + f2[1] * sq.y, f1[2] * zl.z + f2[2] * sq.z,
+                              f1[3] * zl.w + f2[3] * sq.w));
+    }
+    put(r0, make_float4(f[0], f[1], f[2], f[3]));
+  }
+}
+
 // The last activation of a readout MLP fused with its readout vector:
 // F[q] = sum_c SiLU-layer(Z + b)[q][c] * wv[c] for every row q of every block
 // (same forward-Laplacian rules as fl_act_kernel), without storing the

@@ -276,6 +276,20 @@ struct Runner {
     return false;
   }
 
+  // Forward-Laplacian SiLU layer over ragged blocks (fl_act_kernel); the
+  // float rows take the four-column form where its alignment holds.
+  void fl_act(int ncol, const int64_t* off, int64_t stride, const T* Z, int64_t ldz, const T* bias, T* Y,
+              int64_t ldy, int residual, __nv_bfloat16* Yb, int ync, int64_t ycs, int yall, int64_t nblk) {
+    if constexpr (sizeof(T) == 4) {
+      if (fl_act4_ok(ncol, ldz, ldy, ycs, Z, Y, Yb)) {
+        fl_act4_kernel<T><<<nblk, 64, 0, s>>>(ncol, off, stride, reinterpret_cast<const float*>(Z), ldz, bias,
+                                              reinterpret_cast<float*>(Y), ldy, residual, Yb, ync, ycs, yall);
+        return;
+      }
+    }
+    fl_act_kernel<T, T><<<nblk, 256, 0, s>>>(ncol, off, stride, Z, ldz, bias, Y, ldy, residual, Yb, ync, ycs, yall);
+  }
+
   // SiLU-MLP readout with two hidden layers over ragged blocks (rows of X
   // given by blk offsets or a fixed stride) -> per-row scalar F.
   void mlp_readout(const T* Xin, const __nv_bfloat16* Xinb, int64_t ldx, int din, const int64_t* range,
@@ -291,8 +305,7 @@ struct Runner {
     // rows only the value rows (read again in fp32) are stored; should the
     // product not apply, the layer is recomputed in full for the fallback
     const bool via_b = sizeof(T) == 4 && Yb && w2b && J % 64 == 0;
-    fl_act_kernel<T, T><<<nblk, 256, 0, s>>>(J, off, stride, Z, ldz, b1, Y, ldy, 0, Yb, nc, a_rows * ldy,
-                                             via_b ? 0 : 1);
+    fl_act(J, off, stride, Z, ldz, b1, Y, ldy, 0, Yb, nc, a_rows * ldy, via_b ? 0 : 1, nblk);
     if (!row_gemm_tc(Y, Yb, ldy, a_rows, w2, w2b, J, Z, ldz, range, rb, re, cap, J, J, nc)) {
       if (via_b) fl_act_kernel<T, T><<<nblk, 256, 0, s>>>(J, off, stride, Z, ldz, b1, Y, ldy, 0);
       gemm<T>(s, Y, ldy, w2, J, false, Z, ldz, rb, re, range, cap, J, J);
@@ -787,8 +800,10 @@ struct Runner {
         return (WB && (tc_mask >> bit & 1)) ? WB + off : nullptr;
       };
       mark("msg", 1);
-      msg_kernel<T, T><<<nb, d, 0, s>>>(wc, n, n_up, d, K, r, c, p, idx, cnt, boff, H0, PQ, X, Xb, ncw,
-                                        capA * d, deriv);
+      // bf16 components of h^1: those the first MLP layer reads, else (no
+      // MLP layers) all that any consumer reads
+      msg_kernel<T, T><<<nb, d, 0, s>>>(wc, n, n_up, d, K, r, c, p, idx, cnt, boff, H0, PQ, X, Xb,
+                                        dm.L > 0 ? nc_mlp : ncw, capA * d, deriv);
       check("msg");
       if (dm.op == FIRE_OP_MCMC) {   // the Metropolis state keeps h^1 (value rows, block order)
         cudaMemcpyAsync(at<T>(pl.mc_H1), X, sizeof(T) * (size_t)nb * d, cudaMemcpyDeviceToDevice, s);
@@ -807,8 +822,10 @@ struct Runner {
         row_gemm(X, Xb, d, capA, p.mlp_w + (int64_t)l * d * d, wbm(0, pl.wb_mlp + kMaxSplit * (int64_t)l * d * d),
                  d, Z, ldb, fullr, 0, 0, cap, d, d, nc_mlp);
         mark("fl_act", 1);
-        fl_act_kernel<T, T><<<nb, 256, 0, s>>>(d, boff, 0, Z, ldb, p.mlp_b + (int64_t)l * d, X, d, 1, Xb,
-                                               ncw, capA * d);
+        // the bf16 components of the hidden rows: those the next layer's
+        // product reads, all that any consumer reads after the last layer
+        const int ncl = l + 1 < dm.L ? nc_mlp : ncw;
+        fl_act(d, boff, 0, Z, ldb, p.mlp_b + (int64_t)l * d, X, d, 1, Xb, ncl, capA * d, 1, nb);
       }
       // 7. envelopes and orbital values
       const int E = dm.E, NE = N * E;
