@@ -46,9 +46,28 @@ static bool make_map(CUtensorMap* m, const void* base, uint64_t rows, uint64_t c
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// fp32 output [rows][cols] with row stride ld (elements): 32 x 32 boxes,
+// 128-byte swizzle (the layout of the epilogue's store buffers).  The row
+// extent is left open (2^31 - 1 rows, or fewer so that it spans less than
+// 2^40 bytes): only tiles wholly inside the row range are stored through it.
+static bool make_map_c(CUtensorMap* m, const float* base, uint64_t cols, uint64_t ld) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || ((ld * 4) & 15) || cols < 1 || ld < cols) return false;
+  uint64_t rows = ((uint64_t)1 << 40) / (ld * 4);
+  if (rows > 0x7fffffffull) rows = 0x7fffffffull;
+  cuuint64_t dims[2] = {cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {ld * 4};
+  cuuint32_t box[2] = {32, 32};
+  cuuint32_t es[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int STAGES, int NC>
-static int launch(cudaStream_t s, const CUtensorMap& ma, const CUtensorMap& mb, const TcArgs& g, int64_t m_cap,
-                  int nt) {
+static int launch(cudaStream_t s, const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& mc,
+                  const TcArgs& g, int64_t m_cap, int nt) {
   const size_t sm = tc_smem_bytes(STAGES, NC, g.BN);
   if (cudaFuncSetAttribute(tc_gemm_kernel<STAGES, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
       cudaSuccess)
@@ -62,7 +81,7 @@ static int launch(cudaStream_t s, const CUtensorMap& ma, const CUtensorMap& mb, 
   }
   const int64_t tiles = ((m_cap + BM - 1) / BM) * nt;
   const int grid = (int)(tiles < n_sm ? tiles : n_sm);
-  tc_gemm_kernel<STAGES, NC><<<grid, 192, sm, s>>>(ma, mb, g);
+  tc_gemm_kernel<STAGES, NC><<<grid, 192, sm, s>>>(ma, mb, mc, g);
   return cudaGetLastError() == cudaSuccess ? FIRE_OK : FIRE_ERR_CUDA;
 }
 
@@ -113,15 +132,21 @@ int gemm_bf16_rows(cudaStream_t s, const void* A, int64_t lda, int64_t a_rows, c
   CUtensorMap ma, mb;
   if (!make_map(&ma, A, (uint64_t)a_rows * nc, (uint64_t)K, (uint64_t)lda, BM)) return FIRE_ERR_CUDA;
   if (!make_map(&mb, Bt, (uint64_t)b_rows * nc, (uint64_t)K, (uint64_t)K, (uint32_t)BN)) return FIRE_ERR_CUDA;
-  TcArgs g{C, ldc, m_begin, m_end, m_range, N, K, BN, a_rows, b_rows, b_row0, err};
-  if (nc == 1) return stages == 2 ? launch<2, 1>(s, ma, mb, g, m_cap, nt)
-                                   : (stages == 3 ? launch<3, 1>(s, ma, mb, g, m_cap, nt)
-                                                  : launch<4, 1>(s, ma, mb, g, m_cap, nt));
-  if (nc == 2) return stages == 2 ? launch<2, 2>(s, ma, mb, g, m_cap, nt)
-                                   : (stages == 3 ? launch<3, 2>(s, ma, mb, g, m_cap, nt)
-                                                  : launch<4, 2>(s, ma, mb, g, m_cap, nt));
-  return stages == 2 ? launch<2, 3>(s, ma, mb, g, m_cap, nt)
-                     : (stages == 3 ? launch<3, 3>(s, ma, mb, g, m_cap, nt) : launch<4, 3>(s, ma, mb, g, m_cap, nt));
+  // FIRE_TC_CSTORE=direct (diagnostic): every tile through the lanes' own stores
+  CUtensorMap mc;
+  memset(&mc, 0, sizeof(mc));
+  const char* cs = getenv("FIRE_TC_CSTORE");
+  const bool direct = cs && strcmp(cs, "direct") == 0;
+  const int c_tma = (!direct && make_map_c(&mc, C, (uint64_t)N, (uint64_t)ldc)) ? 1 : 0;
+  TcArgs g{C, ldc, m_begin, m_end, m_range, N, K, BN, a_rows, b_rows, b_row0, err, c_tma};
+  if (nc == 1) return stages == 2 ? launch<2, 1>(s, ma, mb, mc, g, m_cap, nt)
+                                   : (stages == 3 ? launch<3, 1>(s, ma, mb, mc, g, m_cap, nt)
+                                                  : launch<4, 1>(s, ma, mb, mc, g, m_cap, nt));
+  if (nc == 2) return stages == 2 ? launch<2, 2>(s, ma, mb, mc, g, m_cap, nt)
+                                   : (stages == 3 ? launch<3, 2>(s, ma, mb, mc, g, m_cap, nt)
+                                                  : launch<4, 2>(s, ma, mb, mc, g, m_cap, nt));
+  return stages == 2 ? launch<2, 3>(s, ma, mb, mc, g, m_cap, nt)
+                     : (stages == 3 ? launch<3, 3>(s, ma, mb, mc, g, m_cap, nt) : launch<4, 3>(s, ma, mb, mc, g, m_cap, nt));
 }
 
 // dst[c][n][k] = component c of src[k * lds + n] for a [K][N] source

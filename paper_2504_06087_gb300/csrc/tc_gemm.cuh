@@ -11,7 +11,12 @@
 // accumulator (tcgen05.ld 32x32b, each warp its 32-lane quarter; every lane
 // stores its row's 32-column slices straight from registers with 128-bit
 // stores), so a tile's epilogue overlaps the next tile's main loop.  The row range of A may live on the
-// device ({begin, end}).
+// device ({begin, end}).  Where C allows a tensor map (16-byte aligned rows),
+// the full 128-row tiles leave through TMA instead: each epilogue warp
+// writes its 32 x 32 chunk into a 128-byte-swizzled shared buffer
+// (conflict-free) and one lane stores it with cp.async.bulk.tensor, so the
+// L1 -> L2 path carries whole lines rather than a 16-byte piece of 32 rows
+// per store instruction (that request path, 76 % busy, bounded the product).
 //
 // Every mbarrier wait is bounded: after kSpinLimit polls the kernel records
 // an error in *err, stops issuing work, waits (bounded) for its own copies
@@ -67,6 +72,21 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
       ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
       : "memory");
+}
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"((uint64_t)map),
+               "r"(smem_u32(src)), "r"(x), "r"(y)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the shared-memory sources of this thread's bulk stores have been read
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// this thread's bulk stores are complete
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// generic-proxy shared-memory writes become visible to the async proxy (TMA)
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
@@ -146,6 +166,7 @@ struct TcArgs {
   int64_t b_comp_rows;           // rows between the bf16 components of Bt
   int64_t b_row0;                // first row of Bt inside each component
   int* err;                      // device error word (timeouts)
+  int c_tma;                     // full tiles leave through the C tensor map
 };
 
 // Split-bf16 products (Henry, Tang & Heinecke 2019): a value x is stored as
@@ -161,15 +182,18 @@ __host__ __device__ constexpr int split_q(int nc, int k) {
 }
 
 // Dynamic shared memory: STAGES x NC x (A tile 16 KB + B tile BN*128 B),
-// 1024-aligned.
+// then one 4 KB store buffer (32 rows x 32 fp32, 128-byte swizzle) per
+// epilogue warp, 1024-aligned.
 constexpr int kEpiWarps = 4;
+constexpr int kStoreBuf = 32 * 32 * 4;
 __host__ __device__ inline size_t tc_smem_bytes(int stages, int nc, int bn) {
-  return (size_t)stages * nc * ((size_t)BM * BK * 2 + (size_t)bn * BK * 2) + 1024;
+  return (size_t)stages * nc * ((size_t)BM * BK * 2 + (size_t)bn * BK * 2) + (size_t)kEpiWarps * kStoreBuf + 1024;
 }
 
 template <int STAGES, int NC>
 __global__ void __launch_bounds__(192, 1)
-tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcArgs g) {
+tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+               const __grid_constant__ CUtensorMap mapC, TcArgs g) {
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
   __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], tfull_bar[2], tempty_bar[2], done_bar;
   __shared__ uint32_t tmem_slot;
@@ -270,6 +294,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   } else if (warp >= 2) {
     // epilogue: warp w drains tensor-memory lanes 32 (w % 4) .. + 31
     const int q = warp & 3;
+    unsigned char* stbuf = base + (size_t)STAGES * stage_bytes;   // 1024-aligned (stage_bytes is)
     const bool vec = (g.ldc % 4 == 0) && ((reinterpret_cast<uintptr_t>(g.C) & 15) == 0);
     int64_t tl = 0;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
@@ -292,10 +317,30 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       // straight from registers to its row of C (eight 128-bit stores)
       const int64_t row = m0 + 32 * q + lane;
       float* crow = g.C + row * g.ldc + n0;
+      // full tiles through the tensor map (columns past N are clipped by it)
+      const bool tma = g.c_tma && m0 + BM <= me;
       for (int c0 = 0; c0 < BN; c0 += 32) {
         float v[32];
         tmem_ld32(tbase + (uint32_t)c0, v);
         const int nval = ncol - c0;
+        if (tma) {
+          if (nval <= 0) continue;
+          // the previous chunk's store has read the buffer
+          if (lane == 0) bulk_wait_read0();
+          __syncwarp();
+          unsigned char* sb = stbuf + (size_t)q * kStoreBuf + (size_t)lane * 128;
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            *reinterpret_cast<float4*>(sb + ((j ^ (lane & 7)) << 4)) =
+                make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) {
+            tma_store_2d(&mapC, stbuf + (size_t)q * kStoreBuf, n0 + c0, (int)(m0 + 32 * q));
+            bulk_commit();
+          }
+          continue;
+        }
         if (row < me && nval > 0) {
           if (vec && nval >= 32) {
             float4* d4 = reinterpret_cast<float4*>(crow + c0);
@@ -312,6 +357,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       __syncwarp();
       if (lane == 0) mbar_expect_tx(&tempty_bar[buf], 0);   // one arrival per epilogue warp
     }
+    // this warp's tensor stores complete before the CTA (and its shared memory) ends
+    if (lane == 0) bulk_wait0();
+    __syncwarp();
   }
   fence_before_sync();
   __syncthreads();
