@@ -317,14 +317,17 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       // straight from registers to its row of C (eight 128-bit stores)
       const int64_t row = m0 + 32 * q + lane;
       float* crow = g.C + row * g.ldc + n0;
-      // full tiles through the tensor map (columns past N are clipped by it)
+      // full-row tiles through the tensor map: a 32-column box either lies
+      // inside the tile or runs past N (clipped by the map); a box that
+      // would reach into the next tile (BN not a multiple of 32) takes the
+      // direct stores
       const bool tma = g.c_tma && m0 + BM <= me;
+      const bool last_nt = n0 + ncol == g.N;
       for (int c0 = 0; c0 < BN; c0 += 32) {
         float v[32];
         tmem_ld32(tbase + (uint32_t)c0, v);
         const int nval = ncol - c0;
-        if (tma) {
-          if (nval <= 0) continue;
+        if (tma && nval > 0 && (nval >= 32 || last_nt)) {
           // the previous chunk's store has read the buffer
           if (lane == 0) bulk_wait_read0();
           __syncwarp();
