@@ -70,8 +70,10 @@ static int launch(cudaStream_t s, const CUtensorMap& ma, const CUtensorMap& mb, 
                   const TcArgs& g, int64_t m_cap, int nt) {
   const size_t sm = tc_smem_bytes(STAGES, NC, g.BN);
   if (cudaFuncSetAttribute(tc_gemm_kernel<STAGES, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
-      cudaSuccess)
+      cudaSuccess) {
+    cudaGetLastError();   // the caller's next CUDA call must not see this error
     return FIRE_ERR_CUDA;
+  }
   static int n_sm = 0;
   if (n_sm == 0) {
     int dev = 0;
@@ -122,7 +124,7 @@ int gemm_bf16_rows(cudaStream_t s, const void* A, int64_t lda, int64_t a_rows, c
     const int v = atoi(e);
     if (v >= 2 && v <= 4) stages = v;
   }
-  int BN = bn_pref ? bn_pref : choose_bn(N, nc, stages);
+  int BN = bn_pref && tc_smem_bytes(stages, nc, bn_pref) <= 227 * 1024 ? bn_pref : choose_bn(N, nc, stages);
   if (const char* e = getenv("FIRE_TC_BN")) {
     const int v = atoi(e);
     if (v >= 16 && v <= 256 && v % 16 == 0 && tc_smem_bytes(stages, nc, v) <= 227 * 1024) BN = v;
