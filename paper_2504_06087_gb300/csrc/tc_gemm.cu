@@ -114,11 +114,16 @@ int gemm_bf16_rows(cudaStream_t s, const void* A, int64_t lda, int64_t a_rows, c
   if (b_row0 < 0 || b_row0 + N > b_rows) return FIRE_ERR_UNSUPPORTED;
   if (N < 1 || K < BK || K % BK || m_cap <= 0 || nc < 1 || nc > 3) return FIRE_ERR_UNSUPPORTED;
   int stages = nc == 1 ? 4 : (nc == 2 ? 3 : 2);
-  // wide two-component products (N >= 512): two stages of 192-column tiles
-  // moved the least data per output on GB300 (measured 890 vs 733 TFLOP/s of
-  // split products at M = 400k, N = 720, K = 256)
+  // wide two-component products (N >= 512): two stages of 256- or
+  // 192-column tiles, whichever computes fewer columns (256 on a tie).
+  // Measured on GB300 with the tensor-store epilogue at M = 400k, N = 720,
+  // K = 256: 1271 TFLOP/s of split products with 256 columns, 1149 with 192,
+  // 1210 with three stages of 128
   int bn_pref = 0;
-  if (nc == 2 && N >= 512) { stages = 2; bn_pref = 192; }
+  if (nc == 2 && N >= 512) {
+    stages = 2;
+    bn_pref = (N + 255) / 256 * 256 <= (N + 191) / 192 * 192 ? 256 : 192;
+  }
   // FIRE_TC_STAGES / FIRE_TC_BN (diagnostic): pipeline depth and tile width
   if (const char* e = getenv("FIRE_TC_STAGES")) {
     const int v = atoi(e);
