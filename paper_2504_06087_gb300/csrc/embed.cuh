@@ -663,7 +663,7 @@ __global__ void gather_value_rows_kernel(int nb, int d, const int64_t* __restric
   const int64_t ld = ldx < 0 ? d : ldx;
   for (int c = threadIdx.x; c < d; c += blockDim.x) {
     const T v = X[r0 * ld + c];
-    Hv[(int64_t)b * d + c] = v;
+    if (Hv) Hv[(int64_t)b * d + c] = v;
     if (Hb) store_split_bf16(Hb + (int64_t)b * d + c, hcs, hnc, (float)v);
   }
 }

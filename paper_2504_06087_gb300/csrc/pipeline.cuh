@@ -246,6 +246,8 @@ struct Runner {
   int vr_nb = 0;
   T* vr_A = nullptr;           // [nb][K] gathered value rows
   T* vr_C = nullptr;           // [nb][N] their products
+  __nv_bfloat16* vr_Ab = nullptr;   // [3][vr_cap][K] the gathered rows as three bf16 components
+  int64_t vr_cap = 0, vr_kmax = 0;  // component stride (rows) and widest K that vr_Ab holds
   void row_gemm(const T* A, const __nv_bfloat16* Ab, int64_t lda, int64_t a_rows, const T* B,
                 const __nv_bfloat16* Bt, int64_t ldb, T* C, int64_t ldc, const int64_t* m_range,
                 int64_t m_begin, int64_t m_end, int64_t m_cap, int N, int K, int nc = 1) {
@@ -262,11 +264,25 @@ struct Runner {
                                m_range, m_cap, &at<DevStatus>(pl.status)->tc_err, nc);
         if (rc == FIRE_OK) {
           if (fix_values && vr_off && m_range) {
-            // value rows (one per block) again in fp32: they set Phi and log|Psi|
-            gather_value_rows_kernel<T><<<vr_nb, 256, 0, s>>>(vr_nb, K, vr_off, A, vr_A, lda);
-            gemm<T>(s, vr_A, K, B, ldb, false, vr_C, N, 0, vr_nb, nullptr, vr_nb, N, K);
+            // value rows (one per block) again at float32 accuracy: they set
+            // Phi and log|Psi|.  Three-component split products (six
+            // products) on the tensor cores where the scratch holds the rows
+            // (the packed weights carry three components), else float32 SIMT
+            bool tcv = false;
+            if (vr_Ab && K <= vr_kmax) {
+              gather_value_rows_kernel<T><<<vr_nb, 256, 0, s>>>(vr_nb, K, vr_off, A, nullptr, lda, vr_Ab, kMaxSplit,
+                                                                vr_cap * K);
+              tcv = tc::gemm_bf16(s, vr_Ab, K, vr_cap, Bt, N, K, reinterpret_cast<float*>(vr_C), N, 0, vr_nb,
+                                  nullptr, vr_nb, &at<DevStatus>(pl.status)->tc_err, kMaxSplit) == FIRE_OK;
+              launches += 2;
+            }
+            if (!tcv) {
+              gather_value_rows_kernel<T><<<vr_nb, 256, 0, s>>>(vr_nb, K, vr_off, A, vr_A, lda);
+              gemm<T>(s, vr_A, K, B, ldb, false, vr_C, N, 0, vr_nb, nullptr, vr_nb, N, K);
+              launches += 2;
+            }
             scatter_value_rows_kernel<T><<<vr_nb, 256, 0, s>>>(N, vr_off, vr_C, C, ldc);
-            launches += 3;
+            launches += 1;
           }
           return true;
         }
@@ -816,6 +832,11 @@ struct Runner {
       vr_nb = nb;
       vr_A = at<T>(pl.Hv);
       vr_C = at<T>(pl.Ov);
+      // the orbital-value scratch (free until the orbital values and again
+      // after them) holds the split value rows, K <= d
+      vr_Ab = pl.Hvb ? at<__nv_bfloat16>(pl.Hvb) : nullptr;
+      vr_cap = (int64_t)pl.Wc * dm.n;
+      vr_kmax = dm.d;
       const int64_t ldb = pl.ld_big;
       for (int l = 0; l < dm.L; ++l) {
         mark("mlp_gemm", 1);
