@@ -207,72 +207,94 @@ __global__ void att_part_kernel(int Wc, int n, int n_up, int K, int R, int dr, c
                                 const int32_t* __restrict__ cnt, const int32_t* __restrict__ rev,
                                 const int64_t* __restrict__ blk_off, const T* __restrict__ SU, int64_t ld,
                                 T* __restrict__ AP) {
+  constexpr int NBAT = 32;   // neighbours whose rows are located together
+  __shared__ int64_t s_rr[NBAT], s_oj[NBAT];
   const int RD = R * dr;
   const int col = threadIdx.x;
-  if (col >= RD) return;
+  const bool act = col < RD;   // every thread takes the barriers below
+  const int colc = act ? col : 0;
   const int w = blockIdx.x / n, i = blockIdx.x % n;
-  const int rg = col / dr;
+  const int rg = colc / dr;
   const T mx = AP[(int64_t)w * R + rg];
   T* rec = AP + (int64_t)Wc * R + (int64_t)blockIdx.x * 12 * RD;
   const int bi = block_index(w, i, Wc, n, n_up);
   const int64_t o = blk_off[bi], o1 = blk_off[bi + 1];
   const T e = dexp<T>(SU[o * ld + rg] - mx);
-  const T u = SU[o * ld + R + col];
-  // tangent rows four at a time (independent partial sums keep four loads
+  const T u = SU[o * ld + R + colc];
+  // tangent rows eight at a time (independent partial sums keep the loads
   // in flight), summed in a fixed order
   T ss4[4] = {T(0), T(0), T(0), T(0)}, su4[4] = {T(0), T(0), T(0), T(0)};
   int64_t q = o + 2;
-  for (; q + 4 <= o1; q += 4) {
-    T st[4], ut[4];
+  for (; q + 8 <= o1; q += 8) {
+    T st[8], ut[8];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      st[u] = SU[(q + u) * ld + rg];
-      ut[u] = SU[(q + u) * ld + R + col];
+    for (int v = 0; v < 8; ++v) {
+      st[v] = SU[(q + v) * ld + rg];
+      ut[v] = SU[(q + v) * ld + R + colc];
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      ss4[u] += st[u] * st[u];
-      su4[u] += st[u] * ut[u];
+    for (int v = 0; v < 8; ++v) {
+      ss4[v & 3] += st[v] * st[v];
+      su4[v & 3] += st[v] * ut[v];
     }
   }
-  for (int u = 0; q < o1; ++q, ++u) {
+  for (int v = 0; q < o1; ++q, ++v) {
     const T st = SU[q * ld + rg];
-    ss4[u] += st * st;
-    su4[u] += st * SU[q * ld + R + col];
+    ss4[v & 3] += st * st;
+    su4[v & 3] += st * SU[q * ld + R + colc];
   }
   const T ss = (ss4[0] + ss4[1]) + (ss4[2] + ss4[3]), su = (su4[0] + su4[1]) + (su4[2] + su4[3]);
-  const T sl = SU[(o + 1) * ld + rg], ul = SU[(o + 1) * ld + R + col];
-  rec[0 * RD + col] = e;
-  rec[1 * RD + col] = e * u;
-  rec[2 * RD + col] = e * (sl + ss);
-  rec[3 * RD + col] = e * ((sl + ss) * u + T(2) * su + ul);
+  const T sl = SU[(o + 1) * ld + rg], ul = SU[(o + 1) * ld + R + colc];
+  if (act) {
+    rec[0 * RD + col] = e;
+    rec[1 * RD + col] = e * u;
+    rec[2 * RD + col] = e * (sl + ss);
+    rec[3 * RD + col] = e * ((sl + ss) * u + T(2) * su + ul);
+  }
   // tangents with respect to r_i: electron i itself (slot 0) and every j
-  // that has i in its list (slot rev + 1)
+  // that has i in its list (slot rev + 1).  The rows of a batch of such j
+  // are located first (one thread each: list, reverse slot, block offset),
+  // so the loop below issues only independent row loads.
   T dZ[3], dN[3];
 #pragma unroll
   for (int x = 0; x < 3; ++x) {
     const T st = SU[(o + 2 + x) * ld + rg];
     dZ[x] = e * st;
-    dN[x] = e * (st * u + SU[(o + 2 + x) * ld + R + col]);
+    dN[x] = e * (st * u + SU[(o + 2 + x) * ld + R + colc]);
   }
   const int64_t base = (int64_t)w * n + i;
   const int ct = cnt[base * 2] + cnt[base * 2 + 1];
-  for (int k = 0; k < ct; ++k) {
-    const int j = idx[base * K + k];
-    const int rv = rev[base * K + k];
-    if (rv < 0) continue;
-    const int bj = block_index(w, j, Wc, n, n_up);
-    const int64_t oj = blk_off[bj];
-    const T ej = dexp<T>(SU[oj * ld + rg] - mx);
-    const T uj = SU[oj * ld + R + col];
-    const int64_t rr = oj + 2 + 3 * (int64_t)(rv + 1);
+  for (int k0 = 0; k0 < ct; k0 += NBAT) {
+    const int nbat = min(NBAT, ct - k0);
+    __syncthreads();   // the previous batch is consumed
+    if (threadIdx.x < nbat) {
+      const int k = k0 + threadIdx.x;
+      const int j = idx[base * K + k];
+      const int rv = rev[base * K + k];
+      if (rv < 0) {
+        s_oj[threadIdx.x] = -1;
+      } else {
+        const int64_t oj = blk_off[block_index(w, j, Wc, n, n_up)];
+        s_oj[threadIdx.x] = oj;
+        s_rr[threadIdx.x] = oj + 2 + 3 * (int64_t)(rv + 1);
+      }
+    }
+    __syncthreads();
+    for (int k = 0; k < nbat; ++k) {
+      const int64_t oj = s_oj[k];
+      if (oj < 0) continue;
+      const int64_t rr = s_rr[k];
+      const T ej = dexp<T>(SU[oj * ld + rg] - mx);
+      const T uj = SU[oj * ld + R + colc];
 #pragma unroll
-    for (int x = 0; x < 3; ++x) {
-      const T st = SU[(rr + x) * ld + rg];
-      dZ[x] += ej * st;
-      dN[x] += ej * (st * uj + SU[(rr + x) * ld + R + col]);
+      for (int x = 0; x < 3; ++x) {
+        const T st = SU[(rr + x) * ld + rg];
+        dZ[x] += ej * st;
+        dN[x] += ej * (st * uj + SU[(rr + x) * ld + R + colc]);
+      }
     }
   }
+  if (!act) return;
   T a1 = T(0), a2 = T(0);
 #pragma unroll
   for (int x = 0; x < 3; ++x) {
