@@ -123,6 +123,8 @@ struct Runner {
     // which products may use the tensor cores.
     if (const char* m = getenv("FIRE_TC_MASK")) tc_mask = atoi(m);
     if (const char* m = getenv("FIRE_TC_FIX_VALUES")) fix_values = atoi(m);
+    // FIRE_TC_VALUE_ROWS=fp32 (diagnostic): value rows by the float32 SIMT product
+    if (const char* m = getenv("FIRE_TC_VALUE_ROWS")) simt_values = strcmp(m, "fp32") == 0;
     // FIRE_INVERSE (diagnostic): 1 = float32 Gauss-Jordan from a float copy of
     // Phi (n <= 192, the default of the float32 forms), 0 = triangular solves
     // on the LU factors (always for float64 and for n > 192)
@@ -218,6 +220,7 @@ struct Runner {
   int tc_rc = FIRE_OK;
   int tc_mask = 0x7F;
   int fix_values = 1;         // value rows recomputed in fp32 after a tensor-core product
+  bool simt_values = false;   // ... by the float32 SIMT product instead of six split products
   // split-bf16 components of each tensor-core product (1: 1 product, 2: 3, 3: 6).
   // Two components (hi + lo, three products) for the products whose value
   // rows are recomputed in fp32 afterwards: measured against the float64 path
@@ -269,7 +272,7 @@ struct Runner {
             // products) on the tensor cores where the scratch holds the rows
             // (the packed weights carry three components), else float32 SIMT
             bool tcv = false;
-            if (vr_Ab && K <= vr_kmax) {
+            if (vr_Ab && K <= vr_kmax && !simt_values) {
               gather_value_rows_kernel<T><<<vr_nb, 256, 0, s>>>(vr_nb, K, vr_off, A, nullptr, lda, vr_Ab, kMaxSplit,
                                                                 vr_cap * K);
               tcv = tc::gemm_bf16(s, vr_Ab, K, vr_cap, Bt, N, K, reinterpret_cast<float*>(vr_C), N, 0, vr_nb,
