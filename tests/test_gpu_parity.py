@@ -188,6 +188,18 @@ def test_c26h24_matches_oracle(prec, tol_e):
     assert rel(out["e_loc"].cpu().numpy(), g["e_loc"]).max() < tol_e
 
 
+def test_c26h24_split_value_rows_match_oracle(monkeypatch):
+    """The value rows of the split products recomputed as six split products
+    on the tensor cores (FIRE_TC_VALUE_ROWS=split) instead of the float32
+    SIMT product: same bounds as the default BF16_FP64 form."""
+    monkeypatch.setenv("FIRE_TC_VALUE_ROWS", "split")
+    w, r, p, g = _golden("c26h24")
+    out = fire.Fire(w.system, w.arch, p, "bf16").local_energy(r)
+    np.testing.assert_array_equal(out["sign"].cpu().numpy(), g["sign"])
+    assert rel(out["logabs"].cpu().numpy(), g["logabs"]).max() < 1e-4
+    assert rel(out["e_loc"].cpu().numpy(), g["e_loc"]).max() < 1e-3
+
+
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
 def test_dense_limit_large_neighbourhoods(prec):
     """c beyond the molecule: every electron has n-1 = 57 neighbours, the
