@@ -13,7 +13,7 @@ Hessian, one second-derivative pass per electron coordinate.  No step uses
 the sparse forward Laplacian or low-rank updates the paper introduces; those
 are what the CUDA path is checked against.
 
-Readings where the paper is silent or garbled (each also listed in the design doc):
+Readings where the paper is silent or garbled:
   R1  one message-passing round (Methods "Wave function ansatz"); "layers" is
       the depth L of the embedding MLP h = MLP(h^1).
   R2  GLU(x) = (SiLU(LN(x) W_g) * (LN(x) W_v)) W_o, LN over the width with

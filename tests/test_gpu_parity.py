@@ -3,7 +3,7 @@
 Tolerances (per walker; relative error |x - x_ref| / max(|x_ref|, 1)):
   FP64 form       1e-10 on E_L and log|Psi|
   FP32 form       1e-4 on E_L, 1e-5 on log|Psi|
-  BF16_FP64 form  stated per test (measured)
+  BF16_FP64 form  stated per test (measured bounds)
 Signs must match exactly; neighbour lists are integer work and must match
 bit for bit.
 """

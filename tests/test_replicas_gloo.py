@@ -1,6 +1,6 @@
 """Walker sharding and the one cross-rank reduction, on CPU ranks (gloo,
-world size 2).  Every GPU machine here has one GPU, so the multi-rank path is
-covered on the host: the data path has no collective to emulate."""
+world size 2).  The multi-rank path is covered on the host: the data path
+has no collective to emulate."""
 import os
 import socket
 
