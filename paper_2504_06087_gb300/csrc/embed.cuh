@@ -324,6 +324,17 @@ __global__ void msg_kernel(int Wc, int n, int n_up, int d, int K, const double* 
   acc.l = deriv ? H0[(hrow + 1) * d + c] : T(0);
 #pragma unroll
   for (int t = 0; t < 3; ++t) acc.t[t] = deriv ? H0[(hrow + 2 + t) * d + c] : T(0);
+  // P_i (the own-electron half of the concatenation product) for both
+  // spin relations: value, Laplacian and tangent rows, read once
+  T pv[2], pl[2], pt[2][3];
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    const int64_t pc = (int64_t)a * d + c;
+    pv[a] = PQ[hrow * ld4 + pc];
+    pl[a] = deriv ? PQ[(hrow + 1) * ld4 + pc] : T(0);
+#pragma unroll
+    for (int t = 0; t < 3; ++t) pt[a][t] = deriv ? PQ[(hrow + 2 + t) * ld4 + pc] : T(0);
+  }
   const int64_t xoff = blk_off[bi];
   const int cpar = cnt[((int64_t)w * n + i) * 2], ctot = cpar + cnt[((int64_t)w * n + i) * 2 + 1];
   const double* rw = r + (int64_t)w * n * 3;
@@ -386,7 +397,7 @@ __global__ void msg_kernel(int Wc, int n, int n_up, int d, int K, const double* 
 #pragma unroll
       for (int t = 0; t < 3; ++t) ebt[t] += q.t[t] * wc[a][k];
     }
-    T zv = PQ[prow * ld4 + pcol] + PQ[qrow * ld4 + qcol] + ebv + bb[a];
+    T zv = (a ? pv[1] : pv[0]) + PQ[qrow * ld4 + qcol] + ebv + bb[a];
     T f, f1, f2;
     silu3<T>(zv, f, f1, f2);
     const T mv = gam.v * f;
@@ -395,11 +406,11 @@ __global__ void msg_kernel(int Wc, int n, int n_up, int d, int K, const double* 
       T zi[3], zj[3], sq = T(0);
 #pragma unroll
       for (int t = 0; t < 3; ++t) {
-        zi[t] = PQ[(prow + 2 + t) * ld4 + pcol] + ebt[t];
+        zi[t] = (a ? pt[1][t] : pt[0][t]) + ebt[t];
         zj[t] = PQ[(qrow + 2 + t) * ld4 + qcol] - ebt[t];
         sq += zi[t] * zi[t] + zj[t] * zj[t];
       }
-      const T zl = PQ[(prow + 1) * ld4 + pcol] + PQ[(qrow + 1) * ld4 + qcol] + T(2) * ebl;
+      const T zl = (a ? pl[1] : pl[0]) + PQ[(qrow + 1) * ld4 + qcol] + T(2) * ebl;
       const T sl = f1 * zl + f2 * sq;
       T cross = T(0);
 #pragma unroll
