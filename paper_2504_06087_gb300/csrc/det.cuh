@@ -1241,17 +1241,10 @@ contract3_kernel(int Wc, int n, int n_up, int K, int mlo, int mhi, int dd, int D
     g1 += Ms[(3 * k + 1) * m + k];
     g2 += Ms[(3 * k + 2) * m + k];
   }
-  // pairs e = k m + k' in steps of NT, (k, k') advanced without a division
-  {
-    int k = tid / m, kp = tid - (tid / m) * m;
-    const int dk = NT / m, dkp = NT - (NT / m) * m;
-    for (int e = tid; e < m * m; e += NT) {
+  for (int e = tid; e < m * m; e += NT) {
+    const int k = e / m, kp = e - k * m;
 #pragma unroll
-      for (int x = 0; x < 3; ++x) tr += Ms[(3 * k + x) * m + kp] * Ms[(3 * kp + x) * m + k];
-      k += dk;
-      kp += dkp;
-      if (kp >= m) { kp -= m; ++k; }
-    }
+    for (int x = 0; x < 3; ++x) tr += Ms[(3 * k + x) * m + kp] * Ms[(3 * kp + x) * m + k];
   }
   float v[5] = {g0, g1, g2, tr, lt};
 #pragma unroll
