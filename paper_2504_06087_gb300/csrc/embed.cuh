@@ -592,8 +592,9 @@ __global__ void __launch_bounds__(64, 6) fl_act4_kernel(int ncol, const int64_t*
 // F[q] = sum_c SiLU-layer(Z + b)[q][c] * wv[c] for every row q of every block
 // (same forward-Laplacian rules as fl_act_kernel), without storing the
 // activated rows.  One CTA per block, threads over the columns; the per-row
-// sums go through warp shuffles and a [warps][rows] shared array, summed in
-// warp order.  Dynamic shared memory: (blockDim / 32) * max_rows floats.
+// sums go through warp reductions (32 tangent rows at a time) and a
+// [warps][rows] shared array, summed in warp order.  Dynamic shared memory:
+// (blockDim / 32) * max_rows floats.
 template <typename T, typename W>
 __global__ void fl_act_dot_kernel(int ncol, const int64_t* __restrict__ off, int64_t stride,
                                   const T* __restrict__ Z, int64_t ldz, const W* bias, const W* wv,
@@ -607,7 +608,7 @@ __global__ void fl_act_dot_kernel(int ncol, const int64_t* __restrict__ off, int
   const int nr = (int)(r1 - r0);
   if (nr <= 0) return;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  // per-thread column partials of every row, reduced per warp as we go
+  // per-thread column partials of one row, reduced over the warp
   auto emit = [&](int rl, T part) {
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
     if (lane == 0) red[wid * max_rows + rl] = part;
@@ -623,12 +624,31 @@ __global__ void fl_act_dot_kernel(int ncol, const int64_t* __restrict__ off, int
       w = T(wv[c]);
     }
     T sq = T(0);
-    for (int q = 2; q < nr; ++q) {
-      const T zt = in ? Z[(r0 + q) * ldz + c] : T(0);
-      sq += zt * zt;
-      T part = f1 * zt * w;
-      if (c0 > 0) part += red[wid * max_rows + q] * (lane == 0 ? T(1) : T(0));
-      emit(q, part);
+    // tangent rows 32 at a time: the loads of a group are in flight
+    // together, and a transpose-halving reduction (at each step a lane keeps
+    // half of its partials and adds its partner's copy of them) leaves lane L
+    // with the warp sum of row qb + L: 31 shuffles per 32 rows
+    for (int qb = 2; qb < nr; qb += 32) {
+      T a[32];
+#pragma unroll
+      for (int u = 0; u < 32; ++u) {
+        const int q = qb + u;
+        const T zt = (in && q < nr) ? Z[(r0 + q) * ldz + c] : T(0);
+        sq += zt * zt;
+        a[u] = f1 * zt * w;
+      }
+#pragma unroll
+      for (int sft = 16; sft >= 1; sft >>= 1) {
+        const bool up = (lane & sft) != 0;
+#pragma unroll
+        for (int k = 0; k < sft; ++k) {
+          const T send = up ? a[k] : a[k + sft];
+          const T keep = up ? a[k + sft] : a[k];
+          a[k] = keep + __shfl_xor_sync(0xffffffffu, send, sft);
+        }
+      }
+      const int q = qb + lane;
+      if (q < nr) red[wid * max_rows + q] = a[0] + (c0 > 0 ? red[wid * max_rows + q] : T(0));
     }
     if (nr > 1) {
       T part = (in ? (f1 * Z[(r0 + 1) * ldz + c] + f2 * sq) : T(0)) * w;
