@@ -55,6 +55,33 @@ __global__ void env_feat_kernel(int Wc, int n, int n_up, int N, int E, const dou
       for (int k = 0; k < R5; ++k) store_split_bf16(Qb + (row + k) * ldb + q, cs, nc, 0.f);
 }
 
+// The float64 product of two float32 values, which is exact, formed from the
+// 24 x 24-bit integer product of their significands (no float64 operation:
+// on GB300 a float64 multiply and the two widening conversions take the
+// float64 pipe, which the LU of the same step saturates).  Zeros, subnormals,
+// infinities and NaNs take the float64 multiply.
+__device__ __forceinline__ double exact_product_f32(float a, float b) {
+  const uint32_t ua = __float_as_uint(a), ub = __float_as_uint(b);
+  const uint32_t ea = (ua >> 23) & 0xffu, eb = (ub >> 23) & 0xffu;
+  if (ea == 0u || eb == 0u || ea == 0xffu || eb == 0xffu) return (double)a * (double)b;
+  const uint64_t m = (uint64_t)((ua & 0x7fffffu) | 0x800000u) * (uint64_t)((ub & 0x7fffffu) | 0x800000u);
+  // a b = m 2^(ea + eb - 300), m in [2^46, 2^48)
+  const bool hi = (m >> 47) != 0;
+  const int e = (int)(ea + eb) - 300 + (hi ? 47 : 46);
+  uint64_t bits = (m << (hi ? 5 : 6)) & 0xfffffffffffffull;
+  bits |= (uint64_t)(e + 1023) << 52;
+  bits |= (uint64_t)((ua ^ ub) & 0x80000000u) << 32;
+  return __longlong_as_double((long long)bits);
+}
+template <typename A, typename LT>
+__device__ __forceinline__ LT phi_product(A x, A y) {
+  return LT(x) * LT(y);
+}
+template <>
+__device__ __forceinline__ double phi_product<float, double>(float x, float y) {
+  return exact_product_f32(x, y);
+}
+
 // Phi[w][d][i][l] = O_v[b(i)][d*n + l] * Fenv[b(i)*R5][d*n + l].
 // One CTA per (w, d).
 template <typename T, typename LT>
@@ -67,9 +94,12 @@ __global__ void phi_assemble_kernel(int Wc, int n, int n_up, int D, const T* __r
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     const int i = e / n, l = e % n;
     const int64_t b = block_index(w, i, Wc, n, n_up);
-    const LT v = LT(Ov[b * Dn + dd * n + l]) * LT(Fenv[b * R5 * Dn + dd * n + l]);
+    const T x = Ov[b * Dn + dd * n + l], y = Fenv[b * R5 * Dn + dd * n + l];
+    const LT v = phi_product<T, LT>(x, y);
     P[e] = v;
-    if (Phif) Phif[(int64_t)blockIdx.x * n * n + e] = (float)v;
+    // float copy: for float inputs the float product is the rounding of the
+    // exact product v, without a float64 conversion
+    if (Phif) Phif[(int64_t)blockIdx.x * n * n + e] = sizeof(T) == 4 ? (float)(x * y) : (float)v;
   }
 }
 
