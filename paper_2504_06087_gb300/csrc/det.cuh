@@ -273,16 +273,15 @@ inline size_t lu_smem_bytes(int n, size_t lsz, int nb = 16) { return (size_t)(2 
 // pivot column is addressed statically; every element takes the same fused
 // update a_ij -= f_i s_j (f_p = 0), and only the owners of column k and of
 // row p rewrite their entries afterwards.  The broadcast buffers alternate
-// between steps, so three barriers separate the steps (one when the pivot
-// rows come from the LU's interchanges).
+// between steps, so three barriers separate the steps.  With pivot rows from
+// an LU of the same matrix, gj_inverse_pre_kernel needs one.
 constexpr int kGjTR = 12, kGjTC = 8;
 inline int gj_threads(int n) {
   const int t = ((n + kGjTR - 1) / kGjTR) * ((n + kGjTC - 1) / kGjTC);
   return ((t + 31) / 32) * 32;
 }
 template <typename IT, typename OT>
-__global__ void __launch_bounds__(384, 1) gj_inverse_kernel(int n, const IT* __restrict__ Phi, OT* __restrict__ AT,
-                                                            const int32_t* __restrict__ lu_piv = nullptr) {
+__global__ void __launch_bounds__(384, 1) gj_inverse_kernel(int n, const IT* __restrict__ Phi, OT* __restrict__ AT) {
   constexpr int TR = kGjTR, TC = kGjTC;
   extern __shared__ unsigned char gj_smem[];
   float* S = reinterpret_cast<float*>(gj_smem);          // [n][n] final matrix
@@ -307,23 +306,6 @@ __global__ void __launch_bounds__(384, 1) gj_inverse_kernel(int n, const IT* __r
       a[i][j] = (live && r < n && c < n) ? (float)P[(int64_t)r * n + c] : 0.f;
     }
   for (int r = tid; r < 256; r += blockDim.x) used[r] = 0;
-  // With the row interchanges of a partial-pivoting LU of the same matrix
-  // (lu_piv, LAPACK order: step k swapped rows k and lu_piv[k]) the pivot
-  // rows are known up front: piv[k] is the original row at position k after
-  // the first k + 1 interchanges.  Each step then needs one barrier.
-  const bool pre = lu_piv != nullptr;
-  if (pre && tid == 0) {
-    const int32_t* lp = lu_piv + (int64_t)blockIdx.x * n;
-    for (int k = 0; k < n; ++k) stp[k] = k;   // stp: position -> original row
-    for (int k = 0; k < n; ++k) {
-      const int q = lp[k];
-      const int t = stp[k];
-      stp[k] = stp[q];
-      stp[q] = t;
-    }
-    for (int k = 0; k < n; ++k) piv[k] = stp[k];
-    for (int k = 0; k < n; ++k) stp[piv[k]] = k;
-  }
   __syncthreads();
   for (int kt = 0; kt < Gc; ++kt) {
 #pragma unroll
@@ -335,7 +317,6 @@ __global__ void __launch_bounds__(384, 1) gj_inverse_kernel(int n, const IT* __r
         float* pc = pcol + 256 * bsel;
         float* cvb = cv + 32 * bsel;
         int* cib = ci + 32 * bsel;
-        if (!pre) {
         // candidates: the threads of column block kt, one per row block
         if (live && tc == kt) {
           float best = -1.f;
@@ -368,7 +349,6 @@ __global__ void __launch_bounds__(384, 1) gj_inverse_kernel(int n, const IT* __r
           }
         }
         __syncthreads();
-        }
         const int p = piv[k];
         const int pt = p / TR, pi = p % TR;
         if (live && tr == pt)

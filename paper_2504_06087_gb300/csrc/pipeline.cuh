@@ -957,7 +957,7 @@ struct Runner {
         if (gj) {
           const int thr = gj_threads(n);
           // pivot rows from the float64 LU when it has already run on this stream
-          if (lu_side) gj_inverse_kernel<float, T><<<wc * D, thr, gj_smem_bytes(n), s>>>(n, Phif, Ainv, nullptr);
+          if (lu_side) gj_inverse_kernel<float, T><<<wc * D, thr, gj_smem_bytes(n), s>>>(n, Phif, Ainv);
           else gj_inverse_pre_kernel<float, T><<<wc * D, thr, gj_smem_bytes(n), s>>>(n, Phif, Ainv, piv);
         } else {
           inverse_from_lu(n, (int64_t)wc * D, LUb, piv, Ainv);
