@@ -203,7 +203,17 @@ def orbitals(system, arch, p, r, h) -> torch.Tensor:
 def slater_part(system, arch, p, r, h):
     """Signed sum of determinants: (log|sum_d det Phi_d|, sign, per-det logs)."""
     phi = orbitals(system, arch, p, r, h)
-    sgn, lad = torch.linalg.slogdet(phi)                                    # [B,D]
+    n = phi.shape[-1]
+    if n > 128 and torch.backends.mkl.is_available():
+        # one LAPACK factorisation per matrix: batched torch.linalg.slogdet
+        # stalled on an x86 build whose LAPACK is MKL once several intra-op
+        # threads ran (n = 180; n <= 128 ran); per matrix it does not, with
+        # the same LU
+        per = [torch.linalg.slogdet(m) for m in phi.reshape(-1, n, n)]
+        sgn = torch.stack([x[0] for x in per]).reshape(phi.shape[:-2])     # [B,D]
+        lad = torch.stack([x[1] for x in per]).reshape(phi.shape[:-2])
+    else:
+        sgn, lad = torch.linalg.slogdet(phi)                                # [B,D]
     lmax = lad.max(dim=1, keepdim=True).values.detach()
     lmax = torch.where(torch.isfinite(lmax), lmax, torch.zeros_like(lmax))
     ssum = (sgn * torch.exp(lad - lmax)).sum(dim=1)
