@@ -72,6 +72,21 @@ def test_workspace_size_and_chunking(monkeypatch):
     assert L.fire_workspace_size(ctypes.byref(sys_c), ctypes.byref(arch_c), 4, 7, 64, 2) == 0
 
 
+def test_lu_panel_limit_is_reported_on_the_host():
+    """The float64 LU keeps a panel and the U12 block of n rows in shared
+    memory ((2 * 16 + 1) n doubles <= 227 KB, so n <= 880): a larger system is
+    rejected by the plan (workspace size 0), a system just below runs."""
+    _lib_or_skip()
+    L = fire.lib()
+    arch_c = fire.make_arch(synth.workload("c26h24").arch)
+    for k, ok in ((124, True), (128, False)):      # C_kH_{k+2}: n_el = 7k + 2 = 870, 898
+        s = synth.zigzag_polyene(k)
+        assert s.n_el == 7 * k + 2
+        sys_c = fire.System(s.n_el, s.n_up, s.n_nuc, 0, None, None, s.cutoff, s.cutoff_nuc)
+        size = L.fire_workspace_size(ctypes.byref(sys_c), ctypes.byref(arch_c), 2, 2, 64, fire.OP_LOGPSI)
+        assert (size > 0) == ok, (s.n_el, size)
+
+
 def test_host_side_argument_errors():
     _lib_or_skip()
     w, sys_c, arch_c = _c_structs("water")
