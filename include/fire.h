@@ -67,9 +67,13 @@ typedef enum {
  *  FP64       every step in float64 (theta float64).
  *  FP32       every step in float32, the final E_L reduction included
  *             ("plain FP32"; theta float32).
- *  BF16_FP64  embedding-MLP and Jastrow-MLP matrix products in BF16 on the
- *             tensor cores with FP32 accumulation; LU / slogdet and the final
- *             E_L reduction in float64; everything else float32 (theta
+ *  BF16_FP64  every matrix product (embedding MLP, Jastrow MLPs, attention
+ *             scores and register MLPs, h^0 products, envelopes, orbital
+ *             rows) on the tensor cores as split-bf16 products: each operand
+ *             held as 2 or 3 bf16 components, the component products summed
+ *             with FP32 accumulation; the value rows of the MLP products
+ *             recomputed in float32; LU / slogdet and the final E_L reduction
+ *             in float64; the inverse and everything else float32 (theta
  *             float32). */
 typedef enum {
   FIRE_PREC_FP64 = 0,
