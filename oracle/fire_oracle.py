@@ -145,11 +145,10 @@ def spins(n_el: int, n_up: int) -> torch.Tensor:
     return s
 
 
-def embeddings(system, arch, p: Dict[str, torch.Tensor], r: torch.Tensor):
-    """Return (h0, h1, h), each [B, n, d]."""
+def en_sum(system, p: Dict[str, torch.Tensor], r: torch.Tensor) -> torch.Tensor:
+    """Argument of the GLU in h^0_i: sum_m Gamma_m(e^_im) * (h^nuc_m + e^bar_im W)
+    (Methods, eq. of h^0_i), masked to |r_i - R_m| <= c_n.  [B, n, d]."""
     R = _t(system.nuc_pos)
-    B, n, _ = r.shape
-    # electron-nucleus features e^_im and rescaled e^bar_im
     den = r[:, :, None, :] - R[None, None, :, :]                      # [B,n,N,3]
     valid_en = torch.ones(den.shape[:-1], dtype=torch.bool)
     e_en, eb_en, dist_en = pair_features(den, valid_en)
@@ -157,10 +156,13 @@ def embeddings(system, arch, p: Dict[str, torch.Tensor], r: torch.Tensor):
                         p["en_sigma"], system.cutoff_nuc)                  # [B,n,N,d]
     mask_en = (dist_en <= system.cutoff_nuc).to(DT)[..., None]
     feat = p["nuc_emb"][None, None] + eb_en @ p["en_wfeat"]
-    s = (mask_en * gam * feat).sum(dim=2)                                  # [B,n,d]
-    h0 = glu(s, p)
+    return (mask_en * gam * feat).sum(dim=2)
 
-    # electron-electron message passing (one round, R1)
+
+def message_pass(system, p: Dict[str, torch.Tensor], r: torch.Tensor, h0: torch.Tensor) -> torch.Tensor:
+    """h^1_i = h^0_i + m^par_i + m^anti_i, one round (Methods, eq. of m^alpha_i; R1, R11):
+    m^alpha_i = sum_{j in N^alpha_i} Gamma(e_ij) * SiLU(Concat[h^0_i, h^0_j, e^bar_ij] W^alpha + b^alpha)."""
+    B, n, _ = r.shape
     dee = r[:, :, None, :] - r[:, None, :, :]                           # r_i - r_j
     offdiag = ~torch.eye(n, dtype=torch.bool)[None].expand(B, n, n)
     e_ee, eb_ee, dist_ee = pair_features(dee, offdiag)
@@ -177,10 +179,22 @@ def embeddings(system, arch, p: Dict[str, torch.Tensor], r: torch.Tensor):
         msg = gam_ee * silu(z)
         m = ((within & sel).to(DT)[..., None] * msg).sum(dim=2)
         h1 = h1 + m
+    return h1
+
+
+def embedding_mlp(arch, p: Dict[str, torch.Tensor], h1: torch.Tensor) -> torch.Tensor:
+    """h = MLP(h^1): L residual blocks h <- h + SiLU(h W_l + b_l) (Methods; R12)."""
     h = h1
     for l in range(arch.n_layers):
         h = h + silu(h @ p["mlp_w"][l] + p["mlp_b"][l])
-    return h0, h1, h
+    return h
+
+
+def embeddings(system, arch, p: Dict[str, torch.Tensor], r: torch.Tensor):
+    """Return (h0, h1, h), each [B, n, d] (Methods, "Finite-range embeddings")."""
+    h0 = glu(en_sum(system, p, r), p)
+    h1 = message_pass(system, p, r, h0)
+    return h0, h1, embedding_mlp(arch, p, h1)
 
 
 # ---------------------------------------------------------------------------
