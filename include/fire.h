@@ -19,9 +19,14 @@
  * Conventions shared by every call
  * --------------------------------
  * Pointers.  Unless a comment says "host", every array pointer is DEVICE
- *   memory, allocated and freed by the caller.  The library allocates no
- *   device memory: scratch space is the caller-allocated workspace `ws` of at
- *   least fire_workspace_size() bytes.  Arrays are dense row-major (C order).
+ *   memory, allocated and freed by the caller.  The calls allocate no device
+ *   memory: scratch space is the caller-allocated workspace `ws` of at least
+ *   fire_workspace_size() bytes.  Two things are held by the library itself
+ *   for the life of the process: the static device array of
+ *   fire_local_energy_static() (FIRE_STATIC_WORKSPACE_BYTES on every GPU that
+ *   loads the library) and, on a device where a call first needs it, one
+ *   extra non-blocking CUDA stream for work that runs beside the caller's
+ *   stream inside a call.  Arrays are dense row-major (C order).
  * Electrons.  r is [W][n_el][3] float64, bohr.  Electrons 0 .. n_up-1 are
  *   spin-up, n_up .. n_el-1 spin-down (Methods, "Variational Monte Carlo").
  * Parameters.  theta is ONE flat buffer; fire_param_layout() gives the name,
@@ -38,8 +43,13 @@
  *   (FIRE_ERR_NONFINITE is reported only when a walker is non-finite without
  *   being on a node).  A walker on a node of Psi (sign 0, log|Psi| = -inf)
  *   is not an error; it is counted in fire_info_t.n_nodes.
- * Concurrency.  No global state: calls are re-entrant and may run on
- *   different streams with different workspaces.
+ * Concurrency.  Calls with their own workspaces are re-entrant and may run
+ *   on different streams and host threads.  The shared state is: the
+ *   per-device side stream above (work a call puts on it is joined back to
+ *   the caller's stream before the call returns), the static array of
+ *   fire_local_energy_static() (calls of that entry point that overlap on a
+ *   GPU race), and thread-local diagnostics (fire_last_error, the stage
+ *   profiler).
  */
 #ifndef FIRE_H
 #define FIRE_H
@@ -311,8 +321,10 @@ int fire_selftest_tc_gemm(int64_t M, int32_t N, int32_t K, int32_t nc, const voi
  *    with FIRE_ERR_WORKSPACE before any launch; fire_last_error() then
  *    states the size needed.  (About 20 water-sized walkers in FP64.)
  *  - The first call on a device looks up the array's device address on that
- *    device (with it current); make that first call before any stream
- *    capture.
+ *    device (with it current) and keeps it; make that first call before any
+ *    stream capture.  The kept address belongs to the device's current
+ *    context: do not call this entry point on a device after
+ *    cudaDeviceReset() on it in the same process.
  *  - Every call on a device shares the one array, which keeps the previous
  *    call's contents (the call clears what must start at zero): calls that
  *    overlap on the GPU, on different streams or host threads, race. */
