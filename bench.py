@@ -98,23 +98,53 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def simt_peaks(dev):
+    """Measured multiply-add rates of the float32 and float64 SIMT pipes
+    (fire_selftest_fma_rate: eight independent FMA chains per thread, eight
+    256-thread CTAs per SM), best of three launches after a warm-up, in
+    TFLOP/s.  These are the peaks of the kernels bound by the FP32 or FP64
+    pipe."""
+    from paper_2504_06087_gb300 import fire
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    stream = torch.cuda.current_stream(dev)
+    out = {"sm_count": sms}
+    for key, dt, iters in (("fp32_tflops", torch.float32, 1 << 20), ("fp64_tflops", torch.float64, 1 << 14)):
+        fire.fma_probe(dt, 1024, sms * 8, dev)
+        best = 0.0
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            flops = fire.fma_probe(dt, iters, sms * 8, dev)
+            e1.record(stream)
+            e1.synchronize()
+            best = max(best, flops / (e0.elapsed_time(e1) / 1e3) / 1e12)
+        out[key] = best
+    return out
+
+
 # ---------------------------------------------------------------------------
 # algorithmic work per stage (for the roofline of the dominant kernel)
 # ---------------------------------------------------------------------------
 
+# DRAM bytes (read + write) per walker-determinant of a stage, from an ncu
+# capture of that kernel (dram__bytes_read.sum + dram__bytes_write.sum of its
+# bucket launches for one determinant of a 32-walker chunk, divided by the 32
+# walker-determinants); the capture and its command are summarised in the
+# named profiles/ file.  A stage whose kernel changed since its capture has
+# no entry.
+STAGE_TRAFFIC = {
+    "contract": (2.1812e7, "ncu capture of one determinant of a 32-walker chunk (profiles/contract_c26h24.md)"),
+}
+
+
 def stage_traffic(stage, walker_dets, launches):
-    """DRAM bytes (read + write) per stage launch, from the ncu capture summarised
-    in profiles/<stage>_c26h24.md (a line 'dram_bytes_per_walker_det: X'); the
-    stage launches once per determinant and chunk, so one launch covers
-    walker_dets / launches walker-determinants.  None without a capture."""
-    path = os.path.join(ROOT, "profiles", f"{stage}_c26h24.md")
-    if not os.path.exists(path):
-        return None
-    for ln in open(path):
-        if ln.strip().startswith("dram_bytes_per_walker_det:"):
-            per = float(ln.split(":", 1)[1].split()[0])
-            return per * walker_dets / launches
-    return None
+    """(bytes per launch, source) of a stage, scaled from its capture by the
+    walker-determinants one launch covers; (None, None) without a capture."""
+    if stage not in STAGE_TRAFFIC:
+        return None, None
+    per, src = STAGE_TRAFFIC[stage]
+    return per * walker_dets / launches, src + f", scaled to {walker_dets // max(launches, 1)} walker-determinants per launch"
 
 
 def stage_work(stage, w, info, n_walkers, nbr_sq_sum):
@@ -269,22 +299,25 @@ def main():
     cnt = nb["cnt"].sum(-1).to(torch.float64)
     nbr_sq_sum = float(((1.0 + cnt) ** 2).sum().item())
     peaks, peak_src = load_peaks()
+    simt = simt_peaks(dev)
     dom = max(stages.items(), key=lambda kv: kv[1][1])
     dname, (dl, dms) = dom
     flops, _, bound = stage_work(dname, w, info, args.walkers, nbr_sq_sum)
+    traffic, traffic_src = stage_traffic(dname, args.walkers * w.arch.n_det, dl)
     roof = {"kernel": dname, "share_of_step": dms / sum(v[1] for v in stages.values()), "launches": dl,
-            "traffic": stage_traffic(dname, args.walkers * w.arch.n_det, dl)}
+            "traffic": traffic, "traffic_source": traffic_src}
     if flops is not None:
         per_launch = flops / dl
         achieved = per_launch / (dms / dl / 1e3) / 1e12
+        fp32_note = f"FP32 SIMT, measured in this run (FFMA probe, {simt['sm_count']} SMs)"
         if bound == "tensor":
             peak, pnote = peaks["bf16_tflops_sustained"], f"bf16 dense sustained, {peak_src}"
             if args.precision != "bf16":
-                peak, pnote = 80.5, "FP32 SIMT, 152 SMs x 128 FMA/clk x 2070 MHz (derived)"
+                peak, pnote = simt["fp32_tflops"], fp32_note
         elif bound == "fp64":
-            peak, pnote = 1.25, "FP64 nominal 1.25 TFLOP/s (GB300 table)"
+            peak, pnote = simt["fp64_tflops"], f"FP64 SIMT, measured in this run (DFMA probe, {simt['sm_count']} SMs)"
         else:
-            peak, pnote = 80.5, "FP32 SIMT, 152 SMs x 128 FMA/clk x 2070 MHz (derived)"
+            peak, pnote = simt["fp32_tflops"], fp32_note
         roof.update({"bound": "tensor" if bound == "tensor" else "alu", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "peak_source": pnote,
                      "flops_per_launch": per_launch, "ms_per_launch": dms / dl})
@@ -339,6 +372,7 @@ def main():
                                   f"all-reduce of E_L moments after the timed calls)"},
         "e2e": e2e, "gpu_launches": int(info["n_launches"]) * args.steps,
         "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "comparison": comparison,
+        "simt_peaks": simt,
         "diag": {"e_loc_moments_all_ranks": moments, "rows_total": info["rows_total"], "mean_neighbors": info["mean_neighbors"],
                  "k_required": info["k_required"], "n_chunks": info["n_chunks"], "n_nodes": info["n_nodes"],
                  "launches_per_step": info["n_launches"], "step_ms": times},
@@ -377,6 +411,7 @@ def oracle_baseline(w, coords):
     from paper_2504_06087_gb300 import synth
     torch.set_num_threads(os.cpu_count() or 1)
     r1, p = synth.make_inputs(w, 1)
+    oracle_sample(w, r1, p, 1)          # warm-up: thread pool, allocator, first graph build
     spent, full = oracle_sample(w, r1, p, coords)
     return {"value": 1.0 / full, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
             "sample": f"1 walker of the same workload: forward, gradient and {coords} of the {3 * w.system.n_el} "

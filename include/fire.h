@@ -302,6 +302,17 @@ int fire_workspace_layout(const fire_system_t* sys, const fire_arch_t* arch, int
 int fire_selftest_tc_gemm(int64_t M, int32_t N, int32_t K, int32_t nc, const void* A, const void* Bt,
                           float* C, int32_t* err, void* stream);
 
+/* Diagnostic: the multiply-add rate of the SIMT pipes.  Launches `blocks`
+ * CTAs of 256 threads; each thread runs eight independent chains of
+ * 4 * ceil(iters / 4) dependent fused multiply-adds (fma.rn) in float64
+ * (dtype 0) or float32 (dtype 1) and writes one value to out[blocks * 256]
+ * (device, of that dtype).  FLOPs = 2 * 8 * 4 * ceil(iters / 4) * blocks * 256;
+ * the caller times the launch on `stream`.  The paper has no counterpart: the
+ * measured rate is the peak that the roofline fractions of the float32 and
+ * float64 kernels are quoted against.  FIRE_ERR_INVALID_ARG on a bad dtype,
+ * iters < 1, blocks < 1 or out == NULL. */
+int fire_selftest_fma_rate(int32_t dtype, int64_t iters, int32_t blocks, void* out, void* stream);
+
 /* Size of the workspace that fire_local_energy_static() owns (32 MiB). */
 #define FIRE_STATIC_WORKSPACE_BYTES (32u * 1024u * 1024u)
 

@@ -96,6 +96,7 @@ SIGNATURES = {
                                              ctypes.c_int32, P(WsEntry), P(ctypes.c_int32), P(ctypes.c_int64)]),
     "fire_selftest_tc_gemm": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, VP, VP,
                                              VP, VP, VP]),
+    "fire_selftest_fma_rate": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, VP, VP]),
     "fire_neighbors": (ctypes.c_int, [P(System), ctypes.c_int64, VP, ctypes.c_int32, VP, VP,
                                       P(ctypes.c_int32), VP, ctypes.c_size_t, VP]),
     "fire_logpsi": (ctypes.c_int, [P(System), P(Arch), P(Params), ctypes.c_int64, VP, ctypes.c_int32,
@@ -174,6 +175,19 @@ def tc_gemm_selftest(A: torch.Tensor, Bt: torch.Tensor, nc: int = 1) -> torch.Te
     if int(err.item()):
         raise RuntimeError(f"tensor-core product: bounded wait gave up (code {int(err.item())})")
     return C
+
+
+def fma_probe(dtype: torch.dtype, iters: int, blocks: int, device="cuda") -> int:
+    """Launches the SIMT multiply-add probe on the current stream (not
+    synchronised; the caller times it).  Returns the FLOPs of the launch."""
+    out = torch.empty(blocks * 256, dtype=dtype, device=device)
+    code = 0 if dtype == torch.float64 else 1
+    rc = lib().fire_selftest_fma_rate(code, iters, blocks, _ptr(out),
+                                      ctypes.c_void_p(torch.cuda.current_stream(out.device).cuda_stream))
+    if rc:
+        raise FireError(rc, "fire_selftest_fma_rate")
+    rounds = (iters + 3) // 4
+    return 2 * 8 * 4 * rounds * blocks * 256
 
 
 def _ptr(t: Optional[torch.Tensor]):

@@ -4,8 +4,8 @@ Calls only the CPU oracle (oracle/) on inputs from the seeded generator; no
 value here comes from the CUDA path.  Each file records a hash of its inputs
 so a test can confirm that it regenerates the same walkers and parameters.
 
-    python tests/golden/make_golden.py c8h10 8
-    python tests/golden/make_golden.py c26h24 2
+    python tests/golden/make_golden.py c8h10 64
+    python tests/golden/make_golden.py c26h24 16 4     # 4 processes, one walker each at a time
     python tests/golden/make_golden.py c26h24 16 grad
 """
 import hashlib
@@ -43,11 +43,29 @@ def input_summary(r, params):
     return out
 
 
-def main(key: str, nw: int):
+def _one_walker(args):
+    """Oracle local energy of walker b alone (a process of its own: the dense
+    second-derivative graph of one C26H24 walker holds several GB)."""
+    key, nw, b, threads = args
+    torch.set_num_threads(threads)
+    w = synth.workload(key)
+    r, p = synth.make_inputs(w, nw)
+    return O.local_energy(w.system, w.arch, p, r[b:b + 1], return_parts=True)
+
+
+def main(key: str, nw: int, procs: int = 1):
     w = synth.workload(key)
     r, p = synth.make_inputs(w, nw)
     t0 = time.time()
-    e, la, sg, kin, v, g, lap = O.local_energy(w.system, w.arch, p, r, return_parts=True)
+    if procs <= 1:
+        e, la, sg, kin, v, g, lap = O.local_energy(w.system, w.arch, p, r, return_parts=True)
+    else:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        threads = max(1, (os.cpu_count() or 1) // procs)
+        with cf.ProcessPoolExecutor(procs, mp_context=mp.get_context("spawn")) as ex:
+            parts = list(ex.map(_one_walker, [(key, nw, b, threads) for b in range(nw)]))
+        e, la, sg, kin, v, g, lap = (np.concatenate([q[k] for q in parts]) for k in range(7))
     out = {
         "workload": key,
         "n_walkers": nw,
@@ -121,4 +139,4 @@ if __name__ == "__main__":
     if len(sys.argv) > 3 and sys.argv[3] == "grad":
         main_grad(sys.argv[1], int(sys.argv[2]))
     else:
-        main(sys.argv[1], int(sys.argv[2]))
+        main(sys.argv[1], int(sys.argv[2]), int(sys.argv[3]) if len(sys.argv) > 3 else 1)
