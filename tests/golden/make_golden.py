@@ -7,6 +7,7 @@ so a test can confirm that it regenerates the same walkers and parameters.
     python tests/golden/make_golden.py c8h10 64
     python tests/golden/make_golden.py c26h24 16 4     # 4 processes, one walker each at a time
     python tests/golden/make_golden.py c26h24 16 grad
+    python tests/golden/make_golden.py c8h10 cond local   # add cond_dominant to an existing file
 """
 import hashlib
 import json
@@ -76,6 +77,7 @@ def main(key: str, nw: int, procs: int = 1):
         "e_loc": e.tolist(), "logabs": la.tolist(), "sign": sg.tolist(),
         "e_kin": kin.tolist(), "e_pot": v.tolist(), "lap": lap.tolist(),
         "grad_norm2": (g ** 2).sum(axis=(1, 2)).tolist(),
+        "cond_dominant": dominant_conditioning(w, r, p).tolist(),
     }
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"{key}_oracle.json")
     with open(path, "w") as f:
@@ -119,9 +121,11 @@ def dominant_conditioning(w, r, p) -> np.ndarray:
     return np.array([np.linalg.cond(phi[b, dom[b]]) for b in range(phi.shape[0])])
 
 
-def add_conditioning(key: str):
-    """Adds cond_dominant to an existing {key}_grad_oracle.json (same inputs)."""
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"{key}_grad_oracle.json")
+def add_conditioning(key: str, kind: str = "grad"):
+    """Adds cond_dominant to an existing {key}_grad_oracle.json or (kind
+    "local") {key}_oracle.json (same inputs)."""
+    name = f"{key}_grad_oracle.json" if kind == "grad" else f"{key}_oracle.json"
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), name)
     out = json.load(open(path))
     w = synth.workload(key)
     r, p = synth.make_inputs(w, out["n_walkers"])
@@ -134,7 +138,7 @@ def add_conditioning(key: str):
 
 if __name__ == "__main__":
     if len(sys.argv) > 2 and sys.argv[2] == "cond":
-        add_conditioning(sys.argv[1])
+        add_conditioning(sys.argv[1], sys.argv[3] if len(sys.argv) > 3 else "grad")
         sys.exit(0)
     if len(sys.argv) > 3 and sys.argv[3] == "grad":
         main_grad(sys.argv[1], int(sys.argv[2]))

@@ -122,3 +122,39 @@ def test_autograd_function_contracts_the_walker_rows():
                                for name, _, _ in f.layout])
     err = np.abs(gt.cpu().numpy() - flat_ref) / np.maximum(np.abs(flat_ref), 1.0)
     assert err.max() < 1e-9
+
+
+def test_c26h24_gradient_matches_finite_differences():
+    """The gradient check of the 1e6-parameter configuration: central
+    differences with h = 1e-4 of fire_logpsi on 64 seeded flat parameter
+    indices, four C26H24 walkers (n_el = 180, 5.1 M parameters).
+
+    FP64 form: the adjoint equals the central difference to
+    1e-6 max(|g|, 1) per entry (truncation h^2 f'''/6 and rounding
+    eps |log Psi| / h are both below 1e-8 here).  FP32 form: per walker the
+    relative 2-norm error of its 64 entries against the FP64 central
+    differences is at most 1e-4 + 2 kappa u, the bound of the stored-oracle
+    test (u = 2^-24, kappa the condition number of the walker's dominant
+    orbital matrix)."""
+    from tests.golden.make_golden import dominant_conditioning
+    w = synth.workload("c26h24")
+    r, p = synth.make_inputs(w, 4)
+    f = fire.Fire(w.system, w.arch, p, "fp64")
+    g64 = f.grad_logpsi(r)["grad"].cpu().numpy()
+    picks = np.sort(np.random.default_rng(1004).choice(f.n_params, size=64, replace=False))
+    h = 1e-4
+    fd = np.zeros((r.shape[0], picks.size))
+    for q, k in enumerate(picks):
+        old = float(f.theta[k])
+        f.theta[k] = old + h
+        lp = f.logpsi(r)["logabs"].cpu().numpy()
+        f.theta[k] = old - h
+        lm = f.logpsi(r)["logabs"].cpu().numpy()
+        f.theta[k] = old
+        fd[:, q] = (lp - lm) / (2 * h)
+    np.testing.assert_allclose(g64[:, picks], fd, rtol=1e-6, atol=1e-6)
+    f32 = fire.Fire(w.system, w.arch, p, "fp32")
+    g32 = f32.grad_logpsi(r)["grad"].cpu().numpy().astype(np.float64)[:, picks]
+    norm = np.linalg.norm(g32 - fd, axis=1) / np.linalg.norm(fd, axis=1)
+    kappa = dominant_conditioning(w, r, p)
+    assert np.all(norm <= 1e-4 + 2.0 * kappa * 2.0 ** -24), (norm, kappa)
