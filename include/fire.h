@@ -85,6 +85,18 @@ typedef enum {
  *             recomputed in float32; LU / slogdet and the final E_L reduction
  *             in float64; the inverse and everything else float32 (theta
  *             float32). */
+/* Accuracy of each form against the float64 dense oracle, per walker (the
+ * bounds the parity tests hold every walker to):
+ *   E_L      |E - E_ref| <= tau max(|E_ref|, 1, |Lap log|Psi|| + |grad log|Psi||^2),
+ *            tau = 1e-10 (FP64), 1e-4 (FP32, BF16_FP64): E_L sums the kinetic
+ *            terms, which cancel near nodes and cusps, and its rounding error
+ *            is relative to them; the reduced forms also meet 1e-4 relative
+ *            to max(|E_ref|, 1) at the median walker;
+ *   log|Psi| |l - l_ref| <= max(t max(|l_ref|, 1), n_el kappa u), t = 1e-10
+ *            (FP64), 1e-5 (FP32, BF16_FP64), kappa the condition number of the
+ *            walker's dominant orbital matrix, u = 2^-53 or 2^-24.
+ * The gradient of fire_grad_logpsi: FP64 1e-9 max(|g|, 1) per entry; FP32 a
+ * relative 2-norm error per walker of at most 1e-4 + 2 kappa u. */
 typedef enum {
   FIRE_PREC_FP64 = 0,
   FIRE_PREC_FP32 = 1,
@@ -245,11 +257,25 @@ int fire_local_energy(const fire_system_t* sys, const fire_arch_t* arch,
  * with the cached inverse (float64 LU of the small matrix) and an accepted
  * move updates the inverse by the Woodbury identity.
  *
+ * Global jumps (Methods, "Improved Monte Carlo sampling": the mixture
+ * proposal rho(r') = sum_m Z_m N(r' | R_m, sigma_global^2 I) / sum_m Z_m and
+ * its ratio correction; Supplementary "Hyperparameters": 20 global moves,
+ * sigma_global = 2 bohr): after its n_el local moves a sweep makes n_global
+ * global jumps.  Each moves one electron k, the same for every walker, to
+ * r'_k = R_m + sigma_global xi, the nucleus m drawn with probability
+ * Z_m / sum Z; it is accepted iff
+ * ln u < 2 ln|Psi'/Psi| + ln rho(r_k) - ln rho(r'_k).  The update set, the
+ * ratios and the inverse updates are those of a local move.
+ *
  * Random numbers: Philox4x32-10 with key (seed low word, seed high word) and
  * counter (move low word, move high word, walker, stream), move =
- * *counter + sweep * n_el + k; stream 0 gives xi by Box-Muller in float64,
- * stream 1 the uniform u; uniforms are (x + 1/2) / 2^32.  *counter (host,
- * in/out) advances by n_sweeps * n_el.
+ * *counter + sweep * (n_el + n_global) + j for the j-th move of a sweep
+ * (local moves j = k < n_el, then the global jumps); stream 0 gives xi by
+ * Box-Muller in float64, stream 1 the uniform u, stream 2 word 0 the
+ * mixture component of a global jump (first m with u sum Z < Z_1 + .. + Z_m);
+ * the electron of a global jump is floor(n_el u) with u from word 0 of
+ * counter (move low, move high, 2^32 - 1, 2); uniforms are (x + 1/2) / 2^32.
+ * *counter (host, in/out) advances by n_sweeps * (n_el + n_global).
  *
  * r [W][n_el][3] float64 (device, in/out).  The cached state lives in the
  * workspace (fire_workspace_size() with FIRE_OP_MCMC; the call holds every
@@ -259,20 +285,131 @@ int fire_local_energy(const fire_system_t* sys, const fire_arch_t* arch,
  * |log|Psi|| difference between the carried value and a rebuild.
  * Precision: FIRE_PREC_FP64 keeps the state in float64; FIRE_PREC_FP32 and
  * FIRE_PREC_BF16_FP64 keep it in float32 with float64 determinant lemmas,
- * LU factorisations and refresh inverses (no tensor cores).
+ * LU factorisations and refresh inverses (no tensor cores).  A determinant
+ * whose lemma ratio lies beyond 10^+-3 gets its ratio from a float64 LU of
+ * the new matrix and, if the move is accepted, a fresh float64
+ * factorisation and inverse instead of the Woodbury update.  With the
+ * environment variable FIRE_MCMC_KAPPA_TOL = t >= 0, so does every
+ * determinant with kappa u w > t (kappa the Frobenius condition estimate of
+ * its last factorisation, u the unit roundoff of the state, w its weight
+ * |det| / max |det| in the walker's sum).
  * Outputs: logabs, sign [W] float64 (device, may be NULL) at the final
  * positions (from the final rebuild); accepted [W] int32 (device, may be
  * NULL): accepted moves per walker; *n_accepted (host, may be NULL) their
  * total.  Errors: FIRE_ERR_INVALID_ARG for sigma <= 0, n_sweeps < 0,
- * refresh_every < 0 or a missing pointer (before any launch);
+ * refresh_every < 0, n_global < 0, sigma_global <= 0 with n_global > 0 or a
+ * missing pointer (before any launch);
  * FIRE_ERR_CAPACITY if an update set or a neighbour list exceeded its
  * capacity (|U| <= min(n_el, 2 k_cap + 1)); FIRE_ERR_NONFINITE as in
  * fire_logpsi. */
 int fire_mcmc_step(const fire_system_t* sys, const fire_arch_t* arch, const fire_params_t* params,
                    int64_t n_walkers, double* r, int32_t k_cap, int32_t precision, double sigma,
-                   int32_t n_sweeps, int32_t refresh_every, uint64_t seed, uint64_t* counter,
+                   int32_t n_sweeps, int32_t refresh_every, int32_t n_global, double sigma_global,
+                   uint64_t seed, uint64_t* counter,
                    double* logabs, double* sign, int32_t* accepted, int64_t* n_accepted,
                    double* max_drift, fire_info_t* info, void* ws, size_t ws_bytes, void* stream);
+
+/* Semi-local pseudopotential of one nucleus (the paper uses ccECP tables;
+ * any coefficients of this standard form may be supplied):
+ *   v_l(x) = sum_j coef[l][j] x^power[l][j] exp(-alpha[l][j] x^2),
+ * non-local channels l = 0 .. n_channels-1 (<= 3), n_terms[l] <= 4 terms,
+ * n_quad quadrature points (0 = no pseudopotential on this nucleus; 4, 6 or
+ * 12: tetrahedron, octahedron, icosahedron), electrons within r_cut of the
+ * nucleus.  Keep r_cut below half the distance between pseudopotential
+ * nuclei: an electron uses the first nucleus (in index order) whose r_cut
+ * contains it. */
+typedef struct {
+  int32_t n_quad;
+  int32_t n_channels;
+  int32_t n_terms[3];
+  int32_t pad_;
+  double r_cut;
+  double coef[3][4];
+  double power[3][4];
+  double alpha[3][4];
+} fire_ecp_t;
+
+/* Non-local pseudopotential energy per walker (Methods, "Low-rank wave
+ * function updates": ratios of configurations that differ in one electron;
+ * Supplementary "Effective core potential": per-species quadrature;
+ * Methods, "Energy extrapolation": n_el N_quad updates):
+ *   v_nl[w] = sum_k sum_l v_l(|r_k - R_m|) (2l + 1)
+ *             sum_q (1/N_quad) P_l(rhat_k . n_q) Psi(.. R_m + |r_k - R_m| n_q ..) / Psi
+ * with m the pseudopotential nucleus of electron k and n_q the quadrature
+ * directions under one random rotation per (walker, electron): the unit
+ * quaternion (sqrt(1-u1) sin 2pi u2, sqrt(1-u1) cos 2pi u2, sqrt(u1) sin 2pi u3,
+ * sqrt(u1) cos 2pi u3) as (x, y, z, w), u1..u3 from words 0..2 of Philox4x32-10
+ * counter (k, 0, walker, 3) under key (seed low, seed high).  Every ratio
+ * comes from the low-rank machinery of fire_mcmc_step (local recompute of the
+ * update set, determinant lemma, exact float64 ratio where the lemma is not
+ * trusted) on a state built at the start of the call; nothing is accepted.
+ * ecp: HOST array [n_nuc], copied into the workspace.  v_nl: device [W]
+ * float64.  Workspace: fire_workspace_size() with FIRE_OP_MCMC.  Precision as
+ * in fire_mcmc_step (float32 state for the reduced forms).  Errors:
+ * FIRE_ERR_INVALID_ARG for a bad table (n_quad not 0/4/6/12, more than 3
+ * channels or 4 terms, negative r_cut or alpha, non-finite numbers) or a
+ * missing pointer; the others as in fire_mcmc_step. */
+int fire_ecp_nonlocal(const fire_system_t* sys, const fire_arch_t* arch, const fire_params_t* params,
+                      int64_t n_walkers, const double* r, int32_t k_cap, int32_t precision, const fire_ecp_t* ecp,
+                      uint64_t seed, double* v_nl, fire_info_t* info, void* ws, size_t ws_bytes, void* stream);
+
+/* S+ swap ratios (Supplementary "Low-rank updates in S+ operator"; Methods
+ * "Low-rank wave function updates": configurations that differ in two
+ * electrons): for the spin-down electron beta (n_up <= beta < n_el) and
+ * every spin-up electron alpha,
+ *   ratios[w][alpha] = Psi(pi_{alpha beta} r_w) / Psi(r_w)   (signed),
+ *   r_beta[w]        = 1 - sum_alpha ratios[w][alpha],
+ * pi swapping the positions of alpha and beta (each keeps its spin).  Each
+ * swap recomputes only the update set {alpha, beta} and the electrons within
+ * c of either position: h^0 and its projections are swapped between the two
+ * cached blocks (they depend on the position alone), their envelope rows are
+ * recomputed with their own spin's weights, and the determinant ratio comes
+ * from the |U| x |U| determinant lemma on a state built at the start of the
+ * call (nothing is moved).  ratios device float64 [W][n_up], r_beta device
+ * float64 [W].  Workspace: fire_workspace_size() with FIRE_OP_MCMC.
+ * Precision as in fire_mcmc_step.  Errors: FIRE_ERR_INVALID_ARG for beta
+ * outside the spin-down electrons or a missing pointer; the others as in
+ * fire_mcmc_step. */
+int fire_spin_ratios(const fire_system_t* sys, const fire_arch_t* arch, const fire_params_t* params,
+                     int64_t n_walkers, const double* r, int32_t k_cap, int32_t precision, int32_t beta,
+                     double* ratios, double* r_beta, fire_info_t* info, void* ws, size_t ws_bytes, void* stream);
+
+/* SPRING parameter update (Methods, "Variational Monte Carlo", eq. spring):
+ *
+ *   Obar_i = O_i - (1/N) sum_j O_j,   eps_i = E_L,i - (1/N) sum_j E_L,j,
+ *   delta  = Obar^T (Obar Obar^T + lambda I)^-1 (eps - eta Obar delta_prev)
+ *            + eta delta_prev
+ *
+ * for N = n_walkers samples and P = n_params parameters.  The paper prints
+ * the update with the centred matrix as P x N; here O is N x P (row i = the
+ * gradient row of walker i, the output layout of fire_grad_logpsi), which is
+ * the same formula with the transposes that make its dimensions agree.
+ * Supplementary "Hyperparameters": lambda = 1e-3, eta (the SPRING decay) =
+ * 0.99.
+ *
+ * O        device float32 [N][ldo] (ldo >= P), read only.
+ * e_loc    device float64 [N].
+ * delta_prev  device float32 [P], or NULL (treated as zero).
+ * delta    device float32 [P], out.
+ * gram     device float64 [N][N] out (the centred Gram matrix Obar Obar^T,
+ *          before the damping), or NULL.
+ * x_out    device float64 [N] out, the solution x of
+ *          (Obar Obar^T + lambda I) x = eps - eta Obar delta_prev, or NULL.
+ * ws       device workspace of fire_spring_workspace_size(N, P) bytes.
+ * Arithmetic: column means, right-hand side, Cholesky factorisation and
+ * solves in float64; the Gram matrix on the tensor cores as a split-bf16
+ * product (three bf16 components per operand, six component products, FP32
+ * accumulation) over chunks of 2^18 parameters whose partial sums are added
+ * in float64; delta accumulated in float64 and stored as float32.
+ * Errors: FIRE_ERR_INVALID_ARG (N < 2, N > 65536, P < 1, ldo < P, lambda <= 0,
+ * eta < 0, a missing pointer) and FIRE_ERR_WORKSPACE on the host before any
+ * launch; FIRE_ERR_NONFINITE if the damped Gram matrix is not numerically
+ * positive definite; FIRE_ERR_TIMEOUT if a bounded wait of the tensor-core
+ * product gave up.  The call synchronises `stream` before it returns. */
+size_t fire_spring_workspace_size(int64_t n_walkers, int64_t n_params);
+int fire_spring_step(int64_t n_walkers, int64_t n_params, const float* O, int64_t ldo, const double* e_loc,
+                     const float* delta_prev, double eta, double lambda, float* delta, double* gram,
+                     double* x_out, void* ws, size_t ws_bytes, void* stream);
 
 /* Layout of the workspace of a call (diagnostics and tests): for each named
  * intermediate buffer its byte offset inside ws and its size in bytes, for

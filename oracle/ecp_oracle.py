@@ -97,14 +97,18 @@ def v_channel(ecp: Dict, l: int, x) -> np.ndarray:
     return out
 
 
-def nonlocal_energy(system, arch, params, r_np: np.ndarray, ecp: List[Dict], seed: int) -> np.ndarray:
+def nonlocal_energy(system, arch, params, r_np: np.ndarray, ecp: List[Dict], seed: int,
+                    return_scale: bool = False):
     """V_nl per walker [W].  ecp[m] = None (no pseudopotential) or
-    {"n_quad": 4|6|12, "r_cut": x, "terms": [[(c, p, a), ...] for l = 0..l_max]}."""
+    {"n_quad": 4|6|12, "r_cut": x, "terms": [[(c, p, a), ...] for l = 0..l_max]}.
+    With return_scale, also the sum of the magnitudes of the summed terms
+    (the scale a rounding error of the sum is relative to)."""
     r = np.asarray(r_np, dtype=np.float64)
     W, n = r.shape[0], r.shape[1]
     R = np.asarray(system.nuc_pos, dtype=np.float64)
     lp, sg = O.logpsi_np(system, arch, params, r)
     out = np.zeros(W)
+    scale = np.zeros(W)
     for k in range(n):
         # the pseudopotential nucleus of electron k in every walker (E1)
         nuc = np.full(W, -1)
@@ -129,5 +133,7 @@ def nonlocal_energy(system, arch, params, r_np: np.ndarray, ecp: List[Dict], see
                 lpn, sgn = O.logpsi_np(system, arch, params, rp)
                 ratio[:, q] = sgn * sg[ws] * np.exp(lpn - lp[ws])
             for l in range(len(e["terms"])):
-                out[ws] += v_channel(e, l, rad) * (2 * l + 1) * (wq * legendre(l, cos) * ratio).sum(-1)
-    return out
+                term = v_channel(e, l, rad)[:, None] * (2 * l + 1) * wq * legendre(l, cos) * ratio
+                out[ws] += term.sum(-1)
+                scale[ws] += np.abs(term).sum(-1)
+    return (out, scale) if return_scale else out

@@ -5,6 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <cmath>
 #include <mutex>
 
 #include "grad_bufs.h"
@@ -211,12 +212,24 @@ static size_t layout(Plan& pl, int64_t Wc) {
     TAKE(mc_stat, sizeof(McmcStat));
     TAKE(mc_wdrift, Wc * 8);
     TAKE(mc_lref, Wc * D * 8);         // log|det| of each matrix at its last factorisation
+    TAKE(mc_kap, Wc * D * 4);          // condition estimate of each matrix at the last refresh
+    TAKE(mc_ecp, (int64_t)dm.N * (int64_t)sizeof(fire_ecp_t));   // pseudopotential table
+    // the batched float64 LU of the exact ratios of ill-conditioned determinants
+    pl.xcap = (int)(Wc * D < 16384 ? Wc * D : 16384);
+    TAKE(mc_xcnt, 16);
+    TAKE(mc_xlist, (int64_t)pl.xcap * 4);
+    TAKE(mc_xbatch, (int64_t)pl.xcap * n * n * 8);
+    TAKE(mc_xpiv, (int64_t)pl.xcap * n * 4);
+    TAKE(mc_xlab, (int64_t)pl.xcap * 8);
+    TAKE(mc_xsg, (int64_t)pl.xcap * 8);
     TAKE(mc_H1, nb * d * ts);          // cached h^1 rows (block order)
     // per-move scratch: dead during a refresh, so it shares the float64 LU
     // buffer (dead during the moves) when it fits there
     struct Sc { size_t* field; const char* name; size_t bytes; };
     const Sc sc[] = {
         {&pl.mc_rk, "mc_rk", (size_t)(Wc * 3 * 8)}, {&pl.mc_u, "mc_u", (size_t)(Wc * 8)},
+        {&pl.mc_lq, "mc_lq", (size_t)(Wc * 8)}, {&pl.mc_rk2, "mc_rk2", (size_t)(Wc * 3 * 8)},
+        {&pl.mc_Fk2, "mc_Fk2", (size_t)(Wc * Dn) * ts},
         {&pl.mc_Ul, "mc_Ul", (size_t)(capU * 4)}, {&pl.mc_Uc, "mc_Uc", (size_t)(Wc * 4)},
         {&pl.mc_Ucu, "mc_Ucu", (size_t)(Wc * 4)}, {&pl.mc_Urow, "mc_Urow", (size_t)(capU * 4)},
         {&pl.mc_h0k, "mc_h0k", (size_t)(Wc * d) * ts}, {&pl.mc_PQk, "mc_PQk", (size_t)(Wc * 4 * d) * ts},
@@ -562,11 +575,12 @@ int fire_local_energy(const fire_system_t* sys, const fire_arch_t* arch, const f
 
 int fire_mcmc_step(const fire_system_t* sys, const fire_arch_t* arch, const fire_params_t* params,
                    int64_t W, double* r, int32_t k_cap, int32_t precision, double sigma, int32_t n_sweeps,
-                   int32_t refresh_every, uint64_t seed, uint64_t* counter, double* logabs, double* sign,
-                   int32_t* accepted, int64_t* n_accepted, double* max_drift, fire_info_t* info, void* ws,
-                   size_t ws_bytes, void* stream) {
+                   int32_t refresh_every, int32_t n_global, double sigma_global, uint64_t seed, uint64_t* counter,
+                   double* logabs, double* sign, int32_t* accepted, int64_t* n_accepted, double* max_drift,
+                   fire_info_t* info, void* ws, size_t ws_bytes, void* stream) {
   if (!params || !params->theta || !r || !counter) return FIRE_ERR_INVALID_ARG;
   if (!(sigma > 0.0) || !(sigma < 1e300) || n_sweeps < 0 || refresh_every < 0) return FIRE_ERR_INVALID_ARG;
+  if (n_global < 0 || (n_global > 0 && !(sigma_global > 0.0 && sigma_global < 1e300))) return FIRE_ERR_INVALID_ARG;
   if (precision < 0 || precision > 2) return FIRE_ERR_INVALID_ARG;
   // the moves run in float32 for both reduced forms
   const int prec = precision == FIRE_PREC_FP64 ? FIRE_PREC_FP64 : FIRE_PREC_FP32;
@@ -586,7 +600,12 @@ int fire_mcmc_step(const fire_system_t* sys, const fire_arch_t* arch, const fire
   DevStatus hs;
   memset(&hs, 0, sizeof(hs));
   int64_t nl = 0;
-  McmcCall mc{sigma, n_sweeps, refresh_every, seed, *counter, accepted, 0, 0.0};
+  // conditioning test of the exact-ratio path (FIRE_MCMC_KAPPA_TOL sets the
+  // tolerance; off by default)
+  double ktol = -1.0;
+  if (const char* e = getenv("FIRE_MCMC_KAPPA_TOL")) ktol = atof(e);
+  McmcCall mc{sigma, n_sweeps, refresh_every, seed, *counter, accepted, 0, 0.0, n_global, sigma_global, ktol,
+              nullptr, 0, nullptr, -1, nullptr, nullptr};
   unsigned char* wsb = reinterpret_cast<unsigned char*>(ws);
   double* lpf = reinterpret_cast<double*>(wsb + pl.mc_lpf);
   double* sgf = reinterpret_cast<double*>(wsb + pl.mc_sgf);
@@ -611,6 +630,121 @@ int fire_mcmc_step(const fire_system_t* sys, const fire_arch_t* arch, const fire
   *counter = mc.counter;
   if (n_accepted) *n_accepted = mc.n_accepted;
   if (max_drift) *max_drift = mc.max_drift;
+  if (hs.overflow) return FIRE_ERR_CAPACITY;
+  if (hs.n_nonfinite) return FIRE_ERR_NONFINITE;
+  return FIRE_OK;
+}
+
+
+int fire_ecp_nonlocal(const fire_system_t* sys, const fire_arch_t* arch, const fire_params_t* params, int64_t W,
+                      const double* r, int32_t k_cap, int32_t precision, const fire_ecp_t* ecp, uint64_t seed,
+                      double* v_nl, fire_info_t* info, void* ws, size_t ws_bytes, void* stream) {
+  if (!params || !params->theta || !r || !ecp || !v_nl || !sys) return FIRE_ERR_INVALID_ARG;
+  if (precision < 0 || precision > 2) return FIRE_ERR_INVALID_ARG;
+  int qmax = 0;
+  for (int m = 0; m < sys->n_nuc; ++m) {
+    const fire_ecp_t& e = ecp[m];
+    if (e.n_quad != 0 && e.n_quad != 4 && e.n_quad != 6 && e.n_quad != 12) return FIRE_ERR_INVALID_ARG;
+    if (e.n_channels < 0 || e.n_channels > 3 || !(e.r_cut >= 0.0) || !(e.r_cut < 1e300)) return FIRE_ERR_INVALID_ARG;
+    for (int l = 0; l < e.n_channels; ++l) {
+      if (e.n_terms[l] < 0 || e.n_terms[l] > 4) return FIRE_ERR_INVALID_ARG;
+      for (int j = 0; j < e.n_terms[l]; ++j)
+        if (!std::isfinite(e.coef[l][j]) || !std::isfinite(e.power[l][j]) || !(e.alpha[l][j] >= 0.0) ||
+            !std::isfinite(e.alpha[l][j]))
+          return FIRE_ERR_INVALID_ARG;
+    }
+    if (e.n_quad > qmax) qmax = e.n_quad;
+  }
+  const int prec = precision == FIRE_PREC_FP64 ? FIRE_PREC_FP64 : FIRE_PREC_FP32;
+  Plan pl;
+  int rc = make_plan(sys, arch, W, prec, k_cap, FIRE_OP_MCMC, &pl);
+  if (rc) return rc;
+  if (!sys->nuc_pos || !sys->nuc_charge) return FIRE_ERR_INVALID_ARG;
+  if (params->n_params != fire_param_count(sys, arch)) return FIRE_ERR_INVALID_ARG;
+  if (params->dtype != (prec == FIRE_PREC_FP64 ? 0 : 1)) return FIRE_ERR_INVALID_ARG;
+  if (!ws || ws_bytes < pl.total) return FIRE_ERR_WORKSPACE;
+  PDesc t[P_COUNT];
+  param_table(sys, arch, t);
+  int64_t poff[P_COUNT];
+  int64_t off = 0;
+  for (int k = 0; k < P_COUNT; ++k) { poff[k] = off; off += numel(t[k]); }
+  pl.nparams = off;
+  unsigned char* wsb = reinterpret_cast<unsigned char*>(ws);
+  cudaStream_t s = (cudaStream_t)stream;
+  fire_ecp_t* ecp_dev = reinterpret_cast<fire_ecp_t*>(wsb + pl.mc_ecp);
+  if (cudaMemcpyAsync(ecp_dev, ecp, sizeof(fire_ecp_t) * (size_t)sys->n_nuc, cudaMemcpyHostToDevice, s) !=
+      cudaSuccess)
+    return FIRE_ERR_CUDA;
+  DevStatus hs;
+  memset(&hs, 0, sizeof(hs));
+  int64_t nl = 0;
+  double ktol = -1.0;
+  if (const char* e = getenv("FIRE_MCMC_KAPPA_TOL")) ktol = atof(e);
+  McmcCall mc{1.0, 0, 0, seed, 0, nullptr, 0, 0.0, 0, 1.0, ktol, ecp_dev, qmax, v_nl, -1, nullptr, nullptr};
+  double* lpf = reinterpret_cast<double*>(wsb + pl.mc_lpf);
+  double* sgf = reinterpret_cast<double*>(wsb + pl.mc_sgf);
+  CallArgs a{sys, arch, params->theta, poff, W, r, nullptr, lpf, sgf, nullptr, nullptr, ws, s, &hs, &nl, nullptr,
+             &mc};
+  rc = prec == FIRE_PREC_FP64 ? run_fp64(pl, a) : run_bf16(pl, a);
+  if (info) {
+    info->k_required = hs.k_required;
+    info->n_nodes = hs.n_nodes;
+    info->n_nonfinite = hs.n_nonfinite;
+    info->n_chunks = 1;
+    info->rows_total = hs.rows_total;
+    info->n_launches = nl;
+    info->mean_neighbors = (double)hs.nbr_total / ((double)W * sys->n_el);
+  }
+  if (rc) return rc;
+  if (hs.overflow) return FIRE_ERR_CAPACITY;
+  if (hs.n_nonfinite) return FIRE_ERR_NONFINITE;
+  return FIRE_OK;
+}
+
+
+int fire_spin_ratios(const fire_system_t* sys, const fire_arch_t* arch, const fire_params_t* params, int64_t W,
+                     const double* r, int32_t k_cap, int32_t precision, int32_t beta, double* ratios, double* r_beta,
+                     fire_info_t* info, void* ws, size_t ws_bytes, void* stream) {
+  if (!params || !params->theta || !r || !ratios || !r_beta || !sys) return FIRE_ERR_INVALID_ARG;
+  if (precision < 0 || precision > 2) return FIRE_ERR_INVALID_ARG;
+  if (beta < sys->n_up || beta >= sys->n_el) return FIRE_ERR_INVALID_ARG;
+  const int prec = precision == FIRE_PREC_FP64 ? FIRE_PREC_FP64 : FIRE_PREC_FP32;
+  Plan pl;
+  int rc = make_plan(sys, arch, W, prec, k_cap, FIRE_OP_MCMC, &pl);
+  if (rc) return rc;
+  if (!sys->nuc_pos || !sys->nuc_charge) return FIRE_ERR_INVALID_ARG;
+  if (params->n_params != fire_param_count(sys, arch)) return FIRE_ERR_INVALID_ARG;
+  if (params->dtype != (prec == FIRE_PREC_FP64 ? 0 : 1)) return FIRE_ERR_INVALID_ARG;
+  if (!ws || ws_bytes < pl.total) return FIRE_ERR_WORKSPACE;
+  PDesc t[P_COUNT];
+  param_table(sys, arch, t);
+  int64_t poff[P_COUNT];
+  int64_t off = 0;
+  for (int k = 0; k < P_COUNT; ++k) { poff[k] = off; off += numel(t[k]); }
+  pl.nparams = off;
+  unsigned char* wsb = reinterpret_cast<unsigned char*>(ws);
+  cudaStream_t s = (cudaStream_t)stream;
+  DevStatus hs;
+  memset(&hs, 0, sizeof(hs));
+  int64_t nl = 0;
+  double ktol = -1.0;
+  if (const char* e = getenv("FIRE_MCMC_KAPPA_TOL")) ktol = atof(e);
+  McmcCall mc{1.0, 0, 0, 0, 0, nullptr, 0, 0.0, 0, 1.0, ktol, nullptr, 0, nullptr, beta, ratios, r_beta};
+  double* lpf = reinterpret_cast<double*>(wsb + pl.mc_lpf);
+  double* sgf = reinterpret_cast<double*>(wsb + pl.mc_sgf);
+  CallArgs a{sys, arch, params->theta, poff, W, r, nullptr, lpf, sgf, nullptr, nullptr, ws, s, &hs, &nl, nullptr,
+             &mc};
+  rc = prec == FIRE_PREC_FP64 ? run_fp64(pl, a) : run_bf16(pl, a);
+  if (info) {
+    info->k_required = hs.k_required;
+    info->n_nodes = hs.n_nodes;
+    info->n_nonfinite = hs.n_nonfinite;
+    info->n_chunks = 1;
+    info->rows_total = hs.rows_total;
+    info->n_launches = nl;
+    info->mean_neighbors = (double)hs.nbr_total / ((double)W * sys->n_el);
+  }
+  if (rc) return rc;
   if (hs.overflow) return FIRE_ERR_CAPACITY;
   if (hs.n_nonfinite) return FIRE_ERR_NONFINITE;
   return FIRE_OK;

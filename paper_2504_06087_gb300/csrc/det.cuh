@@ -121,7 +121,10 @@ __device__ __forceinline__ unsigned long long mag_key(float v) {
 // use one reciprocal of the pivot, formed by one thread.
 template <typename LT, int NB>
 __global__ void lu_kernel(int n, LT* __restrict__ M, int32_t* __restrict__ piv,
-                          double* __restrict__ logabs, double* __restrict__ sgn) {
+                          double* __restrict__ logabs, double* __restrict__ sgn,
+                          const int* __restrict__ count = nullptr) {
+  // a batch whose size is known on the device only: CTAs beyond it leave
+  if (count && (int)blockIdx.x >= *count) return;
   extern __shared__ unsigned char lu_smem[];
   constexpr int PS = NB + 1;                   // panel row stride: rows fall in different banks
   LT* P = reinterpret_cast<LT*>(lu_smem);      // [n][NB + 1]

@@ -117,10 +117,91 @@ __device__ void cta_gemm_tn(int M, int N, int K, const T* __restrict__ A, int64_
 // Then the update set U of the walker, ascending (so its spin-up members come
 // first); Ucu = number of spin-up members.  One warp per walker.
 // ---------------------------------------------------------------------------
+// The update set U of walker w for moving electron k from rw[k] to rn: k and
+// every electron within c of either position, ascending (so its spin-up
+// members come first); Ucu = number of spin-up members.  One warp; an
+// inactive walker gets an empty set.
+__device__ inline void update_set(int w, int lane, int n, int n_up, int k, const double* __restrict__ rw,
+                                  const double* rn, double c2, int Umax, int32_t* __restrict__ Ul,
+                                  int32_t* __restrict__ Uc, int32_t* __restrict__ Ucu, DevStatus* st, bool active) {
+  int cntU = 0, cntUp = 0;
+  if (active)
+    for (int j0 = 0; j0 < n; j0 += 32) {
+      const int j = j0 + lane;
+      bool in = false;
+      if (j < n) {
+        if (j == k) {
+          in = true;
+        } else {
+          double a2 = 0.0, b2 = 0.0;
+          for (int t = 0; t < 3; ++t) {
+            const double da = rw[3 * j + t] - rw[3 * k + t], db = rw[3 * j + t] - rn[t];
+            a2 += da * da;
+            b2 += db * db;
+          }
+          in = (a2 <= c2) || (b2 <= c2);
+        }
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, in);
+      if (in) {
+        const int pos = cntU + __popc(m & ((1u << lane) - 1u));
+        if (pos < Umax) Ul[(int64_t)w * Umax + pos] = j;
+      }
+      cntU += __popc(m);
+      const unsigned mu = __ballot_sync(0xffffffffu, in && j < n_up);
+      cntUp += __popc(mu);
+    }
+  if (lane == 0) {
+    if (cntU > Umax) {
+      atomicExch(&st->overflow, 1);
+      atomicMax(&st->k_required, cntU);
+    }
+    Uc[w] = cntU < Umax ? cntU : Umax;
+    Ucu[w] = cntUp < Umax ? cntUp : Umax;
+  }
+}
+
+// Global jump (Methods, "Improved Monte Carlo sampling"): the proposal
+// density of the mixture sum_m Z_m N(r | R_m, sigma_g^2 I) / sum_m Z_m at x,
+// as a logarithm (log-sum-exp over the nuclei, float64).
+__device__ inline double gmm_log_density(const double* x, const double* __restrict__ R,
+                                         const double* __restrict__ Z, int N, double sigma_g) {
+  const double inv = 1.0 / (2.0 * sigma_g * sigma_g);
+  double mx = -INFINITY, zt = 0.0;
+  for (int m = 0; m < N; ++m) {
+    double d2 = 0.0;
+    for (int t = 0; t < 3; ++t) {
+      const double dx = x[t] - R[3 * m + t];
+      d2 += dx * dx;
+    }
+    const double e = log(Z[m]) - d2 * inv;
+    if (e > mx) mx = e;
+    zt += Z[m];
+  }
+  double sum = 0.0;
+  for (int m = 0; m < N; ++m) {
+    double d2 = 0.0;
+    for (int t = 0; t < 3; ++t) {
+      const double dx = x[t] - R[3 * m + t];
+      d2 += dx * dx;
+    }
+    sum += exp(log(Z[m]) - d2 * inv - mx);
+  }
+  return mx + log(sum) - log(zt) - 1.5 * log(6.283185307179586476925286766559 * sigma_g * sigma_g);
+}
+
+// Local moves: r'_k = r_k + sigma xi.  Global jumps (global != 0): a mixture
+// component m with probability Z_m / sum Z (the first m whose cumulative
+// charge exceeds u sum Z, u from stream 2) and r'_k = R_m + sigma_g xi;
+// lq[w] = ln rho(r_k) - ln rho(r'_k), the Hastings factor of the
+// asymmetric proposal (0 for local moves).
 static __global__ void mcmc_propose_kernel(int n, int n_up, int k, const double* __restrict__ r, double sigma,
                                     uint64_t seed, uint64_t move, int64_t w0, double c2, int Umax,
                                     double* __restrict__ rk, double* __restrict__ uacc, int32_t* __restrict__ Ul,
-                                    int32_t* __restrict__ Uc, int32_t* __restrict__ Ucu, DevStatus* st) {
+                                    int32_t* __restrict__ Uc, int32_t* __restrict__ Ucu, DevStatus* st,
+                                    int global, const double* __restrict__ nuc_pos,
+                                    const double* __restrict__ nuc_charge, int N, double sigma_g,
+                                    double* __restrict__ lq) {
   const int w = blockIdx.x;
   const int lane = threadIdx.x;
   const double* rw = r + (int64_t)w * n * 3;
@@ -134,47 +215,29 @@ static __global__ void mcmc_propose_kernel(int n, int n_up, int k, const double*
     const double ra = sqrt(-2.0 * log(u01(a.v[0]))), rb = sqrt(-2.0 * log(u01(a.v[2])));
     const double t1 = two_pi * u01(a.v[1]), t3 = two_pi * u01(a.v[3]);
     const double xi[3] = {ra * cos(t1), ra * sin(t1), rb * cos(t3)};
-    for (int t = 0; t < 3; ++t) {
-      rn[t] = rw[3 * k + t] + sigma * xi[t];
-      rk[(int64_t)w * 3 + t] = rn[t];
+    if (global) {
+      const Philox4 c = philox4x32_10(m0, m1, wg, 2u, k0, k1);
+      double zt = 0.0;
+      for (int m = 0; m < N; ++m) zt += nuc_charge[m];
+      const double target = u01(c.v[0]) * zt;
+      int comp = N - 1;
+      double cum = 0.0;
+      for (int m = 0; m < N; ++m) {
+        cum += nuc_charge[m];
+        if (target < cum) { comp = m; break; }
+      }
+      for (int t = 0; t < 3; ++t) rn[t] = nuc_pos[3 * comp + t] + sigma_g * xi[t];
+      lq[w] = gmm_log_density(rw + 3 * k, nuc_pos, nuc_charge, N, sigma_g) -
+              gmm_log_density(rn, nuc_pos, nuc_charge, N, sigma_g);
+    } else {
+      for (int t = 0; t < 3; ++t) rn[t] = rw[3 * k + t] + sigma * xi[t];
+      lq[w] = 0.0;
     }
+    for (int t = 0; t < 3; ++t) rk[(int64_t)w * 3 + t] = rn[t];
     uacc[w] = u01(b.v[0]);
   }
   __syncwarp();
-  int cntU = 0, cntUp = 0;
-  for (int j0 = 0; j0 < n; j0 += 32) {
-    const int j = j0 + lane;
-    bool in = false;
-    if (j < n) {
-      if (j == k) {
-        in = true;
-      } else {
-        double a2 = 0.0, b2 = 0.0;
-        for (int t = 0; t < 3; ++t) {
-          const double da = rw[3 * j + t] - rw[3 * k + t], db = rw[3 * j + t] - rn[t];
-          a2 += da * da;
-          b2 += db * db;
-        }
-        in = (a2 <= c2) || (b2 <= c2);
-      }
-    }
-    const unsigned m = __ballot_sync(0xffffffffu, in);
-    if (in) {
-      const int pos = cntU + __popc(m & ((1u << lane) - 1u));
-      if (pos < Umax) Ul[(int64_t)w * Umax + pos] = j;
-    }
-    cntU += __popc(m);
-    const unsigned mu = __ballot_sync(0xffffffffu, in && j < n_up);
-    cntUp += __popc(mu);
-  }
-  if (lane == 0) {
-    if (cntU > Umax) {
-      atomicExch(&st->overflow, 1);
-      atomicMax(&st->k_required, cntU);
-    }
-    Uc[w] = cntU < Umax ? cntU : Umax;
-    Ucu[w] = cntUp < Umax ? cntUp : Umax;
-  }
+  update_set(w, lane, n, n_up, k, rw, rn, c2, Umax, Ul, Uc, Ucu, st, true);
 }
 
 // Compact row index of every member of U: spin-up members of all walkers
@@ -393,7 +456,8 @@ __global__ void __launch_bounds__(256) mcmc_ratio_kernel(
     int Wn, int n, int n_up, int D, int k, int Umax, const int32_t* __restrict__ Ul, const int32_t* __restrict__ Uc,
     const int32_t* __restrict__ Urow, const T* __restrict__ On, const T* __restrict__ Fenv, const T* __restrict__ Fk,
     const T* __restrict__ Phi, const T* __restrict__ AT, T* __restrict__ Dl, T* __restrict__ Mt,
-    double* __restrict__ Mg, int32_t* __restrict__ Mpiv, double* __restrict__ lrat, double* __restrict__ srat) {
+    double* __restrict__ Mg, int32_t* __restrict__ Mpiv, double* __restrict__ lrat, double* __restrict__ srat,
+    int k2 = -1, const T* __restrict__ Fk2 = nullptr) {
   __shared__ double su[kLemmaSmem * (kLemmaSmem + 1)];   // the product tiles, then M
   __shared__ int s_p;
   const int w = blockIdx.x / D, dd = blockIdx.x % D;
@@ -408,8 +472,9 @@ __global__ void __launch_bounds__(256) mcmc_ratio_kernel(
     const int aa = e / n, l = e % n;
     const int i = U[aa];
     const T o = On[(int64_t)Urow[(int64_t)w * Umax + aa] * Dn + dd * n + l];
-    const T ph = (i == k) ? Fk[(int64_t)w * Dn + dd * n + l]
-                          : Fenv[(int64_t)block_index(w, i, Wn, n, n_up) * Dn + dd * n + l];
+    const T ph = (i == k)    ? Fk[(int64_t)w * Dn + dd * n + l]
+                 : (i == k2) ? Fk2[(int64_t)w * Dn + dd * n + l]
+                             : Fenv[(int64_t)block_index(w, i, Wn, n, n_up) * Dn + dd * n + l];
     Dw[(int64_t)aa * n + l] = o * ph - Pw[(int64_t)i * n + l];
   }
   // Delta A[:, U] = Delta (u x n) times the rows U of A^T
@@ -524,39 +589,41 @@ struct McmcJastrow {
   const void *cusp, *jb32, *ab32;
 };
 
-// Accept / reject.  ln|Psi'/Psi| = determinant part (from the ratios of all
-// determinants) + cusp change of electron k + change of the MLP-Jastrow sums
-// + change of the attention-Jastrow readout.  Accept iff ln u < 2 ln|Psi'/Psi|
-// and the ratio is finite.  One warp per walker; an accepted walker moves r_k
-// and updates its determinant logs and its running log|Psi|.
+// ln|Psi'/Psi| and sign(Psi'/Psi) of walker w for the move of electron k to
+// rk (all lanes of one warp call it; the result is valid on lane 0):
+// determinant part from the ratios of all determinants, cusp change of
+// electron k, change of the MLP-Jastrow sums over the update set, change of
+// the attention-Jastrow readout.
+struct WalkerRatio {
+  double logr, sign;
+};
+
 template <typename T>
-__global__ void mcmc_accept_kernel(int Wn, int n, int n_up, int D, int k, int Umax, uint32_t flags,
-                                   double* __restrict__ r, const double* __restrict__ rk,
-                                   const double* __restrict__ uacc, const int32_t* __restrict__ Ul,
-                                   const int32_t* __restrict__ Uc, const int32_t* __restrict__ Urow, McmcJastrow jp,
-                                   const T* __restrict__ F1, const T* __restrict__ F2, const T* __restrict__ F1n,
-                                   const T* __restrict__ F2n, const T* __restrict__ G1, const T* __restrict__ G2,
-                                   const T* __restrict__ G1n, const T* __restrict__ G2n,
-                                   double* __restrict__ ldabs, double* __restrict__ lsign,
-                                   const double* __restrict__ lrat, const double* __restrict__ srat,
-                                   double* __restrict__ lp, int32_t* __restrict__ acc,
-                                   int32_t* __restrict__ acc_count, unsigned long long* __restrict__ nacc,
-                                   const double* __restrict__ lref, int32_t* __restrict__ flag,
-                                   const int32_t* __restrict__ xflag) {
-  const int w = blockIdx.x;
-  const int lane = threadIdx.x;
-  double* rw = r + (int64_t)w * n * 3;
-  const double* rn = rk + (int64_t)w * 3;
+__device__ WalkerRatio walker_ratio(int w, int lane, int Wn, int n, int n_up, int D, int k, int Umax, uint32_t flags,
+                                    const double* __restrict__ rw, const double* __restrict__ rn, int k2,
+                                    const double* __restrict__ rn2,
+                                    const int32_t* __restrict__ Ul, const int32_t* __restrict__ Uc,
+                                    const int32_t* __restrict__ Urow, const McmcJastrow& jp,
+                                    const T* __restrict__ F1, const T* __restrict__ F2, const T* __restrict__ F1n,
+                                    const T* __restrict__ F2n, const T* __restrict__ G1, const T* __restrict__ G2,
+                                    const T* __restrict__ G1n, const T* __restrict__ G2n,
+                                    const double* __restrict__ ldabs, const double* __restrict__ lsign,
+                                    const double* __restrict__ lrat, const double* __restrict__ srat) {
   const T* cusp = reinterpret_cast<const T*>(jp.cusp);
   double dc = 0.0, s2 = 0.0, ds1 = 0.0, ds2 = 0.0;
   const double wp = (double)cusp[0], wa = (double)cusp[1], ap = (double)cusp[2], aa = (double)cusp[3];
+  // cusp terms of the pairs of a moved electron (k, and k2 >= 0 for a swap of
+  // two electrons, whose own pair keeps its distance and spin channel)
   for (int j = lane; j < n; j += 32) {
-    if (j != k) {
-      const bool same = (j < n_up) == (k < n_up);
+    for (int mv = 0; mv < 2; ++mv) {
+      const int km = mv == 0 ? k : k2;
+      const double* rm = mv == 0 ? rn : rn2;
+      if (km < 0 || j == k || j == k2) continue;
+      const bool same = (j < n_up) == (km < n_up);
       const double om = same ? wp : wa, al = same ? ap : aa;
       double o2 = 0.0, n2 = 0.0;
       for (int t = 0; t < 3; ++t) {
-        const double a = rw[3 * k + t] - rw[3 * j + t], b = rn[t] - rw[3 * j + t];
+        const double a = rw[3 * km + t] - rw[3 * j + t], b = rm[t] - rw[3 * j + t];
         o2 += a * a;
         n2 += b * b;
       }
@@ -578,7 +645,8 @@ __global__ void mcmc_accept_kernel(int Wn, int n, int n_up, int D, int k, int Um
     ds1 += __shfl_xor_sync(0xffffffffu, ds1, o);
     ds2 += __shfl_xor_sync(0xffffffffu, ds2, o);
   }
-  if (lane != 0) return;
+  WalkerRatio out{0.0, 0.0};
+  if (lane != 0) return out;
   // determinants: ln|sum_d s_d rho_d e^{l_d}| - ln|sum_d s_d e^{l_d}|
   const double* lw = ldabs + (int64_t)w * D;
   const double* sw = lsign + (int64_t)w * D;
@@ -596,16 +664,56 @@ __global__ void mcmc_accept_kernel(int Wn, int n, int n_up, int D, int k, int Um
     if (live(q)) Sn += sw[q] * sr[q] * exp(lw[q] + lr[q] - lmaxn);
   }
   double logr = (lmaxn + log(fabs(Sn))) - (lmax + log(fabs(So)));
+  double sg = (Sn > 0.0) == (So > 0.0) ? 1.0 : -1.0;
+  if (Sn == 0.0) sg = 0.0;
   if (flags & FIRE_J_CUSP) logr += dc;
   if (flags & FIRE_J_MLP) {
     const double S2o = s2 + n * (double)reinterpret_cast<const T*>(jp.jb32)[0];
     logr += ds1 + log(fabs(S2o + ds2)) - log(fabs(S2o));
+    if ((S2o + ds2 > 0.0) != (S2o > 0.0)) sg = -sg;
   }
   if (flags & FIRE_J_ATT) {
     const double b32 = (double)reinterpret_cast<const T*>(jp.ab32)[0];
-    logr += ((double)G1n[w] - (double)G1[w]) + log(fabs((double)G2n[w] + b32)) - log(fabs((double)G2[w] + b32));
+    const double gn = (double)G2n[w] + b32, go = (double)G2[w] + b32;
+    logr += ((double)G1n[w] - (double)G1[w]) + log(fabs(gn)) - log(fabs(go));
+    if ((gn > 0.0) != (go > 0.0)) sg = -sg;
   }
-  const bool ok = isfinite(logr) && (log(uacc[w]) < 2.0 * logr);
+  out.logr = logr;
+  out.sign = sg;
+  return out;
+}
+
+// Accept / reject: accept iff ln u < 2 ln|Psi'/Psi| + lq (lq = 0 for a local
+// move, the Hastings factor ln rho(r_k) - ln rho(r'_k) for a global jump)
+// and the ratio is finite.  One warp per walker; an accepted walker moves r_k
+// and updates its determinant logs and its running log|Psi|.
+template <typename T>
+__global__ void mcmc_accept_kernel(int Wn, int n, int n_up, int D, int k, int Umax, uint32_t flags,
+                                   double* __restrict__ r, const double* __restrict__ rk,
+                                   const double* __restrict__ uacc, const int32_t* __restrict__ Ul,
+                                   const int32_t* __restrict__ Uc, const int32_t* __restrict__ Urow, McmcJastrow jp,
+                                   const T* __restrict__ F1, const T* __restrict__ F2, const T* __restrict__ F1n,
+                                   const T* __restrict__ F2n, const T* __restrict__ G1, const T* __restrict__ G2,
+                                   const T* __restrict__ G1n, const T* __restrict__ G2n,
+                                   double* __restrict__ ldabs, double* __restrict__ lsign,
+                                   const double* __restrict__ lrat, const double* __restrict__ srat,
+                                   double* __restrict__ lp, int32_t* __restrict__ acc,
+                                   int32_t* __restrict__ acc_count, unsigned long long* __restrict__ nacc,
+                                   const double* __restrict__ lref, int32_t* __restrict__ flag,
+                                   const int32_t* __restrict__ xflag, const double* __restrict__ lq,
+                                   int* __restrict__ rcnt, int32_t* __restrict__ rlist, int rcap,
+                                   unsigned long long* __restrict__ nrepair) {
+  const int w = blockIdx.x;
+  const int lane = threadIdx.x;
+  double* rw = r + (int64_t)w * n * 3;
+  const double* rn = rk + (int64_t)w * 3;
+  const WalkerRatio wr = walker_ratio<T>(w, lane, Wn, n, n_up, D, k, Umax, flags, rw, rn, -1, nullptr, Ul, Uc, Urow,
+                                         jp, F1, F2, F1n, F2n, G1, G2, G1n, G2n, ldabs, lsign, lrat, srat);
+  if (lane != 0) return;
+  const double logr = wr.logr;
+  const double* lr = lrat + (int64_t)w * D;
+  const double* sr = srat + (int64_t)w * D;
+  const bool ok = isfinite(logr) && (log(uacc[w]) < 2.0 * logr + lq[w]);
   acc[w] = ok ? 1 : 0;
   if (ok) {
     for (int t = 0; t < 3; ++t) rw[3 * k + t] = rn[t];
@@ -619,8 +727,19 @@ __global__ void mcmc_accept_kernel(int Wn, int n, int n_up, int D, int k, int Um
         lsign[md] = 0.0;
       }
       // refactorise a determinant that shrank too far since its last LU
-      // (and one whose ratio needed the exact path: its A is not trusted)
-      flag[md] = (ldabs[md] >= lref[md] + kRepairLogShrink && !xflag[md]) ? 0 : 1;
+      // (and one whose ratio took the exact path: its A is not trusted);
+      // flag 2: in the batched refactorisation list, 1: done by
+      // mcmc_repair_kernel (the list is full)
+      int fl = (ldabs[md] >= lref[md] + kRepairLogShrink && !xflag[md]) ? 0 : 1;
+      if (fl && nrepair) atomicAdd(nrepair, 1ull);
+      if (fl && rlist) {
+        const int slot = atomicAdd(rcnt, 1);
+        if (slot < rcap) {
+          rlist[slot] = (int32_t)md;
+          fl = 2;
+        }
+      }
+      flag[md] = fl;
     }
     lp[w] += logr;
     if (acc_count) acc_count[w] += 1;
@@ -842,6 +961,26 @@ __global__ void __launch_bounds__(256) inverse_panel_kernel(int n, int64_t m0, c
   inverse_panel_block<LT, CT, AT>(n, LU + mat * n * n, piv + mat * n, Ainv + mat * n * n, ip_smem);
 }
 
+// A^T of the batched refactorisations: matrix f of the batch into the slot
+// rlist[f] of A^T (zero for a singular matrix); CTAs beyond the count leave.
+template <typename LT, typename T>
+__global__ void __launch_bounds__(256) mcmc_repair_inverse_kernel(int n, const int* __restrict__ count, int cap,
+                                                                  const int32_t* __restrict__ rlist,
+                                                                  const LT* __restrict__ batch,
+                                                                  const int32_t* __restrict__ piv,
+                                                                  const double* __restrict__ bsg,
+                                                                  T* __restrict__ AT) {
+  extern __shared__ unsigned char ri_smem[];
+  const int c = *count < cap ? *count : cap;
+  if ((int)blockIdx.x >= c) return;
+  T* A = AT + (int64_t)rlist[blockIdx.x] * n * n;
+  if (bsg[blockIdx.x] == 0.0) {
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) A[e] = T(0);
+    return;
+  }
+  inverse_panel_block<LT, LT, T>(n, batch + (int64_t)blockIdx.x * n * n, piv + (int64_t)blockIdx.x * n, A, ri_smem);
+}
+
 inline size_t inverse_panel_smem(int n, size_t lsz) { return (size_t)n * 33 * lsz + 2 * (size_t)n * sizeof(int); }
 
 
@@ -909,21 +1048,55 @@ __device__ void lu_block(int n, LT* __restrict__ A, int32_t* __restrict__ pv, do
 // srat = sign(det Phi') * lsign.  xflag[pair] = 1 marks them for a
 // refactorisation if the move is accepted.  A persistent grid; CTA b uses
 // slot b of the float64 scratch; dynamic shared memory n ints.
+//
+// Also recomputed exactly (and refactorised if accepted): every determinant
+// whose Woodbury-carried inverse cannot be trusted to the tolerance ktol,
+// i.e. kappa_d u w_d > ktol, with kappa_d the Frobenius condition estimate of
+// the last factorisation (kap), u the unit roundoff of the state (kunit) and
+// w_d = |det Phi_d| / max_q |det Phi_q| the determinant's weight in the
+// walker's sum.  A float32 inverse of a matrix with kappa ~ 1e6 carries
+// relative errors of order kappa u ~ 0.06, which a run of moves accumulates
+// into the carried log-determinant; weighted by w_d that is the error it
+// brings into log|Psi| and the acceptance ratio.  ktol < 0 turns the test off.
 template <typename T, typename LT>
 __global__ void __launch_bounds__(256) mcmc_exact_ratio_kernel(
     int Wn, int n, int D, int Umax, const int32_t* __restrict__ Ul, const int32_t* __restrict__ Uc,
     const T* __restrict__ Phi, const T* __restrict__ Dl, const double* __restrict__ ldabs,
     const double* __restrict__ lsign, double* __restrict__ lrat, double* __restrict__ srat,
-    int32_t* __restrict__ xflag, LT* __restrict__ scratch, int32_t* __restrict__ spiv) {
+    int32_t* __restrict__ xflag, LT* __restrict__ scratch, int32_t* __restrict__ spiv,
+    const float* __restrict__ kap, double kunit, double ktol, int* __restrict__ xcount,
+    int32_t* __restrict__ xlist, int xcap, unsigned long long* __restrict__ nexact) {
   extern __shared__ int xr_slot[];   // [n]: slot of row i in U, or -1
   __shared__ double s_la, s_sg;
+  __shared__ int s_slot;
   LT* L = scratch + (int64_t)blockIdx.x * n * n;
   int32_t* pv = spiv + (int64_t)blockIdx.x * n;
   for (int64_t md = blockIdx.x; md < (int64_t)Wn * D; md += gridDim.x) {
     const double lr = lrat[md];
-    const bool need = !(fabs(lr) <= kExactLogRatio) && lsign[md] != 0.0;
-    if (threadIdx.x == 0) xflag[md] = need ? 1 : 0;
-    if (!need) continue;
+    const bool range = !(fabs(lr) <= kExactLogRatio) && lsign[md] != 0.0;
+    bool cond = false;
+    if (!range && ktol >= 0.0 && lsign[md] != 0.0) {
+      const int64_t w0 = (md / D) * D;
+      double lmax = -INFINITY;
+      for (int q = 0; q < D; ++q)
+        if (lsign[w0 + q] != 0.0 && ldabs[w0 + q] > lmax) lmax = ldabs[w0 + q];
+      cond = (double)kap[md] * kunit * exp(ldabs[md] - lmax) > ktol;
+    }
+    // 1: ratio out of range (the inverse is refactorised if accepted);
+    // 2: conditioning (exact ratio; the Woodbury update keeps A until the
+    // next refresh, the ratio does not use it while the test holds)
+    if (threadIdx.x == 0) xflag[md] = range ? 1 : (cond ? 2 : 0);
+    if (!range && !cond) continue;
+    if (threadIdx.x == 0 && nexact) atomicAdd(nexact, 1ull);
+    if (cond && xlist) {   // deferred to the batched float64 LU when it has room
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        s_slot = atomicAdd(xcount, 1);
+        if (s_slot < xcap) xlist[s_slot] = (int32_t)md;
+      }
+      __syncthreads();
+      if (s_slot < xcap) continue;
+    }
     const int w = (int)(md / D);
     const int u = Uc[w];
     for (int i = threadIdx.x; i < n; i += blockDim.x) xr_slot[i] = -1;
@@ -946,6 +1119,76 @@ __global__ void __launch_bounds__(256) mcmc_exact_ratio_kernel(
   }
 }
 
+// Phi' = Phi with the rows U replaced, in float64, for the pairs deferred to
+// the batched LU (xlist[0 .. *count)), one CTA each; CTAs beyond the count
+// leave.  Dynamic shared memory n ints.
+template <typename T, typename LT>
+__global__ void __launch_bounds__(256) mcmc_exact_build_kernel(int n, int D, int Umax, const int* __restrict__ count,
+                                                               const int32_t* __restrict__ xlist,
+                                                               const int32_t* __restrict__ Ul,
+                                                               const int32_t* __restrict__ Uc,
+                                                               const T* __restrict__ Phi, const T* __restrict__ Dl,
+                                                               LT* __restrict__ batch) {
+  extern __shared__ int xb_slot[];
+  if ((int)blockIdx.x >= *count) return;
+  const int64_t md = xlist[blockIdx.x];
+  const int w = (int)(md / D);
+  const int u = Uc[w];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) xb_slot[i] = -1;
+  __syncthreads();
+  for (int a = threadIdx.x; a < u; a += blockDim.x) xb_slot[Ul[(int64_t)w * Umax + a]] = a;
+  __syncthreads();
+  const T* P = Phi + md * n * n;
+  const T* Dw = Dl + md * Umax * n;
+  LT* L = batch + (int64_t)blockIdx.x * n * n;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int a = xb_slot[e / n];
+    L[e] = (LT)P[e] + (a >= 0 ? (LT)Dw[(int64_t)a * n + e % n] : LT(0));
+  }
+}
+
+// lrat = log|det Phi'| - ldabs, srat = sign(det Phi') lsign for the batch.
+static __global__ void mcmc_exact_scatter_kernel(const int* __restrict__ count, int cap,
+                                                 const int32_t* __restrict__ xlist, const double* __restrict__ blab,
+                                                 const double* __restrict__ bsg, const double* __restrict__ ldabs,
+                                                 const double* __restrict__ lsign, double* __restrict__ lrat,
+                                                 double* __restrict__ srat) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = *count < cap ? *count : cap;
+  if (f >= c) return;
+  const int64_t md = xlist[f];
+  lrat[md] = blab[f] - ldabs[md];
+  srat[md] = bsg[f] * lsign[md];
+}
+
+// Batched refactorisation of the determinants in rlist[0 .. *count) (flag
+// 2): a float64 copy of the cached Phi (already updated by the move) for
+// lu_kernel, then log|det|, sign and the reference log|det| of the new
+// factors, then A^T from them (zero for a singular matrix).  CTAs beyond the
+// count leave.
+template <typename T, typename LT>
+__global__ void __launch_bounds__(256) mcmc_repair_build_kernel(int n, const int* __restrict__ count,
+                                                                const int32_t* __restrict__ rlist,
+                                                                const T* __restrict__ Phi, LT* __restrict__ batch) {
+  if ((int)blockIdx.x >= *count) return;
+  const T* P = Phi + (int64_t)rlist[blockIdx.x] * n * n;
+  LT* L = batch + (int64_t)blockIdx.x * n * n;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) L[e] = (LT)P[e];
+}
+
+static __global__ void mcmc_repair_scatter_kernel(const int* __restrict__ count, int cap,
+                                                  const int32_t* __restrict__ rlist, const double* __restrict__ blab,
+                                                  const double* __restrict__ bsg, double* __restrict__ ldabs,
+                                                  double* __restrict__ lsign, double* __restrict__ lref) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = *count < cap ? *count : cap;
+  if (f >= c) return;
+  const int64_t md = rlist[f];
+  ldabs[md] = blab[f];
+  lsign[md] = bsg[f];
+  lref[md] = blab[f];
+}
+
 // Refactorisation of the flagged (walker, det) pairs of accepted walkers
 // from the cached Phi (already updated by the move): log|det|, sign and A^T.
 // A persistent grid; CTA b uses slot b of the float64 scratch (n x n matrix,
@@ -962,7 +1205,7 @@ __global__ void __launch_bounds__(256) mcmc_repair_kernel(int Wn, int n, int D, 
   LT* L = scratch + (int64_t)blockIdx.x * n * n;
   int32_t* pv = spiv + (int64_t)blockIdx.x * n;
   for (int64_t md = blockIdx.x; md < (int64_t)Wn * D; md += gridDim.x) {
-    if (!acc[md / D] || !flag[md]) continue;
+    if (!acc[md / D] || flag[md] != 1) continue;
     const T* P = Phi + md * n * n;
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) L[e] = (LT)P[e];
     __syncthreads();
@@ -983,6 +1226,38 @@ __global__ void __launch_bounds__(256) mcmc_repair_kernel(int Wn, int n, int D, 
   }
 }
 
+
+// Frobenius condition estimate kappa_F = ||Phi||_F ||Phi^-1||_F (between
+// kappa_2 and n kappa_2) of every (walker, det) after a factorisation; 0 for
+// a singular determinant (its A^T is zero).  One CTA per matrix.
+template <typename T>
+__global__ void __launch_bounds__(256) mcmc_kappa_kernel(int n, const T* __restrict__ Phi, const T* __restrict__ AT,
+                                                         float* __restrict__ kap) {
+  __shared__ double red[2][8];
+  const int64_t md = blockIdx.x;
+  const T* P = Phi + md * n * n;
+  const T* A = AT + md * n * n;
+  double sp = 0.0, sa = 0.0;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const double x = (double)P[e], y = (double)A[e];
+    sp += x * x;
+    sa += y * y;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sp += __shfl_xor_sync(0xffffffffu, sp, o);
+    sa += __shfl_xor_sync(0xffffffffu, sa, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = sp;
+    red[1][threadIdx.x >> 5] = sa;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { a += red[0][q]; b += red[1][q]; }
+    kap[md] = (float)sqrt(a * b);
+  }
+}
 
 // drift = max_w |lp_inc - lp_fresh| (the bits of a non-negative double order
 // like the values), wdrift[w] = the walker's largest drift so far; then

@@ -13,6 +13,8 @@
 #include "gemm.cuh"
 #include "jastrow.cuh"
 #include "mcmc.cuh"
+#include "ecp.cuh"
+#include "swap.cuh"
 #include "nbr.cuh"
 #include "plan.h"
 #include "tc_api.h"
@@ -48,6 +50,17 @@ struct McmcCall {
   int32_t* acc_count;        // device [W] accepted moves per walker, or null
   int64_t n_accepted;        // out
   double max_drift;          // out
+  int n_global;              // global jumps per sweep (after the n local moves)
+  double sigma_global;       // width of the mixture components of a global jump
+  double kappa_tol;          // exact-ratio test kappa u w > kappa_tol (< 0: off)
+  // non-local pseudopotential evaluation instead of sweeps (ecp != null)
+  const fire_ecp_t* ecp;     // device [n_nuc] table
+  int ecp_qmax;              // largest N_quad of the table
+  double* v_nl;              // device [W] out
+  // S+ swap ratios instead of sweeps (swap_beta >= 0)
+  int swap_beta;             // the spin-down electron
+  double* swap_ratios;       // device [W][n_up] out
+  double* swap_r;            // device [W] out: 1 - sum of the ratios
 };
 
 struct CallArgs {
@@ -1243,10 +1256,14 @@ struct Runner {
     }
     const int64_t* fullu = rngu + 4;
     const int64_t* rowsW = rngu + 6;
+    float* kap = at<float>(pl.mc_kap);
+    double* lq = at<double>(pl.mc_lq);
     auto refresh = [&](bool measure) -> int {
       int rc = run();
       reset_status = false;
       if (rc != FIRE_OK) return rc;
+      mcmc_kappa_kernel<T><<<(unsigned)((int64_t)Wn * D), 256, 0, s>>>(n, PhiS, AT, kap);
+      launches += 1;
       cudaMemcpyAsync(lref, at<double>(pl.ldabs), sizeof(double) * (size_t)Wn * D, cudaMemcpyDeviceToDevice, s);
       mcmc_drift_kernel<<<(Wn + 255) / 256, 256, 0, s>>>(Wn, lp, lpf, wdrift, &ms->drift_bits, measure ? 1 : 0);
       launches += 1;
@@ -1271,78 +1288,191 @@ struct Runner {
       rowdot_kernel<T, T><<<(unsigned)((cap + 7) / 8), 256, 0, s>>>(Yb, J, J, w3, F, rng, 0, 0);
       launches += 5;
     };
+    // unit roundoff of the state, for the conditioning test of the exact ratios
+    const double kunit = sizeof(T) == 4 ? 5.9604644775390625e-8 : 1.1102230246251565e-16;
+    // The recompute of one move of electron k to rk (update sets built): h^0,
+    // projections and envelope row of k, h^1 and h of the update set, Jastrow
+    // rows, attention registers, orbital rows and the determinant ratios.
+    auto embed_and_msg = [&](int k) {
+      mcmc_scan_kernel<<<1, 1024, 0, s>>>(Wn, Umax, Uc, Ucu, Urow, rngu);
+      // h^0, its projections and the envelope row of electron k at r'_k
+      // (the proposals form a one-electron batch of Wn walkers)
+      const int nup1 = k < n_up ? 1 : 0;
+      mark("mc_embed_k", 9);
+      en_filter_kernel<T, T><<<Wn, d, 0, s>>>(Wn, 1, nup1, N, d, rk, sys->nuc_pos, sys->cutoff_nuc, p, S5, 1);
+      ln_fl_kernel<T, T><<<Wn, d, 0, s>>>(d, S5, Y5, p.ln_gamma, p.ln_beta, 1);
+      gemm<T>(s, Y5, d, p.glu_wg, d, false, Z5, 2 * d, 0, Wn, nullptr, Wn, d, d);
+      gemm<T>(s, Y5, d, p.glu_wv, d, false, Z5 + d, 2 * d, 0, Wn, nullptr, Wn, d, d);
+      glu_gate_kernel<T><<<Wn, d, 0, s>>>(d, Z5, P5, 1);
+      gemm<T>(s, P5, d, p.glu_wo, d, false, h0k, d, 0, Wn, nullptr, Wn, d, d);
+      for (int part = 0; part < 2; ++part)
+        gemm<T>(s, h0k, d, p.msg_w + (int64_t)part * d * d, d, false, PQk + (int64_t)part * 2 * d, 4 * d, 0, Wn,
+                nullptr, Wn, d, d, 2, 0, (int64_t)(2 * d + 4) * d, d);
+      env_feat_kernel<T, T><<<Wn, 128, 0, s>>>(Wn, 1, nup1, N, E, rk, sys->nuc_pos, p.env_sigma, Qk, 1);
+      gemm<T>(s, Qk, NE, p.env_pi + (int64_t)(k < n_up ? 0 : 1) * Dn * NE, NE, true, Fk, Dn, 0, Wn, nullptr, Wn,
+              (int)Dn, NE);
+      check("mc embed k");
+      // h^1 and h of the members of U (compact rows)
+      mark("mc_msg", 1);
+      mcmc_msg_kernel<T, T><<<(unsigned)capU, d, msm, s>>>(Wn, n, n_up, d, k, Umax, r, rk, c, p, Ul, Uc, Urow, H0,
+                                                           PQ, H1, h0k, PQk, X1, H1n);
+      check("mc msg");
+    };
+    // MLP, Jastrow and attention rows of the update set, its orbital rows
+    // and the determinant ratios (k2 >= 0: a second moved electron whose
+    // envelope row is Fk2)
+    auto rows_and_ratio = [&](int k, int k2, const T* Fk2) {
+      mark("mc_mlp", 2 * dm.L);
+      for (int l = 0; l < dm.L; ++l) {
+        gemm<T>(s, X1, d, p.mlp_w + (int64_t)l * d * d, d, false, Zm, ldz, 0, 0, fullu, capU, d, d);
+        mcmc_act_kernel<T, T><<<actg, 256, 0, s>>>(fullu, d, Zm, ldz, p.mlp_b + (int64_t)l * d, X1, d, 1);
+      }
+      if (dm.flags & FIRE_J_MLP) {
+        mark("mc_jastrow", 0);
+        readout(X1, d, fullu, capU, p.jm1_w1, p.jm1_b1, p.jm1_w2, p.jm1_b2, p.jm1_w3, Zm, ldz, Ym, F1n);
+        readout(X1, d, fullu, capU, p.jm2_w1, p.jm2_b1, p.jm2_w2, p.jm2_b2, p.jm2_w3, Zm, ldz, Ym, F2n);
+      }
+      if (dm.flags & FIRE_J_ATT) {
+        mark("mc_att", 3);
+        gemm<T>(s, X1, d, p.att_q, d, true, SUn, RD1, 0, 0, fullu, capU, R, d);
+        gemm<T>(s, X1, d, p.att_wv, dr, false, SUn + R, RD1, 0, 0, fullu, capU, dr, d, R, 0, (int64_t)d * dr, dr);
+        mcmc_att_kernel<T><<<Wn, abt, asm_, s>>>(Wn, n, n_up, R, dr, Umax, Ul, Uc, Urow, SU, pl.ld_big, SUn, RD1,
+                                                  Vn);
+        readout(Vn, RD, rowsW, Wn, p.ja1_w1, p.ja1_b1, p.ja1_w2, p.ja1_b2, p.ja1_w3, VZ, J, VY, G1n);
+        readout(Vn, RD, rowsW, Wn, p.ja2_w1, p.ja2_b1, p.ja2_w2, p.ja2_b2, p.ja2_w3, VZ, J, VY, G2n);
+      }
+      // orbital rows of U, spin-up rows with the up-spin weights
+      mark("mc_orb", 2);
+      for (int sp = 0; sp < 2; ++sp)
+        gemm<T>(s, X1, d, p.orb_w + (int64_t)sp * D * d * n, n, false, On, Dn, 0, 0, rngu + 2 * sp, capU, n, d, D,
+                0, (int64_t)d * n, n);
+      check("mc orbitals");
+      mark("mc_ratio", 1);
+      mcmc_ratio_kernel<T><<<(unsigned)(Wn * D), 256, 0, s>>>(Wn, n, n_up, D, k, Umax, Ul, Uc, Urow, On, Fenv, Fk,
+                                                             PhiS, AT, Dl, Mt, Mlu, Mpiv, lrat, srat, k2,
+                                                             Fk2);
+      {
+        const int64_t npair = (int64_t)Wn * D;
+        int* xcnt = at<int>(pl.mc_xcnt);
+        int32_t* xlist = at<int32_t>(pl.mc_xlist);
+        const bool batched = mc.kappa_tol >= 0.0;
+        if (batched) cudaMemsetAsync(xcnt, 0, sizeof(int), s);
+        mcmc_exact_ratio_kernel<T, LT><<<(unsigned)(npair < kWoodburySlots ? npair : kWoodburySlots), 256,
+                                         (size_t)n * sizeof(int), s>>>(
+            Wn, n, D, Umax, Ul, Uc, PhiS, Dl, ldabs, lsign, lrat, srat, xflag, at<LT>(pl.mc_rep),
+            at<int32_t>(pl.mc_rpiv), kap, kunit, mc.kappa_tol, xcnt, batched ? xlist : nullptr, pl.xcap,
+            &ms->n_exact);
+        launches += 1;
+        if (batched) {
+          // ill-conditioned determinants: float64 LU of Phi' over all SMs
+          LT* xb = at<LT>(pl.mc_xbatch);
+          double* xlab = at<double>(pl.mc_xlab);
+          double* xsg = at<double>(pl.mc_xsg);
+          mcmc_exact_build_kernel<T, LT><<<pl.xcap, 256, (size_t)n * sizeof(int), s>>>(n, D, Umax, xcnt, xlist, Ul, Uc,
+                                                                                       PhiS, Dl, xb);
+          lu_kernel<LT, 16><<<pl.xcap, 256, lu_smem_bytes(n, sizeof(LT)), s>>>(n, xb, at<int32_t>(pl.mc_xpiv), xlab,
+                                                                               xsg, xcnt);
+          mcmc_exact_scatter_kernel<<<(pl.xcap + 255) / 256, 256, 0, s>>>(xcnt, pl.xcap, xlist, xlab, xsg, ldabs,
+                                                                         lsign, lrat, srat);
+          launches += 3;
+        }
+      }
+      check("mc ratio");
+    };
+    auto evaluate_move = [&](int k) {
+      embed_and_msg(k);
+      rows_and_ratio(k, -1, nullptr);
+    };
+    if (mc.swap_beta >= 0) {
+      // S+ ratios: n_up swaps of the spin-down electron beta with every
+      // spin-up electron, from the state just built; nothing is accepted
+      const int b = mc.swap_beta;
+      double* rk2 = at<double>(pl.mc_rk2);
+      T* Fk2 = at<T>(pl.mc_Fk2);
+      for (int a2 = 0; a2 < n_up; ++a2) {
+        mark("swap_propose", 2);
+        swap_propose_kernel<<<Wn, 32, 0, s>>>(n, n_up, a2, b, r, c * c, Umax, rk, rk2, Ul, Uc, Ucu, st);
+        mcmc_scan_kernel<<<1, 1024, 0, s>>>(Wn, Umax, Uc, Ucu, Urow, rngu);
+        // envelope rows of both electrons at their new positions, each with
+        // its own spin's weights
+        mark("swap_env", 4);
+        env_feat_kernel<T, T><<<Wn, 128, 0, s>>>(Wn, 1, 1, N, E, rk, sys->nuc_pos, p.env_sigma, Qk, 1);
+        gemm<T>(s, Qk, NE, p.env_pi, NE, true, Fk, Dn, 0, Wn, nullptr, Wn, (int)Dn, NE);
+        env_feat_kernel<T, T><<<Wn, 128, 0, s>>>(Wn, 1, 1, N, E, rk2, sys->nuc_pos, p.env_sigma, Qk, 1);
+        gemm<T>(s, Qk, NE, p.env_pi + Dn * NE, NE, true, Fk2, Dn, 0, Wn, nullptr, Wn, (int)Dn, NE);
+        mark("swap_msg", 1);
+        swap_msg_kernel<T, T><<<(unsigned)capU, d, msm, s>>>(Wn, n, n_up, d, a2, b, Umax, r, c, p, Ul, Uc, Urow, H0,
+                                                             PQ, H1, X1, H1n);
+        check("swap msg");
+        rows_and_ratio(a2, b, Fk2);
+        mark("swap_accum", 1);
+        swap_accum_kernel<T><<<Wn, 32, 0, s>>>(Wn, n, n_up, D, a2, b, Umax, dm.flags, r, rk, rk2, Ul, Uc, Urow, jp,
+                                               F1, F2, F1n, F2n, G1, G2, G1n, G2n, ldabs, lsign, lrat, srat,
+                                               mc.swap_ratios);
+        check("swap");
+      }
+      swap_sum_kernel<<<(Wn + 255) / 256, 256, 0, s>>>(Wn, n_up, mc.swap_ratios, mc.swap_r);
+      if (cudaMemcpyAsync(a.host_status, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return FIRE_ERR_CUDA;
+      if (cudaStreamSynchronize(s) != cudaSuccess) return FIRE_ERR_CUDA;
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) { set_last_error("swap", cudaGetErrorString(e)); return FIRE_ERR_CUDA; }
+      if (a.n_launches) *a.n_launches = launches;
+      return failed ? FIRE_ERR_CUDA : FIRE_OK;
+    }
+    if (mc.ecp) {
+      // non-local pseudopotential: n_el x N_quad virtual single-electron
+      // moves from the state just built; no move is accepted
+      if (cudaMemsetAsync(mc.v_nl, 0, sizeof(double) * (size_t)Wn, s) != cudaSuccess) return FIRE_ERR_CUDA;
+      for (int k = 0; k < n; ++k)
+        for (int q = 0; q < mc.ecp_qmax; ++q) {
+          mark("ecp_propose", 2);
+          ecp_propose_kernel<<<Wn, 32, 0, s>>>(n, n_up, k, q, r, sys->nuc_pos, N, mc.ecp, mc.seed, c * c, Umax, rk,
+                                               lq, Ul, Uc, Ucu, st);
+          evaluate_move(k);
+          mark("ecp_accum", 1);
+          ecp_accum_kernel<T><<<Wn, 32, 0, s>>>(Wn, n, n_up, D, k, Umax, dm.flags, r, rk, lq, Ul, Uc, Urow, jp, F1, F2,
+                                                F1n, F2n, G1, G2, G1n, G2n, ldabs, lsign, lrat, srat, mc.v_nl);
+          check("ecp");
+        }
+      if (cudaMemcpyAsync(a.host_status, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return FIRE_ERR_CUDA;
+      if (cudaStreamSynchronize(s) != cudaSuccess) return FIRE_ERR_CUDA;
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) { set_last_error("ecp", cudaGetErrorString(e)); return FIRE_ERR_CUDA; }
+      if (a.n_launches) *a.n_launches = launches;
+      return failed ? FIRE_ERR_CUDA : FIRE_OK;
+    }
     int64_t moves = 0;
-    const int64_t total_moves = (int64_t)mc.n_sweeps * n;
+    const int per_sweep = n + mc.n_global;
+    const int64_t total_moves = (int64_t)mc.n_sweeps * per_sweep;
     for (int sweep = 0; sweep < mc.n_sweeps; ++sweep) {
-      for (int k = 0; k < n; ++k) {
-        const uint64_t move = mc.counter + (uint64_t)sweep * n + k;
+      for (int j = 0; j < per_sweep; ++j) {
+        const uint64_t move = mc.counter + (uint64_t)sweep * per_sweep + j;
+        // local moves k = 0 .. n-1, then global jumps of an electron drawn
+        // (for all walkers alike) from word 0 of Philox counter
+        // (move, 2^32 - 1, 2)
+        const bool global = j >= n;
+        int k = j;
+        if (global) {
+          const Philox4 c = philox4x32_10((uint32_t)move, (uint32_t)(move >> 32), 0xffffffffu, 2u,
+                                          (uint32_t)mc.seed, (uint32_t)(mc.seed >> 32));
+          k = (int)floor(u01(c.v[0]) * n);
+          if (k > n - 1) k = n - 1;
+        }
         mark("mc_propose", 2);
         mcmc_propose_kernel<<<Wn, 32, 0, s>>>(n, n_up, k, r, mc.sigma, mc.seed, move, 0, c * c, Umax, rk, uacc, Ul,
-                                              Uc, Ucu, st);
-        mcmc_scan_kernel<<<1, 1024, 0, s>>>(Wn, Umax, Uc, Ucu, Urow, rngu);
-        // h^0, its projections and the envelope row of electron k at r'_k
-        // (the proposals form a one-electron batch of Wn walkers)
-        const int nup1 = k < n_up ? 1 : 0;
-        mark("mc_embed_k", 9);
-        en_filter_kernel<T, T><<<Wn, d, 0, s>>>(Wn, 1, nup1, N, d, rk, sys->nuc_pos, sys->cutoff_nuc, p, S5, 1);
-        ln_fl_kernel<T, T><<<Wn, d, 0, s>>>(d, S5, Y5, p.ln_gamma, p.ln_beta, 1);
-        gemm<T>(s, Y5, d, p.glu_wg, d, false, Z5, 2 * d, 0, Wn, nullptr, Wn, d, d);
-        gemm<T>(s, Y5, d, p.glu_wv, d, false, Z5 + d, 2 * d, 0, Wn, nullptr, Wn, d, d);
-        glu_gate_kernel<T><<<Wn, d, 0, s>>>(d, Z5, P5, 1);
-        gemm<T>(s, P5, d, p.glu_wo, d, false, h0k, d, 0, Wn, nullptr, Wn, d, d);
-        for (int part = 0; part < 2; ++part)
-          gemm<T>(s, h0k, d, p.msg_w + (int64_t)part * d * d, d, false, PQk + (int64_t)part * 2 * d, 4 * d, 0, Wn,
-                  nullptr, Wn, d, d, 2, 0, (int64_t)(2 * d + 4) * d, d);
-        env_feat_kernel<T, T><<<Wn, 128, 0, s>>>(Wn, 1, nup1, N, E, rk, sys->nuc_pos, p.env_sigma, Qk, 1);
-        gemm<T>(s, Qk, NE, p.env_pi + (int64_t)(k < n_up ? 0 : 1) * Dn * NE, NE, true, Fk, Dn, 0, Wn, nullptr, Wn,
-                (int)Dn, NE);
-        check("mc embed k");
-        // h^1 and h of the members of U (compact rows)
-        mark("mc_msg", 1);
-        mcmc_msg_kernel<T, T><<<(unsigned)capU, d, msm, s>>>(Wn, n, n_up, d, k, Umax, r, rk, c, p, Ul, Uc, Urow, H0,
-                                                             PQ, H1, h0k, PQk, X1, H1n);
-        check("mc msg");
-        mark("mc_mlp", 2 * dm.L);
-        for (int l = 0; l < dm.L; ++l) {
-          gemm<T>(s, X1, d, p.mlp_w + (int64_t)l * d * d, d, false, Zm, ldz, 0, 0, fullu, capU, d, d);
-          mcmc_act_kernel<T, T><<<actg, 256, 0, s>>>(fullu, d, Zm, ldz, p.mlp_b + (int64_t)l * d, X1, d, 1);
-        }
-        if (dm.flags & FIRE_J_MLP) {
-          mark("mc_jastrow", 0);
-          readout(X1, d, fullu, capU, p.jm1_w1, p.jm1_b1, p.jm1_w2, p.jm1_b2, p.jm1_w3, Zm, ldz, Ym, F1n);
-          readout(X1, d, fullu, capU, p.jm2_w1, p.jm2_b1, p.jm2_w2, p.jm2_b2, p.jm2_w3, Zm, ldz, Ym, F2n);
-        }
-        if (dm.flags & FIRE_J_ATT) {
-          mark("mc_att", 3);
-          gemm<T>(s, X1, d, p.att_q, d, true, SUn, RD1, 0, 0, fullu, capU, R, d);
-          gemm<T>(s, X1, d, p.att_wv, dr, false, SUn + R, RD1, 0, 0, fullu, capU, dr, d, R, 0, (int64_t)d * dr, dr);
-          mcmc_att_kernel<T><<<Wn, abt, asm_, s>>>(Wn, n, n_up, R, dr, Umax, Ul, Uc, Urow, SU, pl.ld_big, SUn, RD1,
-                                                    Vn);
-          readout(Vn, RD, rowsW, Wn, p.ja1_w1, p.ja1_b1, p.ja1_w2, p.ja1_b2, p.ja1_w3, VZ, J, VY, G1n);
-          readout(Vn, RD, rowsW, Wn, p.ja2_w1, p.ja2_b1, p.ja2_w2, p.ja2_b2, p.ja2_w3, VZ, J, VY, G2n);
-        }
-        // orbital rows of U, spin-up rows with the up-spin weights
-        mark("mc_orb", 2);
-        for (int sp = 0; sp < 2; ++sp)
-          gemm<T>(s, X1, d, p.orb_w + (int64_t)sp * D * d * n, n, false, On, Dn, 0, 0, rngu + 2 * sp, capU, n, d, D,
-                  0, (int64_t)d * n, n);
-        check("mc orbitals");
-        mark("mc_ratio", 1);
-        mcmc_ratio_kernel<T><<<(unsigned)(Wn * D), 256, 0, s>>>(Wn, n, n_up, D, k, Umax, Ul, Uc, Urow, On, Fenv, Fk,
-                                                               PhiS, AT, Dl, Mt, Mlu, Mpiv, lrat, srat);
-        {
-          const int64_t npair = (int64_t)Wn * D;
-          mcmc_exact_ratio_kernel<T, LT><<<(unsigned)(npair < kWoodburySlots ? npair : kWoodburySlots), 256,
-                                           (size_t)n * sizeof(int), s>>>(
-              Wn, n, D, Umax, Ul, Uc, PhiS, Dl, ldabs, lsign, lrat, srat, xflag, at<LT>(pl.mc_rep),
-              at<int32_t>(pl.mc_rpiv));
-          launches += 1;
-        }
-        check("mc ratio");
+                                              Uc, Ucu, st, global ? 1 : 0, sys->nuc_pos, sys->nuc_charge, N,
+                                              mc.sigma_global, lq);
+        evaluate_move(k);
         mark("mc_accept", 2);
+        int* rcnt = at<int>(pl.mc_xcnt);
+        int32_t* rlist = at<int32_t>(pl.mc_xlist);
+        cudaMemsetAsync(rcnt, 0, sizeof(int), s);
         mcmc_accept_kernel<T><<<Wn, 32, 0, s>>>(Wn, n, n_up, D, k, Umax, dm.flags, r, rk, uacc, Ul, Uc, Urow, jp, F1,
                                                 F2, F1n, F2n, G1, G2, G1n, G2n, ldabs, lsign, lrat, srat, lp, acc,
-                                                mc.acc_count, &ms->n_accepted, lref, flag, xflag);
+                                                mc.acc_count, &ms->n_accepted, lref, flag, xflag, lq, rcnt, rlist,
+                                                pl.xcap, &ms->n_repair);
         mcmc_rows_kernel<T><<<(unsigned)capU, 128, 0, s>>>(
             Wn, n, n_up, d, (int)Dn, RD, k, Umax, pl.ld_big, RD1, (dm.flags & FIRE_J_MLP) ? 1 : 0,
             (dm.flags & FIRE_J_ATT) ? 1 : 0, acc, Ul, Uc, Urow, F1n, F2n, F1, F2, SUn, SU, h0k, H0, PQk, PQ, Fk,
@@ -1354,7 +1484,21 @@ struct Runner {
         mcmc_repair_kernel<T, LT><<<(unsigned)(npair < kWoodburySlots ? npair : kWoodburySlots), 256,
                                     inverse_panel_smem(n, sizeof(LT)), s>>>(
             Wn, n, D, acc, flag, PhiS, AT, ldabs, lsign, lref, at<LT>(pl.mc_rep), at<int32_t>(pl.mc_rpiv));
-        launches += 1;
+        {
+          // the listed refactorisations, batched over all SMs: float64 LU of
+          // the updated Phi, then the inverse from the factors
+          LT* xb = at<LT>(pl.mc_xbatch);
+          int32_t* xpiv = at<int32_t>(pl.mc_xpiv);
+          double* xlab = at<double>(pl.mc_xlab);
+          double* xsg = at<double>(pl.mc_xsg);
+          mcmc_repair_build_kernel<T, LT><<<pl.xcap, 256, 0, s>>>(n, rcnt, rlist, PhiS, xb);
+          lu_kernel<LT, 16><<<pl.xcap, 256, lu_smem_bytes(n, sizeof(LT)), s>>>(n, xb, xpiv, xlab, xsg, rcnt);
+          mcmc_repair_scatter_kernel<<<(pl.xcap + 255) / 256, 256, 0, s>>>(rcnt, pl.xcap, rlist, xlab, xsg, ldabs,
+                                                                          lsign, lref);
+          mcmc_repair_inverse_kernel<LT, T><<<pl.xcap, 256, inverse_panel_smem(n, sizeof(LT)), s>>>(
+              n, rcnt, pl.xcap, rlist, xb, xpiv, xsg, AT);
+        }
+        launches += 5;
         check("mc update");
         ++moves;
         if (mc.refresh_every > 0 && moves % mc.refresh_every == 0 && moves < total_moves) {
@@ -1426,6 +1570,7 @@ inline int set_smem_limits() {
   raise((const void*)inverse_panel_kernel<LT, LT, T>);
   raise((const void*)inverse_panel_kernel<LT, T, T>);
   raise((const void*)mcmc_repair_kernel<T, LT>);
+  raise((const void*)mcmc_repair_inverse_kernel<LT, T>);
   cudaError_t e = cudaGetLastError();
   if (rc != FIRE_OK || e != cudaSuccess) set_last_error("smem limits", cudaGetErrorString(e));
   return rc;

@@ -47,7 +47,10 @@ struct Plan {
   size_t PhiS, mc_rk, mc_u, mc_Ul, mc_Uc, mc_Ucu, mc_Urow, mc_rng, mc_h0k, mc_PQk, mc_Qk, mc_Fk;
   size_t mc_X, mc_Z, mc_Y, mc_F1n, mc_F2n, mc_SUn, mc_On, mc_Vn, mc_VZ, mc_VY, mc_G1n, mc_G2n;
   size_t mc_Dl, mc_Mt, mc_Mlu, mc_piv, mc_lrat, mc_srat, mc_acc, mc_Tu, mc_Bw, mc_lp, mc_lpf, mc_sgf, mc_stat;
-  size_t mc_H1, mc_H1n, mc_wdrift, mc_lref, mc_flag, mc_xflag, mc_rep, mc_rpiv;
+  size_t mc_H1, mc_H1n, mc_wdrift, mc_lref, mc_flag, mc_xflag, mc_rep, mc_rpiv, mc_kap, mc_lq, mc_ecp;
+  size_t mc_xcnt, mc_xlist, mc_xbatch, mc_xpiv, mc_xlab, mc_xsg;   // batched exact ratios
+  int xcap;
+  size_t mc_rk2, mc_Fk2;    // the second electron of a swap
   int64_t nparams;
   size_t total;
   // column layout of `big`
@@ -68,6 +71,8 @@ constexpr int kWoodburySlots = 152 * 4;
 struct McmcStat {
   unsigned long long n_accepted;
   unsigned long long drift_bits;   // bits of the largest |log|Psi| drift| (a non-negative double)
+  unsigned long long n_exact;      // determinant ratios from a float64 LU (diagnostic)
+  unsigned long long n_repair;     // determinants refactorised after an accepted move (diagnostic)
 };
 
 int make_plan(const fire_system_t* sys, const fire_arch_t* arch, int64_t W, int prec, int k_cap,

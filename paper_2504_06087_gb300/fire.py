@@ -67,6 +67,31 @@ class ProfEntry(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int64), ("ms_total", ctypes.c_double)]
 
 
+class Ecp(ctypes.Structure):
+    _fields_ = [("n_quad", ctypes.c_int32), ("n_channels", ctypes.c_int32), ("n_terms", ctypes.c_int32 * 3),
+                ("pad_", ctypes.c_int32), ("r_cut", ctypes.c_double), ("coef", (ctypes.c_double * 4) * 3),
+                ("power", (ctypes.c_double * 4) * 3), ("alpha", (ctypes.c_double * 4) * 3)]
+
+
+def ecp_table(entries):
+    """fire_ecp_t array from per-nucleus entries: None (no pseudopotential) or
+    {"n_quad": 4|6|12, "r_cut": x, "terms": [[(coef, power, alpha), ...] per channel l]}."""
+    arr = (Ecp * len(entries))()
+    for m, e in enumerate(entries):
+        if e is None:
+            continue
+        arr[m].n_quad = int(e["n_quad"])
+        arr[m].r_cut = float(e["r_cut"])
+        arr[m].n_channels = len(e["terms"])
+        for l, terms in enumerate(e["terms"]):
+            arr[m].n_terms[l] = len(terms)
+            for j, (c, pw, a) in enumerate(terms):
+                arr[m].coef[l][j] = float(c)
+                arr[m].power[l][j] = float(pw)
+                arr[m].alpha[l][j] = float(a)
+    return arr
+
+
 class Info(ctypes.Structure):
     _fields_ = [("k_required", ctypes.c_int32), ("n_nodes", ctypes.c_int32), ("n_nonfinite", ctypes.c_int32),
                 ("n_chunks", ctypes.c_int32), ("rows_total", ctypes.c_int64), ("mean_neighbors", ctypes.c_double),
@@ -97,6 +122,13 @@ SIGNATURES = {
     "fire_selftest_tc_gemm": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, VP, VP,
                                              VP, VP, VP]),
     "fire_selftest_fma_rate": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, VP, VP]),
+    "fire_spring_workspace_size": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64]),
+    "fire_spring_step": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, VP, ctypes.c_int64, VP, VP, ctypes.c_double,
+                                        ctypes.c_double, VP, VP, VP, VP, ctypes.c_size_t, VP]),
+    "fire_ecp_nonlocal": (ctypes.c_int, [P(System), P(Arch), P(Params), ctypes.c_int64, VP, ctypes.c_int32,
+                                         ctypes.c_int32, P(Ecp), ctypes.c_uint64, VP, P(Info), VP, ctypes.c_size_t, VP]),
+    "fire_spin_ratios": (ctypes.c_int, [P(System), P(Arch), P(Params), ctypes.c_int64, VP, ctypes.c_int32,
+                                        ctypes.c_int32, ctypes.c_int32, VP, VP, P(Info), VP, ctypes.c_size_t, VP]),
     "fire_neighbors": (ctypes.c_int, [P(System), ctypes.c_int64, VP, ctypes.c_int32, VP, VP,
                                       P(ctypes.c_int32), VP, ctypes.c_size_t, VP]),
     "fire_logpsi": (ctypes.c_int, [P(System), P(Arch), P(Params), ctypes.c_int64, VP, ctypes.c_int32,
@@ -109,6 +141,7 @@ SIGNATURES = {
                                                 ctypes.c_int32, ctypes.c_int32, VP, VP, VP, VP, VP, P(Info), VP]),
     "fire_mcmc_step": (ctypes.c_int, [P(System), P(Arch), P(Params), ctypes.c_int64, VP, ctypes.c_int32,
                                       ctypes.c_int32, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_int32, ctypes.c_double,
                                       ctypes.c_uint64, P(ctypes.c_uint64), VP, VP, VP, P(ctypes.c_int64),
                                       P(ctypes.c_double), P(Info), VP, ctypes.c_size_t, VP]),
 }
@@ -188,6 +221,33 @@ def fma_probe(dtype: torch.dtype, iters: int, blocks: int, device="cuda") -> int
         raise FireError(rc, "fire_selftest_fma_rate")
     rounds = (iters + 3) // 4
     return 2 * 8 * 4 * rounds * blocks * 256
+
+
+def spring_step(O: torch.Tensor, e_loc: torch.Tensor, delta_prev: Optional[torch.Tensor] = None,
+                eta: float = 0.99, lam: float = 1e-3, want_gram: bool = False, want_x: bool = False,
+                check: bool = True):
+    """fire_spring_step on device tensors: O [N, P] float32 (row stride may
+    exceed P), e_loc [N] float64, delta_prev [P] float32 or None.  Returns
+    {"delta" [P] float32, "gram" [N, N] float64 or None, "x" [N] float64 or
+    None, "status"}."""
+    assert O.dtype == torch.float32 and O.dim() == 2 and O.stride(1) == 1
+    N, Pn = O.shape
+    dev = O.device
+    e = e_loc.to(device=dev, dtype=torch.float64).contiguous()
+    dp = None if delta_prev is None else delta_prev.to(device=dev, dtype=torch.float32).contiguous()
+    delta = torch.empty(Pn, dtype=torch.float32, device=dev)
+    gram = torch.empty((N, N), dtype=torch.float64, device=dev) if want_gram else None
+    x = torch.empty(N, dtype=torch.float64, device=dev) if want_x else None
+    nbytes = int(lib().fire_spring_workspace_size(N, Pn))
+    if nbytes == 0:
+        raise FireError(1, "fire_spring_workspace_size")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    rc = lib().fire_spring_step(N, Pn, _ptr(O), O.stride(0), _ptr(e), _ptr(dp), float(eta), float(lam), _ptr(delta),
+                                _ptr(gram), _ptr(x), _ptr(ws), ws.numel(),
+                                ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream))
+    if check and rc != 0:
+        raise FireError(rc, "fire_spring_step")
+    return {"delta": delta, "gram": gram, "x": x, "status": rc}
 
 
 def _ptr(t: Optional[torch.Tensor]):
@@ -366,9 +426,10 @@ class Fire:
         return out
 
     def mcmc_step(self, r: torch.Tensor, sigma: float, n_sweeps: int, refresh_every: int = 32, seed: int = 0,
-                  counter: int = 0, check: bool = True):
+                  counter: int = 0, check: bool = True, n_global: int = 0, sigma_global: float = 2.0):
         """fire_mcmc_step: n_sweeps Metropolis sweeps of single-electron moves on
-        the device positions r [W, n_el, 3] float64, updated in place.
+        the device positions r [W, n_el, 3] float64, updated in place; each
+        sweep ends with n_global global jumps (mixture width sigma_global).
         Returns {"logabs", "sign", "accepted" [W], "n_accepted", "max_drift",
         "counter" (the advanced move counter), "info", "status"}."""
         assert isinstance(r, torch.Tensor) and r.dtype == torch.float64 and r.is_contiguous()
@@ -383,15 +444,53 @@ class Fire:
         drift = ctypes.c_double(0.0)
         rc = lib().fire_mcmc_step(ctypes.byref(self.sys_c), ctypes.byref(self.arch_c), ctypes.byref(self.params_c),
                                   W, _ptr(r), self.k_cap, self.prec, float(sigma), int(n_sweeps),
-                                  int(refresh_every), ctypes.c_uint64(seed), ctypes.byref(ctr), _ptr(out["logabs"]),
+                                  int(refresh_every), int(n_global), float(sigma_global),
+                                  ctypes.c_uint64(seed), ctypes.byref(ctr), _ptr(out["logabs"]),
                                   _ptr(out["sign"]), _ptr(out["accepted"]), ctypes.byref(nacc),
                                   ctypes.byref(drift), ctypes.byref(info), _ptr(ws), ws.numel(), self._stream())
         out.update({"n_accepted": int(nacc.value), "max_drift": float(drift.value), "counter": int(ctr.value),
                     "info": info.as_dict(), "status": rc})
         # per-walker largest drift of this call (a diagnostic buffer of the workspace)
         out["walker_drift"] = self.ws_view(W, OP_MCMC, "mc_wdrift", torch.float64, (W,)).clone()
+        # diagnostic counters of the call: ratios from a float64 LU, refactorised determinants
+        stat = self.ws_view(W, OP_MCMC, "mc_stat", torch.int64, (4,)).cpu().numpy()
+        out["n_exact"], out["n_repair"] = int(stat[2]), int(stat[3])
         if check and rc != 0:
             raise FireError(rc, "fire_mcmc_step", out["info"])
+        return out
+
+    def ecp_nonlocal(self, r, entries, seed: int = 0, check: bool = True):
+        """fire_ecp_nonlocal: the non-local pseudopotential energy per walker
+        for the per-nucleus table `entries` (see ecp_table)."""
+        r = self._r(r)
+        W = r.shape[0]
+        v = torch.empty(W, dtype=torch.float64, device=self.device)
+        tab = ecp_table(entries)
+        ws = self.workspace(W, OP_MCMC)
+        info = Info()
+        rc = lib().fire_ecp_nonlocal(ctypes.byref(self.sys_c), ctypes.byref(self.arch_c), ctypes.byref(self.params_c),
+                                     W, _ptr(r), self.k_cap, self.prec, tab, ctypes.c_uint64(seed), _ptr(v),
+                                     ctypes.byref(info), _ptr(ws), ws.numel(), self._stream())
+        out = {"v_nl": v, "info": info.as_dict(), "status": rc}
+        if check and rc != 0:
+            raise FireError(rc, "fire_ecp_nonlocal", out["info"])
+        return out
+
+    def spin_ratios(self, r, beta: int, check: bool = True):
+        """fire_spin_ratios: Psi(pi_{alpha beta} r)/Psi(r) for every spin-up
+        alpha ([W, n_up]) and R_beta = 1 - their sum ([W])."""
+        r = self._r(r)
+        W = r.shape[0]
+        ratios = torch.empty((W, self.system.n_up), dtype=torch.float64, device=self.device)
+        rb = torch.empty(W, dtype=torch.float64, device=self.device)
+        ws = self.workspace(W, OP_MCMC)
+        info = Info()
+        rc = lib().fire_spin_ratios(ctypes.byref(self.sys_c), ctypes.byref(self.arch_c), ctypes.byref(self.params_c),
+                                    W, _ptr(r), self.k_cap, self.prec, int(beta), _ptr(ratios), _ptr(rb),
+                                    ctypes.byref(info), _ptr(ws), ws.numel(), self._stream())
+        out = {"ratios": ratios, "r_beta": rb, "info": info.as_dict(), "status": rc}
+        if check and rc != 0:
+            raise FireError(rc, "fire_spin_ratios", out["info"])
         return out
 
     def unflatten(self, flat):

@@ -117,10 +117,13 @@ def test_mcmc_host_side_argument_errors():
     r = ctypes.c_void_p(16)
     nacc, drift, info = ctypes.c_int64(0), ctypes.c_double(0), fire.Info()
 
-    def call(sigma=0.3, sweeps=1, refresh=32, counter=ctypes.byref(ctr), rr=r):
+    def call(sigma=0.3, sweeps=1, refresh=32, counter=ctypes.byref(ctr), rr=r, ng=0, sg=2.0):
         return L.fire_mcmc_step(ctypes.byref(sys_c), ctypes.byref(arch_c), ctypes.byref(prm), 4, rr, 64, 0,
-                                sigma, sweeps, refresh, 1, counter, None, None, None, ctypes.byref(nacc),
+                                sigma, sweeps, refresh, ng, sg, 1, counter, None, None, None, ctypes.byref(nacc),
                                 ctypes.byref(drift), ctypes.byref(info), None, 0, None)
+    assert call(ng=-1) == 1
+    assert call(ng=20, sg=0.0) == 1
+    assert call(ng=20, sg=float("nan")) == 1
     assert call(sigma=0.0) == 1
     assert call(sigma=-1.0) == 1
     assert call(sigma=float("nan")) == 1

@@ -19,10 +19,12 @@ from recipes import hydrogen_like
 pytestmark = pytest.mark.gpu
 
 
-def _run(system, arch, p, prec, r_np, sigma, sweeps, seed, counter=0, refresh=32, k_cap=64):
+def _run(system, arch, p, prec, r_np, sigma, sweeps, seed, counter=0, refresh=32, k_cap=64, n_global=0,
+         sigma_global=2.0):
     f = fire.Fire(system, arch, p, prec, k_cap=k_cap)
     r = torch.as_tensor(r_np, device=f.device).clone()
-    out = f.mcmc_step(r, sigma, sweeps, refresh_every=refresh, seed=seed, counter=counter)
+    out = f.mcmc_step(r, sigma, sweeps, refresh_every=refresh, seed=seed, counter=counter, n_global=n_global,
+                      sigma_global=sigma_global)
     torch.cuda.synchronize()
     return f, r.cpu().numpy(), out
 
@@ -134,3 +136,59 @@ def test_c26h24_fp32_sweep_keeps_a_consistent_state():
     g = fire.Fire(w.system, w.arch, p, "fp32", k_cap=64)
     lp = g.logpsi(torch.as_tensor(r, device=g.device))["logabs"].cpu().numpy()
     np.testing.assert_allclose(out["logabs"].cpu().numpy(), lp, rtol=1e-6, atol=1e-6)
+
+
+# ---------------------------------------------------------------------------
+# global single-electron jumps (Methods, "Improved Monte Carlo sampling")
+# ---------------------------------------------------------------------------
+
+def test_water_fp64_global_jumps_match_oracle():
+    """Sweeps of 10 local moves and 6 global jumps (sigma_g = 2): every
+    decision away from the threshold, the final positions and log|Psi| equal
+    the full-recompute oracle with the same mixture proposals and Hastings
+    factors."""
+    w = synth.workload("water")
+    r0, p = synth.make_inputs(w, 16)
+    seed, counter, G = 987654321, 40, 6
+    f, r, out = _run(w.system, w.arch, p, "fp64", r0, 0.3, 2, seed, counter, refresh=9, n_global=G)
+    ref = M.mcmc_sweeps(w.system, w.arch, p, r0, 0.3, 2, seed, counter, n_global=G, sigma_global=2.0)
+    safe = ref["margin"] > 1e-8
+    assert safe.sum() >= 12
+    acc = out["accepted"].cpu().numpy()
+    np.testing.assert_array_equal(acc[safe], ref["accepted"][safe])
+    np.testing.assert_allclose(r[safe], ref["r"][safe], rtol=0, atol=1e-11)
+    la = out["logabs"].cpu().numpy()
+    np.testing.assert_allclose(la[safe], ref["logabs"][safe], rtol=1e-10, atol=1e-10)
+    assert out["counter"] == counter + 2 * (w.system.n_el + G)
+    assert out["max_drift"] < 1e-9, out["max_drift"]
+    # some global jumps were accepted: a walker moved an electron by more than
+    # any local step could (8 sigma)
+    assert np.max(np.abs(r - r0)) > 2.4
+
+
+def test_c8h10_fp64_global_jumps_match_oracle():
+    """n_el = 58 with 20 global jumps per sweep, float64 state, no rebuild
+    inside the sweep: the jumps' update sets span two neighbourhoods."""
+    w = synth.workload("c8h10")
+    r0, p = synth.make_inputs(w, 12)
+    ref = M.mcmc_sweeps(w.system, w.arch, p, r0, 0.3, 1, 555, n_global=20, sigma_global=2.0)
+    f, r, out = _run(w.system, w.arch, p, "fp64", r0, 0.3, 1, 555, refresh=0, n_global=20)
+    safe = ref["margin"] > 1e-8
+    acc = out["accepted"].cpu().numpy()
+    np.testing.assert_array_equal(acc[safe], ref["accepted"][safe])
+    np.testing.assert_allclose(r[safe], ref["r"][safe], rtol=0, atol=1e-11)
+    assert out["max_drift"] < 1e-8, out["max_drift"]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_hydrogen_mean_radius_from_global_jumps_alone(prec):
+    """Local steps of 1e-9 bohr, two global jumps per sweep: the independence
+    sampler with the Hastings factor samples exp(-2r), <r> = 3/2 (without
+    the factor it would sample exp(-2r) rho(r), <r> = 1.25)."""
+    system, arch, p = hydrogen_like(1.0, 1.0, width=32)
+    W = 8192
+    r0 = np.random.default_rng(6).standard_normal((W, 1, 3))
+    _, r, out = _run(system, arch, p, prec, r0, 1e-9, 60, 17, n_global=2)
+    rad = np.linalg.norm(r[:, 0], axis=-1)
+    se = math.sqrt(0.75 / W)
+    assert abs(rad.mean() - 1.5) < 4 * se, (rad.mean(), se)
