@@ -185,8 +185,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-coords", type=int, default=8,
                     help="second-derivative passes in one oracle sample (of 3 n_el)")
-    ap.add_argument("--op", default="local_energy", choices=["local_energy", "grad", "mcmc"],
-                    help="local_energy: the headline metric; grad / mcmc: the adjoint and the sampler")
+    ap.add_argument("--op", default="local_energy", choices=["local_energy", "grad", "mcmc", "spring", "ecp", "spin"],
+                    help="local_energy: the headline metric; grad / mcmc / spring / ecp: the adjoint, the "
+                         "sampler, the SPRING update and the non-local pseudopotential")
+    ap.add_argument("--global-moves", type=int, default=0, help="--op mcmc: global jumps per sweep")
     ap.add_argument("--chain", type=int, default=26, help="--op mcmc: zigzag chain C_kH_{k+2}")
     ap.add_argument("--scan", action="store_true", help="--op mcmc: every chain k = 2, 8, ..., 44")
     ap.add_argument("--sweeps", type=int, default=2, help="--op mcmc: sweeps per timed call")
@@ -476,6 +478,12 @@ def bench_other(args, rank, world, local):
     dev = torch.device("cuda", local)
     base = {"n_gpus": world, "steps": args.steps, "warmup": args.warmup, "scaling": "weak", "vs_baseline": None,
             "data": "synthetic"}
+    if args.op == "spring":
+        return bench_spring(args, rank, dev, base)
+    if args.op == "ecp":
+        return bench_ecp(args, rank, dev, base)
+    if args.op == "spin":
+        return bench_spin(args, rank, dev, base)
     if args.op == "grad":
         w = synth.workload("c26h24", args.walkers)
         r_np, p = synth.make_inputs(w, args.walkers)
@@ -511,7 +519,8 @@ def bench_other(args, rank, world, local):
         ctr = [0]
 
         def call():
-            o = f.mcmc_step(r, 0.3, args.sweeps, refresh_every=32, seed=2504, counter=ctr[0])
+            o = f.mcmc_step(r, 0.3, args.sweeps, refresh_every=32, seed=2504, counter=ctr[0],
+                            n_global=args.global_moves, sigma_global=2.0)
             ctr[0] = o["counter"]
             return {kk: o[kk] for kk in ("n_accepted", "max_drift", "info", "walker_drift")}
         sampler = ClockSampler(local)
@@ -553,6 +562,114 @@ def bench_other(args, rank, world, local):
         slope = float(np.polyfit(x, y, 1)[0])
         print(json.dumps({"metric": "fit: seconds per sweep ~ n_el^a", "a": slope,
                           "points": [{"n_el": q[0], "s_per_sweep": q[1]} for q in pts]}), flush=True)
+
+def bench_spring(args, rank, dev, base):
+    """One SPRING update (fire_spring_step) on the C26H24 workload: the
+    gradient rows of 4096 walkers (fire_grad_logpsi, float32, 5.1 M
+    parameters) and their local energies, computed once before timing."""
+    from paper_2504_06087_gb300 import fire, synth
+    w = synth.workload("c26h24", args.walkers)
+    r_np, p = synth.make_inputs(w, args.walkers)
+    r = torch.as_tensor(r_np, device=dev)
+    f = fire.Fire(w.system, w.arch, p, "fp32", k_cap=64, device=str(dev))
+    O = f.grad_logpsi(r)["grad"]
+    del f
+    torch.cuda.empty_cache()
+    fb = fire.Fire(w.system, w.arch, p, "bf16", k_cap=64, device=str(dev))
+    e = fb.local_energy(r)["e_loc"]
+    del fb
+    torch.cuda.empty_cache()
+    N, P = O.shape
+    d0 = torch.zeros(P, dtype=torch.float32, device=dev)
+    state = {"d": d0}
+
+    def step():
+        out = fire.spring_step(O, e, state["d"], 0.99, 1e-3)
+        state["d"] = out["delta"]
+        return out["status"]
+    sampler = ClockSampler(dev.index or 0)
+    sampler.start()
+    times, _ = _timed(step, args.steps, args.warmup, dev)
+    clocks = sampler.stop()
+    fire.profile(True)
+    step()
+    torch.cuda.synchronize(dev)
+    stages = fire.profile_report()
+    fire.profile(False)
+    ms = float(np.mean(times))
+    peaks, src = load_peaks()
+    gram_flops = 2.0 * N * N * P
+    line = dict(base, metric="SPRING updates/sec, C26H24 gradient rows (4096 walkers x 5.1 M parameters)",
+                value=1e3 / ms, unit="updates/s", ms_per_step=ms, higher_is_better=True, dtype="f32+f64",
+                config={"workload": f"zigzag C26H24, {N} walkers, {P} parameters, O [N, P] float32 from "
+                                    f"fire_grad_logpsi, lambda=1e-3, eta=0.99",
+                        "precision": "Gram matrix as six split-bf16 products (FP32 accumulation), float64 solve"},
+                roofline={"kernel": "tc_gemm (Gram)", "bound": "tensor",
+                          "achieved": gram_flops / (ms / 1e3) / 1e12,
+                          "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                          "frac": gram_flops / (ms / 1e3) / 1e12 / peaks["bf16_tflops_sustained"],
+                          "note": "algorithmic 2 N^2 P of the whole update time; the tensor cores execute six "
+                                  f"split products of it; peak: bf16 dense sustained, {src}"},
+                clocks=clocks, gpu_launches=None,
+                stages_ms={k: round(v[1], 3) for k, v in sorted(stages.items(), key=lambda kv: -kv[1][1])})
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def bench_ecp(args, rank, dev, base):
+    """Non-local pseudopotential energy (fire_ecp_nonlocal) on C26H24 with a
+    synthetic semi-local pseudopotential on every carbon (N_quad = 4,
+    r_cut = 1.2 bohr, s and d channels)."""
+    from paper_2504_06087_gb300 import fire, synth
+    w = synth.workload("c26h24", args.walkers)
+    r_np, p = synth.make_inputs(w, args.walkers)
+    r = torch.as_tensor(r_np, device=dev)
+    ecp = [{"n_quad": 4, "r_cut": 1.2, "terms": [[(4.0, 0, 1.0)], [], [(1.5, 0, 0.6)]]} if z == 6.0 else None
+           for z in w.system.nuc_charge]
+    f = fire.Fire(w.system, w.arch, p, "fp32", k_cap=64, device=str(dev))
+    sampler = ClockSampler(dev.index or 0)
+    sampler.start()
+    times, outs = _timed(lambda: f.ecp_nonlocal(r, ecp, seed=5)["info"], args.steps, args.warmup, dev)
+    clocks = sampler.stop()
+    ms = float(np.mean(times))
+    n = w.system.n_el
+    line = dict(base, metric=f"non-local pseudopotential evaluations/sec, zigzag C26H24 (n_el={n}), "
+                             f"{args.walkers} walkers, N_quad=4 on carbons",
+                value=args.walkers / (ms / 1e3), unit="walkers/s", ms_per_step=ms, higher_is_better=True,
+                dtype="f32+f64", config={"workload": f"zigzag C26H24, {args.walkers} walkers, synthetic "
+                                                     "pseudopotential on the 26 carbons (s and d channels), "
+                                                     f"{n} x 4 virtual single-electron moves per call",
+                                         "precision": "fp32 state, float64 lemma and exact ratios"},
+                s_per_virtual_move=ms / 1e3 / (n * 4), gpu_launches=int(outs[-1]["n_launches"]), clocks=clocks)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def bench_spin(args, rank, dev, base):
+    """S+ swap ratios (fire_spin_ratios) on C26H24: the last spin-down electron
+    swapped with each of the 90 spin-up electrons, every walker."""
+    from paper_2504_06087_gb300 import fire, synth
+    w = synth.workload("c26h24", args.walkers)
+    r_np, p = synth.make_inputs(w, args.walkers)
+    r = torch.as_tensor(r_np, device=dev)
+    f = fire.Fire(w.system, w.arch, p, "fp32", k_cap=64, device=str(dev))
+    beta = w.system.n_el - 1
+    sampler = ClockSampler(dev.index or 0)
+    sampler.start()
+    times, outs = _timed(lambda: f.spin_ratios(r, beta)["info"], args.steps, args.warmup, dev)
+    clocks = sampler.stop()
+    ms = float(np.mean(times))
+    nu = w.system.n_up
+    line = dict(base, metric=f"S+ swap-ratio evaluations/sec, zigzag C26H24 (n_el={w.system.n_el}), "
+                             f"{args.walkers} walkers, {nu} swaps per walker",
+                value=args.walkers / (ms / 1e3), unit="walkers/s", ms_per_step=ms, higher_is_better=True,
+                dtype="f32+f64", config={"workload": f"zigzag C26H24, {args.walkers} walkers, beta = electron "
+                                                     f"{beta}, {nu} two-electron swaps per walker",
+                                         "precision": "fp32 state, float64 lemma and exact ratios"},
+                s_per_swap=ms / 1e3 / nu, gpu_launches=int(outs[-1]["n_launches"]), clocks=clocks)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
 
 if __name__ == "__main__":
     main()
