@@ -286,13 +286,15 @@ int fire_local_energy(const fire_system_t* sys, const fire_arch_t* arch,
  * Precision: FIRE_PREC_FP64 keeps the state in float64; FIRE_PREC_FP32 and
  * FIRE_PREC_BF16_FP64 keep it in float32 with float64 determinant lemmas,
  * LU factorisations and refresh inverses (no tensor cores).  A determinant
- * whose lemma ratio lies beyond 10^+-3 gets its ratio from a float64 LU of
- * the new matrix and, if the move is accepted, a fresh float64
- * factorisation and inverse instead of the Woodbury update.  With the
- * environment variable FIRE_MCMC_KAPPA_TOL = t >= 0, so does every
- * determinant with kappa u w > t (kappa the Frobenius condition estimate of
- * its last factorisation, u the unit roundoff of the state, w its weight
- * |det| / max |det| in the walker's sum).
+ * whose lemma ratio lies beyond 10^+-3, or whose kappa u w exceeds 1e-4
+ * (kappa the Frobenius condition estimate of its last factorisation, u the
+ * unit roundoff of the state, w its weight |det| / max |det| in the walker's
+ * sum), gets its ratio from a float64 LU of the new matrix and, if the move
+ * is accepted, a fresh float64 factorisation and inverse instead of the
+ * Woodbury update (batched over the SMs).  The environment variable
+ * FIRE_MCMC_KAPPA_TOL overrides 1e-4 (negative: lemma ratios only, about
+ * twice as fast at n_el = 184, with carried log|Psi| up to ~5e-2 off the
+ * rebuilds instead of 1e-2).
  * Outputs: logabs, sign [W] float64 (device, may be NULL) at the final
  * positions (from the final rebuild); accepted [W] int32 (device, may be
  * NULL): accepted moves per walker; *n_accepted (host, may be NULL) their

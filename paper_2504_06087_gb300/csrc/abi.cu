@@ -573,6 +573,9 @@ int fire_local_energy(const fire_system_t* sys, const fire_arch_t* arch, const f
                   e_pot, info, ws, ws_bytes, stream);
 }
 
+// Default tolerance of the conditioning test of the exact-ratio path.
+static constexpr double kKappaTolDefault = 1e-4;
+
 int fire_mcmc_step(const fire_system_t* sys, const fire_arch_t* arch, const fire_params_t* params,
                    int64_t W, double* r, int32_t k_cap, int32_t precision, double sigma, int32_t n_sweeps,
                    int32_t refresh_every, int32_t n_global, double sigma_global, uint64_t seed, uint64_t* counter,
@@ -600,9 +603,10 @@ int fire_mcmc_step(const fire_system_t* sys, const fire_arch_t* arch, const fire
   DevStatus hs;
   memset(&hs, 0, sizeof(hs));
   int64_t nl = 0;
-  // conditioning test of the exact-ratio path (FIRE_MCMC_KAPPA_TOL sets the
-  // tolerance; off by default)
-  double ktol = -1.0;
+  // conditioning test of the exact-ratio path: 1e-4 keeps the carried
+  // log|Psi| of every walker within 1e-2 of the rebuilds over 32 moves
+  // (FIRE_MCMC_KAPPA_TOL overrides it; negative: off)
+  double ktol = kKappaTolDefault;
   if (const char* e = getenv("FIRE_MCMC_KAPPA_TOL")) ktol = atof(e);
   McmcCall mc{sigma, n_sweeps, refresh_every, seed, *counter, accepted, 0, 0.0, n_global, sigma_global, ktol,
               nullptr, 0, nullptr, -1, nullptr, nullptr};
@@ -678,7 +682,7 @@ int fire_ecp_nonlocal(const fire_system_t* sys, const fire_arch_t* arch, const f
   DevStatus hs;
   memset(&hs, 0, sizeof(hs));
   int64_t nl = 0;
-  double ktol = -1.0;
+  double ktol = kKappaTolDefault;
   if (const char* e = getenv("FIRE_MCMC_KAPPA_TOL")) ktol = atof(e);
   McmcCall mc{1.0, 0, 0, seed, 0, nullptr, 0, 0.0, 0, 1.0, ktol, ecp_dev, qmax, v_nl, -1, nullptr, nullptr};
   double* lpf = reinterpret_cast<double*>(wsb + pl.mc_lpf);
@@ -727,7 +731,7 @@ int fire_spin_ratios(const fire_system_t* sys, const fire_arch_t* arch, const fi
   DevStatus hs;
   memset(&hs, 0, sizeof(hs));
   int64_t nl = 0;
-  double ktol = -1.0;
+  double ktol = kKappaTolDefault;
   if (const char* e = getenv("FIRE_MCMC_KAPPA_TOL")) ktol = atof(e);
   McmcCall mc{1.0, 0, 0, 0, 0, nullptr, 0, 0.0, 0, 1.0, ktol, nullptr, 0, nullptr, beta, ratios, r_beta};
   double* lpf = reinterpret_cast<double*>(wsb + pl.mc_lpf);

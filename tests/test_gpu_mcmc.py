@@ -122,16 +122,19 @@ def test_c8h10_fp32_against_oracle_and_rebuild(c8h10_oracle):
 
 
 def test_c26h24_fp32_sweep_keeps_a_consistent_state():
-    """n_el = 180 (the local-energy workload), one sweep: the carried log|Psi|
-    agrees with each float64 rebuild, and the final log|Psi| with a separate
-    fire_logpsi call at the final positions.  The drift bound is float32
-    rounding amplified by the conditioning of Phi (kappa ~ 1e4 here):
-    ~2e-4 per move, 6e-3 measured over 32 moves."""
+    """n_el = 180 (the local-energy workload), 256 walkers, one sweep: the
+    carried log|Psi| of every walker stays within 1e-2 of each float64
+    rebuild (the conditioning test sends every determinant with
+    kappa u w > 1e-4 to float64 ratios and refactorisation, so a run of 32
+    moves accumulates at most ~32 x 1e-4 from the rest; over 4096 walkers
+    the largest drift measured was 8.8e-3), and the final log|Psi| agrees
+    with a separate fire_logpsi call at the final positions."""
     w = synth.workload("c26h24")
-    r0, p = synth.make_inputs(w, 8)
+    r0, p = synth.make_inputs(w, 256)
     f, r, out = _run(w.system, w.arch, p, "fp32", r0, 0.3, 1, 99, refresh=32)
-    assert out["max_drift"] < 2e-2, out["max_drift"]
-    rate = out["n_accepted"] / (8 * w.system.n_el)
+    assert out["max_drift"] < 1e-2, out["max_drift"]
+    assert float(out["walker_drift"].max()) < 1e-2
+    rate = out["n_accepted"] / (256 * w.system.n_el)
     assert 0.2 < rate < 0.99, rate
     g = fire.Fire(w.system, w.arch, p, "fp32", k_cap=64)
     lp = g.logpsi(torch.as_tensor(r, device=g.device))["logabs"].cpu().numpy()
