@@ -132,8 +132,9 @@ struct Runner {
     dbg = getenv("FIRE_DEBUG_SYNC") != nullptr;
     // FIRE_TC_MASK (diagnostic): bit 0 embedding MLP, 1 Jastrow MLPs,
     // 2 attention, 3 orbitals, 4 envelopes, 5 h^0 products (GLU, message
-    // projections) and orbital value rows, 6 attention register MLPs --
-    // which products may use the tensor cores.
+    // projections) and orbital value rows, 6 attention register MLPs, 7 the
+    // restricted log-det contraction -- which products may use the tensor
+    // cores.
     if (const char* m = getenv("FIRE_TC_MASK")) tc_mask = atoi(m);
     if (const char* m = getenv("FIRE_TC_FIX_VALUES")) fix_values = atoi(m);
     // FIRE_TC_VALUE_ROWS=split: value rows by six split products on the
@@ -235,7 +236,7 @@ struct Runner {
   // stride lda, a_rows rows allocated) and packed bf16 weights Bt [N][K] it
   // runs on the tensor cores (BF16_FP64 form); otherwise SIMT in T.
   int tc_rc = FIRE_OK;
-  int tc_mask = 0x7F;
+  int tc_mask = 0xFF;
   int fix_values = 1;         // value rows recomputed in fp32 after a tensor-core product
   bool simt_values = true;    // ... by the float32 SIMT product (else six split products)
   // split-bf16 components of each tensor-core product (1: 1 product, 2: 3, 3: 6).
@@ -756,10 +757,14 @@ struct Runner {
       int* ccount = pl.clist ? at<int>(pl.clist) : nullptr;
       int* clists = pl.clist ? ccount + 16 : nullptr;
       int hcount[kC3Buckets] = {0};
+      // BF16_FP64 form: neighbourhoods of up to 42 members contract on the
+      // tensor cores (bucket 0), larger ones in the SIMT buckets of 48 and 60
+      const bool ctc = c3 && pl.wbf16 && (tc_mask & 128);
       if (c3) {
         cudaMemsetAsync(ccount, 0, 16 * sizeof(int), s);
         C3Buckets bm;
-        for (int q = 0; q < kC3Buckets; ++q) bm.v[q] = kC3BucketMax[q];
+        for (int q = 0; q < kC3Buckets; ++q)
+          bm.v[q] = ctc && q < 3 ? tc::kContractTcMaxMembers : kC3BucketMax[q];
         contract_bucket_kernel<0><<<(nb + 255) / 256, 256, 0, s>>>(nb, cnt, bm, ccount, clists);
         cudaMemcpyAsync(hcount, ccount, sizeof(hcount), cudaMemcpyDeviceToHost, s);
         launches += 1;
@@ -1015,6 +1020,20 @@ struct Runner {
                 gemm<T>(s, X, d, p.orb_w + ((int64_t)sp * D + dd0 + j) * d * n, n, false, O + (int64_t)j * n, ldo,
                         0, 0, rng + 2 * sp, cap, n, d);
           }
+          if constexpr (sizeof(T) == 4) {
+            if (ctc && c2 && hcount[0] > 0) {
+              // neighbourhoods of up to 42 members, all g determinants of the group in one launch
+              mark("contract", 1);
+              const int rc = tc::contract_tc(s, wc, n, n_up, K, dd0, g, D, idx, cnt, rev, boff,
+                                             reinterpret_cast<const float*>(O), ldo,
+                                             reinterpret_cast<const float*>(Fenv),
+                                             reinterpret_cast<const float*>(Ainv), reinterpret_cast<float*>(gdet),
+                                             reinterpret_cast<float*>(ldet), st, clists, hcount[0], &st->tc_err);
+              if (rc != FIRE_OK) { set_last_error("contract", "tensor-core contraction launch failed"); return rc; }
+              launches += 1;
+              check("contract");
+            }
+          }
           for (int j = 0; j < g; ++j) {
             const int dd = dd0 + j;
             const T* Oj = O + (int64_t)j * n;
@@ -1022,7 +1041,7 @@ struct Runner {
             if constexpr (sizeof(T) == 4) {
               if (c3 && c2) {
                 // one launch per non-empty bucket, over exactly its electrons
-                for (int q = 0; q < kC3Buckets; ++q) {
+                for (int q = ctc ? 1 : 0; q < kC3Buckets; ++q) {
                   if (hcount[q] <= 0) continue;
                   auto kern = q == 0 ? contract3_kernel<64>
                                      : (q == 1 ? contract3_kernel<96>
