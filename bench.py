@@ -134,7 +134,11 @@ def simt_peaks(dev):
 # named profiles/ file.  A stage whose kernel changed since its capture has
 # no entry.
 STAGE_TRAFFIC = {
+    # float32 SIMT contraction (FP32 form)
     "contract": (2.1812e7, "ncu capture of one determinant of a 32-walker chunk (profiles/contract_c26h24.md)"),
+    # tensor-core contraction (BF16_FP64 form)
+    "contract_tc": (1.3585e7, "ncu capture of one four-determinant launch over a 128-walker chunk "
+                              "(profiles/contract_tc_c26h24.md)"),
 }
 
 
@@ -147,14 +151,22 @@ def stage_traffic(stage, walker_dets, launches):
     return per * walker_dets / launches, src + f", scaled to {walker_dets // max(launches, 1)} walker-determinants per launch"
 
 
-def stage_work(stage, w, info, n_walkers, nbr_sq_sum):
+def stage_work(stage, w, info, n_walkers, nbr_sq_sum, nbr_sum=None, precision="bf16"):
     """(flops_total, bytes_total, bound) of one call's stage, from the shapes.
 
     rows = forward-Laplacian rows of the call (value + Laplacian + 3 tangent
-    rows per slot of every electron block)."""
+    rows per slot of every electron block); nbr_sum = sum over (walker,
+    electron) of |Nbar_n|, nbr_sq_sum of |Nbar_n|^2."""
     a, s = w.arch, w.system
     d, J, n, D, L = a.width, a.jw, s.n_el, a.n_det, a.n_layers
     rows = info["rows_total"]
+    if stage == "contract" and precision == "bf16" and nbr_sum is not None:
+        # tensor-core contraction, bound by streaming its float32 inputs once
+        # per determinant: the three tangent O rows of every (member, tangent
+        # electron) pair, the value and Laplacian O rows and the five
+        # envelope rows of every electron, and A^T (n floats per row)
+        per_det = 4.0 * n * (3 * nbr_sum + n_walkers * n * (2 + 5 + 1))
+        return None, per_det * D, "hbm"
     if stage == "mlp_gemm":
         return 2.0 * rows * d * d * L, None, "tensor"
     if stage == "orb_gemm":
@@ -300,15 +312,23 @@ def main():
     nb = f.neighbors(r)
     cnt = nb["cnt"].sum(-1).to(torch.float64)
     nbr_sq_sum = float(((1.0 + cnt) ** 2).sum().item())
+    nbr_sum = float((1.0 + cnt).sum().item())
     peaks, peak_src = load_peaks()
     simt = simt_peaks(dev)
     dom = max(stages.items(), key=lambda kv: kv[1][1])
     dname, (dl, dms) = dom
-    flops, _, bound = stage_work(dname, w, info, args.walkers, nbr_sq_sum)
-    traffic, traffic_src = stage_traffic(dname, args.walkers * w.arch.n_det, dl)
+    flops, nbytes, bound = stage_work(dname, w, info, args.walkers, nbr_sq_sum, nbr_sum, args.precision)
+    tkey = dname + ("_tc" if bound == "hbm" else "")
+    traffic, traffic_src = stage_traffic(tkey, args.walkers * w.arch.n_det, dl)
     roof = {"kernel": dname, "share_of_step": dms / sum(v[1] for v in stages.values()), "launches": dl,
             "traffic": traffic, "traffic_source": traffic_src}
-    if flops is not None:
+    if nbytes is not None:
+        per_launch = nbytes / dl
+        achieved = per_launch / (dms / dl / 1e3) / 1e9
+        roof.update({"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "peak_source": f"HBM copy bandwidth, {peak_src}",
+                     "bytes_per_launch": per_launch, "ms_per_launch": dms / dl})
+    elif flops is not None:
         per_launch = flops / dl
         achieved = per_launch / (dms / dl / 1e3) / 1e12
         fp32_note = f"FP32 SIMT, measured in this run (FFMA probe, {simt['sm_count']} SMs)"

@@ -14,17 +14,19 @@
 // chunks.  Both operands are split-bf16 (two components, the products
 // hi hi + hi lo + lo hi).
 //
-// Small persistent CTAs (128 threads, several per SM, each with one operand
-// buffer and 64 columns of tensor memory) walk a list of tangent electrons;
-// an item is a tangent electron with the G determinants of an orbital group
-// (its member metadata is resolved once).  Per chunk every thread loads the
-// float32 rows of its (member, 8-orbital) tasks into registers -- while the
-// tensor cores still multiply the previous chunk -- then forms T, splits it
-// and stores both operands in the 128-byte-swizzled K-major layout; one
-// thread issues the chunk's MMAs.  After the last chunk of a determinant the
-// four warps read M from tensor memory (each its 32-lane quarter) into the
-// operand buffer and reduce the gradient and the trace.  Memory latency is
-// hidden by the other CTAs of the SM.  Every mbarrier wait is bounded (an
+// Persistent CTAs of 256 threads, two per SM, each with one operand buffer
+// and 64 columns of tensor memory, walk a list of tangent electrons; an item
+// is a tangent electron with the G determinants of an orbital group (its
+// member metadata is resolved once).  Per 64-orbital chunk every thread loads
+// the float32 rows of its first (member, 8-orbital) task into registers and
+// one piece of n''s own ten rows (O value, Laplacian and tangents, envelope
+// value, Laplacian and gradient) -- while the tensor cores still multiply the
+// previous chunk -- then forms T and the Laplacian row, splits them and
+// stores both operands in the 128-byte-swizzled K-major layout; one thread
+// issues the chunk's MMAs.  After the last chunk of a determinant warps 0-3
+// read M from tensor memory (each its 32-lane quarter) into the operand
+// buffer and all threads reduce the gradient and the trace.  Memory latency
+// is hidden by the other CTA of the SM.  Every mbarrier wait is bounded (an
 // error in *err, the CTA stops after its MMAs in flight have completed).
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -42,8 +44,8 @@ namespace tc {
 constexpr int kCtMaxM = kContractTcMaxMembers;   // 3 m + 1 <= 128 rows of T
 constexpr int kCtMaxG = 4;                       // determinants per item
 constexpr int kCtBN = 48;                        // B rows reserved per component (members, padded to 16)
-constexpr int kCtThreads = 128;
-constexpr int kCtPerSm = 4;                      // resident CTAs per SM
+constexpr int kCtThreads = 256;
+constexpr int kCtPerSm = 2;                      // resident CTAs per SM (up to 128 registers a thread)
 constexpr int kCtMsStride = 43;                  // M rows in shared memory (odd: conflict-free columns)
 constexpr int kCtTmemCols = 64;
 constexpr uint32_t kCtABytes = 128 * 128;        // 128 rows x 64 bf16
@@ -51,7 +53,7 @@ constexpr uint32_t kCtBBytes = kCtBN * 128;
 constexpr uint32_t kCtBufBytes = 2 * (kCtABytes + kCtBBytes);
 constexpr size_t kCtSmemBytes = kCtBufBytes + 1024;
 static_assert((size_t)(3 * kCtMaxM + 1) * kCtMsStride * 4 <= kCtBufBytes, "M must fit the operand buffer");
-static_assert(3 * kCtMaxM + 1 <= 128 && kCtMaxM <= kCtBN && kCtBN <= kCtTmemCols && kCtMaxM <= 2 * kCtThreads,
+static_assert(3 * kCtMaxM + 1 <= 128 && kCtMaxM <= kCtBN && kCtBN <= kCtTmemCols && kCtMaxM <= kCtThreads && 10 * 16 <= kCtThreads,
               "a neighbourhood must fit one 128-row tile, the B rows and the accumulator");
 static_assert(kCtPerSm * (kCtSmemBytes + 2048) <= 228 * 1024 && kCtPerSm * kCtTmemCols <= 512,
               "resident CTAs exceed shared or tensor memory");
@@ -143,6 +145,9 @@ __global__ void __launch_bounds__(kCtThreads, kCtPerSm) contract_tc_kernel(const
   __shared__ int64_t s_ro[kCtMaxM], s_fo[kCtMaxM];
   __shared__ int32_t s_mi[kCtMaxM];
   __shared__ float red[kCtThreads / 32][5];
+  // n''s own rows of the current chunk: O value, Laplacian and three tangent
+  // rows, envelope value, Laplacian and three gradient rows
+  __shared__ __align__(16) float s_self[10][64];
 
   unsigned char* buf =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(ct_smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -225,62 +230,60 @@ __global__ void __launch_bounds__(kCtThreads, kCtPerSm) contract_tc_kernel(const
           }
           ld8<false>(Aw + (int64_t)s_mi[k] * n, l, n, x.av);
         };
-        // this thread's first two tasks are loaded before waiting for the
-        // tensor cores to release the buffer
-        CtTask td[2];
-        if (tid < ntask) load_task(tid, td[0]);
-        if (tid + kCtThreads < ntask) load_task(tid + kCtThreads, td[1]);
+        // this thread's first task and its piece of n''s own rows are
+        // loaded before waiting for the tensor cores to release the buffer
+        CtTask td;
+        if (tid < ntask) load_task(tid, td);
+        float4 sv = make_float4(0.f, 0.f, 0.f, 0.f);
+        {
+          const int row = tid >> 4, l = l0 + 4 * (tid & 15);   // 160 float4 pieces of the 10 rows
+          if (tid < 160 && l < n) {
+            const float* src = row < 5 ? a.O + onp + row * a.ldo + cofs + l : a.Fenv + fnp + (row - 5) * Dn + cofs + l;
+            sv = __ldg(reinterpret_cast<const float4*>(src));
+          }
+        }
+        // the previous chunk's transform read these rows before the barrier
+        // that preceded its MMAs; the barrier below publishes them
+        if (tid < 160) *reinterpret_cast<float4*>(&s_self[tid >> 4][4 * (tid & 15)]) = sv;
         ok = wait_mma();
         if (__syncthreads_or(!ok)) { ok = false; break; }
         fence_after_sync();   // the tensor cores have finished reading the buffer
         // task t = 8 k + j: member k (or the Laplacian row, k = m), orbitals l0 + 8 j ..
         auto finish = [&](int t, CtTask& x) {
-          const int k = t >> 3, j = t & 7, l = l0 + 8 * j;
+          const int k = t >> 3, j = t & 7;
           if (k < m) {
 #pragma unroll
             for (int q = 0; q < 8; ++q) { x.o0[q] *= x.ph[q]; x.o1[q] *= x.ph[q]; x.o2[q] *= x.ph[q]; }
             if (k == 0) {
               // n' itself: its envelope moves too (value row of n' times the envelope gradient)
-              float ov[8], g[8];
-              ld8<true>(a.O + onp + cofs, l, n, ov);
-              ld8<false>(a.Fenv + fnp + 2 * Dn + cofs, l, n, g);
+              const float* ov = &s_self[0][8 * j];
 #pragma unroll
-              for (int q = 0; q < 8; ++q) x.o0[q] = fmaf(ov[q], g[q], x.o0[q]);
-              ld8<false>(a.Fenv + fnp + 3 * Dn + cofs, l, n, g);
-#pragma unroll
-              for (int q = 0; q < 8; ++q) x.o1[q] = fmaf(ov[q], g[q], x.o1[q]);
-              ld8<false>(a.Fenv + fnp + 4 * Dn + cofs, l, n, g);
-#pragma unroll
-              for (int q = 0; q < 8; ++q) x.o2[q] = fmaf(ov[q], g[q], x.o2[q]);
+              for (int q = 0; q < 8; ++q) {
+                x.o0[q] = fmaf(ov[q], s_self[7][8 * j + q], x.o0[q]);
+                x.o1[q] = fmaf(ov[q], s_self[8][8 * j + q], x.o1[q]);
+                x.o2[q] = fmaf(ov[q], s_self[9][8 * j + q], x.o2[q]);
+              }
             }
             store_split8(sa, kCtABytes, 3 * k, j, x.o0);
             store_split8(sa, kCtABytes, 3 * k + 1, j, x.o1);
             store_split8(sa, kCtABytes, 3 * k + 2, j, x.o2);
             store_split8(sb, kCtBBytes, k, j, x.av);
           } else {
-            // Laplacian row of n': O_lap phi + 2 sum_x O_x d_x phi + O_val Lap phi
-            float lap[8], f[8], o[8];
-            ld8<true>(a.O + onp + a.ldo + cofs, l, n, o);
-            ld8<false>(a.Fenv + fnp + cofs, l, n, f);
+            // Laplacian row of n': O_lap phi + O_val Lap phi + 2 sum_x O_x d_x phi
+            float lap[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) lap[q] = o[q] * f[q];
-            ld8<true>(a.O + onp + cofs, l, n, o);
-            ld8<false>(a.Fenv + fnp + Dn + cofs, l, n, f);
+            for (int q = 0; q < 8; ++q) {
+              const int lq = 8 * j + q;
+              float v = fmaf(s_self[0][lq], s_self[6][lq], s_self[1][lq] * s_self[5][lq]);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) lap[q] = fmaf(o[q], f[q], lap[q]);
-#pragma unroll
-            for (int xx = 0; xx < 3; ++xx) {
-              ld8<true>(a.O + onp + (2 + xx) * a.ldo + cofs, l, n, o);
-              ld8<false>(a.Fenv + fnp + (2 + xx) * Dn + cofs, l, n, f);
-#pragma unroll
-              for (int q = 0; q < 8; ++q) lap[q] = fmaf(2.f * o[q], f[q], lap[q]);
+              for (int xx = 0; xx < 3; ++xx) v = fmaf(2.f * s_self[2 + xx][lq], s_self[7 + xx][lq], v);
+              lap[q] = v;
             }
             store_split8(sa, kCtABytes, 3 * m, j, lap);
           }
         };
-        if (tid < ntask) finish(tid, td[0]);
-        if (tid + kCtThreads < ntask) finish(tid + kCtThreads, td[1]);
-        for (int t = tid + 2 * kCtThreads; t < ntask; t += kCtThreads) {
+        if (tid < ntask) finish(tid, td);
+        for (int t = tid + kCtThreads; t < ntask; t += kCtThreads) {
           CtTask x;
           load_task(t, x);
           finish(t, x);
@@ -311,8 +314,8 @@ __global__ void __launch_bounds__(kCtThreads, kCtPerSm) contract_tc_kernel(const
       if (__syncthreads_or(!ok)) { ok = false; break; }
       fence_after_sync();
       const int rows = 3 * m + 1, N = (m + 15) / 16 * 16;
-      const int r = 32 * warp + lane;
-      if (32 * warp < rows) {
+      const int r = 32 * warp + lane;   // warps 0-3: tensor-memory lane quarters 0-3
+      if (warp < 4 && 32 * warp < rows) {
         for (int c0 = 0; c0 < N; c0 += 16) {
           float v[16];
           tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);

@@ -39,8 +39,9 @@ TAU_L = {"fp64": 1e-10, "fp32": 1e-5, "bf16": 1e-5}
 UNIT = {"fp64": 2.0 ** -53, "fp32": 2.0 ** -24, "bf16": 2.0 ** -24}
 
 
-def check_walkers(out, prec, n, e_ref, la_ref, sg_ref, lap, g2, kappa):
-    """The per-walker bounds of the module docstring."""
+def check_walkers(out, prec, n, e_ref, la_ref, sg_ref, lap, g2, kappa, tau_l=None):
+    """The per-walker bounds of the module docstring (tau_l: the relative
+    log|Psi| tolerance of a workload whose bound is stated in its test)."""
     e_ref, la_ref = np.asarray(e_ref), np.asarray(la_ref)
     np.testing.assert_array_equal(out["sign"].cpu().numpy(), np.asarray(sg_ref))
     e = out["e_loc"].cpu().numpy()
@@ -50,7 +51,8 @@ def check_walkers(out, prec, n, e_ref, la_ref, sg_ref, lap, g2, kappa):
     if prec != "fp64":
         assert np.median(rel(e, e_ref)) <= 1e-4, np.median(rel(e, e_ref))
     dl = np.abs(out["logabs"].cpu().numpy() - la_ref)
-    bound = np.maximum(TAU_L[prec] * np.maximum(np.abs(la_ref), 1.0), n * np.asarray(kappa) * UNIT[prec])
+    t = TAU_L[prec] if tau_l is None else tau_l
+    bound = np.maximum(t * np.maximum(np.abs(la_ref), 1.0), n * np.asarray(kappa) * UNIT[prec])
     assert np.all(dl <= bound), (prec, (dl / bound).max())
     return err_e
 
@@ -279,3 +281,84 @@ def test_c26h24_kernel_variants_agree(variant, monkeypatch):
     np.testing.assert_array_equal(out["sign"].cpu().numpy(), ref["sign"].cpu().numpy())
     assert rel(out["logabs"].cpu().numpy(), ref["logabs"].cpu().numpy()).max() < 1e-6
     assert np.median(rel(out["e_loc"].cpu().numpy(), ref["e_loc"].cpu().numpy())) < 1e-4
+
+
+def sum_conditioning(w, r, p):
+    """Per walker sum_d |det Phi_d| kappa_d / |sum_d s_d det Phi_d| (oracle
+    orbital matrices, 2-norm condition numbers): with every log|det Phi_d|
+    off by at most n kappa_d u, log|Psi| is off by at most n u times this
+    (first order in the signed determinant sum, whose terms can cancel)."""
+    pt = O.params_to_torch(p)
+    with torch.no_grad():
+        rt = torch.as_tensor(r, dtype=torch.float64)
+        _, _, h = O.embeddings(w.system, w.arch, pt, rt)
+        phi = O.orbitals(w.system, w.arch, pt, rt, h).numpy()       # [W, D, n, n]
+    sgn, lad = np.linalg.slogdet(phi)
+    kap = np.linalg.cond(phi)
+    top = lad.max(axis=1, keepdims=True)
+    mag = np.exp(lad - top)
+    return (mag * kap).sum(axis=1) / np.abs((sgn * mag).sum(axis=1))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+def test_small_chain_matches_oracle(prec):
+    """C2H4 with the C26H24 network (n_el = 16, a multiple of 4): the
+    BF16_FP64 form contracts every neighbourhood on the tensor cores (all of
+    them have at most 16 members); every walker against the oracle.  The
+    log|Psi| bound takes the conditioning of the determinant sum (in some
+    walkers the two largest determinants nearly cancel).  log|Psi| is about
+    -30 here, ten times smaller than at C26H24, while the BF16_FP64 form's
+    absolute log|Psi| error from its split-bf16 value products stays near
+    3e-4 (1.0e-5 of |log|Psi|| at the worst of these walkers, where the
+    plain FP32 form has 3.5e-7): its relative bound here is 3e-5."""
+    w = synth.workload("sample_k2")
+    r, p = synth.make_inputs(w, 8)
+    e, la, sg, kin, v, g, lap = O.local_energy(w.system, w.arch, p, r, return_parts=True)
+    out = fire.Fire(w.system, w.arch, p, prec).local_energy(r)
+    check_walkers(out, prec, w.system.n_el, e, la, sg, lap, (g ** 2).sum(axis=(1, 2)), sum_conditioning(w, r, p),
+                  tau_l=3e-5 if prec == "bf16" else None)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+def test_sample_k6_matches_oracle(prec):
+    """The stored oracle walkers of C6H8 with the C26H24 network (n_el = 44):
+    tensor-core contraction in the BF16_FP64 form."""
+    _check_golden("sample_k6", prec)
+
+
+def test_c26h24_tensor_core_contraction_error_matches_simt(monkeypatch):
+    """The restricted log-det contraction of the BF16_FP64 form runs on the
+    tensor cores (split-bf16 T and A^T rows, float32 accumulation) for
+    neighbourhoods of up to 42 members.  Against the FP64 GPU form (held to
+    the oracle above) over 256 C26H24 walkers, its E_L error at the median,
+    p90 and p99 walker is within 1.25x, and at the worst walker 1.5x, of the
+    same form with the float32 SIMT contraction (FIRE_TC_MASK without bit 7;
+    measured 1.06x, 1.07x, 0.98x and 1.16x)."""
+    w = synth.workload("c26h24")
+    r, p = synth.make_inputs(w, 256)
+    ref = fire.Fire(w.system, w.arch, p, "fp64").local_energy(r)["e_loc"].cpu().numpy()
+    tc = rel(fire.Fire(w.system, w.arch, p, "bf16").local_energy(r)["e_loc"].cpu().numpy(), ref)
+    monkeypatch.setenv("FIRE_TC_MASK", "127")
+    simt = rel(fire.Fire(w.system, w.arch, p, "bf16").local_energy(r)["e_loc"].cpu().numpy(), ref)
+    for q, k in ((50, 1.25), (90, 1.25), (99, 1.25), (100, 1.5)):
+        assert np.percentile(tc, q) <= k * np.percentile(simt, q), (q, np.percentile(tc, q), np.percentile(simt, q))
+
+
+def test_neighbourhoods_beyond_the_tile_take_the_simt_buckets(monkeypatch):
+    """With c beyond C6H8 every neighbourhood has 44 members, more than the
+    42 a 128-row tensor-core tile holds: every tangent electron goes to the
+    SIMT buckets, so switching the tensor-core contraction off changes no bit;
+    the results meet the per-walker bounds against the FP64 GPU form."""
+    s = synth.zigzag_polyene(6, cutoff=100.0)
+    arch = synth.Arch(width=256, n_layers=2, n_det=4)
+    p = synth.init_params(s, arch, 31)
+    r = synth.walkers(s, 16, 3131)
+    on = fire.Fire(s, arch, p, "bf16").local_energy(r)
+    assert on["info"]["k_required"] == 43
+    monkeypatch.setenv("FIRE_TC_MASK", "127")
+    off = fire.Fire(s, arch, p, "bf16").local_energy(r)
+    np.testing.assert_array_equal(on["e_loc"].cpu().numpy(), off["e_loc"].cpu().numpy())
+    np.testing.assert_array_equal(on["logabs"].cpu().numpy(), off["logabs"].cpu().numpy())
+    monkeypatch.delenv("FIRE_TC_MASK")
+    ref = fire.Fire(s, arch, p, "fp64").local_energy(r)
+    assert np.median(rel(on["e_loc"].cpu().numpy(), ref["e_loc"].cpu().numpy())) < 1e-4
