@@ -185,6 +185,29 @@ def stage_work(stage, w, info, n_walkers, nbr_sq_sum, nbr_sum=None, precision="b
     return None, None, None
 
 
+def grad_flops(w):
+    """Algorithmic FLOPs of one walker's d log|Psi| / d theta: the value
+    forward's multiply-adds (one row per electron; every pair feature within
+    the cutoffs counted at the mean neighbour count of the workload), times
+    three (forward, input adjoint and weight adjoint of every product), times
+    two.  The filters: Gamma's 4 -> 16 -> width layers and the 32 Gaussians
+    -> width; the envelopes: N_nuc N_env D n per electron."""
+    a, s = w.arch, w.system
+    d, J, n, D, L = a.width, a.jw, s.n_el, a.n_det, a.n_layers
+    filt = 4 * 16 + 16 * d + 32 * d
+    kbar = 24.8 if n == 180 else float(n - 1)
+    mac = (n * s.n_nuc * filt            # electron-nucleus filters
+           + 3 * n * d * d               # GLU ([W_g | W_v] and W_o)
+           + 4 * n * d * d               # message projections
+           + n * kbar * filt             # electron-electron filters
+           + L * n * d * d               # embedding MLP
+           + n * d * D * n               # orbitals
+           + n * s.n_nuc * a.n_env * D * n   # envelopes
+           + 2 * n * (d * J + J * J + J)     # MLP Jastrows
+           + n * d * (a.n_reg + a.n_reg * a.d_reg))   # attention scores and values
+    return 2.0 * 3.0 * mac
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -204,6 +227,8 @@ def main():
     ap.add_argument("--chain", type=int, default=26, help="--op mcmc: zigzag chain C_kH_{k+2}")
     ap.add_argument("--scan", action="store_true", help="--op mcmc: every chain k = 2, 8, ..., 44")
     ap.add_argument("--sweeps", type=int, default=2, help="--op mcmc: sweeps per timed call")
+    ap.add_argument("--no-stages", action="store_true",
+                    help="--op mcmc: no extra profiled call for the stage times")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -519,12 +544,25 @@ def bench_other(args, rank, world, local):
         stages = fire.profile_report()
         fire.profile(False)
         ms = float(np.mean(times))
+        simt = simt_peaks(dev)
+        flops = grad_flops(w) * args.walkers
+        out_bytes = 4.0 * args.walkers * f.n_params
+        peaks, peak_src = load_peaks()
+        achieved = flops / (ms / 1e3) / 1e12
+        roof = {"kernel": "whole call (value forward with intermediates + adjoint)", "bound": "alu",
+                "achieved": achieved, "peak": simt["fp32_tflops"], "unit": "TFLOP/s",
+                "frac": achieved / simt["fp32_tflops"],
+                "peak_source": f"FP32 SIMT, measured in this run (FFMA probe, {simt['sm_count']} SMs)",
+                "flops_per_walker": grad_flops(w),
+                "output_bytes": out_bytes, "output_write_ms_at_hbm_peak": out_bytes / (peaks["hbm_gbs"] * 1e9) * 1e3,
+                "note": "algorithmic FLOPs = 3x the multiply-adds of the value forward (forward, input adjoint, "
+                        "weight adjoint of every product) x 2; every weight-gradient product runs on the SIMT pipe"}
         line = dict(base, metric="per-walker d log|Psi|/d theta evaluations/sec at n_el=180 (FP32 adjoint)",
                     value=args.walkers / (ms / 1e3), unit="walkers/s", ms_per_step=ms, higher_is_better=True,
                     dtype="f32+f64", config={"workload": f"zigzag C26H24, n_el=180, {args.walkers} walkers, "
                                                          f"{f.n_params} parameters, output [W, P] float32",
                                              "precision": "fp32 (float64 LU)"},
-                    gpu_launches=int(outs[-1]["n_launches"]), clocks=clocks,
+                    gpu_launches=int(outs[-1]["n_launches"]), clocks=clocks, roofline=roof,
                     stages_ms={k: round(v[1], 3) for k, v in sorted(stages.items(), key=lambda kv: -kv[1][1])})
         if rank == 0:
             print(json.dumps(line), flush=True)
@@ -547,11 +585,13 @@ def bench_other(args, rank, world, local):
         sampler.start()
         times, outs = _timed(call, args.steps, args.warmup, dev)
         clocks = sampler.stop()
-        fire.profile(True)
-        call()
-        torch.cuda.synchronize(dev)
-        stages = fire.profile_report()
-        fire.profile(False)
+        stages = {}
+        if not args.no_stages:
+            fire.profile(True)
+            call()
+            torch.cuda.synchronize(dev)
+            stages = fire.profile_report()
+            fire.profile(False)
         n = w.system.n_el
         ms = float(np.mean(times))
         sweeps_s = args.sweeps / (ms / 1e3)
