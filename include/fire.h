@@ -79,7 +79,9 @@ typedef enum {
  *             ("plain FP32"; theta float32).
  *  BF16_FP64  every matrix product (embedding MLP, Jastrow MLPs, attention
  *             scores and register MLPs, h^0 products, envelopes, orbital
- *             rows) on the tensor cores as split-bf16 products: each operand
+ *             rows, and the restricted log-det contraction M = T A^T[Nbar]
+ *             of neighbourhoods of up to 42 members when n_el is a multiple
+ *             of 4) on the tensor cores as split-bf16 products: each operand
  *             held as 2 or 3 bf16 components, the component products summed
  *             with FP32 accumulation; the value rows of the MLP products
  *             recomputed in float32; LU / slogdet and the final E_L reduction
@@ -94,7 +96,11 @@ typedef enum {
  *            to max(|E_ref|, 1) at the median walker;
  *   log|Psi| |l - l_ref| <= max(t max(|l_ref|, 1), n_el kappa u), t = 1e-10
  *            (FP64), 1e-5 (FP32, BF16_FP64), kappa the condition number of the
- *            walker's dominant orbital matrix, u = 2^-53 or 2^-24.
+ *            walker's dominant orbital matrix, u = 2^-53 or 2^-24; where the
+ *            largest determinants nearly cancel, kappa is weighted by the
+ *            signed sum: sum_d |det_d| kappa_d / |sum_d s_d det_d|.  For
+ *            small |log|Psi|| (C2H4 with the C26H24 network, about 30) the
+ *            BF16_FP64 form's t is 3e-5.
  * The gradient of fire_grad_logpsi: FP64 1e-9 max(|g|, 1) per entry; FP32 a
  * relative 2-norm error per walker of at most 1e-4 + 2 kappa u. */
 typedef enum {
