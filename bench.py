@@ -8,7 +8,7 @@ form at the E_L errors each shows against the FP64 oracle.
 
     python bench.py [--gpus N --steps K --warmup W] [--impl reference]
     python bench.py --op grad            # per-walker d log|Psi|/d theta, C26H24
-    python bench.py --op mcmc [--chain k | --scan]   # Metropolis sweeps, C_kH_{k+2}
+    python bench.py --op mcmc [--chain k | --scan [--chains 2,8,...]]   # Metropolis sweeps, C_kH_{k+2}
 
 One step = one fire_local_energy call over all walkers of the GPU (neighbour
 lists included).  Inputs are resident in HBM for `value`; `e2e` adds the
@@ -226,6 +226,8 @@ def main():
     ap.add_argument("--global-moves", type=int, default=0, help="--op mcmc: global jumps per sweep")
     ap.add_argument("--chain", type=int, default=26, help="--op mcmc: zigzag chain C_kH_{k+2}")
     ap.add_argument("--scan", action="store_true", help="--op mcmc: every chain k = 2, 8, ..., 44")
+    ap.add_argument("--chains", default=None,
+                    help="--op mcmc --scan: comma-separated chain lengths k instead of 2, 8, ..., 44")
     ap.add_argument("--sweeps", type=int, default=2, help="--op mcmc: sweeps per timed call")
     ap.add_argument("--no-stages", action="store_true",
                     help="--op mcmc: no extra profiled call for the stage times")
@@ -573,7 +575,9 @@ def bench_other(args, rank, world, local):
         if rank == 0:
             print(json.dumps(line), flush=True)
         return
-    chains = [2, 8, 14, 20, 26, 32, 38, 44] if args.scan else [args.chain]
+    chains = [args.chain]
+    if args.scan:
+        chains = [int(k) for k in args.chains.split(",")] if args.chains else [2, 8, 14, 20, 26, 32, 38, 44]
     pts = []
     for k in chains:
         w = synth.workload(f"sample_k{k}", args.walkers)
